@@ -1,0 +1,158 @@
+"""Pins of the oracle's block time step (Sec. 1; Sec. 2.7, Eqs. 15-19)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1610_07279_gb300 import ics
+
+
+def test_level_from_amag_brute_force(oracle_lib):
+    O = oracle_lib
+    eta, eps, M, L = 0.025, 0.01, 2, 8
+    rng = np.random.default_rng(3)
+    for am in np.concatenate([10.0 ** rng.uniform(-6, 3, 3000), [0.0, 1e300]]):
+        want = 0
+        if am > 0:
+            dti = math.sqrt(((2.0 * eta) * eps) / am)
+            # smallest k with dt_max 2^-k <= dt_i, clamped to [0, L-1]
+            want = next((k for k in range(L) if math.ldexp(1.0, M - k) <= dti), L - 1)
+        assert O.level_from_amag(am, eta, eps, M, L) == want, am
+    # exactly on a level boundary: dt_i == dt_k belongs to level k
+    am = (2.0 * eta) * eps / (math.ldexp(1.0, M - 3) ** 2)
+    assert math.sqrt(((2.0 * eta) * eps) / am) == math.ldexp(1.0, M - 3)
+    assert O.level_from_amag(am, eta, eps, M, L) == 3
+
+
+def _one(O, kold, kc_amag, T, t0, L=6, M=0, eta=0.025, eps=0.01):
+    r0 = np.zeros((1, 3))
+    vh = np.zeros((1, 3))
+    t0a = np.array([t0], np.int64)
+    lv = np.array([kold], np.uint8)
+    ao = np.zeros(1, np.float32)
+    acc = np.array([[kc_amag, 0, 0, 0]], np.float32)
+    O.correct(np.array([0], np.uint32), acc, T, math.ldexp(1.0, M), M, L, eta, eps, r0, vh, t0a, lv, ao)
+    return int(lv[0]), int(t0a[0])
+
+
+def _amag_for_level(k, M=0, eta=0.025, eps=0.01):
+    dti = 1.5 * math.ldexp(1.0, int(M) - int(k))  # level k holds dt in [dt_k, 2 dt_k)
+    return float(np.float32((2.0 * eta) * eps / (dti * dti)))
+
+
+def test_level_change_rules(oracle_lib):
+    O = oracle_lib
+    L = 6  # ticks(k) = 2^(5-k)
+    # a shorter step is always taken, whatever T
+    assert _one(O, 2, _amag_for_level(4), T=8 + 8, t0=8) == (4, 16)
+    # a longer step only by one level, and only when T is a multiple of the longer step
+    assert _one(O, 3, _amag_for_level(1), T=8, t0=4) == (2, 8)      # 8 % ticks(2)=8 == 0
+    assert _one(O, 3, _amag_for_level(1), T=12, t0=8) == (3, 12)    # 12 % 8 != 0: stay
+    assert _one(O, 0, _amag_for_level(0), T=32, t0=0) == (0, 32)
+    assert _one(O, 5, _amag_for_level(5), T=33, t0=32) == (5, 33)
+
+
+def test_active_counts_closed_form(oracle_lib):
+    """Fixed levels: the active count at tick T is sum_k n_k [T mod 2^(L-1-k) == 0]."""
+    O = oracle_lib
+    L, M = 5, 0
+    n_k = [3, 5, 7, 11, 13]
+    level = np.repeat(np.arange(L), n_k).astype(np.uint8)
+    n = level.size
+    amg = np.array([_amag_for_level(k, M) for k in level], np.float32)
+    acc = np.zeros((n, 4), np.float32)
+    acc[:, 0] = amg
+    r0 = np.zeros((n, 3))
+    vh = np.zeros((n, 3))
+    t0 = np.zeros(n, np.int64)
+    aold = np.zeros(n, np.float32)
+    ticks = lambda lv: np.left_shift(1, (L - 1 - lv.astype(np.int64)))
+    seen = []
+    for _ in range(40):
+        T = int((t0 + ticks(level)).min())
+        active = np.nonzero(t0 + ticks(level) == T)[0].astype(np.uint32)
+        want = sum(nk for k, nk in enumerate(n_k) if T % (1 << (L - 1 - k)) == 0)
+        assert active.size == want
+        O.correct(active, acc[active], T, 1.0, M, L, 0.025, 0.01, r0, vh, t0, level, aold)
+        seen.append(T)
+    assert seen == list(range(1, 41))
+    assert np.array_equal(level, np.repeat(np.arange(L), n_k))
+
+
+def test_shared_step_reduces_to_leapfrog(oracle_lib):
+    """L = 1 (one shared, fixed step): the block-step scheme is the KDK leap-frog."""
+    O = oracle_lib
+    n = 512
+    pos, vel, m, eps = ics.plummer(n, seed=21)
+    prm = O.Params(eps=eps, mac=0, theta=0.5, levels=1, dt_max=2.0 ** -6)
+    sim = O.BlockStepSim(pos, vel, m, prm)
+    sim.start()
+
+    def force(r):
+        p4 = np.zeros((n, 4), np.float32)
+        p4[:, :3] = r
+        p4[:, 3] = m
+        res = O.tree_force(p4, prm, mac=0)
+        a = np.empty((n, 4), np.float32)
+        a[res["order"]] = res["acc"].astype(np.float32)
+        return a[:, :3].astype(np.float64)
+
+    dt = 2.0 ** -6
+    r = pos.copy()
+    a = force(r)
+    vh = vel + (0.5 * dt) * a
+    for step in range(6):
+        sim.step()
+        r = r + dt * vh
+        a = force(r)
+        v = vh + (0.5 * dt) * a
+        vh = v + (0.5 * dt) * a
+        back = np.empty_like(sim.r0)
+        back[sim.id] = sim.r0
+        np.testing.assert_array_equal(back, r)
+        bv = np.empty_like(sim.vh)
+        bv[sim.id] = sim.vh
+        np.testing.assert_array_equal(bv, vh)
+        assert sim.T == step + 1
+
+
+def test_kepler_orbit(oracle_lib):
+    """Two equal bodies on a circular orbit: one period 2 pi returns them, energy kept."""
+    O = oracle_lib
+    pos = np.array([[0.5, 0.0, 0.0], [-0.5, 0.0, 0.0]])
+    vel = np.array([[0.0, 0.5, 0.0], [0.0, -0.5, 0.0]])
+    m = np.array([0.5, 0.5], np.float32)
+    dt = 2.0 ** -8
+    prm = O.Params(eps=2.0 ** -20, mac=0, theta=0.5, levels=1, dt_max=dt)
+    sim = O.BlockStepSim(pos, vel, m, prm)
+    sim.start()
+
+    def energy():
+        v = sim.vh - (0.5 * dt) * sim.acc[:, :3].astype(np.float64)
+        r = np.linalg.norm(sim.r0[0] - sim.r0[1])
+        return 0.5 * float((m.astype(np.float64) * (v * v).sum(1)).sum()) - 0.25 / r
+
+    e0 = energy()
+    nsteps = int(round(2.0 * math.pi / dt))
+    emax = 0.0
+    for _ in range(nsteps):
+        sim.step()
+        emax = max(emax, abs(energy() - e0))
+    assert emax < 1e-4 * abs(e0)
+    back = np.empty_like(sim.r0)
+    back[sim.id] = sim.r0
+    # after one period the bodies are back where they started (to O(dt))
+    assert np.linalg.norm(back - pos) < 2e-2
+
+
+def test_block_step_runs_and_levels_spread(oracle_lib):
+    O = oracle_lib
+    pos, vel, m, eps = ics.nfw(4096, seed=2)
+    prm = O.Params(eps=eps, levels=6)
+    sim = O.BlockStepSim(pos, vel, m, prm)
+    sim.start()
+    assert len(np.unique(sim.level)) >= 3
+    Ts = [sim.step()["T"] for _ in range(8)]
+    assert all(b > a for a, b in zip(Ts, Ts[1:]))
+    assert np.all(sim.t0 <= sim.T)
+    assert np.all((sim.t0 % np.left_shift(1, (prm.levels - 1 - sim.level.astype(np.int64)))) == 0)

@@ -1,0 +1,146 @@
+"""Pins of the oracle's MAC (Eqs. 2, 5-7), groups (Sec. 2.3) and tree walk."""
+import numpy as np
+import pytest
+
+from paper_1610_07279_gb300 import ics
+
+
+def _p4(n, seed=1, kind="plummer"):
+    gen = ics.plummer if kind == "plummer" else ics.nfw
+    pos, vel, m, eps = gen(n, seed=seed)
+    p4 = np.zeros((n, 4), np.float32)
+    p4[:, :3] = pos
+    p4[:, 3] = m
+    return p4, eps
+
+
+def _acc(oracle_lib, n=2048, seed=1, kind="plummer", **kw):
+    O = oracle_lib
+    p4, eps = _p4(n, seed, kind)
+    prm = O.Params(eps=eps, **kw)
+    return O, p4, prm
+
+
+# ---------------------------------------------------------------- MAC by hand
+def test_mac_opening_angle_boundary(oracle_lib):
+    O = oracle_lib
+    g = [0.0, 0.0, 0.0, 0.0]
+    node = [2.0, 0.0, 0.0, 1.0]
+    assert O.mac_accept(0, 0.5, 0, 0, 1, g, node, 1.0)             # b_J = theta d: accept
+    assert not O.mac_accept(0, 0.5, 0, 0, 1, g, node, np.nextafter(np.float32(1), np.float32(2)))
+    # pseudo i radius shortens the distance: d = lambda r = r - b_I (Eqs. 6-7)
+    g2 = [0.0, 0.0, 0.0, 1.0]
+    node3 = [3.0, 0.0, 0.0, 1.0]
+    assert O.mac_accept(0, 0.5, 0, 0, 1, g2, node3, 1.0)            # d = 2
+    assert not O.mac_accept(0, 0.5, 0, 0, 1, [0, 0, 0, 2.5], node3, 1.0)  # d = 0.5
+    # b_I >= r: lambda = 0, only a point-like cell (b_J = 0) is accepted
+    assert not O.mac_accept(0, 0.5, 0, 0, 1, [0, 0, 0, 3.0], node3, 1e-30)
+    assert O.mac_accept(0, 0.5, 0, 0, 1, [0, 0, 0, 3.0], node3, 0.0)
+
+
+def test_mac_acceleration_boundary(oracle_lib):
+    O = oracle_lib
+    # accept iff d^4 D_acc |a_old| >= G m_J b_J^2; with D_acc |a_old| = 1/16, m=b=G=1: d >= 2
+    g = [0.0, 0.0, 0.0, 0.0]
+    assert O.mac_accept(1, 0, 0.25, 0.25, 1.0, g, [2.0, 0, 0, 1.0], 1.0)
+    below = float(np.nextafter(np.float32(2.0), np.float32(0)))
+    assert not O.mac_accept(1, 0, 0.25, 0.25, 1.0, g, [below, 0, 0, 1.0], 1.0)
+    # doubling G m_J b_J^2 needs d larger by 2^(1/4)
+    assert not O.mac_accept(1, 0, 0.25, 0.25, 2.0, g, [2.0, 0, 0, 1.0], 1.0)
+    assert O.mac_accept(1, 0, 0.25, 0.25, 2.0, g, [2.0 * 2 ** 0.25 * 1.000001, 0, 0, 1.0], 1.0)
+    # |a_old| = 0 accepts only cells with b_J = 0 or m_J = 0
+    assert not O.mac_accept(1, 0, 0.25, 0.0, 1.0, g, [100.0, 0, 0, 1.0], 1.0)
+    assert O.mac_accept(1, 0, 0.25, 0.0, 1.0, g, [100.0, 0, 0, 1.0], 0.0)
+
+
+# ---------------------------------------------------------------- groups
+def test_groups_enclose_members(oracle_lib):
+    O = oracle_lib
+    p4, eps = _p4(4096, seed=3, kind="nfw")
+    key, _ = O.keys(p4)
+    order, skey = O.sort(key)
+    sp4 = p4[order]
+    rng = np.random.default_rng(0)
+    active = np.sort(rng.choice(4096, 1000, replace=False)).astype(np.uint32)
+    aold = rng.uniform(0.1, 2.0, 4096).astype(np.float32)
+    for gmax in (1, 7, 32, 64):
+        gI, gamin = O.groups(active, gmax, sp4, aold)
+        assert len(gI) == -(-1000 // gmax)
+        for g in range(len(gI)):
+            mem = active[g * gmax:(g + 1) * gmax]
+            pts = sp4[mem, :3]
+            np.testing.assert_array_equal(gI[g, :3], np.float32(0.5) * (pts.min(0) + pts.max(0)))
+            d = np.linalg.norm(pts.astype(np.float64) - gI[g, :3].astype(np.float64), axis=1)
+            assert d.max() <= gI[g, 3]
+            assert np.nextafter(gI[g, 3], np.float32(0)) < d.max() or gI[g, 3] == 0
+            assert gamin[g] == aold[mem].min()
+
+
+# ---------------------------------------------------------------- walk
+def _rel(a, b):
+    return np.linalg.norm(a[:, :3] - b[:, :3], axis=1) / np.linalg.norm(b[:, :3], axis=1)
+
+
+def test_theta_zero_equals_direct(oracle_lib):
+    O, p4, prm = _acc(oracle_lib, 2048, seed=2)
+    r = O.tree_force(p4, prm, mac=0, theta=0.0)
+    d = O.direct(p4, prm.eps)[r["order"]]
+    assert np.all(r["inter"] == 2048)
+    np.testing.assert_allclose(r["acc"], d, rtol=1e-12, atol=1e-12)
+
+
+def test_delta_acc_to_zero_equals_direct(oracle_lib):
+    O, p4, prm = _acc(oracle_lib, 2048, seed=5, kind="nfw", delta_acc=1e-30)
+    aold = np.ones(2048, np.float32)
+    r = O.tree_force(p4, prm, aold=aold)
+    d = O.direct(p4, prm.eps)[r["order"]]
+    np.testing.assert_allclose(r["acc"], d, rtol=1e-12, atol=1e-12)
+
+
+def test_error_decreases_with_theta(oracle_lib):
+    O, p4, prm = _acc(oracle_lib, 4096, seed=1)
+    d = O.direct(p4, prm.eps)
+    meds, inters = [], []
+    for th in (0.9, 0.7, 0.5, 0.3, 0.1):
+        r = O.tree_force(p4, prm, mac=0, theta=th)
+        meds.append(np.median(_rel(r["acc"], d[r["order"]])))
+        inters.append(r["inter"].mean())
+    assert all(a > b for a, b in zip(meds, meds[1:]))
+    assert all(a < b for a, b in zip(inters, inters[1:]))
+    # the paper's typical accuracy: ~1e-3 for theta 0.5-0.7
+    assert 1e-4 < meds[2] < 3e-3 and 1e-4 < meds[1] < 3e-3
+
+
+def test_acceleration_mac_accuracy_band(oracle_lib):
+    O, p4, prm = _acc(oracle_lib, 4096, seed=1)
+    d = O.direct(p4, prm.eps)
+    aold = O.bootstrap_aold(p4, prm)
+    errs = []
+    for k in (5, 7, 9, 11):
+        prm.delta_acc = 2.0 ** -k
+        r = O.tree_force(p4, prm, aold=aold)
+        errs.append(np.median(_rel(r["acc"], d[r["order"]])))
+    assert all(a > b for a, b in zip(errs, errs[1:]))
+    assert 1e-4 < errs[1] < 3e-3   # Delta_acc = 2^-7, the paper's fiducial value
+
+
+def test_walk_sampled_groups_equal_full(oracle_lib):
+    O, p4, prm = _acc(oracle_lib, 3000, seed=8, kind="nfw")
+    aold = O.bootstrap_aold(p4, prm)
+    full = O.tree_force(p4, prm, aold=aold)
+    gids = np.array([0, 5, 17, len(full["gI"]) - 1])
+    part = O.tree_force(p4, prm, aold=aold, group_ids=gids)
+    for g in gids:
+        sl = slice(g * prm.group_max, (g + 1) * prm.group_max)
+        np.testing.assert_array_equal(part["acc"][sl], full["acc"][sl])
+        np.testing.assert_array_equal(part["inter"][sl], full["inter"][sl])
+
+
+def test_walk_single_and_empty(oracle_lib):
+    O = oracle_lib
+    prm = O.Params(eps=0.1)
+    p4 = np.array([[1.0, 2.0, 3.0, 0.5]], np.float32)
+    r = O.tree_force(p4, prm, aold=np.ones(1, np.float32))
+    assert np.all(r["acc"] == 0.0) and r["inter"][0] == 1
+    r = O.tree_force(np.zeros((0, 4), np.float32), prm)
+    assert r["acc"].shape == (0, 4)
