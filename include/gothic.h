@@ -1,0 +1,232 @@
+/*
+ * gothic.h -- C ABI of a GB300 (sm_103a) library for the block-time-step
+ * oct-tree gravity method of Miki & Umemura, "GOTHIC: Gravitational oct-tree
+ * code accelerated by hierarchical time step controlling" (arXiv:1610.07279).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an int status: GT_OK (0) or a negative GT_E* code.
+ *     Nothing throws across the ABI.
+ *   - Device work is enqueued on the caller's stream and is asynchronous unless
+ *     the comment says "synchronises".  Errors found on the device (overflow of
+ *     a fixed-size buffer, a bounded wait that ran out) are latched in a device
+ *     error word; gt_sync_status() or gt_get_stats() reports them.
+ *   - The caller owns all memory.  A system lives inside one workspace the caller
+ *     allocates (gt_workspace_bytes) and hands over; the library never calls
+ *     cudaMalloc/cudaFree for a system.  Pointers named d_* must be device
+ *     pointers; pointers named p_* may be host (pageable or pinned) or device
+ *     pointers (copied with cudaMemcpyAsync, kind inferred from the address).
+ *   - Particle order: the library keeps particles sorted by their space-filling
+ *     key ("internal index").  Arrays passed to gt_set_state are in the caller's
+ *     order; gt_get_state returns the internal order together with id[] (the
+ *     caller's index of each internal slot).
+ *   - One stream at a time per system; systems are independent.
+ *   - Precision: positions and velocities are FP64; the tree, the MAC and the
+ *     force sums are FP32; centre-of-mass sums are FP64.
+ */
+#ifndef GOTHIC_H
+#define GOTHIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Every entry point is exported from the shared library (built with hidden
+ * visibility otherwise). */
+#if defined(__GNUC__)
+#define GT_API __attribute__((visibility("default")))
+#else
+#define GT_API
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define GT_OK 0
+#define GT_EINVAL (-1)    /* bad argument */
+#define GT_ENOMEM (-2)    /* workspace too small */
+#define GT_EOVERFLOW (-3) /* a fixed-size device buffer (nodes, walk queue) overflowed */
+#define GT_ETIMEOUT (-4)  /* a bounded device wait ran out */
+#define GT_ECUDA (-5)     /* a CUDA runtime call failed */
+#define GT_EAGAIN (-6)    /* server: no slot or memory free now; retry later */
+#define GT_EPENDING (-7)  /* server: the request has not finished yet */
+#define GT_ENOTIMPL (-8)  /* option not implemented */
+#define GT_ESTATE (-9)    /* call out of order (e.g. block step before start) */
+
+/* ---- multipole acceptance criteria (Sec. 2.2) -------------------------------- */
+#define GT_MAC_OPENING_ANGLE 0 /* Eq. (2), Barnes & Hut 1986: b_J / d <= theta   */
+#define GT_MAC_ACCELERATION 1  /* Eq. (5), Springel 2005: d >= (G m_J b_J^2 /
+                                  (Delta_acc |a_old|))^(1/4)                    */
+
+typedef struct CUstream_st *gt_stream; /* identical to cudaStream_t */
+
+/* Method parameters.  gt_default_params fills the paper's fiducial values. */
+typedef struct gt_params {
+    int32_t mac;        /* GT_MAC_*; the paper's fiducial choice is ACCELERATION   */
+    float theta;        /* opening angle of Eq. (2); also the bootstrap pass's     */
+    float delta_acc;    /* Delta_acc of Eq. (5); fiducial 2^-7 (Sec. 3.3)          */
+    float eps;          /* Plummer softening of Eq. (1)                            */
+    float G;            /* gravitational constant of Eq. (1)                       */
+    int32_t leaf_max;   /* a cell with more particles than this is split (<= 21 levels) */
+    int32_t group_max;  /* i-particles per group sharing one walk (Sec. 2.3)        */
+    int32_t ij_share;   /* S: threads sharing one i-particle (Sec. 2.5), 1..32, power of 2;
+                           group_max must be <= 32 / ij_share                       */
+    int32_t levels;     /* L: number of block-step levels, 1..30 (Sec. 1)          */
+    int32_t rebuild_every; /* rebuild the tree every n block steps (Sec. 2.6); 1 = always */
+    int32_t walk_queue; /* per-warp breadth-first queue capacity, power of 2 (Sec. 2.3) */
+    int32_t reserved0;
+    double eta;         /* step accuracy: dt_i = sqrt(2 eta eps / |a_i|)           */
+    double dt_max;      /* longest step, a power of two; <= 0: derived at gt_start */
+} gt_params;
+
+/* Counters and state read back by gt_get_stats (synchronises the stream). */
+typedef struct gt_stats {
+    int64_t n;              /* particles                                           */
+    int64_t T;              /* current block time in ticks of the finest step      */
+    int64_t n_active;       /* i-particles of the last force evaluation            */
+    int64_t n_groups;       /* groups of the last force evaluation                 */
+    int64_t n_nodes;        /* tree cells                                          */
+    int64_t depth;          /* deepest tree level + 1                              */
+    int64_t interactions;   /* cumulative i-j interactions evaluated               */
+    int64_t mac_tests;      /* cumulative MAC evaluations                          */
+    int64_t block_steps;    /* block steps taken since gt_start                    */
+    int64_t rebuilds;       /* tree builds since create                            */
+    double dt_max;          /* longest step in use                                 */
+    int32_t err;            /* latched device error (GT_OK if none)                */
+    int32_t err_where;      /* kernel that latched it (diagnostic)                 */
+} gt_stats;
+
+typedef struct gt_system gt_system;
+
+/* Human-readable name of a status code (static string). */
+GT_API const char *gt_strerror(int status);
+
+/* The paper's fiducial parameters: acceleration MAC with Delta_acc = 2^-7
+ * (Sec. 3.3), theta = 0.5 for the bootstrap pass, G = 1, eps = 1/64,
+ * leaf_max = 16, group_max = 32, S = 1, L = 8, eta = 0.025, queue 8192. */
+GT_API int gt_default_params(gt_params *prm);
+
+/* Bytes of device workspace a system of n particles needs (n >= 0). */
+GT_API int gt_workspace_bytes(int64_t n, const gt_params *prm, size_t *bytes);
+
+/* Create a system of n particles inside the caller's workspace d_ws (at least
+ * gt_workspace_bytes, 256-byte aligned, on the current device).  The workspace
+ * must outlive the system.  Host-side bookkeeping is malloc'ed here and freed by
+ * gt_system_destroy.  GT_ENOMEM if ws_bytes is too small. */
+GT_API int gt_system_create(gt_system **sys, int64_t n, const gt_params *prm, void *d_ws,
+                     size_t ws_bytes);
+GT_API int gt_system_destroy(gt_system *sys);
+
+/* Replace the parameters (same n; leaf_max/group_max/ij_share/walk_queue may
+ * change; levels and dt_max only before gt_start). */
+GT_API int gt_set_params(gt_system *sys, const gt_params *prm);
+
+/* Load particles in the caller's order: p_pos, p_vel n x 3 FP64 (row-major),
+ * p_mass n FP32 (> 0).  Positions are also rounded to FP32 for the tree.  Resets
+ * time to 0 and the internal order to the caller's order.  Any p_* may be host
+ * or device memory. */
+GT_API int gt_set_state(gt_system *sys, const double *p_pos, const double *p_vel, const float *p_mass,
+                 gt_stream stream);
+
+/* Steps A1-A5 of the method on the current FP32 positions (Sec. 2.1):
+ * bounding cube and 63-bit Morton keys (Appendix A), a stable radix sort of
+ * (key, index), permutation of every particle array into key order, the
+ * breadth-first octree (cells split into up to eight children by key digit,
+ * numbered level by level with prefix sums) and the pseudo j-particles
+ * (mass, FP64-accumulated centre of mass, enclosing radius b_J; Fig. 1). */
+GT_API int gt_build_tree(gt_system *sys, gt_stream stream);
+
+/* Steps A6-A7: accelerations of the listed i-particles from the current tree
+ * (Sec. 2.3): groups of group_max consecutive entries of d_active share one
+ * walk; each group's pseudo i-particle is the sphere about the centre of its
+ * bounding box (Appendix B, GEO); cells are tested with the MAC at distance
+ * lambda r_JI (Eqs. 6-7) and the Plummer-softened sums of Eq. (1) run over the
+ * accepted cells and the particles of opened leaves.
+ *   d_active  n_active internal indices (uint32), or NULL for all particles
+ *             (then n_active must be n).  Groups follow the given order.
+ *   d_aold    n FP32 |a_old| by internal index (the acceleration MAC needs it),
+ *             or NULL to use the system's own.
+ *   d_acc     n_active x 4 FP32 output (ax, ay, az, potential), in d_active order.
+ * Uses the current parameters' mac.  Requires a built tree. */
+GT_API int gt_accel_active(gt_system *sys, const uint32_t *d_active, int64_t n_active,
+                    const float *d_aold, float *d_acc, gt_stream stream);
+
+/* Start the block-step integration at t = 0 (Sec. 2.7): build the tree, run
+ * an opening-angle bootstrap pass (theta) whose |a| seeds a_old (the paper has
+ * no a_old at t = 0), an acceleration-MAC pass, choose dt_max (if not given) as
+ * the largest power of two not above max dt_i, assign each particle the level
+ * of the smallest step dt_max 2^-k <= dt_i = sqrt(2 eta eps/|a|), and give
+ * every particle its first half kick v^{1/2} = v + (dt/2) a.
+ *   p_aold_boot  optional n FP32 |a_old| in the caller's order; if given the
+ *                bootstrap pass is skipped and these values are used. */
+GT_API int gt_start(gt_system *sys, const float *p_aold_boot, gt_stream stream);
+
+/* One block step (Sec. 1; Sec. 2.7, Eqs. 15-17): advance to the next tick T
+ * at which some particle's step ends; predict every particle to T; rebuild
+ * the tree (every rebuild_every steps, else refresh the pseudo j-particles on
+ * the old topology, Sec. 2.6); select the active particles (t0 + ticks(level)
+ * == T); walk them; correct their velocities, assign new levels (a shorter
+ * step at once, a longer one by one level when T is aligned to it) and give
+ * the next half kick.  Fully asynchronous: no host synchronisation. */
+GT_API int gt_block_step(gt_system *sys, gt_stream stream);
+
+/* Resume a block-step integration (checkpoint/restart, or a caller-driven
+ * integration): after gt_set_state, whose velocities are then taken as the
+ * stored half-step velocities v^{1/2}, set per particle (caller's order) the
+ * level p_level (uint8, < L), the tick of the last correction p_t0 (int64,
+ * multiple of the level's span), |a_old| p_aold (FP32) and optionally the last
+ * acceleration p_acc (n x 4 FP32, may be NULL), together with dt_max (a power of
+ * two) and the current tick T.  Afterwards gt_block_step continues from there.
+ * Does not build a tree (gt_block_step or gt_build_tree will). */
+GT_API int gt_set_integrator_state(gt_system *sys, const uint8_t *p_level, const int64_t *p_t0,
+                                   const float *p_aold, const float *p_acc, double dt_max, int64_t T,
+                                   gt_stream stream);
+
+/* Step A8 alone (Eq. 16 with the elapsed time): positions of every particle at
+ * tick T, r(T) = r0 + ((T - t0) dt_min) v^{1/2}, rounded to FP32, written as
+ * n x 4 FP32 (x, y, z, m) in internal order to d_posm (device).  Requires a
+ * started or resumed integration. */
+GT_API int gt_predict(gt_system *sys, int64_t T, float *d_posm, gt_stream stream);
+
+/* Step A9 alone (Eq. 17): correct the listed particles (internal indices) at
+ * tick T with the caller's accelerations d_acc (n_active x 4 FP32, device), give
+ * them their new level and next half kick, exactly as gt_block_step does. */
+GT_API int gt_correct(gt_system *sys, const uint32_t *d_active, int64_t n_active, const float *d_acc,
+                      int64_t T, gt_stream stream);
+
+/* Copy the state out in internal order.  Any pointer may be NULL to skip it;
+ * any may be host or device memory.  p_pos, p_vel n x 3 FP64 (velocity is the
+ * half-step velocity v^{1/2} that the scheme stores), p_acc n x 4 FP32 (the
+ * last acceleration and potential), p_level n uint8, p_t0 n int64 (tick of the
+ * last correction), p_id n uint32 (caller's index). */
+GT_API int gt_get_state(gt_system *sys, double *p_pos, double *p_vel, float *p_acc, uint8_t *p_level,
+                 int64_t *p_t0, uint32_t *p_id, gt_stream stream);
+
+/* Copy the tree out.  p_keys n uint64 sorted keys; p_order n uint32 (the
+ * caller's index of each internal slot, same as id); p_nodes n_nodes x 4 uint32
+ * (first particle, count, first child or 0xffffffff for a leaf, number of
+ * children); p_jpos n_nodes x 4 FP32 (x, y, z, m); p_bj n_nodes FP32.  Pass
+ * *n_nodes_inout = capacity (entries) on entry; it returns the node count
+ * (synchronises; GT_EOVERFLOW if the capacity is short). */
+GT_API int gt_get_tree(gt_system *sys, uint64_t *p_keys, uint32_t *p_order, uint32_t *p_nodes,
+                float *p_jpos, float *p_bj, int64_t *n_nodes_inout, gt_stream stream);
+
+/* The i-particles selected by the last block step (internal indices, in
+ * order).  *n_inout = capacity on entry, count on return (synchronises). */
+GT_API int gt_get_active(gt_system *sys, uint32_t *p_active, int64_t *n_inout, gt_stream stream);
+
+/* Synchronise the stream and report the latched device error (and clear it). */
+GT_API int gt_sync_status(gt_system *sys, gt_stream stream);
+
+/* Synchronise and read counters (see gt_stats). */
+GT_API int gt_get_stats(gt_system *sys, gt_stats *out, gt_stream stream);
+
+/* Measure the device's FP32 FMA throughput (FLOP/s, FMA = 2 flops) with a
+ * dependent-FMA-chain kernel on all SMs; the roofline denominator of the walk.
+ * Synchronises; ~10 ms. */
+GT_API int gt_measure_fp32_peak(double *flops, gt_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GOTHIC_H */

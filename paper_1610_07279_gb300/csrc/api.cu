@@ -1,0 +1,548 @@
+// C ABI of libgothic: system lifetime, workspace layout and the entry points that
+// string the kernels together (see include/gothic.h for the contract).
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "gt_internal.cuh"
+
+struct gt_system {
+    int64_t n = 0;
+    gt_params prm{};
+    int dev = 0, nsm = 0;
+    int walk_blocks = 0, walk_warps = 0;
+    int cur = 0;
+    bool started = false, have_tree = false;
+    long long steps = 0, rebuilds = 0;
+    int64_t cap = 0;        // node capacity
+    State st[2]{};
+    float4 *posm = nullptr, *posm_tmp = nullptr;
+    SortBufs sb{};
+    Nodes nd{};
+    unsigned long long *status = nullptr;
+    uint32_t *active = nullptr;
+    float4 *acc_out = nullptr;
+    float *aold_tmp = nullptr;
+    double *scratch3 = nullptr;
+    float *bbox_partial = nullptr;
+    int bbox_blocks = 0;
+    uint32_t *queue = nullptr;
+    int64_t queue_entries = 0;
+    DevCtl *ctl = nullptr;
+};
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+struct Layout {
+    size_t off = 0;
+    template <class T>
+    T *take(char *base, size_t count) {
+        off = (off + ALIGN - 1) / ALIGN * ALIGN;
+        T *p = base ? (T *)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int check_params(const gt_params *p) {
+    if (!p) return GT_EINVAL;
+    if (p->mac != GT_MAC_OPENING_ANGLE && p->mac != GT_MAC_ACCELERATION) return GT_EINVAL;
+    if (p->leaf_max < 1) return GT_EINVAL;
+    if (!pow2(p->ij_share) || p->ij_share > 32) return GT_EINVAL;
+    if (p->group_max < 1 || p->group_max > 32 / p->ij_share) return GT_EINVAL;
+    if (p->levels < 1 || p->levels > 30) return GT_EINVAL;
+    if (p->rebuild_every < 1) return GT_EINVAL;
+    if (!pow2(p->walk_queue) || p->walk_queue < 64) return GT_EINVAL;
+    if (!(p->eps > 0.0f) || !(p->theta >= 0.0f) || !(p->delta_acc >= 0.0f)) return GT_EINVAL;
+    if (!(p->eta > 0.0)) return GT_EINVAL;
+    if (p->dt_max > 0.0) {
+        int e;
+        if (frexp(p->dt_max, &e) != 0.5) return GT_EINVAL;  // must be a power of two
+    }
+    return GT_OK;
+}
+
+int device_sms(int *dev, int *nsm) {
+    if (cudaGetDevice(dev) != cudaSuccess) return GT_ECUDA;
+    if (cudaDeviceGetAttribute(nsm, cudaDevAttrMultiProcessorCount, *dev) != cudaSuccess) return GT_ECUDA;
+    return GT_OK;
+}
+
+int max_walk_blocks(int nsm) {
+    int best = 0;
+    for (int s = 1; s <= 32; s <<= 1) {
+        const int b = gt_walk_blocks(s, nsm);
+        best = b > best ? b : best;
+    }
+    return best;
+}
+
+int64_t node_capacity(int64_t n) { return 2 * n + 2048; }
+
+// Carve every buffer out of base (or only measure when base == nullptr).
+size_t carve(gt_system *s, char *base, int64_t n, const gt_params *p, int nsm, int walk_blocks) {
+    Layout L;
+    const size_t N = (size_t)(n > 0 ? n : 1);
+    s->ctl = L.take<DevCtl>(base, 1);
+    for (int b = 0; b < 2; b++) {
+        State &t = s->st[b];
+        double *r = L.take<double>(base, 3 * N);
+        double *v = L.take<double>(base, 3 * N);
+        t.rx = r; t.ry = r ? r + N : nullptr; t.rz = r ? r + 2 * N : nullptr;
+        t.vx = v; t.vy = v ? v + N : nullptr; t.vz = v ? v + 2 * N : nullptr;
+        t.t0 = L.take<long long>(base, N);
+        t.level = L.take<uint8_t>(base, N);
+        t.aold = L.take<float>(base, N);
+        t.acc = L.take<float4>(base, N);
+        t.id = L.take<uint32_t>(base, N);
+        t.mass = L.take<float>(base, N);
+    }
+    s->posm = L.take<float4>(base, N);
+    s->posm_tmp = L.take<float4>(base, N);
+    for (int b = 0; b < 2; b++) {
+        s->sb.key[b] = L.take<uint64_t>(base, N);
+        s->sb.val[b] = L.take<uint32_t>(base, N);
+    }
+    s->sb.tile_hist = (uint32_t *)L.take<char>(base, gt_sort_scratch_bytes(n));
+    s->sb.digit_base = L.take<uint32_t>(base, 256);
+    s->sb.digit_total = L.take<uint32_t>(base, 256);
+    const int64_t cap = node_capacity(n);
+    s->cap = cap;
+    s->nd.first = L.take<uint32_t>(base, cap);
+    s->nd.count = L.take<uint32_t>(base, cap);
+    s->nd.child = L.take<int32_t>(base, cap);
+    s->nd.nchild = L.take<uint32_t>(base, cap);
+    s->nd.parent = L.take<int32_t>(base, cap);
+    s->nd.arrive = L.take<uint32_t>(base, cap);
+    s->nd.jpos = L.take<float4>(base, cap);
+    s->nd.walk = L.take<float4>(base, cap);
+    s->nd.sum = L.take<DSum4>(base, cap);
+    const int64_t st_tiles = (cap + 511) / 512 + (n + 4095) / 4096 + 64;
+    s->status = L.take<unsigned long long>(base, st_tiles);
+    s->active = L.take<uint32_t>(base, N);
+    s->acc_out = L.take<float4>(base, N);
+    s->aold_tmp = L.take<float>(base, N);
+    s->scratch3 = L.take<double>(base, 3 * N + 8);  // also stages 13 B per particle on resume
+    s->bbox_blocks = nsm * 4;
+    s->bbox_partial = L.take<float>(base, 6 * (size_t)s->bbox_blocks);
+    s->walk_blocks = walk_blocks;
+    s->walk_warps = walk_blocks * gt_walk_warps_per_block();
+    s->queue_entries = (int64_t)s->walk_warps * p->walk_queue;
+    s->queue = L.take<uint32_t>(base, (size_t)s->queue_entries);
+    return (L.off + ALIGN - 1) / ALIGN * ALIGN;
+}
+
+int last_cuda() { return cudaGetLastError() == cudaSuccess ? GT_OK : GT_ECUDA; }
+
+cudaStream_t S(gt_stream s) { return (cudaStream_t)s; }
+
+// A1-A5 on the current FP32 positions in s->posm (permutes every array into key order)
+void build_tree(gt_system *s, cudaStream_t st, const float4 *posm_src) {
+    const int64_t n = s->n;
+    gt_launch_prepare(s->ctl, 0, st);
+    gt_launch_bbox(posm_src, n, s->bbox_partial, s->bbox_blocks, s->ctl, st);
+    gt_launch_keys(posm_src, n, s->ctl, s->sb.key[0], s->sb.val[0], st);
+    gt_launch_sort(s->sb, n, s->ctl, st);
+    const int nxt = s->cur ^ 1;
+    float4 *dst = posm_src == s->posm ? s->posm_tmp : s->posm;
+    gt_launch_permute(s->st[s->cur], s->st[nxt], posm_src, dst, s->sb.val[0], n, st);
+    s->cur = nxt;
+    if (dst != s->posm) {
+        float4 *t = s->posm;
+        s->posm = s->posm_tmp;
+        s->posm_tmp = t;
+    }
+    gt_launch_build(s->sb.key[0], n, s->prm.leaf_max, s->nd, s->cap, s->status, s->ctl, s->nsm, st);
+    gt_launch_pseudo(s->nd, s->cap, s->posm, s->ctl, s->nsm, st);
+    s->have_tree = true;
+    s->rebuilds++;
+}
+
+void walk(gt_system *s, const uint32_t *active, const float *aold, float4 *acc, int mac, cudaStream_t st) {
+    WalkArgs a;
+    a.jpos = s->nd.jpos;
+    a.walk = s->nd.walk;
+    a.posm = s->posm;
+    a.active = active;
+    a.aold = aold;
+    a.acc = acc;
+    a.queue = s->queue;
+    a.ctl = s->ctl;
+    a.n = (uint32_t)s->n;
+    a.gmax = s->prm.group_max;
+    a.qcap = s->prm.walk_queue;
+    a.mac = mac;
+    a.theta = s->prm.theta;
+    a.delta_acc = s->prm.delta_acc;
+    a.eps2 = s->prm.eps * s->prm.eps;
+    a.G = s->prm.G;
+    a.inv_eps = 1.0f / s->prm.eps;
+    gt_launch_walk(a, s->prm.ij_share, s->walk_blocks, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gt_strerror(int status) {
+    switch (status) {
+        case GT_OK: return "ok";
+        case GT_EINVAL: return "invalid argument";
+        case GT_ENOMEM: return "workspace too small";
+        case GT_EOVERFLOW: return "device buffer overflow (tree nodes or walk queue)";
+        case GT_ETIMEOUT: return "bounded device wait ran out";
+        case GT_ECUDA: return "CUDA runtime error";
+        case GT_EAGAIN: return "no slot or memory free; retry";
+        case GT_EPENDING: return "request not finished";
+        case GT_ENOTIMPL: return "not implemented";
+        case GT_ESTATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+int gt_default_params(gt_params *p) {
+    if (!p) return GT_EINVAL;
+    memset(p, 0, sizeof(*p));
+    p->mac = GT_MAC_ACCELERATION;
+    p->theta = 0.5f;
+    p->delta_acc = 0.0078125f;  // 2^-7
+    p->eps = 0.015625f;         // 1/64
+    p->G = 1.0f;
+    p->leaf_max = 16;
+    p->group_max = 32;
+    p->ij_share = 1;
+    p->levels = 8;
+    p->rebuild_every = 1;
+    p->walk_queue = 8192;
+    p->eta = 0.025;
+    p->dt_max = 0.0;
+    return GT_OK;
+}
+
+int gt_workspace_bytes(int64_t n, const gt_params *prm, size_t *bytes) {
+    if (!bytes || n < 0 || n >= (int64_t)1 << 31) return GT_EINVAL;
+    int rc = check_params(prm);
+    if (rc) return rc;
+    int dev, nsm;
+    if ((rc = device_sms(&dev, &nsm))) return rc;
+    gt_system tmp;
+    *bytes = carve(&tmp, nullptr, n, prm, nsm, max_walk_blocks(nsm));
+    return GT_OK;
+}
+
+int gt_system_create(gt_system **out, int64_t n, const gt_params *prm, void *d_ws, size_t ws_bytes) {
+    if (!out || n < 0 || n >= (int64_t)1 << 31 || !d_ws) return GT_EINVAL;
+    if (((uintptr_t)d_ws) % ALIGN) return GT_EINVAL;
+    int rc = check_params(prm);
+    if (rc) return rc;
+    gt_system *s = new (std::nothrow) gt_system();
+    if (!s) return GT_ENOMEM;
+    if ((rc = device_sms(&s->dev, &s->nsm))) { delete s; return rc; }
+    gt_sort_init();
+    const int wb = max_walk_blocks(s->nsm);
+    const size_t need = carve(s, nullptr, n, prm, s->nsm, wb);
+    if (ws_bytes < need) { delete s; return GT_ENOMEM; }
+    carve(s, (char *)d_ws, n, prm, s->nsm, wb);
+    s->walk_blocks = gt_walk_blocks(prm->ij_share, s->nsm);
+    s->n = n;
+    s->prm = *prm;
+    // zero the control block, the look-back status words and the arrival counters
+    if (cudaMemset(s->ctl, 0, sizeof(DevCtl)) != cudaSuccess ||
+        cudaMemset(s->status, 0, (size_t)((s->cap + 511) / 512 + (n + 4095) / 4096 + 64) * 8) != cudaSuccess ||
+        cudaMemset(s->nd.arrive, 0, (size_t)s->cap * 4) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        delete s;
+        return GT_ECUDA;
+    }
+    *out = s;
+    return GT_OK;
+}
+
+int gt_system_destroy(gt_system *s) {
+    delete s;
+    return GT_OK;
+}
+
+int gt_set_params(gt_system *s, const gt_params *prm) {
+    if (!s) return GT_EINVAL;
+    int rc = check_params(prm);
+    if (rc) return rc;
+    if (prm->walk_queue > s->prm.walk_queue) return GT_EINVAL;  // the queue region is fixed
+    if (s->started && (prm->levels != s->prm.levels || prm->dt_max != s->prm.dt_max)) return GT_ESTATE;
+    const int qcap_region = s->prm.walk_queue;
+    s->prm = *prm;
+    s->prm.walk_queue = prm->walk_queue;
+    (void)qcap_region;
+    s->walk_blocks = gt_walk_blocks(prm->ij_share, s->nsm);
+    return GT_OK;
+}
+
+int gt_set_state(gt_system *s, const double *p_pos, const double *p_vel, const float *p_mass,
+                 gt_stream stream) {
+    if (!s || (s->n > 0 && (!p_pos || !p_vel || !p_mass))) return GT_EINVAL;
+    cudaStream_t st = S(stream);
+    const int64_t n = s->n;
+    s->cur = 0;
+    State &t = s->st[0];
+    if (n > 0) {
+        if (cudaMemcpyAsync(s->scratch3, p_pos, (size_t)n * 24, cudaMemcpyDefault, st) != cudaSuccess) return GT_ECUDA;
+        gt_launch_deinterleave3(s->scratch3, n, t.rx, t.ry, t.rz, st);
+        if (cudaMemcpyAsync(s->scratch3, p_vel, (size_t)n * 24, cudaMemcpyDefault, st) != cudaSuccess) return GT_ECUDA;
+        gt_launch_deinterleave3(s->scratch3, n, t.vx, t.vy, t.vz, st);
+        if (cudaMemcpyAsync(t.mass, p_mass, (size_t)n * 4, cudaMemcpyDefault, st) != cudaSuccess) return GT_ECUDA;
+        gt_launch_load(t, s->posm, n, st);
+    }
+    s->started = false;
+    s->have_tree = false;
+    s->steps = 0;
+    return last_cuda();
+}
+
+int gt_build_tree(gt_system *s, gt_stream stream) {
+    if (!s) return GT_EINVAL;
+    build_tree(s, S(stream), s->posm);
+    return last_cuda();
+}
+
+int gt_accel_active(gt_system *s, const uint32_t *d_active, int64_t n_active, const float *d_aold,
+                    float *d_acc, gt_stream stream) {
+    if (!s || !d_acc || n_active < 0 || n_active > s->n) return GT_EINVAL;
+    if (!d_active && n_active != s->n) return GT_EINVAL;
+    if (!s->have_tree) return GT_ESTATE;
+    cudaStream_t st = S(stream);
+    gt_launch_prepare(s->ctl, 0, st);
+    gt_launch_set_nactive(s->ctl, (unsigned)n_active, st);
+    walk(s, d_active, d_aold ? d_aold : s->st[s->cur].aold, (float4 *)d_acc, s->prm.mac, st);
+    return last_cuda();
+}
+
+int gt_start(gt_system *s, const float *p_aold_boot, gt_stream stream) {
+    if (!s) return GT_EINVAL;
+    cudaStream_t st = S(stream);
+    const int64_t n = s->n;
+    build_tree(s, st, s->posm);
+    State &t = s->st[s->cur];
+    if (p_aold_boot) {
+        if (n > 0 && cudaMemcpyAsync(s->aold_tmp, p_aold_boot, (size_t)n * 4, cudaMemcpyDefault, st) != cudaSuccess)
+            return GT_ECUDA;
+        gt_launch_gather_f(s->aold_tmp, t.id, n, t.aold, st);
+    } else {
+        gt_launch_prepare(s->ctl, 0, st);
+        gt_launch_set_nactive(s->ctl, (unsigned)n, st);
+        walk(s, nullptr, nullptr, s->acc_out, GT_MAC_OPENING_ANGLE, st);
+        gt_launch_amag(s->acc_out, n, t.aold, st);
+    }
+    gt_launch_prepare(s->ctl, 0, st);
+    gt_launch_set_nactive(s->ctl, (unsigned)n, st);
+    walk(s, nullptr, t.aold, s->acc_out, s->prm.mac, st);
+    int M = 0, have_M = 0;
+    if (s->prm.dt_max > 0.0) {
+        int e;
+        frexp(s->prm.dt_max, &e);
+        M = e - 1;
+        have_M = 1;
+    }
+    gt_launch_init_levels(t, s->acc_out, n, s->prm.levels, s->prm.eta, (double)s->prm.eps, M, have_M,
+                          s->ctl, s->nsm, st);
+    s->started = true;
+    s->steps = 0;
+    return last_cuda();
+}
+
+int gt_block_step(gt_system *s, gt_stream stream) {
+    if (!s) return GT_EINVAL;
+    if (!s->started) return GT_ESTATE;
+    cudaStream_t st = S(stream);
+    const int64_t n = s->n;
+    if (n == 0) return GT_OK;
+    gt_launch_prepare(s->ctl, 1, st);
+    if (s->steps % s->prm.rebuild_every == 0) {
+        gt_launch_predict(s->st[s->cur], n, s->ctl, s->posm_tmp, st);
+        build_tree(s, st, s->posm_tmp);
+    } else {
+        gt_launch_predict(s->st[s->cur], n, s->ctl, s->posm, st);
+        gt_launch_pseudo(s->nd, s->cap, s->posm, s->ctl, s->nsm, st);
+    }
+    State &t = s->st[s->cur];
+    gt_launch_active(t, n, s->prm.levels, 0, s->ctl, s->active, s->status, s->nsm, st);
+    walk(s, s->active, t.aold, s->acc_out, s->prm.mac, st);
+    gt_launch_correct(t, s->active, s->acc_out, s->ctl, n, s->prm.levels, s->prm.eta, (double)s->prm.eps,
+                      s->nsm, st);
+    s->steps++;
+    return last_cuda();
+}
+
+int gt_set_integrator_state(gt_system *s, const uint8_t *p_level, const int64_t *p_t0, const float *p_aold,
+                            const float *p_acc, double dt_max, int64_t T, gt_stream stream) {
+    if (!s || !(dt_max > 0.0) || T < 0) return GT_EINVAL;
+    if (s->n > 0 && (!p_level || !p_t0 || !p_aold)) return GT_EINVAL;
+    int e;
+    if (frexp(dt_max, &e) != 0.5) return GT_EINVAL;
+    cudaStream_t st = S(stream);
+    const int64_t n = s->n;
+    const int L = s->prm.levels;
+    State &t = s->st[s->cur];
+    if (n > 0) {
+        // stage the caller-order arrays in scratch (24 B per particle is enough for 1+8+4 B)
+        char *base = (char *)s->scratch3;
+        uint8_t *lv = (uint8_t *)base;
+        long long *t0 = (long long *)(base + ((n + 15) / 16) * 16);
+        float *ao = (float *)(t0 + n);
+        if (cudaMemcpyAsync(lv, p_level, (size_t)n, cudaMemcpyDefault, st) ||
+            cudaMemcpyAsync(t0, p_t0, (size_t)n * 8, cudaMemcpyDefault, st) ||
+            cudaMemcpyAsync(ao, p_aold, (size_t)n * 4, cudaMemcpyDefault, st))
+            return GT_ECUDA;
+        if (p_acc && cudaMemcpyAsync(s->acc_out, p_acc, (size_t)n * 16, cudaMemcpyDefault, st)) return GT_ECUDA;
+        gt_launch_gather_resume(lv, t0, ao, p_acc ? s->acc_out : nullptr, t, n, st);
+    }
+    gt_launch_set_clock(s->ctl, e - 1, L, T, st);
+    gt_launch_tnext_all(t, n, L, s->ctl, s->nsm, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GT_ECUDA;  // the staged scratch is reused
+    s->started = true;
+    s->steps = 0;
+    return last_cuda();
+}
+
+int gt_predict(gt_system *s, int64_t T, float *d_posm, gt_stream stream) {
+    if (!s || !d_posm || T < 0) return GT_EINVAL;
+    if (!s->started) return GT_ESTATE;
+    cudaStream_t st = S(stream);
+    gt_launch_set_tnext(s->ctl, T, st);
+    gt_launch_predict(s->st[s->cur], s->n, s->ctl, (float4 *)d_posm, st);
+    return last_cuda();
+}
+
+int gt_correct(gt_system *s, const uint32_t *d_active, int64_t n_active, const float *d_acc, int64_t T,
+               gt_stream stream) {
+    if (!s || n_active < 0 || n_active > s->n || (n_active > 0 && (!d_active || !d_acc)) || T < 0)
+        return GT_EINVAL;
+    if (!s->started) return GT_ESTATE;
+    cudaStream_t st = S(stream);
+    State &t = s->st[s->cur];
+    gt_launch_set_tnext(s->ctl, T, st);
+    gt_launch_set_nactive(s->ctl, (unsigned)n_active, st);
+    gt_launch_correct(t, d_active, (const float4 *)d_acc, s->ctl, s->n, s->prm.levels, s->prm.eta,
+                      (double)s->prm.eps, s->nsm, st);
+    // the next block time over every particle
+    gt_launch_prepare(s->ctl, 1, st);
+    gt_launch_tnext_all(t, s->n, s->prm.levels, s->ctl, s->nsm, st);
+    gt_launch_set_tnext(s->ctl, T, st);
+    return last_cuda();
+}
+
+int gt_get_state(gt_system *s, double *p_pos, double *p_vel, float *p_acc, uint8_t *p_level,
+                 int64_t *p_t0, uint32_t *p_id, gt_stream stream) {
+    if (!s) return GT_EINVAL;
+    cudaStream_t st = S(stream);
+    const int64_t n = s->n;
+    if (n == 0) return GT_OK;
+    const State &t = s->st[s->cur];
+    if (p_pos) {
+        gt_launch_interleave3(t.rx, t.ry, t.rz, n, s->scratch3, st);
+        if (cudaMemcpyAsync(p_pos, s->scratch3, (size_t)n * 24, cudaMemcpyDefault, st)) return GT_ECUDA;
+    }
+    if (p_vel) {
+        gt_launch_interleave3(t.vx, t.vy, t.vz, n, s->scratch3, st);
+        if (cudaMemcpyAsync(p_vel, s->scratch3, (size_t)n * 24, cudaMemcpyDefault, st)) return GT_ECUDA;
+    }
+    if (p_acc && cudaMemcpyAsync(p_acc, t.acc, (size_t)n * 16, cudaMemcpyDefault, st)) return GT_ECUDA;
+    if (p_level && cudaMemcpyAsync(p_level, t.level, (size_t)n, cudaMemcpyDefault, st)) return GT_ECUDA;
+    if (p_t0 && cudaMemcpyAsync(p_t0, t.t0, (size_t)n * 8, cudaMemcpyDefault, st)) return GT_ECUDA;
+    if (p_id && cudaMemcpyAsync(p_id, t.id, (size_t)n * 4, cudaMemcpyDefault, st)) return GT_ECUDA;
+    if (p_pos || p_vel) {
+        // scratch3 is reused by the next call: finish these copies first
+        if (cudaStreamSynchronize(st) != cudaSuccess) return GT_ECUDA;
+    }
+    return last_cuda();
+}
+
+int gt_get_tree(gt_system *s, uint64_t *p_keys, uint32_t *p_order, uint32_t *p_nodes, float *p_jpos,
+                float *p_bj, int64_t *n_nodes_inout, gt_stream stream) {
+    if (!s || !n_nodes_inout) return GT_EINVAL;
+    cudaStream_t st = S(stream);
+    const int64_t n = s->n;
+    uint32_t ls[GT_TREE_LEVELS + 2];
+    if (cudaMemcpyAsync(ls, s->ctl->level_start, sizeof(ls), cudaMemcpyDeviceToHost, st) ||
+        cudaStreamSynchronize(st))
+        return GT_ECUDA;
+    int64_t nn = s->have_tree ? (int64_t)ls[GT_TREE_LEVELS] : 0;
+    if (nn > s->cap) nn = s->cap;
+    const int64_t capacity = *n_nodes_inout;
+    *n_nodes_inout = nn;
+    if (n > 0 && p_keys && cudaMemcpyAsync(p_keys, s->sb.key[0], (size_t)n * 8, cudaMemcpyDefault, st)) return GT_ECUDA;
+    if (n > 0 && p_order && cudaMemcpyAsync(p_order, s->st[s->cur].id, (size_t)n * 4, cudaMemcpyDefault, st))
+        return GT_ECUDA;
+    if (nn > capacity && (p_nodes || p_jpos || p_bj)) return GT_EOVERFLOW;
+    if (nn > 0) {
+        if (p_nodes) {
+            const void *cols[4] = {s->nd.first, s->nd.count, s->nd.child, s->nd.nchild};
+            for (int c = 0; c < 4; c++)
+                if (cudaMemcpy2DAsync(p_nodes + c, 16, cols[c], 4, 4, (size_t)nn, cudaMemcpyDefault, st))
+                    return GT_ECUDA;
+        }
+        if (p_jpos && cudaMemcpyAsync(p_jpos, s->nd.jpos, (size_t)nn * 16, cudaMemcpyDefault, st)) return GT_ECUDA;
+        if (p_bj && cudaMemcpy2DAsync(p_bj, 4, s->nd.walk, 16, 4, (size_t)nn, cudaMemcpyDefault, st)) return GT_ECUDA;
+    }
+    if (cudaStreamSynchronize(st)) return GT_ECUDA;
+    return GT_OK;
+}
+
+int gt_get_active(gt_system *s, uint32_t *p_active, int64_t *n_inout, gt_stream stream) {
+    if (!s || !n_inout) return GT_EINVAL;
+    cudaStream_t st = S(stream);
+    unsigned na = 0;
+    if (cudaMemcpyAsync(&na, &s->ctl->n_active, 4, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
+        return GT_ECUDA;
+    const int64_t cap = *n_inout;
+    *n_inout = na;
+    if (!p_active) return GT_OK;
+    if ((int64_t)na > cap) return GT_EOVERFLOW;
+    if (na && cudaMemcpyAsync(p_active, s->active, (size_t)na * 4, cudaMemcpyDefault, st)) return GT_ECUDA;
+    return cudaStreamSynchronize(st) ? GT_ECUDA : GT_OK;
+}
+
+int gt_sync_status(gt_system *s, gt_stream stream) {
+    if (!s) return GT_EINVAL;
+    cudaStream_t st = S(stream);
+    int err[2] = {0, 0};
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GT_ECUDA;
+    if (cudaMemcpy(err, &s->ctl->err, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess) return GT_ECUDA;
+    if (err[0]) {
+        const int zero[2] = {0, 0};
+        if (cudaMemcpy(&s->ctl->err, zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess) return GT_ECUDA;
+    }
+    return err[0];
+}
+
+int gt_get_stats(gt_system *s, gt_stats *o, gt_stream stream) {
+    if (!s || !o) return GT_EINVAL;
+    cudaStream_t st = S(stream);
+    DevCtl c;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GT_ECUDA;
+    if (cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return GT_ECUDA;
+    memset(o, 0, sizeof(*o));
+    o->n = s->n;
+    o->T = s->started ? (int64_t)c.tnext : 0;
+    o->n_active = c.n_active;
+    o->n_groups = ((int64_t)c.n_active + s->prm.group_max - 1) / s->prm.group_max;
+    o->n_nodes = s->have_tree ? (int64_t)c.level_start[GT_TREE_LEVELS] : 0;
+    int depth = 0;
+    for (int l = 0; l < GT_TREE_LEVELS; l++)
+        if (c.level_start[l + 1] > c.level_start[l]) depth = l + 1;
+    o->depth = s->have_tree ? depth : 0;
+    o->interactions = (int64_t)c.interactions;
+    o->mac_tests = (int64_t)c.mac_tests;
+    o->block_steps = s->steps;
+    o->rebuilds = s->rebuilds;
+    o->dt_max = s->started ? c.dt_max : s->prm.dt_max;
+    o->err = c.err;
+    o->err_where = c.err_where;
+    return GT_OK;
+}
+
+}  // extern "C"

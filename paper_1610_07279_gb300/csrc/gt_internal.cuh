@@ -1,0 +1,225 @@
+// Internal declarations shared by the CUDA translation units of libgothic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gothic.h"
+
+#define GT_KEY_LEVELS 21              // 21 bits per axis -> 63-bit Morton keys
+#define GT_TREE_LEVELS 22             // tree levels 0..21
+#define GT_LEAF_FLAG 0x80000000u      // set in a node's second link word for a leaf
+#define GT_SPIN_LIMIT (1u << 22)      // bound on every device spin-wait (iterations)
+
+// Kernel ids recorded with a latched error (diagnostic only).
+enum { GTK_NONE = 0, GTK_BUILD, GTK_PSEUDO, GTK_ACTIVE, GTK_WALK, GTK_SORT, GTK_CORRECT };
+
+// Small control block in device memory: counters, per-step scalars and the
+// error word.  One per system, inside the workspace.
+struct DevCtl {
+    int err;                          // first latched GT_E* code
+    int err_where;                    // GTK_* of the kernel that latched it
+    unsigned int epoch;               // bumped once per tree build / compaction
+    unsigned int n_active;            // i-particles of the current force evaluation
+    unsigned int group_next;          // dynamic group counter of the walk
+    unsigned int tile_ticket[GT_TREE_LEVELS + 2];  // dynamic tile ids (build levels, compaction)
+    unsigned int level_start[GT_TREE_LEVELS + 2];  // first cell of each level; [22] = node count
+    unsigned int sort_done;           // last-block counter of the digit scan
+    unsigned int pad0;
+    unsigned long long interactions;  // cumulative
+    unsigned long long mac_tests;     // cumulative
+    unsigned long long tnext;         // block time of the current step
+    unsigned long long tnext_acc;     // running minimum for the next step
+    unsigned long long max_dt_bits;   // bit pattern of the largest dt_i (start only)
+    double dt_max;                    // longest block step (a power of two)
+    int M;                            // log2(dt_max)
+    int levels_m1;                    // L - 1 (finest level)
+    float bbox_min[3];
+    float pad1;
+    double side;                      // side of the bounding cube (FP64)
+    double scale;                     // 2^21 / side
+};
+
+// Particle state, structure of arrays, in internal (key) order.
+struct State {
+    double *rx, *ry, *rz;  // position at t0 (FP64)
+    double *vx, *vy, *vz;  // half-step velocity v^{1/2} (FP64); the velocity before gt_start
+    long long *t0;         // tick of the last correction
+    uint8_t *level;        // block-step level
+    float *aold;           // |a| of the last force evaluation (FP32)
+    float4 *acc;           // last acceleration and potential
+    uint32_t *id;          // caller's index
+    float *mass;
+};
+
+// Node arrays of the tree.
+// FP64 sums of a cell: mass and the three first moments.
+struct __align__(32) DSum4 {
+    double m, x, y, z;
+};
+
+struct Nodes {
+    uint32_t *first, *count;   // particle range
+    int32_t *child;            // first child, -1 for a leaf
+    uint32_t *nchild;
+    int32_t *parent;
+    uint32_t *arrive;          // bottom-up arrival counters (zero between passes)
+    float4 *jpos;              // pseudo j-particle (x, y, z, m) FP32
+    float4 *walk;              // (b_J, link0, link1, 0): link0 = first child or first particle,
+                               // link1 = nchild, or count | GT_LEAF_FLAG for a leaf
+    DSum4 *sum;                // FP64 (m, m x, m y, m z)
+};
+
+__device__ __forceinline__ void gt_set_error(DevCtl *ctl, int code, int where) {
+    if (atomicCAS(&ctl->err, 0, code) == 0) ctl->err_where = where;
+}
+
+__device__ __forceinline__ unsigned int lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned int lanemask_lt() {
+    unsigned int m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Inclusive warp scan of 32-bit counts.
+__device__ __forceinline__ unsigned int warp_incl_scan(unsigned int v) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane_id() >= (unsigned)o) v += t;
+    }
+    return v;
+}
+
+// Exclusive block scan for blockDim.x == NT (multiple of 32, <= 1024).
+// Returns the exclusive prefix of v; *total receives the block sum.
+template <int NT>
+__device__ __forceinline__ unsigned int block_excl_scan(unsigned int v, unsigned int *total,
+                                                        unsigned int *smem /* NT/32 + 1 */) {
+    const unsigned int lane = lane_id(), warp = threadIdx.x >> 5;
+    const unsigned int inc = warp_incl_scan(v);
+    if (lane == 31) smem[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned int w = lane < NT / 32 ? smem[lane] : 0u;
+        unsigned int wi = warp_incl_scan(w);
+        if (lane < NT / 32) smem[lane] = wi - w;
+        if (lane == NT / 32 - 1) smem[NT / 32] = wi;
+    }
+    __syncthreads();
+    const unsigned int r = smem[warp] + inc - v;
+    *total = smem[NT / 32];
+    __syncthreads();
+    return r;
+}
+
+// Decoupled look-back (single thread): publish this tile's aggregate, gather
+// the exclusive prefix from its predecessors, publish the inclusive prefix.
+// Status words pack (tag << 32 | value); tag = 4*epoch + {1: aggregate, 2: prefix}.
+// Tiles are taken in increasing order from a ticket, so every predecessor is
+// held by a running block and the wait ends; it is still bounded, and a wait
+// that runs out latches GT_ETIMEOUT and returns the partial prefix.
+__device__ __forceinline__ unsigned int lookback_prefix(unsigned long long *status, unsigned int tile,
+                                                        unsigned int aggregate, unsigned int epoch,
+                                                        DevCtl *ctl, int where) {
+    const unsigned long long tagA = (unsigned long long)(4u * epoch + 1u) << 32;
+    const unsigned long long tagP = (unsigned long long)(4u * epoch + 2u) << 32;
+    if (tile == 0) {
+        atomicExch(&status[0], tagP | aggregate);
+        return 0u;
+    }
+    atomicExch(&status[tile], tagA | aggregate);
+    unsigned int excl = 0;
+    int t = (int)tile - 1;
+    unsigned int spins = 0;
+    while (t >= 0) {
+        const unsigned long long s = *((volatile unsigned long long *)&status[t]);
+        const unsigned long long tag = s & 0xffffffff00000000ull;
+        if (tag == tagP) {
+            excl += (unsigned int)s;
+            break;
+        }
+        if (tag == tagA) {
+            excl += (unsigned int)s;
+            --t;
+            continue;
+        }
+        if (++spins > GT_SPIN_LIMIT) {
+            gt_set_error(ctl, GT_ETIMEOUT, where);
+            break;
+        }
+        __nanosleep(32);
+    }
+    atomicExch(&status[tile], tagP | (unsigned long long)(excl + aggregate));
+    return excl;
+}
+
+// ---- host-side launch helpers (defined in the .cu files) --------------------
+struct SortBufs {
+    uint64_t *key[2];
+    uint32_t *val[2];
+    uint32_t *tile_hist;     // RADIX x ntiles
+    uint32_t *digit_base;    // RADIX
+    uint32_t *digit_total;   // RADIX
+};
+
+// keys.cu
+void gt_launch_bbox(const float4 *posm, int64_t n, float *partial, int nblk, DevCtl *ctl,
+                    cudaStream_t st);
+void gt_launch_keys(const float4 *posm, int64_t n, const DevCtl *ctl, uint64_t *key, uint32_t *idx,
+                    cudaStream_t st);
+// sort.cu: sorts (key, val) in buffers 0; result in buffers 0 (even passes).
+int gt_sort_tiles(int64_t n);
+size_t gt_sort_scratch_bytes(int64_t n);
+void gt_launch_sort(SortBufs &b, int64_t n, DevCtl *ctl, cudaStream_t st);
+void gt_sort_init();
+// tree.cu
+void gt_launch_build(const uint64_t *skey, int64_t n, int leaf_max, Nodes nd, int64_t cap,
+                     unsigned long long *status, DevCtl *ctl, int nsm, cudaStream_t st);
+void gt_launch_pseudo(Nodes nd, int64_t cap, const float4 *posm, DevCtl *ctl, int nsm,
+                      cudaStream_t st);
+// integrate.cu
+void gt_launch_prepare(DevCtl *ctl, int begin_step, cudaStream_t st);
+void gt_launch_set_nactive(DevCtl *ctl, unsigned int n_active, cudaStream_t st);
+void gt_launch_predict(const State &s, int64_t n, const DevCtl *ctl, float4 *posm, cudaStream_t st);
+void gt_launch_load(const State &s, float4 *posm, int64_t n, cudaStream_t st);
+void gt_launch_permute(const State &src, const State &dst, const float4 *posm_in, float4 *posm_out,
+                       const uint32_t *perm, int64_t n, cudaStream_t st);
+void gt_launch_deinterleave3(const double *in, int64_t n, double *x, double *y, double *z,
+                             cudaStream_t st);
+void gt_launch_interleave3(const double *x, const double *y, const double *z, int64_t n, double *out,
+                           cudaStream_t st);
+void gt_launch_gather_f(const float *in, const uint32_t *id, int64_t n, float *out, cudaStream_t st);
+void gt_launch_active(const State &s, int64_t n, int L, int all, DevCtl *ctl, uint32_t *active,
+                      unsigned long long *status, int nsm, cudaStream_t st);
+void gt_launch_correct(const State &s, const uint32_t *active, const float4 *acc, DevCtl *ctl,
+                       int64_t n, int L, double eta, double eps, int nsm, cudaStream_t st);
+void gt_launch_amag(const float4 *acc, int64_t n, float *aold, cudaStream_t st);
+void gt_launch_set_clock(DevCtl *ctl, int M, int L, long long T, cudaStream_t st);
+void gt_launch_set_tnext(DevCtl *ctl, long long T, cudaStream_t st);
+void gt_launch_tnext_all(const State &s, int64_t n, int L, DevCtl *ctl, int nsm, cudaStream_t st);
+void gt_launch_gather_resume(const uint8_t *lv, const long long *t0, const float *ao, const float4 *acc,
+                             const State &s, int64_t n, cudaStream_t st);
+void gt_launch_init_levels(const State &s, const float4 *acc, int64_t n, int L, double eta,
+                           double eps, int M_given, int have_M, DevCtl *ctl, int nsm,
+                           cudaStream_t st);
+// walk.cu
+struct WalkArgs {
+    const float4 *jpos;
+    const float4 *walk;
+    const float4 *posm;
+    const uint32_t *active;  // may be null: identity
+    const float *aold;
+    float4 *acc;
+    uint32_t *queue;
+    DevCtl *ctl;
+    uint32_t n;              // particles (bound of the indices in active)
+    int gmax;
+    int qcap;                // power of two
+    int mac;
+    float theta, delta_acc, eps2, G, inv_eps;
+};
+int gt_walk_blocks(int ij_share, int nsm);
+int gt_walk_warps_per_block();
+void gt_launch_walk(const WalkArgs &a, int ij_share, int nblocks, cudaStream_t st);

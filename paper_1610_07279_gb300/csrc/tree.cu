@@ -1,0 +1,233 @@
+// Steps A4-A5: breadth-first octree over the sorted keys and the pseudo
+// j-particles (Sec. 2.1, Fig. 1).
+//
+// A4, one kernel per level (Sec. 2.1: cells are examined in parallel and their
+// children numbered serially with prefix sums).  A cell at level l with more than
+// leaf_max particles (and l < 21) splits into the non-empty ranges of the digit
+// (key >> 3(20 - l)) & 7 -- the "seven partitions" of its key range, found by a
+// lock-step 7-way binary search.  Children get consecutive numbers after the level,
+// in the order of their parents and digits, via a block scan plus a decoupled
+// look-back over tiles taken in ticket order (bounded wait).  Numbering is thus
+// level by level and, inside a level, by first particle.
+//
+// A5, one kernel: each leaf sums its particles in FP64 (mass, m x, m y, m z) and
+// climbs; the last child to arrive at a cell (atomic counter, no waiting) sums the
+// children's FP64 sums in child order and continues upward.  r_J and m_J are
+// rounded to FP32; b_J is the largest |r - r_J| of a leaf's particles, or the
+// largest |r_c - r_J| + b_c over a cell's children, in FP64 rounded up to FP32.
+// Every FP64 operation is written with an explicit rounding intrinsic so that no
+// multiply-add is contracted: the result is the same bit for bit on every run.
+#include "gt_internal.cuh"
+
+namespace {
+
+constexpr int BT = 256;         // threads per build block
+constexpr int NPT = 2;          // cells per thread
+constexpr int BTILE = BT * NPT; // cells per tile
+
+__global__ void k_build_init(long long n, Nodes nd, DevCtl *ctl) {
+    // root = level 0, all particles; level_start[0..1]
+    ctl->level_start[0] = 0;
+    ctl->level_start[1] = n > 0 ? 1u : 0u;
+    if (n > 0) {
+        nd.first[0] = 0;
+        nd.count[0] = (uint32_t)n;
+        nd.parent[0] = -1;
+        nd.arrive[0] = 0;
+    }
+}
+
+__global__ __launch_bounds__(BT) void k_build_level(int lvl, const unsigned long long *__restrict__ skey,
+                                                    int leaf_max, Nodes nd, long long cap,
+                                                    unsigned long long *status, DevCtl *ctl) {
+    __shared__ uint32_t tmp[BT / 32 + 1];
+    __shared__ uint32_t tile_sh, excl_sh;
+    const uint32_t lo = ctl->level_start[lvl], hi = ctl->level_start[lvl + 1];
+    const uint32_t cnt = hi - lo;
+    if (cnt == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctl->level_start[lvl + 2] = hi;
+        return;
+    }
+    const uint32_t ntiles = (cnt + BTILE - 1) / BTILE;
+    const uint32_t tag = ctl->epoch * 32u + (uint32_t)lvl;
+    const bool can_split = lvl < GT_KEY_LEVELS;
+    const int shift = 3 * (GT_KEY_LEVELS - 1 - lvl);
+    for (;;) {
+        if (threadIdx.x == 0) tile_sh = atomicAdd(&ctl->tile_ticket[lvl], 1u);
+        __syncthreads();
+        const uint32_t tile = tile_sh;
+        __syncthreads();
+        if (tile >= ntiles) break;
+        uint32_t bnd[NPT][9];
+        uint32_t nc[NPT];
+        uint32_t tsum = 0;
+#pragma unroll
+        for (int q = 0; q < NPT; q++) {
+            const uint32_t c = lo + tile * BTILE + threadIdx.x * NPT + q;
+            nc[q] = 0;
+            if (c < hi) {
+                const uint32_t f = nd.first[c], k = nd.count[c];
+                if (can_split && k > (uint32_t)leaf_max) {
+                    // smallest p in [f, f+k) with digit(p) >= d, for d = 1..7, in lock step
+                    uint32_t l7[7], h7[7];
+#pragma unroll
+                    for (int d = 0; d < 7; d++) { l7[d] = f; h7[d] = f + k; }
+                    const int iters = 32 - __clz(k);
+                    for (int it = 0; it < iters; it++) {
+#pragma unroll
+                        for (int d = 0; d < 7; d++) {
+                            if (l7[d] < h7[d]) {
+                                const uint32_t mid = (l7[d] + h7[d]) >> 1;
+                                const uint32_t dig = (uint32_t)((__ldg(&skey[mid]) >> shift) & 7ull);
+                                if (dig < (uint32_t)(d + 1)) l7[d] = mid + 1; else h7[d] = mid;
+                            }
+                        }
+                    }
+                    bnd[q][0] = f;
+#pragma unroll
+                    for (int d = 0; d < 7; d++) bnd[q][d + 1] = l7[d];
+                    bnd[q][8] = f + k;
+#pragma unroll
+                    for (int d = 0; d < 8; d++) nc[q] += bnd[q][d + 1] > bnd[q][d] ? 1u : 0u;
+                }
+            }
+            tsum += nc[q];
+        }
+        uint32_t total;
+        uint32_t excl = block_excl_scan<BT>(tsum, &total, tmp);
+        if (threadIdx.x == 0) excl_sh = lookback_prefix(status, tile, total, tag, ctl, GTK_BUILD);
+        __syncthreads();
+        uint32_t next = hi + excl_sh + excl;  // node id of this thread's first child
+#pragma unroll
+        for (int q = 0; q < NPT; q++) {
+            const uint32_t c = lo + tile * BTILE + threadIdx.x * NPT + q;
+            if (c >= hi) continue;
+            if (nc[q] == 0) {
+                nd.child[c] = -1;
+                nd.nchild[c] = 0;
+                continue;
+            }
+            if ((long long)next + nc[q] > cap) {
+                gt_set_error(ctl, GT_EOVERFLOW, GTK_BUILD);
+                nd.child[c] = -1;
+                nd.nchild[c] = 0;
+                next += nc[q];
+                continue;
+            }
+            nd.child[c] = (int32_t)next;
+            nd.nchild[c] = nc[q];
+#pragma unroll
+            for (int d = 0; d < 8; d++) {
+                if (bnd[q][d + 1] > bnd[q][d]) {
+                    nd.first[next] = bnd[q][d];
+                    nd.count[next] = bnd[q][d + 1] - bnd[q][d];
+                    nd.parent[next] = (int32_t)c;
+                    nd.child[next] = -1;
+                    nd.nchild[next] = 0;
+                    nd.arrive[next] = 0;
+                    next++;
+                }
+            }
+        }
+        if (tile == ntiles - 1 && threadIdx.x == BT - 1) {
+            unsigned long long end = (unsigned long long)hi + excl_sh + total;
+            if (end > (unsigned long long)cap) {
+                gt_set_error(ctl, GT_EOVERFLOW, GTK_BUILD);
+                end = (unsigned long long)cap;
+            }
+            ctl->level_start[lvl + 2] = (uint32_t)end;
+        }
+    }
+}
+
+__device__ __forceinline__ double sq3(double dx, double dy, double dz) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+__global__ __launch_bounds__(256) void k_pseudo(Nodes nd, long long cap, const float4 *__restrict__ posm,
+                                                DevCtl *ctl) {
+    long long nn = ctl->level_start[GT_TREE_LEVELS];
+    if (nn > cap) nn = cap;
+    for (long long c0 = blockIdx.x * 256ll + threadIdx.x; c0 < nn; c0 += (long long)gridDim.x * 256) {
+        if (nd.child[c0] >= 0) continue;  // cells are finished by their last arriving child
+        const uint32_t f = nd.first[c0], k = nd.count[c0];
+        double m = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+        for (uint32_t i = f; i < f + k; i++) {
+            const float4 p = posm[i];
+            const double mi = (double)p.w;
+            m = __dadd_rn(m, mi);
+            sx = __dadd_rn(sx, __dmul_rn(mi, (double)p.x));
+            sy = __dadd_rn(sy, __dmul_rn(mi, (double)p.y));
+            sz = __dadd_rn(sz, __dmul_rn(mi, (double)p.z));
+        }
+        float jx = __double2float_rn(__ddiv_rn(sx, m));
+        float jy = __double2float_rn(__ddiv_rn(sy, m));
+        float jz = __double2float_rn(__ddiv_rn(sz, m));
+        double d2max = 0.0;
+        for (uint32_t i = f; i < f + k; i++) {
+            const float4 p = posm[i];
+            const double d2 = sq3(__dsub_rn((double)p.x, (double)jx), __dsub_rn((double)p.y, (double)jy),
+                                  __dsub_rn((double)p.z, (double)jz));
+            if (d2 > d2max) d2max = d2;
+        }
+        nd.sum[c0] = DSum4{m, sx, sy, sz};
+        nd.jpos[c0] = make_float4(jx, jy, jz, __double2float_rn(m));
+        nd.walk[c0] = make_float4(__double2float_ru(__dsqrt_rn(d2max)), __uint_as_float(f),
+                                  __uint_as_float(k | GT_LEAF_FLAG), 0.0f);
+        // climb while this thread is the last child to arrive
+        long long c = c0;
+        for (;;) {
+            const int32_t p = nd.parent[c];
+            if (p < 0) break;
+            __threadfence();
+            const uint32_t nch = nd.nchild[p];
+            const uint32_t old = atomicAdd(&nd.arrive[p], 1u);
+            if (old != nch - 1) break;
+            __threadfence();
+            const int32_t ch0 = nd.child[p];
+            m = 0.0; sx = 0.0; sy = 0.0; sz = 0.0;
+            for (uint32_t q = 0; q < nch; q++) {
+                const double2 *sp = (const double2 *)&nd.sum[ch0 + q];
+                const double2 s01 = __ldcg(sp), s23 = __ldcg(sp + 1);
+                m = __dadd_rn(m, s01.x);
+                sx = __dadd_rn(sx, s01.y);
+                sy = __dadd_rn(sy, s23.x);
+                sz = __dadd_rn(sz, s23.y);
+            }
+            jx = __double2float_rn(__ddiv_rn(sx, m));
+            jy = __double2float_rn(__ddiv_rn(sy, m));
+            jz = __double2float_rn(__ddiv_rn(sz, m));
+            double b = 0.0;
+            for (uint32_t q = 0; q < nch; q++) {
+                const float4 cj = __ldcg(&nd.jpos[ch0 + q]);
+                const float4 cw = __ldcg(&nd.walk[ch0 + q]);
+                const double e = __dadd_rn(__dsqrt_rn(sq3(__dsub_rn((double)cj.x, (double)jx),
+                                                          __dsub_rn((double)cj.y, (double)jy),
+                                                          __dsub_rn((double)cj.z, (double)jz))),
+                                           (double)cw.x);
+                if (e > b) b = e;
+            }
+            nd.sum[p] = DSum4{m, sx, sy, sz};
+            nd.jpos[p] = make_float4(jx, jy, jz, __double2float_rn(m));
+            nd.walk[p] = make_float4(__double2float_ru(b), __uint_as_float((uint32_t)ch0),
+                                     __uint_as_float(nch), 0.0f);
+            nd.arrive[p] = 0;
+            c = p;
+        }
+    }
+}
+
+}  // namespace
+
+void gt_launch_build(const uint64_t *skey, int64_t n, int leaf_max, Nodes nd, int64_t cap,
+                     unsigned long long *status, DevCtl *ctl, int nsm, cudaStream_t st) {
+    k_build_init<<<1, 1, 0, st>>>(n, nd, ctl);
+    for (int l = 0; l < GT_TREE_LEVELS; l++)
+        k_build_level<<<nsm * 4, BT, 0, st>>>(l, (const unsigned long long *)skey, leaf_max, nd, cap,
+                                              status, ctl);
+}
+
+void gt_launch_pseudo(Nodes nd, int64_t cap, const float4 *posm, DevCtl *ctl, int nsm,
+                      cudaStream_t st) {
+    k_pseudo<<<nsm * 8, 256, 0, st>>>(nd, cap, posm, ctl);
+}

@@ -1,0 +1,250 @@
+// Step A7: the tree walk for groups of active i-particles (Sec. 2.3) with the
+// ij-parallelisation of Sec. 2.5.
+//
+// One warp walks one group at a time (a persistent grid; groups are taken from an
+// atomic counter, so slow groups do not hold a fixed share of the GPU).  Per group:
+//   * pseudo i-particle: the sphere about the centre of the members' bounding box
+//     (Appendix B, "GEO"), radius rounded up to FP32 from an FP64 distance; |a_old| of
+//     the group is the smallest of its members';
+//   * breadth-first traversal: a ring-buffer queue of cells in a per-warp slice of
+//     global memory; 32 queued cells are tested at once, one per lane, with the MAC at
+//     distance lambda r_JI (Eqs. 2, 5-7) in FP32 with explicit rounding (so the decision
+//     is reproducible); accepted cells join the shared-memory interaction list,
+//     rejected cells push their children (warp prefix sum), rejected leaves copy their
+//     particles into the list (coalesced);
+//   * the list is flushed through Eq. (1) whenever it fills: each i-particle is held by
+//     S lanes that take every S-th list entry (FP32, rsqrt), summed with xor-shuffles at
+//     the end.  The potential is accumulated too; the member's own term -G m_i/eps is
+//     removed at the end (Eq. 1 excludes j = i).
+// Bound: FP32 ALU (the force loop: 3 FADD, 3 FMUL, 7 FFMA and one MUFU rsqrt per
+// interaction); the node records (32 B per cell) stay resident in L2.
+#include <math.h>
+
+#include "gt_internal.cuh"
+
+namespace {
+
+constexpr int WT = 256;           // threads per block
+constexpr int NWARP = WT / 32;
+constexpr int LIST_CAP = 320;     // interaction-list entries per warp
+constexpr int FLUSH_AT = 256;     // flush once the list holds this many
+
+__device__ __forceinline__ bool mac_accept(int mac, float theta, float dacc_amin, float G, float cx,
+                                           float cy, float cz, float bI, float4 jp, float bJ) {
+    const float dx = __fsub_rn(jp.x, cx);
+    const float dy = __fsub_rn(jp.y, cy);
+    const float dz = __fsub_rn(jp.z, cz);
+    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    const float r = __fsqrt_rn(r2);
+    const float d = (bI < r) ? __fsub_rn(r, bI) : 0.0f;   // lambda r_JI, Eqs. (6)-(7)
+    if (mac == GT_MAC_OPENING_ANGLE) return bJ <= __fmul_rn(theta, d);  // Eq. (2)
+    const float d2 = __fmul_rn(d, d);                                   // Eq. (5), raised to the 4th power
+    return __fmul_rn(__fmul_rn(d2, d2), dacc_amin) >= __fmul_rn(__fmul_rn(G, jp.w), __fmul_rn(bJ, bJ));
+}
+
+__device__ __forceinline__ void interact(const float4 s, float xi, float yi, float zi, float eps2,
+                                         float &ax, float &ay, float &az, float &ph) {
+    const float dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+    const float rinv = rsqrtf(r2);
+    const float mr = s.w * rinv;
+    const float mr3 = mr * rinv * rinv;
+    ax = fmaf(mr3, dx, ax);
+    ay = fmaf(mr3, dy, ay);
+    az = fmaf(mr3, dz, az);
+    ph -= mr;
+}
+
+template <int S>
+__global__ __launch_bounds__(WT, 4) void k_walk(WalkArgs a) {
+    __shared__ float4 list_sm[NWARP][LIST_CAP];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4 *list = list_sm[warp];
+    uint32_t *q = a.queue + (size_t)(blockIdx.x * NWARP + warp) * (size_t)a.qcap;
+    const uint32_t qmask = (uint32_t)a.qcap - 1u;
+    const uint32_t na = a.ctl->n_active;
+    const uint32_t gmax = (uint32_t)a.gmax;
+    const uint32_t ngroups = (na + gmax - 1) / gmax;
+    const int slot = lane / S, sub = lane % S;
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lt = lanemask_lt();
+    unsigned long long n_inter = 0, n_tests = 0;
+
+    for (;;) {
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(&a.ctl->group_next, 1u);
+        g = __shfl_sync(FULL, g, 0);
+        if (g >= ngroups) break;
+        const uint32_t a0 = g * gmax;
+        const uint32_t cnt = min(gmax, na - a0);
+        const bool have = (uint32_t)slot < cnt;
+        const uint32_t kk = a0 + (have ? (uint32_t)slot : 0u);
+        uint32_t i = a.active ? a.active[kk] : kk;
+        if (i >= a.n) {  // an index outside the system: report it, walk particle 0 instead
+            gt_set_error(a.ctl, GT_EINVAL, GTK_WALK);
+            i = 0;
+        }
+        const float4 pi = a.posm[i];
+        float ao = have ? (a.aold ? a.aold[i] : 0.0f) : INFINITY;
+
+        // pseudo i-particle (lanes without a member repeat member 0: no effect on the box)
+        float mnx = pi.x, mny = pi.y, mnz = pi.z, mxx = pi.x, mxy = pi.y, mxz = pi.z;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mnx = fminf(mnx, __shfl_xor_sync(FULL, mnx, o));
+            mny = fminf(mny, __shfl_xor_sync(FULL, mny, o));
+            mnz = fminf(mnz, __shfl_xor_sync(FULL, mnz, o));
+            mxx = fmaxf(mxx, __shfl_xor_sync(FULL, mxx, o));
+            mxy = fmaxf(mxy, __shfl_xor_sync(FULL, mxy, o));
+            mxz = fmaxf(mxz, __shfl_xor_sync(FULL, mxz, o));
+            ao = fminf(ao, __shfl_xor_sync(FULL, ao, o));
+        }
+        const float cx = __fmul_rn(0.5f, __fadd_rn(mnx, mxx));
+        const float cy = __fmul_rn(0.5f, __fadd_rn(mny, mxy));
+        const float cz = __fmul_rn(0.5f, __fadd_rn(mnz, mxz));
+        const double ddx = __dsub_rn((double)pi.x, (double)cx);
+        const double ddy = __dsub_rn((double)pi.y, (double)cy);
+        const double ddz = __dsub_rn((double)pi.z, (double)cz);
+        double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d2 = fmax(d2, __shfl_xor_sync(FULL, d2, o));
+        const float bI = __double2float_ru(__dsqrt_rn(d2));
+        const float dacc_amin = __fmul_rn(a.delta_acc, ao);
+
+        float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f;
+        int list_n = 0;
+        auto flush = [&]() {
+            __syncwarp();
+            int j = sub;
+            for (; j + 3 * S < list_n; j += 4 * S) {
+                const float4 s0 = list[j], s1 = list[j + S], s2 = list[j + 2 * S], s3 = list[j + 3 * S];
+                interact(s0, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
+                interact(s1, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
+                interact(s2, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
+                interact(s3, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
+            }
+            for (; j < list_n; j += S) interact(list[j], pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
+            n_inter += (unsigned long long)list_n * cnt;
+            list_n = 0;
+            __syncwarp();
+        };
+
+        uint32_t head = 0, tail = 1;
+        if (lane == 0) q[0] = 0u;  // the root
+        __syncwarp();
+        bool overflow = false;
+        while (head != tail) {
+            const uint32_t nb = min(tail - head, 32u);
+            const bool valid = (uint32_t)lane < nb;
+            float4 jp = make_float4(0.f, 0.f, 0.f, 0.f), wk = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (valid) {
+                const uint32_t node = q[(head + lane) & qmask];
+                jp = a.jpos[node];
+                wk = a.walk[node];
+            }
+            head += nb;
+            n_tests += nb;
+            const bool ok = valid && mac_accept(a.mac, a.theta, dacc_amin, a.G, cx, cy, cz, bI, jp, wk.x);
+            const uint32_t l0 = __float_as_uint(wk.y), l1 = __float_as_uint(wk.z);
+            const bool leaf = (l1 & GT_LEAF_FLAG) != 0u;
+            // accepted cells -> list
+            const unsigned am = __ballot_sync(FULL, ok);
+            if (am) {
+                const int nacc = __popc(am);
+                if (list_n + nacc > LIST_CAP) flush();
+                if (ok) list[list_n + __popc(am & lt)] = jp;
+                list_n += nacc;
+            }
+            // opened cells -> queue their children
+            const uint32_t nch = (valid && !ok && !leaf) ? l1 : 0u;
+            const uint32_t incl = warp_incl_scan(nch);
+            const uint32_t tot = __shfl_sync(FULL, incl, 31);
+            if (tot) {
+                if (tail - head + tot > (uint32_t)a.qcap) {
+                    overflow = true;
+                    break;
+                }
+                const uint32_t pos = tail + incl - nch;
+                for (uint32_t k = 0; k < nch; k++) q[(pos + k) & qmask] = l0 + k;
+                tail += tot;
+            }
+            // opened leaves -> their particles into the list
+            unsigned lm = __ballot_sync(FULL, valid && !ok && leaf);
+            while (lm) {
+                const int src = __ffs(lm) - 1;
+                lm &= lm - 1;
+                const uint32_t lf = __shfl_sync(FULL, l0, src);
+                const uint32_t lc = __shfl_sync(FULL, l1 & ~GT_LEAF_FLAG, src);
+                uint32_t done = 0;
+                while (done < lc) {
+                    if (list_n == LIST_CAP) flush();
+                    const uint32_t take = min(lc - done, (uint32_t)(LIST_CAP - list_n));
+                    for (uint32_t k = lane; k < take; k += 32) list[list_n + k] = a.posm[lf + done + k];
+                    list_n += (int)take;
+                    done += take;
+                }
+            }
+            if (list_n >= FLUSH_AT) flush();
+            __syncwarp();
+        }
+        if (overflow) {
+            if (lane == 0) gt_set_error(a.ctl, GT_EOVERFLOW, GTK_WALK);
+            list_n = 0;
+            if (sub == 0 && have) a.acc[kk] = make_float4(NAN, NAN, NAN, NAN);
+            __syncwarp();
+            continue;
+        }
+        flush();
+#pragma unroll
+        for (int o = 1; o < S; o <<= 1) {
+            ax += __shfl_xor_sync(FULL, ax, o);
+            ay += __shfl_xor_sync(FULL, ay, o);
+            az += __shfl_xor_sync(FULL, az, o);
+            ph += __shfl_xor_sync(FULL, ph, o);
+        }
+        if (sub == 0 && have) {
+            const float phi = fmaf(pi.w, a.inv_eps, ph);
+            a.acc[kk] = make_float4(a.G * ax, a.G * ay, a.G * az, a.G * phi);
+        }
+    }
+    if (lane == 0) {
+        if (n_inter) atomicAdd(&a.ctl->interactions, n_inter);
+        if (n_tests) atomicAdd(&a.ctl->mac_tests, n_tests);
+    }
+}
+
+template <int S>
+int blocks_for(int nsm) {
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk<S>, WT, 0);
+    if (per < 1) per = 1;
+    return per * nsm;
+}
+
+}  // namespace
+
+int gt_walk_blocks(int ij_share, int nsm) {
+    switch (ij_share) {
+        case 1: return blocks_for<1>(nsm);
+        case 2: return blocks_for<2>(nsm);
+        case 4: return blocks_for<4>(nsm);
+        case 8: return blocks_for<8>(nsm);
+        case 16: return blocks_for<16>(nsm);
+        case 32: return blocks_for<32>(nsm);
+        default: return -1;
+    }
+}
+
+int gt_walk_warps_per_block() { return NWARP; }
+
+void gt_launch_walk(const WalkArgs &a, int ij_share, int nblocks, cudaStream_t st) {
+    switch (ij_share) {
+        case 1: k_walk<1><<<nblocks, WT, 0, st>>>(a); break;
+        case 2: k_walk<2><<<nblocks, WT, 0, st>>>(a); break;
+        case 4: k_walk<4><<<nblocks, WT, 0, st>>>(a); break;
+        case 8: k_walk<8><<<nblocks, WT, 0, st>>>(a); break;
+        case 16: k_walk<16><<<nblocks, WT, 0, st>>>(a); break;
+        case 32: k_walk<32><<<nblocks, WT, 0, st>>>(a); break;
+        default: break;
+    }
+}

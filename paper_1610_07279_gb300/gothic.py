@@ -1,0 +1,274 @@
+"""Python binding of libgothic's C ABI (include/gothic.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+The functions keep the C names; ``System`` wraps one ``gt_system`` together with
+its device workspace (a torch byte tensor) and the current torch stream.
+
+The library must have been built (``paper_1610_07279_gb300.build.build()``);
+loading fails loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+GT_OK = 0
+GT_EINVAL = -1
+GT_ENOMEM = -2
+GT_EOVERFLOW = -3
+GT_ETIMEOUT = -4
+GT_ECUDA = -5
+GT_EAGAIN = -6
+GT_EPENDING = -7
+GT_ENOTIMPL = -8
+GT_ESTATE = -9
+GT_MAC_OPENING_ANGLE = 0
+GT_MAC_ACCELERATION = 1
+
+
+class gt_params(C.Structure):
+    _fields_ = [("mac", C.c_int32), ("theta", C.c_float), ("delta_acc", C.c_float),
+                ("eps", C.c_float), ("G", C.c_float), ("leaf_max", C.c_int32),
+                ("group_max", C.c_int32), ("ij_share", C.c_int32), ("levels", C.c_int32),
+                ("rebuild_every", C.c_int32), ("walk_queue", C.c_int32), ("reserved0", C.c_int32),
+                ("eta", C.c_double), ("dt_max", C.c_double)]
+
+
+class gt_stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("T", C.c_int64), ("n_active", C.c_int64),
+                ("n_groups", C.c_int64), ("n_nodes", C.c_int64), ("depth", C.c_int64),
+                ("interactions", C.c_int64), ("mac_tests", C.c_int64),
+                ("block_steps", C.c_int64), ("rebuilds", C.c_int64), ("dt_max", C.c_double),
+                ("err", C.c_int32), ("err_where", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class GothicError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {gt_strerror(status)} ({status})")
+        self.status = status
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def declared_symbols() -> list[str]:
+    """Entry points declared in include/gothic.h."""
+    with open(os.path.join(_build.INCLUDE, "gothic.h")) as f:
+        text = f.read()
+    return re.findall(r"^GT_API\s+[\w\s\*]*?\b(gt_\w+)\s*\(", text, flags=re.M)
+
+
+def load(path: str | None = None):
+    """Load libgothic.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _build.LIB
+    if not os.path.exists(p):
+        raise ImportError(f"libgothic is not built ({p}); run paper_1610_07279_gb300.build.build()")
+    L = C.CDLL(p)
+    P, I64, I32 = C.c_void_p, C.c_int64, C.c_int
+    L.gt_strerror.restype = C.c_char_p
+    L.gt_strerror.argtypes = [I32]
+    L.gt_default_params.argtypes = [C.POINTER(gt_params)]
+    L.gt_workspace_bytes.argtypes = [I64, C.POINTER(gt_params), C.POINTER(C.c_size_t)]
+    L.gt_system_create.argtypes = [C.POINTER(P), I64, C.POINTER(gt_params), P, C.c_size_t]
+    L.gt_system_destroy.argtypes = [P]
+    L.gt_set_params.argtypes = [P, C.POINTER(gt_params)]
+    L.gt_set_state.argtypes = [P, P, P, P, P]
+    L.gt_build_tree.argtypes = [P, P]
+    L.gt_accel_active.argtypes = [P, P, I64, P, P, P]
+    L.gt_start.argtypes = [P, P, P]
+    L.gt_block_step.argtypes = [P, P]
+    L.gt_set_integrator_state.argtypes = [P, P, P, P, P, C.c_double, I64, P]
+    L.gt_predict.argtypes = [P, I64, P, P]
+    L.gt_correct.argtypes = [P, P, I64, P, I64, P]
+    L.gt_get_state.argtypes = [P, P, P, P, P, P, P, P]
+    L.gt_get_tree.argtypes = [P, P, P, P, P, P, C.POINTER(I64), P]
+    L.gt_get_active.argtypes = [P, P, C.POINTER(I64), P]
+    L.gt_sync_status.argtypes = [P, P]
+    L.gt_get_stats.argtypes = [P, C.POINTER(gt_stats), P]
+    L.gt_measure_fp32_peak.argtypes = [C.POINTER(C.c_double), P]
+    for name in declared_symbols():
+        getattr(L, name).restype = C.c_char_p if name == "gt_strerror" else C.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, where: str):
+    if rc != GT_OK:
+        raise GothicError(rc, where)
+
+
+# --------------------------------------------------------------- same-named calls
+def gt_strerror(status: int) -> str:
+    return load().gt_strerror(int(status)).decode()
+
+
+def gt_default_params() -> gt_params:
+    p = gt_params()
+    _check(load().gt_default_params(C.byref(p)), "gt_default_params")
+    return p
+
+
+def gt_workspace_bytes(n: int, prm: gt_params) -> int:
+    b = C.c_size_t(0)
+    _check(load().gt_workspace_bytes(int(n), C.byref(prm), C.byref(b)), "gt_workspace_bytes")
+    return int(b.value)
+
+
+def gt_measure_fp32_peak(stream: int | None = None) -> float:
+    f = C.c_double(0.0)
+    _check(load().gt_measure_fp32_peak(C.byref(f), stream), "gt_measure_fp32_peak")
+    return float(f.value)
+
+
+def _ptr(a):
+    """Device or host address of a torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(type(a))
+
+
+def _current_stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+class System:
+    """One N-body system: a gt_system living in a torch-allocated workspace."""
+
+    def __init__(self, n: int, params: gt_params | None = None, stream: int | None = None):
+        import torch
+        self.n = int(n)
+        self.params = params if params is not None else gt_default_params()
+        nbytes = gt_workspace_bytes(self.n, self.params)
+        self.ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
+        self.stream = stream
+        self._h = C.c_void_p()
+        _check(load().gt_system_create(C.byref(self._h), self.n, C.byref(self.params),
+                                       self.ws.data_ptr(), self.ws.numel()), "gt_system_create")
+
+    # stream defaults to torch's current stream at call time
+    def _s(self):
+        return self.stream if self.stream is not None else _current_stream()
+
+    def close(self):
+        if self._h:
+            load().gt_system_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params: gt_params):
+        _check(load().gt_set_params(self._h, C.byref(params)), "gt_set_params")
+        self.params = params
+
+    def set_state(self, pos, vel, mass):
+        if isinstance(pos, np.ndarray):
+            pos = np.ascontiguousarray(pos, np.float64)
+            vel = np.ascontiguousarray(vel, np.float64)
+            mass = np.ascontiguousarray(mass, np.float32)
+        self._keep = (pos, vel, mass)
+        _check(load().gt_set_state(self._h, _ptr(pos), _ptr(vel), _ptr(mass), self._s()), "gt_set_state")
+
+    def build_tree(self):
+        _check(load().gt_build_tree(self._h, self._s()), "gt_build_tree")
+
+    def accel_active(self, active, aold, acc_out, n_active: int | None = None):
+        na = self.n if active is None else (int(n_active) if n_active is not None else int(active.numel()))
+        _check(load().gt_accel_active(self._h, _ptr(active), na, _ptr(aold), _ptr(acc_out), self._s()),
+               "gt_accel_active")
+
+    def start(self, aold_boot=None):
+        if isinstance(aold_boot, np.ndarray):
+            aold_boot = np.ascontiguousarray(aold_boot, np.float32)
+        _check(load().gt_start(self._h, _ptr(aold_boot), self._s()), "gt_start")
+
+    def block_step(self):
+        _check(load().gt_block_step(self._h, self._s()), "gt_block_step")
+
+    def set_integrator_state(self, level, t0, aold, acc, dt_max: float, T: int):
+        arrs = [np.ascontiguousarray(level, np.uint8), np.ascontiguousarray(t0, np.int64),
+                np.ascontiguousarray(aold, np.float32),
+                None if acc is None else np.ascontiguousarray(acc, np.float32)]
+        _check(load().gt_set_integrator_state(self._h, *[_ptr(a) for a in arrs], float(dt_max), int(T),
+                                              self._s()), "gt_set_integrator_state")
+
+    def predict(self, T: int, posm_out):
+        _check(load().gt_predict(self._h, int(T), _ptr(posm_out), self._s()), "gt_predict")
+
+    def correct(self, active, acc, T: int):
+        _check(load().gt_correct(self._h, _ptr(active), int(active.numel()), _ptr(acc), int(T), self._s()),
+               "gt_correct")
+
+    def get_state(self) -> dict:
+        n = self.n
+        out = {"pos": np.zeros((n, 3)), "vel": np.zeros((n, 3)), "acc": np.zeros((n, 4), np.float32),
+               "level": np.zeros(n, np.uint8), "t0": np.zeros(n, np.int64), "id": np.zeros(n, np.uint32)}
+        _check(load().gt_get_state(self._h, _ptr(out["pos"]), _ptr(out["vel"]), _ptr(out["acc"]),
+                                   _ptr(out["level"]), _ptr(out["t0"]), _ptr(out["id"]), self._s()),
+               "gt_get_state")
+        self.sync()
+        return out
+
+    def get_tree(self) -> dict:
+        n = self.n
+        cnt = C.c_int64(0)
+        _check(load().gt_get_tree(self._h, None, None, None, None, None, C.byref(cnt), self._s()), "gt_get_tree")
+        nn = int(cnt.value)
+        keys = np.zeros(n, np.uint64)
+        order = np.zeros(n, np.uint32)
+        nodes = np.zeros((max(nn, 1), 4), np.uint32)
+        jpos = np.zeros((max(nn, 1), 4), np.float32)
+        bj = np.zeros(max(nn, 1), np.float32)
+        cnt = C.c_int64(max(nn, 1))
+        _check(load().gt_get_tree(self._h, _ptr(keys), _ptr(order), _ptr(nodes), _ptr(jpos), _ptr(bj),
+                                  C.byref(cnt), self._s()), "gt_get_tree")
+        nn = int(cnt.value)
+        return {"keys": keys, "order": order, "first": nodes[:nn, 0].copy(), "count": nodes[:nn, 1].copy(),
+                "child": nodes[:nn, 2].view(np.int32).copy(), "nchild": nodes[:nn, 3].copy(),
+                "jpos": jpos[:nn].copy(), "bj": bj[:nn].copy(), "n_nodes": nn}
+
+    def get_active(self) -> np.ndarray:
+        cnt = C.c_int64(0)
+        _check(load().gt_get_active(self._h, None, C.byref(cnt), self._s()), "gt_get_active")
+        buf = np.zeros(max(int(cnt.value), 1), np.uint32)
+        cnt = C.c_int64(buf.size)
+        _check(load().gt_get_active(self._h, _ptr(buf), C.byref(cnt), self._s()), "gt_get_active")
+        return buf[:int(cnt.value)].copy()
+
+    def sync(self):
+        _check(load().gt_sync_status(self._h, self._s()), "device")
+
+    def status(self) -> int:
+        return int(load().gt_sync_status(self._h, self._s()))
+
+    def stats(self) -> dict:
+        st = gt_stats()
+        _check(load().gt_get_stats(self._h, C.byref(st), self._s()), "gt_get_stats")
+        return st.as_dict()

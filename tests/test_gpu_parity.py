@@ -1,0 +1,376 @@
+"""CUDA path vs the CPU oracle, through the C ABI.
+
+Bit-exact: Morton keys, sort order, tree topology, pseudo j-particles, active
+sets, predicted positions and corrected states.  Floating point: per-particle
+accelerations within 1e-5 relative (median) and 1e-4 (99th percentile) of the
+oracle's FP64 sums over the same interaction lists (the lists themselves are
+identical: the interaction counts must match exactly).
+"""
+import numpy as np
+import pytest
+
+from paper_1610_07279_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+MED_TOL, P99_TOL = 1e-5, 1e-4
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1610_07279_gb300 import build
+    build.build()
+    import oracle as O
+    O.build()
+    from paper_1610_07279_gb300 import gothic as g
+    g.load()
+    return torch, g, O
+
+
+def _model(kind, n, seed):
+    if kind == "plummer":
+        return ics.plummer(n, seed=seed)
+    if kind == "nfw":
+        return ics.nfw(n, seed=seed)
+    if kind == "m31":
+        return ics.andromeda_like(n, seed=seed)
+    if kind == "coincident":
+        pos = np.full((n, 3), 0.375)
+        return pos, np.zeros((n, 3)), np.full(n, 1.0 / n, np.float32), 1.0 / 64
+    if kind == "clustered":  # many exact duplicates and tight clumps
+        base, vel, m, eps = ics.plummer(n // 4 + 1, seed=seed)
+        pos = np.repeat(base, 4, axis=0)[:n]
+        return pos, np.zeros((n, 3)), np.full(n, 1.0 / n, np.float32), eps
+    raise ValueError(kind)
+
+
+def _p4(pos, mass):
+    p4 = np.zeros((len(mass), 4), np.float32)
+    p4[:, :3] = pos
+    p4[:, 3] = mass
+    return p4
+
+
+def _params(g, eps, **kw):
+    prm = g.gt_default_params()
+    prm.eps = eps
+    for k, v in kw.items():
+        setattr(prm, k, v)
+    return prm
+
+
+def _oparams(O, prm):
+    return O.Params(mac=prm.mac, theta=prm.theta, delta_acc=prm.delta_acc, eps=prm.eps, G=prm.G,
+                    leaf_max=prm.leaf_max, group_max=prm.group_max, levels=prm.levels, eta=prm.eta,
+                    dt_max=prm.dt_max)
+
+
+def _rel(a, r):
+    a = np.asarray(a, np.float64)
+    num = np.linalg.norm(a[:, :3] - r[:, :3], axis=1)
+    den = np.linalg.norm(r[:, :3], axis=1)
+    return num / den
+
+
+def _check_tree(t, ref):
+    assert np.array_equal(t["keys"], ref["skey"]), "keys"
+    assert np.array_equal(t["order"], ref["order"]), "order"
+    tr = ref["tree"]
+    assert t["n_nodes"] == tr["n_nodes"], (t["n_nodes"], tr["n_nodes"])
+    assert np.array_equal(t["first"], tr["first"]), "first"
+    assert np.array_equal(t["count"], tr["count"]), "count"
+    assert np.array_equal(t["child"], tr["child"]), "child"
+    assert np.array_equal(t["nchild"], tr["nchild"].astype(np.uint32)), "nchild"
+    assert np.array_equal(t["jpos"].view(np.uint32), ref["jpos"].view(np.uint32)), "jpos"
+    assert np.array_equal(t["bj"].view(np.uint32), ref["bj"].view(np.uint32)), "bj"
+
+
+def _oracle_tree(O, pos, mass, leaf):
+    p4 = _p4(pos, mass)
+    key, box = O.keys(p4)
+    order, skey = O.sort(key)
+    tree = O.build_tree(skey, leaf)
+    jpos, bj = O.pseudo_j(tree, p4[order])
+    return {"p4": p4, "order": order, "skey": skey, "tree": tree, "jpos": jpos, "bj": bj}
+
+
+# ------------------------------------------------------------------ A1-A5 bit-exact
+@pytest.mark.parametrize("kind,n,leaf", [
+    ("plummer", 1 << 13, 16),     # Plummer sphere, 2^13 particles
+    ("nfw", 100003, 16),          # ragged: not a multiple of any tile size
+    ("plummer", 4097, 16),
+    ("plummer", 1, 16),
+    ("plummer", 2, 1),
+    ("plummer", 17, 16),
+    ("plummer", 5000, 1),
+    ("m31", 1 << 16, 8),
+    ("coincident", 1000, 16),     # one chain down to level 21
+    ("clustered", 20000, 3),
+])
+def test_tree_bitexact(env, kind, n, leaf):
+    torch, g, O = env
+    pos, vel, mass, eps = _model(kind, n, seed=n)
+    s = g.System(n, _params(g, eps, leaf_max=leaf))
+    s.set_state(pos, vel, mass)
+    s.build_tree()
+    t = s.get_tree()
+    s.sync()
+    _check_tree(t, _oracle_tree(O, pos, mass, leaf))
+    st = s.get_state()
+    assert np.array_equal(st["id"], t["order"])
+    assert np.array_equal(st["pos"], pos[t["order"]])   # the permutation moved FP64 state exactly
+    s.close()
+
+
+def test_empty_system(env):
+    torch, g, O = env
+    s = g.System(0, _params(g, 0.1))
+    s.set_state(np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0, np.float32))
+    s.build_tree()
+    assert s.get_tree()["n_nodes"] == 0
+    acc = torch.zeros((1, 4), device="cuda")
+    s.accel_active(None, None, acc)
+    s.sync()
+    assert s.stats()["interactions"] == 0
+    s.close()
+
+
+# ------------------------------------------------------------------ A6-A7 walk
+def _walk_case(env, kind, n, seed, mac, S, gmax, active_frac=None, **kw):
+    torch, g, O = env
+    pos, vel, mass, eps = _model(kind, n, seed)
+    prm = _params(g, eps, mac=mac, ij_share=S, group_max=gmax, **kw)
+    oprm = _oparams(O, prm)
+    p4 = _p4(pos, mass)
+    aold = O.bootstrap_aold(p4, oprm) if mac == 1 else None
+    active = None
+    if active_frac is not None:
+        rng = np.random.default_rng(seed)
+        active = np.sort(rng.choice(n, int(active_frac * n), replace=False)).astype(np.uint32)
+    ref = O.tree_force(p4, oprm, aold=aold, active=active)
+    s = g.System(n, prm)
+    s.set_state(pos, vel, mass)
+    s.build_tree()
+    na = n if active is None else active.size
+    acc = torch.zeros((max(na, 1), 4), dtype=torch.float32, device="cuda")
+    d_aold = None if aold is None else torch.from_numpy(aold[ref["order"]]).cuda()
+    d_act = None if active is None else torch.from_numpy(active.astype(np.int32)).cuda()
+    before = s.stats()["interactions"]
+    s.accel_active(d_act, d_aold, acc, n_active=na)
+    s.sync()
+    st = s.stats()
+    a = acc.cpu().numpy()[:na]
+    rel = _rel(a, ref["acc"])
+    prel = np.abs(a[:, 3] - ref["acc"][:, 3]) / np.abs(ref["acc"][:, 3])
+    assert st["interactions"] - before == int(ref["inter"].sum())
+    assert np.median(rel) <= MED_TOL and np.percentile(rel, 99) <= P99_TOL, (np.median(rel), np.percentile(rel, 99))
+    assert np.median(prel) <= MED_TOL and np.percentile(prel, 99) <= P99_TOL
+    s.close()
+    return rel
+
+
+@pytest.mark.parametrize("mac", [0, 1])
+@pytest.mark.parametrize("S,gmax", [(1, 32), (1, 20), (2, 16), (4, 8), (32, 1)])
+def test_walk_plummer_config(env, mac, S, gmax):
+    _walk_case(env, "plummer", 1 << 13, 1, mac, S, gmax)
+
+
+@pytest.mark.parametrize("kind,n", [("nfw", 40000), ("m31", 1 << 15), ("clustered", 9000)])
+def test_walk_other_models(env, kind, n):
+    _walk_case(env, kind, n, 3, 1, 1, 32)
+
+
+def test_walk_active_subset(env):
+    _walk_case(env, "nfw", 30011, 4, 1, 1, 32, active_frac=0.17)
+
+
+def test_walk_small_leaf_and_list(env):
+    _walk_case(env, "plummer", 7000, 5, 1, 1, 32, leaf_max=1)
+    _walk_case(env, "coincident", 700, 5, 1, 1, 32)
+
+
+def test_walk_queue_overflow_is_reported(env):
+    torch, g, O = env
+    pos, vel, mass, eps = _model("plummer", 1 << 14, 6)
+    s = g.System(1 << 14, _params(g, eps, walk_queue=64, mac=0, theta=0.05))
+    s.set_state(pos, vel, mass)
+    s.build_tree()
+    acc = torch.zeros((1 << 14, 4), device="cuda")
+    s.accel_active(None, None, acc)
+    assert s.status() == g.GT_EOVERFLOW
+    assert s.status() == g.GT_OK  # the error word is cleared once read
+    s.close()
+
+
+# ------------------------------------------------------------------ A8-A9 integrator
+def _synthetic_integrator_state(n, L, M, seed):
+    rng = np.random.default_rng(seed)
+    pos, vel, mass, eps = ics.nfw(n, seed=seed)
+    level = rng.integers(0, L, n).astype(np.uint8)
+    T = 3 << (L - 1)  # a tick aligned with every level
+    span = np.left_shift(1, (L - 1 - level.astype(np.int64)))
+    t0 = T - span * rng.integers(0, 2, n)  # half the particles are due at T
+    aold = rng.uniform(0.01, 3.0, n).astype(np.float32)
+    return pos, vel, mass, eps, level, t0.astype(np.int64), aold, T
+
+
+def test_predict_correct_bitexact(env):
+    torch, g, O = env
+    n, L, M = 20011, 7, -1
+    pos, vel, mass, eps, level, t0, aold, T = _synthetic_integrator_state(n, L, M, 9)
+    dt_max = 2.0 ** M
+    prm = _params(g, eps, levels=L)
+    s = g.System(n, prm)
+    s.set_state(pos, vel, mass)
+    s.set_integrator_state(level, t0, aold, None, dt_max, T - 1)
+    # A8: prediction of every particle to T
+    d_p = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+    s.predict(T, d_p)
+    s.sync()
+    ref_p = O.predict(pos, vel, t0, mass, T, float(np.ldexp(dt_max, -(L - 1))))
+    assert np.array_equal(d_p.cpu().numpy().view(np.uint32), ref_p.view(np.uint32))
+    # A9: correction of the due particles with seeded accelerations spanning all levels
+    active = np.nonzero(t0 + np.left_shift(1, (L - 1 - level.astype(np.int64))) == T)[0].astype(np.uint32)
+    rng = np.random.default_rng(1)
+    acc = np.zeros((active.size, 4), np.float32)
+    acc[:, :3] = (rng.standard_normal((active.size, 3)) * 10.0 ** rng.uniform(-3, 3, (active.size, 1))).astype(np.float32)
+    s.correct(torch.from_numpy(active.astype(np.int32)).cuda(), torch.from_numpy(acc).cuda(), T)
+    st = s.get_state()
+    r0, vh, t0o, lvo, aoo = pos.copy(), vel.copy(), t0.copy(), level.copy(), aold.copy()
+    O.correct(active, acc, T, dt_max, M, L, prm.eta, O.f32(eps), r0, vh, t0o, lvo, aoo)
+    assert np.array_equal(st["id"], np.arange(n, dtype=np.uint32))
+    assert np.array_equal(st["level"], lvo)
+    assert np.array_equal(st["t0"], t0o)
+    assert np.array_equal(st["pos"].view(np.uint64), r0.view(np.uint64))
+    assert np.array_equal(st["vel"].view(np.uint64), vh.view(np.uint64))
+    assert len(np.unique(lvo[active])) >= L - 1   # the test spans the levels
+
+
+def test_start_matches_oracle(env):
+    torch, g, O = env
+    n = 1 << 14
+    pos, vel, mass, eps = ics.nfw(n, seed=12)
+    prm = _params(g, eps, levels=6)
+    oprm = _oparams(O, prm)
+    sim = O.BlockStepSim(pos, vel, mass, oprm)
+    boot = O.bootstrap_aold(_p4(pos, mass), oprm)
+    sim.start(aold_boot=boot)
+    s = g.System(n, prm)
+    s.set_state(pos, vel, mass)
+    s.start(boot)
+    st = s.get_state()
+    stats = s.stats()
+    assert stats["dt_max"] == sim.dt_max
+    assert np.array_equal(st["id"], sim.id)
+    agree = np.mean(st["level"] == sim.level)
+    assert agree >= 0.999, agree
+    same = st["level"] == sim.level
+    dv = np.abs(st["vel"][same] - sim.vh[same]).max(axis=1) / (np.abs(sim.vh[same]).max(axis=1) + 1e-30)
+    assert np.percentile(dv, 99) < 1e-5
+    s.close()
+
+
+def test_block_steps_match_oracle(env):
+    torch, g, O = env
+    n = 1 << 14
+    pos, vel, mass, eps = ics.nfw(n, seed=13)
+    prm = _params(g, eps, levels=5)
+    oprm = _oparams(O, prm)
+    sim = O.BlockStepSim(pos, vel, mass, oprm)
+    boot = O.bootstrap_aold(_p4(pos, mass), oprm)
+    sim.start(aold_boot=boot)
+    s = g.System(n, prm)
+    s.set_state(pos, vel, mass)
+    s.start(boot)
+    for k in range(10):
+        r = sim.step()
+        s.block_step()
+        s.sync()
+        st = s.stats()
+        assert st["T"] == r["T"], (k, st["T"], r["T"])
+        act = s.get_active()
+        if act.size == r["active"].size:
+            match = np.mean(act == r["active"])
+        else:
+            match = len(np.intersect1d(act, r["active"])) / max(act.size, r["active"].size)
+        assert match >= 0.999, (k, match)
+    gs = s.get_state()
+    assert np.mean(gs["id"] == sim.id) >= 0.999
+    same = gs["id"] == sim.id
+    dr = np.abs(gs["pos"][same] - sim.r0[same]).max(axis=1)
+    assert np.percentile(dr, 99) < 1e-5
+    assert s.status() == g.GT_OK
+    s.close()
+
+
+def test_checkpoint_resume_bitexact(env):
+    torch, g, O = env
+    n = 1 << 13
+    pos, vel, mass, eps = ics.plummer(n, seed=14)
+    prm = _params(g, eps, levels=5)
+    a = g.System(n, prm)
+    a.set_state(pos, vel, mass)
+    a.start()
+    for _ in range(6):
+        a.block_step()
+    ck = a.get_state()
+    T = a.stats()["T"]
+    dt_max = a.stats()["dt_max"]
+    aold = np.linalg.norm(ck["acc"][:, :3].astype(np.float64), axis=1).astype(np.float32)
+    for _ in range(6):
+        a.block_step()
+    end_a = a.get_state()
+    b = g.System(n, prm)
+    b.set_state(ck["pos"], ck["vel"], mass[ck["id"]])
+    b.set_integrator_state(ck["level"], ck["t0"], aold, ck["acc"], dt_max, T)
+    for _ in range(6):
+        b.block_step()
+    end_b = b.get_state()
+    assert np.array_equal(ck["id"][end_b["id"]], end_a["id"])
+    assert np.array_equal(end_b["pos"].view(np.uint64), end_a["pos"].view(np.uint64))
+    assert np.array_equal(end_b["vel"].view(np.uint64), end_a["vel"].view(np.uint64))
+    assert np.array_equal(end_b["level"], end_a["level"])
+    a.close()
+    b.close()
+
+
+# ------------------------------------------------------------------ full sizes, sampled
+def _full_size_sampled(env, kind, n, seed, ngroups_sample=48):
+    torch, g, O = env
+    pos, vel, mass, eps = _model(kind, n, seed)
+    prm = _params(g, eps)
+    oprm = _oparams(O, prm)
+    ref = _oracle_tree(O, pos, mass, prm.leaf_max)
+    s = g.System(n, prm)
+    s.set_state(pos, vel, mass)
+    s.build_tree()
+    t = s.get_tree()
+    _check_tree(t, ref)
+    # |a_old| for the acceleration MAC: a seeded positive field (any input works for parity)
+    aold = np.random.default_rng(seed).uniform(0.05, 2.0, n).astype(np.float32)
+    acc = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+    s.accel_active(None, torch.from_numpy(aold).cuda(), acc)
+    s.sync()
+    ng = -(-n // prm.group_max)
+    gids = np.unique(np.random.default_rng(seed + 1).integers(0, ng, ngroups_sample))
+    gids = np.union1d(gids, [0, ng - 1])
+    active = np.arange(n, dtype=np.uint32)
+    gI, gamin = O.groups(active, prm.group_max, ref["p4"][ref["order"]], aold)
+    oacc, inter, _ = O.walk(ref["tree"], ref["jpos"], ref["bj"], ref["p4"][ref["order"]], active,
+                            prm.group_max, gI, gamin, prm.mac, prm.theta, prm.delta_acc, prm.eps, prm.G,
+                            group_ids=gids)
+    rows = np.concatenate([np.arange(gg * prm.group_max, min(n, (gg + 1) * prm.group_max)) for gg in gids])
+    rel = _rel(acc.cpu().numpy()[rows], oacc[rows])
+    assert np.median(rel) <= MED_TOL and np.percentile(rel, 99) <= P99_TOL, (np.median(rel), np.percentile(rel, 99))
+    s.close()
+
+
+def test_nfw_2p20_full_size(env):
+    _full_size_sampled(env, "nfw", 1 << 20, 2)
+
+
+def test_andromeda_2p24_full_size(env):
+    _full_size_sampled(env, "m31", 1 << 24, 3, ngroups_sample=32)
