@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Benchmark of the block-step oct-tree gravity path on the Andromeda-like model.
+
+Workload: the three-component Andromeda-like model (Hernquist bulge 3 %, exponential
+disk 5 %, tapered NFW halo 92 %) with N = 2^24 equal-mass particles, eps = 0.01,
+acceleration MAC with Delta_acc = 2^-7, 8 block-step levels.  One benchmark step is
+one full block-step cycle (block steps until the block time reaches the next
+multiple of the longest step), with the tree rebuilt at every block step: every
+step of the method (predict, keys, sort, permute, build, pseudo j-particles, active
+set, walk, correct) runs in it.
+
+Reported: interactions/s of the whole job (value), seconds per block step, the
+end-to-end number through pinned host buffers, the walk kernel against the FP32
+roofline, clocks sampled during the timed region, and the CPU oracle timed on a
+bounded sample (rank 0, N = 1).  --impl reference times the CPU oracle instead.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torch.distributed.run, one replica per GPU (the single system does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "block-step s & interactions/s at N=2^24; p50/p99 batched-solve latency"
+FLOPS_PER_INTERACTION = 20  # 3 sub + 3 mul + 7 FMA (potential included); rsqrt runs on MUFU
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=1 << 24)
+    ap.add_argument("--levels", type=int, default=8)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-groups", type=int, default=2048, help="groups walked by the CPU baseline sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ workload
+def workload(n: int):
+    from paper_1610_07279_gb300 import ics
+    pos, vel, mass, eps = ics.andromeda_like(n, seed=3)
+    return pos, vel, mass, eps
+
+
+def config_dict(args, eps):
+    return {"workload": f"Andromeda-like three-component model (bulge 3%, disk 5%, NFW halo 92%), "
+                        f"N={args.n}, one full block-step cycle per step, tree rebuilt every block step",
+            "n": args.n, "levels": args.levels, "mac": "acceleration", "delta_acc": 2.0 ** -7,
+            "eps": eps, "leaf_max": 16, "group_max": 32, "ij_share": 1,
+            "l2": "inputs larger than L2 (particle state ~1.7 GB, nodes ~0.3 GB)"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def cpu_sample(pos, mass, eps, groups: int, seed: int = 7):
+    """The oracle on a bounded sample of the workload: one full tree build (A1-A5)
+    of all particles and the walk (A6-A7, acceleration MAC) of `groups` random groups.
+    Returns (interactions, seconds for the build share plus the walk, info)."""
+    import oracle as O
+    O.build()
+    n = len(mass)
+    p4 = np.zeros((n, 4), np.float32)
+    p4[:, :3] = pos
+    p4[:, 3] = mass
+    prm = O.Params(eps=O.f32(eps))
+    t0 = time.perf_counter()
+    key, _ = O.keys(p4)
+    order, skey = O.sort(key)
+    sp4 = np.ascontiguousarray(p4[order])
+    tree = O.build_tree(skey, prm.leaf_max)
+    jpos, bj = O.pseudo_j(tree, sp4)
+    t_build = time.perf_counter() - t0
+    ng = -(-n // prm.group_max)
+    rng = np.random.default_rng(seed)
+    gids = np.sort(rng.choice(ng, min(groups, ng), replace=False)).astype(np.int64)
+    active = np.arange(n, dtype=np.uint32)
+    # |a_old| of the sampled members from an opening-angle pass (setup, not timed)
+    gI, gamin = O.groups(active, prm.group_max, sp4, None)
+    boot, _, _ = O.walk(tree, jpos, bj, sp4, active, prm.group_max, gI, gamin, 0, prm.theta,
+                        prm.delta_acc, prm.eps, prm.G, group_ids=gids)
+    aold = np.zeros(n, np.float32)
+    rows = np.isfinite(boot[:, 0])
+    aold[rows] = O.amag(boot[rows].astype(np.float32)).astype(np.float32)
+    gI, gamin = O.groups(active, prm.group_max, sp4, aold)
+    t1 = time.perf_counter()
+    acc, inter, _ = O.walk(tree, jpos, bj, sp4, active, prm.group_max, gI, gamin, 1, prm.theta,
+                           prm.delta_acc, prm.eps, prm.G, group_ids=gids)
+    t_walk = time.perf_counter() - t1
+    n_inter = int(inter[inter >= 0].sum())
+    share = len(gids) / ng
+    secs = t_walk + t_build * share
+    info = {"t_build_s": t_build, "t_walk_s": t_walk, "groups": int(len(gids)), "groups_total": int(ng),
+            "threads": O.num_threads()}
+    return n_inter, secs, info
+
+
+def cpu_baseline_entry(pos, mass, eps, groups):
+    n_inter, secs, info = cpu_sample(pos, mass, eps, groups)
+    return {"value": n_inter / secs, "unit": "interactions/s", "cores": info["threads"], "kind": "oracle",
+            "sample": (f"one oracle tree build of all {len(mass)} particles (A1-A5, {info['t_build_s']:.2f} s, "
+                       f"charged pro rata to the sampled groups) plus the FP64 walk of {info['groups']} of "
+                       f"{info['groups_total']} random groups ({info['t_walk_s']:.2f} s, acceleration MAC)"),
+            "interactions": n_inter}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    pos, vel, mass, eps = workload(args.n)
+    import oracle as O
+    O.build()
+    vals, times = [], []
+    for k in range(args.warmup + args.steps):
+        n_inter, secs, info = cpu_sample(pos, mass, eps, max(64, args.cpu_groups // 4), seed=100 + k)
+        if k >= args.warmup:
+            vals.append(n_inter / secs)
+            times.append(secs)
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "interactions/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(args, eps),
+            "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": info["threads"],
+                             "kind": "oracle",
+                             "sample": "per step: the oracle's full tree build charged pro rata plus the FP64 walk "
+                                       f"of {info['groups']} random groups"},
+            "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def walk_traffic_entry():
+    """DRAM bytes per walk launch from the committed ncu summary, if the kernel is unchanged."""
+    path = os.path.join(ROOT, "profiles", "walk_traffic.json")
+    src = os.path.join(ROOT, "paper_1610_07279_gb300", "csrc", "walk.cu")
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if rec.get("walk_cu_sha256") == h:
+            return rec.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1610_07279_gb300 import build as gbuild
+    from paper_1610_07279_gb300 import gothic as g
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    gbuild.build()
+    g.load()
+
+    pos, vel, mass, eps = workload(args.n)
+    prm = g.gt_default_params()
+    prm.eps = eps
+    prm.levels = args.levels
+    sysm = g.System(args.n, prm)
+    sysm.set_state(pos, vel, mass)
+    sysm.start()
+    sysm.sync()
+    for _ in range(args.warmup):
+        sysm.advance_cycle()
+    sysm.sync()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def allreduce(x, op):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(torch.cuda.current_device())
+    # ---- device-resident timed region
+    sysm.profile(True)
+    st0 = sysm.stats()
+    l0 = g.gt_kernel_launches()
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    block_steps = 0
+    for _ in range(args.steps):
+        block_steps += sysm.advance_cycle()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    st1 = sysm.stats()
+    timers = sysm.timers()
+    launches = g.gt_kernel_launches() - l0
+    sysm.profile(False)
+    inter = st1["interactions"] - st0["interactions"]
+    ms_max = allreduce(ms, dist.ReduceOp.MAX if world > 1 else None)
+    inter_all = allreduce(float(inter), dist.ReduceOp.SUM if world > 1 else None)
+    value = inter_all / (ms_max * 1e-3)
+
+    walk_ms, walk_launches = timers["walk"]
+    achieved = inter * FLOPS_PER_INTERACTION / (walk_ms * 1e-3) / 1e12 if walk_ms > 0 else 0.0
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    nsm = props.multi_processor_count
+    sm_max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = nsm * 128 * 2 * sm_max_mhz * 1e6 / 1e12  # FP32 lanes x FMA x clock
+    measured_ffma = g.gt_measure_fp32_peak(stream.cuda_stream) / 1e12
+    traffic = walk_traffic_entry()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "k_walk (tree walk + force loop)",
+                "flops_per_interaction": FLOPS_PER_INTERACTION,
+                "peak_basis": f"{nsm} SMs x 128 FP32 lanes x 2 flops x {sm_max_mhz:.0f} MHz (derived)",
+                "measured_ffma_tflops": measured_ffma,
+                "walk_launches": walk_launches, "walk_ms_avg": walk_ms / max(walk_launches, 1)}
+
+    # ---- end to end through pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        n = args.n
+        pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True)
+        host = {"pos": pin((n, 3), torch.float64), "vel": pin((n, 3), torch.float64),
+                "mass": pin((n,), torch.float32), "acc": pin((n, 4), torch.float32),
+                "aold": pin((n,), torch.float32), "level": pin((n,), torch.uint8),
+                "t0": pin((n,), torch.int64), "id": pin((n,), torch.int32)}
+        sysm.get_state(out=host)
+        s_e = sysm.stats()
+        T, dt_max = s_e["T"], s_e["dt_max"]
+        h2d = n * (24 + 24 + 4 + 16 + 4 + 1 + 8)
+        d2h = n * (24 + 24 + 4 + 16 + 4 + 1 + 8 + 4)
+        barrier()
+        torch.cuda.synchronize()
+        i0 = sysm.stats()["interactions"]
+        t_start = time.perf_counter()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            sysm.set_state(host["pos"], host["vel"], host["mass"])
+            sysm.set_integrator_state(host["level"], host["t0"], host["aold"], host["acc"], dt_max, T)
+            sysm.advance_cycle()
+            sysm.get_state(out=host)
+            T = sysm.stats()["T"]
+        f1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - t_start
+        ms_e = f0.elapsed_time(f1)
+        i_e = sysm.stats()["interactions"] - i0
+        ms_e_max = allreduce(ms_e, dist.ReduceOp.MAX if world > 1 else None)
+        i_e_all = allreduce(float(i_e), dist.ReduceOp.SUM if world > 1 else None)
+        e2e = {"value": i_e_all / (ms_e_max * 1e-3), "unit": "interactions/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "wall_s": wall,
+               "path": "gt_set_state + gt_set_integrator_state from pinned host, one block-step cycle, "
+                       "gt_get_state to pinned host, every step"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline_entry(pos, mass, eps, args.cpu_groups)
+
+    if rank == 0:
+        breakdown = {k: {"ms_total": v[0], "launches": v[1]} for k, v in timers.items()}
+        line = {"metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": config_dict(args, eps),
+                "block_step_s": ms_max * 1e-3 / max(block_steps, 1), "block_steps": block_steps,
+                "interactions": inter, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+                "cpu_baseline": cpu, "clocks": clk, "phase_ms": breakdown,
+                "gflops_paper_convention": {str(f): inter_all * f / (ms_max * 1e-3) / 1e9
+                                            for f in (20, 24, 28, 38)}}
+        print(json.dumps(line), flush=True)
+    sysm.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

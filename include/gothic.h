@@ -73,8 +73,11 @@ typedef struct gt_params {
                            group_max must be <= 32 / ij_share                       */
     int32_t levels;     /* L: number of block-step levels, 1..30 (Sec. 1)          */
     int32_t rebuild_every; /* rebuild the tree every n block steps (Sec. 2.6); 1 = always */
-    int32_t walk_queue; /* per-warp breadth-first queue capacity, power of 2 (Sec. 2.3) */
-    int32_t reserved0;
+    int32_t walk_queue; /* per-warp cell queue capacity, power of 2 (Sec. 2.3); >= 8192
+                           leaves room for the depth-first fallback that bounds it */
+    int32_t node_factor;   /* tree-cell capacity = node_factor * n + 2048 (>= 1); tight
+                              clumps of more than leaf_max particles form chains down to
+                              level 21 and may need more than the default 2 */
     double eta;         /* step accuracy: dt_i = sqrt(2 eta eps / |a_i|)           */
     double dt_max;      /* longest step, a power of two; <= 0: derived at gt_start */
 } gt_params;
@@ -103,7 +106,8 @@ GT_API const char *gt_strerror(int status);
 
 /* The paper's fiducial parameters: acceleration MAC with Delta_acc = 2^-7
  * (Sec. 3.3), theta = 0.5 for the bootstrap pass, G = 1, eps = 1/64,
- * leaf_max = 16, group_max = 32, S = 1, L = 8, eta = 0.025, queue 8192. */
+ * leaf_max = 16, group_max = 32, S = 1, L = 8, eta = 0.025, queue 16384,
+ * node_factor 2. */
 GT_API int gt_default_params(gt_params *prm);
 
 /* Bytes of device workspace a system of n particles needs (n >= 0). */
@@ -194,13 +198,34 @@ GT_API int gt_predict(gt_system *sys, int64_t T, float *d_posm, gt_stream stream
 GT_API int gt_correct(gt_system *sys, const uint32_t *d_active, int64_t n_active, const float *d_acc,
                       int64_t T, gt_stream stream);
 
+/* Run block steps until the next block time would exceed T_end (ticks of the
+ * finest step); *steps (may be NULL) receives the number taken.  Reads the
+ * next block time back after every step (synchronises per step).  One full
+ * block-step cycle is T_end = the next multiple of 2^(L-1). */
+GT_API int gt_advance(gt_system *sys, int64_t T_end, int64_t *steps, gt_stream stream);
+
+/* Per-phase device timers (CUDA events around each phase of gt_block_step and
+ * the passes of gt_start; the paper monitors per-function times on the fly,
+ * Sec. 1, Sec. 2.4, Sec. 2.6).  Phases: 0 predict, 1 keys+sort, 2 permute,
+ * 3 tree build, 4 pseudo j-particles, 5 active set, 6 walk, 7 correct.
+ * gt_profile(sys, 1) enables and zeroes them; timing is read at the
+ * synchronisations of gt_advance / gt_get_timers.  ms_out[8] total
+ * milliseconds, launches_out[8] number of timed phase executions. */
+#define GT_NPHASES 8
+GT_API int gt_profile(gt_system *sys, int enable);
+GT_API int gt_get_timers(gt_system *sys, double *ms_out, int64_t *launches_out, gt_stream stream);
+
+/* Kernels launched by this library since load (all systems). */
+GT_API int gt_kernel_launches(int64_t *count);
+
 /* Copy the state out in internal order.  Any pointer may be NULL to skip it;
  * any may be host or device memory.  p_pos, p_vel n x 3 FP64 (velocity is the
- * half-step velocity v^{1/2} that the scheme stores), p_acc n x 4 FP32 (the
- * last acceleration and potential), p_level n uint8, p_t0 n int64 (tick of the
+ * half-step velocity v^{1/2} that the scheme stores), p_mass n FP32, p_acc n x 4 FP32 (the
+ * last acceleration and potential), p_aold n FP32 (|a_old| used by the
+ * acceleration MAC), p_level n uint8, p_t0 n int64 (tick of the
  * last correction), p_id n uint32 (caller's index). */
-GT_API int gt_get_state(gt_system *sys, double *p_pos, double *p_vel, float *p_acc, uint8_t *p_level,
-                 int64_t *p_t0, uint32_t *p_id, gt_stream stream);
+GT_API int gt_get_state(gt_system *sys, double *p_pos, double *p_vel, float *p_mass, float *p_acc,
+                        float *p_aold, uint8_t *p_level, int64_t *p_t0, uint32_t *p_id, gt_stream stream);
 
 /* Copy the tree out.  p_keys n uint64 sorted keys; p_order n uint32 (the
  * caller's index of each internal slot, same as id); p_nodes n_nodes x 4 uint32

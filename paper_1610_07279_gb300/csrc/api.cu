@@ -3,12 +3,27 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 
 #include "gt_internal.cuh"
 
+static std::atomic<long long> g_launches{0};
+
+void gt_note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// Per-phase event timers of one system.
+struct PhaseTimers {
+    bool on = false, created = false;
+    cudaEvent_t b[GT_NPHASES]{}, e[GT_NPHASES]{};
+    bool ran[GT_NPHASES]{};
+    double ms[GT_NPHASES]{};
+    long long cnt[GT_NPHASES]{};
+};
+
 struct gt_system {
     int64_t n = 0;
+    PhaseTimers prof;
     gt_params prm{};
     int dev = 0, nsm = 0;
     int walk_blocks = 0, walk_warps = 0;
@@ -56,7 +71,7 @@ int check_params(const gt_params *p) {
     if (!pow2(p->ij_share) || p->ij_share > 32) return GT_EINVAL;
     if (p->group_max < 1 || p->group_max > 32 / p->ij_share) return GT_EINVAL;
     if (p->levels < 1 || p->levels > 30) return GT_EINVAL;
-    if (p->rebuild_every < 1) return GT_EINVAL;
+    if (p->rebuild_every < 1 || p->node_factor < 1 || p->node_factor > 64) return GT_EINVAL;
     if (!pow2(p->walk_queue) || p->walk_queue < 64) return GT_EINVAL;
     if (!(p->eps > 0.0f) || !(p->theta >= 0.0f) || !(p->delta_acc >= 0.0f)) return GT_EINVAL;
     if (!(p->eta > 0.0)) return GT_EINVAL;
@@ -82,7 +97,7 @@ int max_walk_blocks(int nsm) {
     return best;
 }
 
-int64_t node_capacity(int64_t n) { return 2 * n + 2048; }
+int64_t node_capacity(int64_t n, const gt_params *p) { return (int64_t)p->node_factor * n + 2048; }
 
 // Carve every buffer out of base (or only measure when base == nullptr).
 size_t carve(gt_system *s, char *base, int64_t n, const gt_params *p, int nsm, int walk_blocks) {
@@ -111,7 +126,7 @@ size_t carve(gt_system *s, char *base, int64_t n, const gt_params *p, int nsm, i
     s->sb.tile_hist = (uint32_t *)L.take<char>(base, gt_sort_scratch_bytes(n));
     s->sb.digit_base = L.take<uint32_t>(base, 256);
     s->sb.digit_total = L.take<uint32_t>(base, 256);
-    const int64_t cap = node_capacity(n);
+    const int64_t cap = node_capacity(n, p);
     s->cap = cap;
     s->nd.first = L.take<uint32_t>(base, cap);
     s->nd.count = L.take<uint32_t>(base, cap);
@@ -139,26 +154,67 @@ size_t carve(gt_system *s, char *base, int64_t n, const gt_params *p, int nsm, i
 
 int last_cuda() { return cudaGetLastError() == cudaSuccess ? GT_OK : GT_ECUDA; }
 
+enum { PH_PREDICT = 0, PH_SORT, PH_PERMUTE, PH_BUILD, PH_PSEUDO, PH_ACTIVE, PH_WALK, PH_CORRECT };
+
+void ph_begin(gt_system *s, int p, cudaStream_t st) {
+    if (s->prof.on) cudaEventRecord(s->prof.b[p], st);
+}
+
+void ph_end(gt_system *s, int p, cudaStream_t st) {
+    if (s->prof.on) {
+        cudaEventRecord(s->prof.e[p], st);
+        s->prof.ran[p] = true;
+    }
+}
+
+// fold the finished phases' times in (the stream must have been synchronised)
+void ph_collect(gt_system *s) {
+    if (!s->prof.on) return;
+    for (int p = 0; p < GT_NPHASES; p++) {
+        if (!s->prof.ran[p]) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, s->prof.b[p], s->prof.e[p]) == cudaSuccess) {
+            s->prof.ms[p] += ms;
+            s->prof.cnt[p] += 1;
+        }
+        s->prof.ran[p] = false;
+    }
+}
+
+void ph_sync_collect(gt_system *s, cudaStream_t st) {
+    if (!s->prof.on) return;
+    cudaStreamSynchronize(st);
+    ph_collect(s);
+}
+
 cudaStream_t S(gt_stream s) { return (cudaStream_t)s; }
 
 // A1-A5 on the current FP32 positions in s->posm (permutes every array into key order)
 void build_tree(gt_system *s, cudaStream_t st, const float4 *posm_src) {
     const int64_t n = s->n;
     gt_launch_prepare(s->ctl, 0, st);
+    ph_begin(s, PH_SORT, st);
     gt_launch_bbox(posm_src, n, s->bbox_partial, s->bbox_blocks, s->ctl, st);
     gt_launch_keys(posm_src, n, s->ctl, s->sb.key[0], s->sb.val[0], st);
     gt_launch_sort(s->sb, n, s->ctl, st);
+    ph_end(s, PH_SORT, st);
     const int nxt = s->cur ^ 1;
     float4 *dst = posm_src == s->posm ? s->posm_tmp : s->posm;
+    ph_begin(s, PH_PERMUTE, st);
     gt_launch_permute(s->st[s->cur], s->st[nxt], posm_src, dst, s->sb.val[0], n, st);
+    ph_end(s, PH_PERMUTE, st);
     s->cur = nxt;
     if (dst != s->posm) {
         float4 *t = s->posm;
         s->posm = s->posm_tmp;
         s->posm_tmp = t;
     }
+    ph_begin(s, PH_BUILD, st);
     gt_launch_build(s->sb.key[0], n, s->prm.leaf_max, s->nd, s->cap, s->status, s->ctl, s->nsm, st);
+    ph_end(s, PH_BUILD, st);
+    ph_begin(s, PH_PSEUDO, st);
     gt_launch_pseudo(s->nd, s->cap, s->posm, s->ctl, s->nsm, st);
+    ph_end(s, PH_PSEUDO, st);
     s->have_tree = true;
     s->rebuilds++;
 }
@@ -182,7 +238,9 @@ void walk(gt_system *s, const uint32_t *active, const float *aold, float4 *acc, 
     a.eps2 = s->prm.eps * s->prm.eps;
     a.G = s->prm.G;
     a.inv_eps = 1.0f / s->prm.eps;
+    ph_begin(s, PH_WALK, st);
     gt_launch_walk(a, s->prm.ij_share, s->walk_blocks, st);
+    ph_end(s, PH_WALK, st);
 }
 
 }  // namespace
@@ -218,7 +276,8 @@ int gt_default_params(gt_params *p) {
     p->ij_share = 1;
     p->levels = 8;
     p->rebuild_every = 1;
-    p->walk_queue = 8192;
+    p->walk_queue = 16384;
+    p->node_factor = 2;
     p->eta = 0.025;
     p->dt_max = 0.0;
     return GT_OK;
@@ -264,6 +323,11 @@ int gt_system_create(gt_system **out, int64_t n, const gt_params *prm, void *d_w
 }
 
 int gt_system_destroy(gt_system *s) {
+    if (s && s->prof.created)
+        for (int p = 0; p < GT_NPHASES; p++) {
+            cudaEventDestroy(s->prof.b[p]);
+            cudaEventDestroy(s->prof.e[p]);
+        }
     delete s;
     return GT_OK;
 }
@@ -272,7 +336,8 @@ int gt_set_params(gt_system *s, const gt_params *prm) {
     if (!s) return GT_EINVAL;
     int rc = check_params(prm);
     if (rc) return rc;
-    if (prm->walk_queue > s->prm.walk_queue) return GT_EINVAL;  // the queue region is fixed
+    // the queue and node regions are fixed at create
+    if (prm->walk_queue > s->prm.walk_queue || prm->node_factor != s->prm.node_factor) return GT_EINVAL;
     if (s->started && (prm->levels != s->prm.levels || prm->dt_max != s->prm.dt_max)) return GT_ESTATE;
     const int qcap_region = s->prm.walk_queue;
     s->prm = *prm;
@@ -336,6 +401,7 @@ int gt_start(gt_system *s, const float *p_aold_boot, gt_stream stream) {
         gt_launch_set_nactive(s->ctl, (unsigned)n, st);
         walk(s, nullptr, nullptr, s->acc_out, GT_MAC_OPENING_ANGLE, st);
         gt_launch_amag(s->acc_out, n, t.aold, st);
+        ph_sync_collect(s, st);
     }
     gt_launch_prepare(s->ctl, 0, st);
     gt_launch_set_nactive(s->ctl, (unsigned)n, st);
@@ -361,18 +427,26 @@ int gt_block_step(gt_system *s, gt_stream stream) {
     const int64_t n = s->n;
     if (n == 0) return GT_OK;
     gt_launch_prepare(s->ctl, 1, st);
-    if (s->steps % s->prm.rebuild_every == 0) {
-        gt_launch_predict(s->st[s->cur], n, s->ctl, s->posm_tmp, st);
+    const bool rebuild = s->steps % s->prm.rebuild_every == 0;
+    ph_begin(s, PH_PREDICT, st);
+    gt_launch_predict(s->st[s->cur], n, s->ctl, rebuild ? s->posm_tmp : s->posm, st);
+    ph_end(s, PH_PREDICT, st);
+    if (rebuild) {
         build_tree(s, st, s->posm_tmp);
     } else {
-        gt_launch_predict(s->st[s->cur], n, s->ctl, s->posm, st);
+        ph_begin(s, PH_PSEUDO, st);
         gt_launch_pseudo(s->nd, s->cap, s->posm, s->ctl, s->nsm, st);
+        ph_end(s, PH_PSEUDO, st);
     }
     State &t = s->st[s->cur];
+    ph_begin(s, PH_ACTIVE, st);
     gt_launch_active(t, n, s->prm.levels, 0, s->ctl, s->active, s->status, s->nsm, st);
+    ph_end(s, PH_ACTIVE, st);
     walk(s, s->active, t.aold, s->acc_out, s->prm.mac, st);
+    ph_begin(s, PH_CORRECT, st);
     gt_launch_correct(t, s->active, s->acc_out, s->ctl, n, s->prm.levels, s->prm.eta, (double)s->prm.eps,
                       s->nsm, st);
+    ph_end(s, PH_CORRECT, st);
     s->steps++;
     return last_cuda();
 }
@@ -435,8 +509,63 @@ int gt_correct(gt_system *s, const uint32_t *d_active, int64_t n_active, const f
     return last_cuda();
 }
 
-int gt_get_state(gt_system *s, double *p_pos, double *p_vel, float *p_acc, uint8_t *p_level,
-                 int64_t *p_t0, uint32_t *p_id, gt_stream stream) {
+int gt_advance(gt_system *s, int64_t T_end, int64_t *steps, gt_stream stream) {
+    if (!s) return GT_EINVAL;
+    if (!s->started) return GT_ESTATE;
+    cudaStream_t st = S(stream);
+    int64_t k = 0;
+    for (;;) {
+        unsigned long long tn = 0;
+        int err = 0;
+        if (cudaMemcpyAsync(&tn, &s->ctl->tnext_acc, 8, cudaMemcpyDeviceToHost, st) ||
+            cudaMemcpyAsync(&err, &s->ctl->err, 4, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
+            return GT_ECUDA;
+        ph_collect(s);
+        if (err) return err;
+        if (s->n == 0 || tn == ~0ull || (long long)tn > T_end) break;
+        const int rc = gt_block_step(s, stream);
+        if (rc) return rc;
+        k++;
+    }
+    if (steps) *steps = k;
+    return GT_OK;
+}
+
+int gt_profile(gt_system *s, int enable) {
+    if (!s) return GT_EINVAL;
+    if (enable && !s->prof.created) {
+        for (int p = 0; p < GT_NPHASES; p++)
+            if (cudaEventCreate(&s->prof.b[p]) || cudaEventCreate(&s->prof.e[p])) return GT_ECUDA;
+        s->prof.created = true;
+    }
+    s->prof.on = enable != 0;
+    for (int p = 0; p < GT_NPHASES; p++) {
+        s->prof.ms[p] = 0.0;
+        s->prof.cnt[p] = 0;
+        s->prof.ran[p] = false;
+    }
+    return GT_OK;
+}
+
+int gt_get_timers(gt_system *s, double *ms_out, int64_t *launches_out, gt_stream stream) {
+    if (!s) return GT_EINVAL;
+    if (cudaStreamSynchronize(S(stream)) != cudaSuccess) return GT_ECUDA;
+    ph_collect(s);
+    for (int p = 0; p < GT_NPHASES; p++) {
+        if (ms_out) ms_out[p] = s->prof.ms[p];
+        if (launches_out) launches_out[p] = s->prof.cnt[p];
+    }
+    return GT_OK;
+}
+
+int gt_kernel_launches(int64_t *count) {
+    if (!count) return GT_EINVAL;
+    *count = g_launches.load();
+    return GT_OK;
+}
+
+int gt_get_state(gt_system *s, double *p_pos, double *p_vel, float *p_mass, float *p_acc, float *p_aold,
+                 uint8_t *p_level, int64_t *p_t0, uint32_t *p_id, gt_stream stream) {
     if (!s) return GT_EINVAL;
     cudaStream_t st = S(stream);
     const int64_t n = s->n;
@@ -450,7 +579,9 @@ int gt_get_state(gt_system *s, double *p_pos, double *p_vel, float *p_acc, uint8
         gt_launch_interleave3(t.vx, t.vy, t.vz, n, s->scratch3, st);
         if (cudaMemcpyAsync(p_vel, s->scratch3, (size_t)n * 24, cudaMemcpyDefault, st)) return GT_ECUDA;
     }
+    if (p_mass && cudaMemcpyAsync(p_mass, t.mass, (size_t)n * 4, cudaMemcpyDefault, st)) return GT_ECUDA;
     if (p_acc && cudaMemcpyAsync(p_acc, t.acc, (size_t)n * 16, cudaMemcpyDefault, st)) return GT_ECUDA;
+    if (p_aold && cudaMemcpyAsync(p_aold, t.aold, (size_t)n * 4, cudaMemcpyDefault, st)) return GT_ECUDA;
     if (p_level && cudaMemcpyAsync(p_level, t.level, (size_t)n, cudaMemcpyDefault, st)) return GT_ECUDA;
     if (p_t0 && cudaMemcpyAsync(p_t0, t.t0, (size_t)n * 8, cudaMemcpyDefault, st)) return GT_ECUDA;
     if (p_id && cudaMemcpyAsync(p_id, t.id, (size_t)n * 4, cudaMemcpyDefault, st)) return GT_ECUDA;

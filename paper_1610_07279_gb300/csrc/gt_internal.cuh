@@ -156,6 +156,9 @@ __device__ __forceinline__ unsigned int lookback_prefix(unsigned long long *stat
 }
 
 // ---- host-side launch helpers (defined in the .cu files) --------------------
+// Every helper reports the kernels it launched (counted for gt_kernel_launches).
+void gt_note_launches(int k);
+
 struct SortBufs {
     uint64_t *key[2];
     uint32_t *val[2];

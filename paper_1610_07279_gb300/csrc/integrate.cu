@@ -343,77 +343,77 @@ inline unsigned nblk(long long n) { return (unsigned)((n + 255) / 256); }
 }  // namespace
 
 void gt_launch_prepare(DevCtl *ctl, int begin_step, cudaStream_t st) {
-    k_prepare<<<1, 1, 0, st>>>(ctl, begin_step);
+    { k_prepare<<<1, 1, 0, st>>>(ctl, begin_step); gt_note_launches(1); }
 }
 
 void gt_launch_set_nactive(DevCtl *ctl, unsigned int n_active, cudaStream_t st) {
-    k_set_nactive<<<1, 1, 0, st>>>(ctl, n_active);
+    { k_set_nactive<<<1, 1, 0, st>>>(ctl, n_active); gt_note_launches(1); }
 }
 
 void gt_launch_predict(const State &s, int64_t n, const DevCtl *ctl, float4 *posm, cudaStream_t st) {
-    if (n > 0) k_predict<<<nblk(n), 256, 0, st>>>(s, n, ctl, posm);
+    if (n > 0) { k_predict<<<nblk(n), 256, 0, st>>>(s, n, ctl, posm); gt_note_launches(1); }
 }
 
 void gt_launch_load(const State &s, float4 *posm, int64_t n, cudaStream_t st) {
-    if (n > 0) k_load<<<nblk(n), 256, 0, st>>>(s, n, posm);
+    if (n > 0) { k_load<<<nblk(n), 256, 0, st>>>(s, n, posm); gt_note_launches(1); }
 }
 
 void gt_launch_permute(const State &src, const State &dst, const float4 *posm_in, float4 *posm_out,
                        const uint32_t *perm, int64_t n, cudaStream_t st) {
-    if (n > 0) k_permute<<<nblk(n), 256, 0, st>>>(src, dst, posm_in, posm_out, perm, n);
+    if (n > 0) { k_permute<<<nblk(n), 256, 0, st>>>(src, dst, posm_in, posm_out, perm, n); gt_note_launches(1); }
 }
 
 void gt_launch_deinterleave3(const double *in, int64_t n, double *x, double *y, double *z,
                              cudaStream_t st) {
-    if (n > 0) k_deinterleave3<<<nblk(n), 256, 0, st>>>(in, n, x, y, z);
+    if (n > 0) { k_deinterleave3<<<nblk(n), 256, 0, st>>>(in, n, x, y, z); gt_note_launches(1); }
 }
 
 void gt_launch_interleave3(const double *x, const double *y, const double *z, int64_t n, double *out,
                            cudaStream_t st) {
-    if (n > 0) k_interleave3<<<nblk(n), 256, 0, st>>>(x, y, z, n, out);
+    if (n > 0) { k_interleave3<<<nblk(n), 256, 0, st>>>(x, y, z, n, out); gt_note_launches(1); }
 }
 
 void gt_launch_gather_f(const float *in, const uint32_t *id, int64_t n, float *out, cudaStream_t st) {
-    if (n > 0) k_gather_f<<<nblk(n), 256, 0, st>>>(in, id, n, out);
+    if (n > 0) { k_gather_f<<<nblk(n), 256, 0, st>>>(in, id, n, out); gt_note_launches(1); }
 }
 
 void gt_launch_active(const State &s, int64_t n, int L, int all, DevCtl *ctl, uint32_t *active,
                       unsigned long long *status, int nsm, cudaStream_t st) {
     if (n <= 0) {
-        k_set_nactive<<<1, 1, 0, st>>>(ctl, 0u);
+        { k_set_nactive<<<1, 1, 0, st>>>(ctl, 0u); gt_note_launches(1); }
         return;
     }
-    k_active<<<nsm * 4, AT, 0, st>>>(n, s.t0, s.level, L, all, ctl, active, status);
+    { k_active<<<nsm * 4, AT, 0, st>>>(n, s.t0, s.level, L, all, ctl, active, status); gt_note_launches(1); }
 }
 
 void gt_launch_correct(const State &s, const uint32_t *active, const float4 *acc, DevCtl *ctl,
                        int64_t n, int L, double eta, double eps, int nsm, cudaStream_t st) {
-    if (n > 0) k_correct<<<nsm * 8, 256, 0, st>>>(s, active, acc, ctl, n, L, eta, eps);
+    if (n > 0) { k_correct<<<nsm * 8, 256, 0, st>>>(s, active, acc, ctl, n, L, eta, eps); gt_note_launches(1); }
 }
 
 void gt_launch_amag(const float4 *acc, int64_t n, float *aold, cudaStream_t st) {
-    if (n > 0) k_amag<<<nblk(n), 256, 0, st>>>(acc, n, aold);
+    if (n > 0) { k_amag<<<nblk(n), 256, 0, st>>>(acc, n, aold); gt_note_launches(1); }
 }
 
 void gt_launch_set_clock(DevCtl *ctl, int M, int L, long long T, cudaStream_t st) {
-    k_set_clock<<<1, 1, 0, st>>>(ctl, M, L, T);
+    { k_set_clock<<<1, 1, 0, st>>>(ctl, M, L, T); gt_note_launches(1); }
 }
 
-void gt_launch_set_tnext(DevCtl *ctl, long long T, cudaStream_t st) { k_set_tnext<<<1, 1, 0, st>>>(ctl, T); }
+void gt_launch_set_tnext(DevCtl *ctl, long long T, cudaStream_t st) { { k_set_tnext<<<1, 1, 0, st>>>(ctl, T); gt_note_launches(1); } }
 
 void gt_launch_tnext_all(const State &s, int64_t n, int L, DevCtl *ctl, int nsm, cudaStream_t st) {
-    if (n > 0) k_tnext_all<<<nsm * 4, 256, 0, st>>>(s.t0, s.level, n, L, ctl);
+    if (n > 0) { k_tnext_all<<<nsm * 4, 256, 0, st>>>(s.t0, s.level, n, L, ctl); gt_note_launches(1); }
 }
 
 void gt_launch_gather_resume(const uint8_t *lv, const long long *t0, const float *ao, const float4 *acc,
                              const State &s, int64_t n, cudaStream_t st) {
-    if (n > 0) k_gather_resume<<<nblk(n), 256, 0, st>>>(lv, t0, ao, acc, s.id, n, s);
+    if (n > 0) { k_gather_resume<<<nblk(n), 256, 0, st>>>(lv, t0, ao, acc, s.id, n, s); gt_note_launches(1); }
 }
 
 void gt_launch_init_levels(const State &s, const float4 *acc, int64_t n, int L, double eta,
                            double eps, int M_given, int have_M, DevCtl *ctl, int nsm,
                            cudaStream_t st) {
-    k_reset_start<<<1, 1, 0, st>>>(ctl);
-    if (!have_M && n > 0) k_max_dt<<<nsm * 4, 256, 0, st>>>(acc, n, eta, eps, ctl);
-    k_init_levels<<<nsm * 8, 256, 0, st>>>(s, acc, n, L, eta, eps, M_given, have_M, ctl);
+    { k_reset_start<<<1, 1, 0, st>>>(ctl); gt_note_launches(1); }
+    if (!have_M && n > 0) { k_max_dt<<<nsm * 4, 256, 0, st>>>(acc, n, eta, eps, ctl); gt_note_launches(1); }
+    { k_init_levels<<<nsm * 8, 256, 0, st>>>(s, acc, n, L, eta, eps, M_given, have_M, ctl); gt_note_launches(1); }
 }

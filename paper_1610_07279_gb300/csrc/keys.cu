@@ -113,12 +113,12 @@ __global__ __launch_bounds__(256) void k_keys(const float4 *__restrict__ posm, l
 
 void gt_launch_bbox(const float4 *posm, int64_t n, float *partial, int nblk, DevCtl *ctl,
                     cudaStream_t st) {
-    k_bbox_partial<<<nblk, BBOX_THREADS, 0, st>>>(posm, n, partial);
-    k_bbox_final<<<1, 32, 0, st>>>(partial, nblk, n, ctl);
+    { k_bbox_partial<<<nblk, BBOX_THREADS, 0, st>>>(posm, n, partial); gt_note_launches(1); }
+    { k_bbox_final<<<1, 32, 0, st>>>(partial, nblk, n, ctl); gt_note_launches(1); }
 }
 
 void gt_launch_keys(const float4 *posm, int64_t n, const DevCtl *ctl, uint64_t *key, uint32_t *idx,
                     cudaStream_t st) {
     if (n <= 0) return;
-    k_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(posm, n, ctl, (unsigned long long *)key, idx);
+    { k_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(posm, n, ctl, (unsigned long long *)key, idx); gt_note_launches(1); }
 }

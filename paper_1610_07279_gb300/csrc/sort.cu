@@ -172,11 +172,11 @@ void gt_launch_sort(SortBufs &b, int64_t n, DevCtl *ctl, cudaStream_t st) {
     for (int p = 0; p < PASSES; p++) {
         const int src = p & 1, dst = src ^ 1;
         const int shift = p * RB;
-        k_tile_hist<<<ntiles, ST, 0, st>>>(n, shift, (const unsigned long long *)b.key[src],
-                                           b.tile_hist, ntiles);
-        k_digit_scan<<<R, 1024, 0, st>>>(b.tile_hist, ntiles, b.digit_total, b.digit_base, ctl);
-        k_scatter<<<ntiles, ST, SCATTER_SMEM, st>>>(n, shift, (const unsigned long long *)b.key[src],
+        { k_tile_hist<<<ntiles, ST, 0, st>>>(n, shift, (const unsigned long long *)b.key[src],
+                                           b.tile_hist, ntiles); gt_note_launches(1); }
+        { k_digit_scan<<<R, 1024, 0, st>>>(b.tile_hist, ntiles, b.digit_total, b.digit_base, ctl); gt_note_launches(1); }
+        { k_scatter<<<ntiles, ST, SCATTER_SMEM, st>>>(n, shift, (const unsigned long long *)b.key[src],
                                                     b.val[src], (unsigned long long *)b.key[dst],
-                                                    b.val[dst], b.tile_hist, b.digit_base, ntiles);
+                                                    b.val[dst], b.tile_hist, b.digit_base, ntiles); gt_note_launches(1); }
     }
 }

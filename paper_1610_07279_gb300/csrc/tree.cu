@@ -221,13 +221,13 @@ __global__ __launch_bounds__(256) void k_pseudo(Nodes nd, long long cap, const f
 
 void gt_launch_build(const uint64_t *skey, int64_t n, int leaf_max, Nodes nd, int64_t cap,
                      unsigned long long *status, DevCtl *ctl, int nsm, cudaStream_t st) {
-    k_build_init<<<1, 1, 0, st>>>(n, nd, ctl);
+    { k_build_init<<<1, 1, 0, st>>>(n, nd, ctl); gt_note_launches(1); }
     for (int l = 0; l < GT_TREE_LEVELS; l++)
-        k_build_level<<<nsm * 4, BT, 0, st>>>(l, (const unsigned long long *)skey, leaf_max, nd, cap,
-                                              status, ctl);
+        { k_build_level<<<nsm * 4, BT, 0, st>>>(l, (const unsigned long long *)skey, leaf_max, nd, cap,
+                                              status, ctl); gt_note_launches(1); }
 }
 
 void gt_launch_pseudo(Nodes nd, int64_t cap, const float4 *posm, DevCtl *ctl, int nsm,
                       cudaStream_t st) {
-    k_pseudo<<<nsm * 8, 256, 0, st>>>(nd, cap, posm, ctl);
+    { k_pseudo<<<nsm * 8, 256, 0, st>>>(nd, cap, posm, ctl); gt_note_launches(1); }
 }

@@ -7,7 +7,9 @@
 //     (Appendix B, "GEO"), radius rounded up to FP32 from an FP64 distance; |a_old| of
 //     the group is the smallest of its members';
 //   * breadth-first traversal: a ring-buffer queue of cells in a per-warp slice of
-//     global memory; 32 queued cells are tested at once, one per lane, with the MAC at
+//     global memory (when the queue fills up, the newest cells are taken first, i.e.
+//     depth-first, which bounds its size; the order of the interactions does not change
+//     the set of interactions); 32 queued cells are tested at once, one per lane, with the MAC at
 //     distance lambda r_JI (Eqs. 2, 5-7) in FP32 with explicit rounding (so the decision
 //     is reproducible); accepted cells join the shared-memory interaction list,
 //     rejected cells push their children (warp prefix sum), rejected leaves copy their
@@ -28,6 +30,9 @@ constexpr int WT = 256;           // threads per block
 constexpr int NWARP = WT / 32;
 constexpr int LIST_CAP = 320;     // interaction-list entries per warp
 constexpr int FLUSH_AT = 256;     // flush once the list holds this many
+// Depth-first reserve of the queue: popping the newest 32 cells and pushing at most
+// 8 children each grows the queue by <= 224 per tree level, <= ~22 x 256 in all.
+constexpr int LIFO_ROOM = 6144;
 
 __device__ __forceinline__ bool mac_accept(int mac, float theta, float dacc_amin, float G, float cx,
                                            float cy, float cz, float bI, float4 jp, float bJ) {
@@ -62,6 +67,7 @@ __global__ __launch_bounds__(WT, 4) void k_walk(WalkArgs a) {
     float4 *list = list_sm[warp];
     uint32_t *q = a.queue + (size_t)(blockIdx.x * NWARP + warp) * (size_t)a.qcap;
     const uint32_t qmask = (uint32_t)a.qcap - 1u;
+    const int lifo_at = a.qcap - LIFO_ROOM;
     const uint32_t na = a.ctl->n_active;
     const uint32_t gmax = (uint32_t)a.gmax;
     const uint32_t ngroups = (na + gmax - 1) / gmax;
@@ -134,15 +140,24 @@ __global__ __launch_bounds__(WT, 4) void k_walk(WalkArgs a) {
         __syncwarp();
         bool overflow = false;
         while (head != tail) {
-            const uint32_t nb = min(tail - head, 32u);
+            const uint32_t live = tail - head;
+            const uint32_t nb = min(live, 32u);
             const bool valid = (uint32_t)lane < nb;
+            // breadth-first from the head while there is room, depth-first from the tail after
+            uint32_t base;
+            if ((int)live > lifo_at) {
+                tail -= nb;
+                base = tail;
+            } else {
+                base = head;
+                head += nb;
+            }
             float4 jp = make_float4(0.f, 0.f, 0.f, 0.f), wk = make_float4(0.f, 0.f, 0.f, 0.f);
             if (valid) {
-                const uint32_t node = q[(head + lane) & qmask];
+                const uint32_t node = q[(base + lane) & qmask];
                 jp = a.jpos[node];
                 wk = a.walk[node];
             }
-            head += nb;
             n_tests += nb;
             const bool ok = valid && mac_accept(a.mac, a.theta, dacc_amin, a.G, cx, cy, cz, bI, jp, wk.x);
             const uint32_t l0 = __float_as_uint(wk.y), l1 = __float_as_uint(wk.z);
@@ -239,12 +254,12 @@ int gt_walk_warps_per_block() { return NWARP; }
 
 void gt_launch_walk(const WalkArgs &a, int ij_share, int nblocks, cudaStream_t st) {
     switch (ij_share) {
-        case 1: k_walk<1><<<nblocks, WT, 0, st>>>(a); break;
-        case 2: k_walk<2><<<nblocks, WT, 0, st>>>(a); break;
-        case 4: k_walk<4><<<nblocks, WT, 0, st>>>(a); break;
-        case 8: k_walk<8><<<nblocks, WT, 0, st>>>(a); break;
-        case 16: k_walk<16><<<nblocks, WT, 0, st>>>(a); break;
-        case 32: k_walk<32><<<nblocks, WT, 0, st>>>(a); break;
+        case 1: { k_walk<1><<<nblocks, WT, 0, st>>>(a); gt_note_launches(1); } break;
+        case 2: { k_walk<2><<<nblocks, WT, 0, st>>>(a); gt_note_launches(1); } break;
+        case 4: { k_walk<4><<<nblocks, WT, 0, st>>>(a); gt_note_launches(1); } break;
+        case 8: { k_walk<8><<<nblocks, WT, 0, st>>>(a); gt_note_launches(1); } break;
+        case 16: { k_walk<16><<<nblocks, WT, 0, st>>>(a); gt_note_launches(1); } break;
+        case 32: { k_walk<32><<<nblocks, WT, 0, st>>>(a); gt_note_launches(1); } break;
         default: break;
     }
 }

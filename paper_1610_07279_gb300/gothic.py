@@ -35,7 +35,7 @@ class gt_params(C.Structure):
     _fields_ = [("mac", C.c_int32), ("theta", C.c_float), ("delta_acc", C.c_float),
                 ("eps", C.c_float), ("G", C.c_float), ("leaf_max", C.c_int32),
                 ("group_max", C.c_int32), ("ij_share", C.c_int32), ("levels", C.c_int32),
-                ("rebuild_every", C.c_int32), ("walk_queue", C.c_int32), ("reserved0", C.c_int32),
+                ("rebuild_every", C.c_int32), ("walk_queue", C.c_int32), ("node_factor", C.c_int32),
                 ("eta", C.c_double), ("dt_max", C.c_double)]
 
 
@@ -95,7 +95,11 @@ def load(path: str | None = None):
     L.gt_set_integrator_state.argtypes = [P, P, P, P, P, C.c_double, I64, P]
     L.gt_predict.argtypes = [P, I64, P, P]
     L.gt_correct.argtypes = [P, P, I64, P, I64, P]
-    L.gt_get_state.argtypes = [P, P, P, P, P, P, P, P]
+    L.gt_get_state.argtypes = [P, P, P, P, P, P, P, P, P, P]
+    L.gt_advance.argtypes = [P, I64, C.POINTER(I64), P]
+    L.gt_profile.argtypes = [P, I32]
+    L.gt_get_timers.argtypes = [P, C.POINTER(C.c_double), C.POINTER(I64), P]
+    L.gt_kernel_launches.argtypes = [C.POINTER(I64)]
     L.gt_get_tree.argtypes = [P, P, P, P, P, P, C.POINTER(I64), P]
     L.gt_get_active.argtypes = [P, P, C.POINTER(I64), P]
     L.gt_sync_status.argtypes = [P, P]
@@ -133,6 +137,15 @@ def gt_measure_fp32_peak(stream: int | None = None) -> float:
     f = C.c_double(0.0)
     _check(load().gt_measure_fp32_peak(C.byref(f), stream), "gt_measure_fp32_peak")
     return float(f.value)
+
+
+PHASES = ("predict", "keys_sort", "permute", "build", "pseudo_j", "active", "walk", "correct")
+
+
+def gt_kernel_launches() -> int:
+    c = C.c_int64(0)
+    _check(load().gt_kernel_launches(C.byref(c)), "gt_kernel_launches")
+    return int(c.value)
 
 
 def _ptr(a):
@@ -213,9 +226,11 @@ class System:
         _check(load().gt_block_step(self._h, self._s()), "gt_block_step")
 
     def set_integrator_state(self, level, t0, aold, acc, dt_max: float, T: int):
-        arrs = [np.ascontiguousarray(level, np.uint8), np.ascontiguousarray(t0, np.int64),
-                np.ascontiguousarray(aold, np.float32),
-                None if acc is None else np.ascontiguousarray(acc, np.float32)]
+        def host(a, dt):
+            if a is None or hasattr(a, "data_ptr"):
+                return a
+            return np.ascontiguousarray(a, dt)
+        arrs = [host(level, np.uint8), host(t0, np.int64), host(aold, np.float32), host(acc, np.float32)]
         _check(load().gt_set_integrator_state(self._h, *[_ptr(a) for a in arrs], float(dt_max), int(T),
                                               self._s()), "gt_set_integrator_state")
 
@@ -226,13 +241,38 @@ class System:
         _check(load().gt_correct(self._h, _ptr(active), int(active.numel()), _ptr(acc), int(T), self._s()),
                "gt_correct")
 
-    def get_state(self) -> dict:
+    def advance(self, T_end: int) -> int:
+        k = C.c_int64(0)
+        _check(load().gt_advance(self._h, int(T_end), C.byref(k), self._s()), "gt_advance")
+        return int(k.value)
+
+    def advance_cycle(self) -> int:
+        """Block steps up to the next multiple of 2^(L-1) ticks (one full cycle)."""
+        span = 1 << (self.params.levels - 1)
+        T = self.stats()["T"]
+        return self.advance((T // span + 1) * span)
+
+    def profile(self, enable: bool = True):
+        _check(load().gt_profile(self._h, int(bool(enable))), "gt_profile")
+
+    def timers(self) -> dict:
+        ms = (C.c_double * len(PHASES))()
+        cnt = (C.c_int64 * len(PHASES))()
+        _check(load().gt_get_timers(self._h, ms, cnt, self._s()), "gt_get_timers")
+        return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
+
+    def get_state(self, out: dict | None = None) -> dict:
+        """State in internal order (host numpy arrays, or the caller's buffers in ``out``)."""
         n = self.n
-        out = {"pos": np.zeros((n, 3)), "vel": np.zeros((n, 3)), "acc": np.zeros((n, 4), np.float32),
-               "level": np.zeros(n, np.uint8), "t0": np.zeros(n, np.int64), "id": np.zeros(n, np.uint32)}
-        _check(load().gt_get_state(self._h, _ptr(out["pos"]), _ptr(out["vel"]), _ptr(out["acc"]),
-                                   _ptr(out["level"]), _ptr(out["t0"]), _ptr(out["id"]), self._s()),
-               "gt_get_state")
+        if out is None:
+            out = {"pos": np.zeros((n, 3)), "vel": np.zeros((n, 3)), "mass": np.zeros(n, np.float32),
+                   "acc": np.zeros((n, 4), np.float32),
+                   "aold": np.zeros(n, np.float32), "level": np.zeros(n, np.uint8),
+                   "t0": np.zeros(n, np.int64), "id": np.zeros(n, np.uint32)}
+        _check(load().gt_get_state(self._h, _ptr(out.get("pos")), _ptr(out.get("vel")), _ptr(out.get("mass")),
+                                   _ptr(out.get("acc")),
+                                   _ptr(out.get("aold")), _ptr(out.get("level")), _ptr(out.get("t0")),
+                                   _ptr(out.get("id")), self._s()), "gt_get_state")
         self.sync()
         return out
 

@@ -40,7 +40,7 @@ def test_binding_loads_and_strerror(libpath):
 
 def test_struct_layout_matches_header(libpath):
     from paper_1610_07279_gb300 import gothic
-    assert ctypes.sizeof(gothic.gt_params) == 64
+    assert ctypes.sizeof(gothic.gt_params) == 64 and gothic.gt_params.node_factor.offset == 44
     assert gothic.gt_params.eta.offset == 48
     assert ctypes.sizeof(gothic.gt_stats) == 96
 

@@ -69,10 +69,15 @@ def _oparams(O, prm):
 
 
 def _rel(a, r):
+    """|a - r| / |r| per particle; 0 where both vanish exactly (coincident particles)."""
     a = np.asarray(a, np.float64)
     num = np.linalg.norm(a[:, :3] - r[:, :3], axis=1)
     den = np.linalg.norm(r[:, :3], axis=1)
-    return num / den
+    out = np.full(num.shape, np.inf)
+    ok = den > 0
+    out[ok] = num[ok] / den[ok]
+    out[(den == 0) & (num == 0)] = 0.0
+    return out
 
 
 def _check_tree(t, ref):
@@ -88,11 +93,11 @@ def _check_tree(t, ref):
     assert np.array_equal(t["bj"].view(np.uint32), ref["bj"].view(np.uint32)), "bj"
 
 
-def _oracle_tree(O, pos, mass, leaf):
+def _oracle_tree(O, pos, mass, leaf, cap=None):
     p4 = _p4(pos, mass)
     key, box = O.keys(p4)
     order, skey = O.sort(key)
-    tree = O.build_tree(skey, leaf)
+    tree = O.build_tree(skey, leaf, cap=cap)
     jpos, bj = O.pseudo_j(tree, p4[order])
     return {"p4": p4, "order": order, "skey": skey, "tree": tree, "jpos": jpos, "bj": bj}
 
@@ -113,15 +118,26 @@ def _oracle_tree(O, pos, mass, leaf):
 def test_tree_bitexact(env, kind, n, leaf):
     torch, g, O = env
     pos, vel, mass, eps = _model(kind, n, seed=n)
-    s = g.System(n, _params(g, eps, leaf_max=leaf))
+    nf = 8 if kind == "clustered" else 2   # clumps of 4 equal positions chain to level 21
+    s = g.System(n, _params(g, eps, leaf_max=leaf, node_factor=nf))
     s.set_state(pos, vel, mass)
     s.build_tree()
     t = s.get_tree()
     s.sync()
-    _check_tree(t, _oracle_tree(O, pos, mass, leaf))
+    _check_tree(t, _oracle_tree(O, pos, mass, leaf, cap=nf * n + 2048))
     st = s.get_state()
     assert np.array_equal(st["id"], t["order"])
     assert np.array_equal(st["pos"], pos[t["order"]])   # the permutation moved FP64 state exactly
+    s.close()
+
+
+def test_tree_node_overflow_is_reported(env):
+    torch, g, O = env
+    pos, vel, mass, eps = _model("clustered", 20000, 20000)
+    s = g.System(20000, _params(g, eps, leaf_max=3, node_factor=1))
+    s.set_state(pos, vel, mass)
+    s.build_tree()
+    assert s.status() == g.GT_EOVERFLOW
     s.close()
 
 
@@ -319,13 +335,12 @@ def test_checkpoint_resume_bitexact(env):
     ck = a.get_state()
     T = a.stats()["T"]
     dt_max = a.stats()["dt_max"]
-    aold = np.linalg.norm(ck["acc"][:, :3].astype(np.float64), axis=1).astype(np.float32)
     for _ in range(6):
         a.block_step()
     end_a = a.get_state()
     b = g.System(n, prm)
     b.set_state(ck["pos"], ck["vel"], mass[ck["id"]])
-    b.set_integrator_state(ck["level"], ck["t0"], aold, ck["acc"], dt_max, T)
+    b.set_integrator_state(ck["level"], ck["t0"], ck["aold"], ck["acc"], dt_max, T)
     for _ in range(6):
         b.block_step()
     end_b = b.get_state()
