@@ -251,6 +251,32 @@ GT_API int gt_get_stats(gt_system *sys, gt_stats *out, gt_stream stream);
  * Synchronises; ~10 ms. */
 GT_API int gt_measure_fp32_peak(double *flops, gt_stream stream);
 
+/* ---- sort without allocation ------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory when they need the sort: code running inside
+ * another framework's memory budget, loops that must not pay cudaMalloc's
+ * implicit device synchronisation, or host code that cannot own CUDA
+ * allocations at all.
+ *
+ * Sorts n (key, value) pairs in place by key, stably (equal keys keep their
+ * order), with the same radix-sort kernels gt_build_tree uses.  d_keys (n
+ * uint64) and d_vals (n uint32) are device arrays owned by the caller; they
+ * receive the sorted pairs.  The scratch the sort needs (the alternate key and
+ * value buffers, per-tile digit histograms and a control word) lives in one
+ * file-scope device array of the library, sized for GT_NOALLOC_SORT_MAX pairs
+ * (about 12.3 MiB, held on every GPU that loads the library until the process
+ * exits); nothing is allocated or freed by the call.
+ *   - n > GT_NOALLOC_SORT_MAX: rejected with GT_EINVAL before any device work.
+ *   - The first call on a device looks up the array's device address (once per
+ *     device, with that device current); make that first call before any stream
+ *     capture.
+ *   - Every call uses the same array: calls that overlap on the GPU (on two
+ *     streams, or from two threads) race and corrupt each other's results.
+ *     Serialise them on one stream.
+ * Asynchronous on the stream; GT_ECUDA if a launch fails. */
+#define GT_NOALLOC_SORT_MAX (1 << 20)
+GT_API int gt_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals, int64_t n, gt_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,6 +9,8 @@
 //               match/popc ranking), a local sort in shared memory, then coalesced
 //               writes of each digit run to its global slot       (reads and writes 12 B/key)
 // HBM-bound: 32 B per key per pass plus the small tile histograms.
+#include <mutex>
+
 #include "gt_internal.cuh"
 
 namespace {
@@ -179,4 +181,69 @@ void gt_launch_sort(SortBufs &b, int64_t n, DevCtl *ctl, cudaStream_t st) {
                                                     b.val[src], (unsigned long long *)b.key[dst],
                                                     b.val[dst], b.tile_hist, b.digit_base, ntiles); gt_note_launches(1); }
     }
+}
+
+// ---- sort without allocation (gt_sort_pairs_noalloc) -----------------------------
+// All scratch of one sort of up to GT_NOALLOC_SORT_MAX pairs lives in this array:
+// [control block | alternate keys | alternate values | tile histograms | digit bases |
+// digit totals].  Host code must not use the symbol as an address: the device
+// address is looked up once per device below.
+namespace {
+
+constexpr size_t NA_ALIGN = 256;
+constexpr size_t na_up(size_t b) { return (b + NA_ALIGN - 1) / NA_ALIGN * NA_ALIGN; }
+constexpr size_t NA_TILES = (GT_NOALLOC_SORT_MAX + TILE - 1) / TILE;
+constexpr size_t NA_OFF_KEY = na_up(sizeof(DevCtl));
+constexpr size_t NA_OFF_VAL = NA_OFF_KEY + na_up((size_t)GT_NOALLOC_SORT_MAX * sizeof(unsigned long long));
+constexpr size_t NA_OFF_HIST = NA_OFF_VAL + na_up((size_t)GT_NOALLOC_SORT_MAX * sizeof(uint32_t));
+constexpr size_t NA_OFF_BASE = NA_OFF_HIST + na_up(R * NA_TILES * sizeof(uint32_t));
+constexpr size_t NA_OFF_TOTAL = NA_OFF_BASE + na_up(R * sizeof(uint32_t));
+constexpr size_t NA_BYTES = NA_OFF_TOTAL + na_up(R * sizeof(uint32_t));
+
+__device__ __align__(256) unsigned char g_noalloc_sort_scratch[NA_BYTES];
+
+constexpr int NA_MAX_DEVICES = 256;
+std::mutex g_na_mu;
+char *g_na_addr[NA_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device (looked up once per device).
+int noalloc_scratch(char **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GT_ECUDA;
+    if (dev < 0 || dev >= NA_MAX_DEVICES) return GT_EINVAL;
+    std::lock_guard<std::mutex> lock(g_na_mu);
+    if (!g_na_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_sort_scratch) != cudaSuccess || !p) return GT_ECUDA;
+        gt_sort_init();  // the scatter kernel's shared-memory limit, on this device
+        g_na_addr[dev] = (char *)p;
+    }
+    *out = g_na_addr[dev];
+    return GT_OK;
+}
+
+}  // namespace
+
+extern "C" int gt_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals, int64_t n, gt_stream stream) {
+    if (n < 0 || (n > 0 && (!d_keys || !d_vals))) return GT_EINVAL;
+    if (n > GT_NOALLOC_SORT_MAX) return GT_EINVAL;  // larger than the static scratch
+    char *base = nullptr;
+    const int rc = noalloc_scratch(&base);
+    if (rc != GT_OK) return rc;
+    if (n <= 1) return GT_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    DevCtl *ctl = (DevCtl *)base;
+    // the digit scan's last-block counter must start at zero (a previous call may
+    // have been cut short); everything else is fully written before it is read
+    if (cudaMemsetAsync(&ctl->sort_done, 0, sizeof(ctl->sort_done), st) != cudaSuccess) return GT_ECUDA;
+    SortBufs b;
+    b.key[0] = d_keys;
+    b.val[0] = d_vals;
+    b.key[1] = (uint64_t *)(base + NA_OFF_KEY);
+    b.val[1] = (uint32_t *)(base + NA_OFF_VAL);
+    b.tile_hist = (uint32_t *)(base + NA_OFF_HIST);
+    b.digit_base = (uint32_t *)(base + NA_OFF_BASE);
+    b.digit_total = (uint32_t *)(base + NA_OFF_TOTAL);
+    gt_launch_sort(b, n, ctl, st);  // an even number of passes leaves the result in d_keys/d_vals
+    return cudaGetLastError() == cudaSuccess ? GT_OK : GT_ECUDA;
 }

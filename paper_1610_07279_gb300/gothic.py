@@ -100,6 +100,7 @@ def load(path: str | None = None):
     L.gt_profile.argtypes = [P, I32]
     L.gt_get_timers.argtypes = [P, C.POINTER(C.c_double), C.POINTER(I64), P]
     L.gt_kernel_launches.argtypes = [C.POINTER(I64)]
+    L.gt_sort_pairs_noalloc.argtypes = [P, P, I64, P]
     L.gt_get_tree.argtypes = [P, P, P, P, P, P, C.POINTER(I64), P]
     L.gt_get_active.argtypes = [P, P, C.POINTER(I64), P]
     L.gt_sync_status.argtypes = [P, P]
@@ -146,6 +147,16 @@ def gt_kernel_launches() -> int:
     c = C.c_int64(0)
     _check(load().gt_kernel_launches(C.byref(c)), "gt_kernel_launches")
     return int(c.value)
+
+
+GT_NOALLOC_SORT_MAX = 1 << 20
+
+
+def gt_sort_pairs_noalloc(d_keys, d_vals, n: int, stream: int | None = None):
+    """Stable in-place sort of n (uint64 key, uint32 value) device pairs by key, using
+    the library's static scratch instead of any allocation (n <= GT_NOALLOC_SORT_MAX)."""
+    st = stream if stream is not None else _current_stream()
+    _check(load().gt_sort_pairs_noalloc(_ptr(d_keys), _ptr(d_vals), int(n), st), "gt_sort_pairs_noalloc")
 
 
 def _ptr(a):
