@@ -62,7 +62,8 @@ def config_dict(args, eps):
     return {"workload": f"Andromeda-like three-component model (bulge 3%, disk 5%, NFW halo 92%), "
                         f"N={args.n}, one full block-step cycle per step, tree rebuilt every block step",
             "n": args.n, "levels": args.levels, "mac": "acceleration", "delta_acc": 2.0 ** -7,
-            "eps": eps, "leaf_max": 16, "group_max": 32, "ij_share": 1,
+            "eps": eps, "leaf_max": 16, "group_max": 32, "ij_share": "per group",
+            "groups": "tree cells with at most 32 actives",
             "l2": "inputs larger than L2 (particle state ~1.7 GB, nodes ~0.3 GB)"}
 
 
@@ -134,21 +135,22 @@ def cpu_sample(pos, mass, eps, groups: int, seed: int = 7):
     sp4 = np.ascontiguousarray(p4[order])
     tree = O.build_tree(skey, prm.leaf_max)
     jpos, bj = O.pseudo_j(tree, sp4)
+    active = np.arange(n, dtype=np.uint32)
+    starts = O.group_starts(tree, n, active, prm.group_max, prm.group_mode)
     t_build = time.perf_counter() - t0
-    ng = -(-n // prm.group_max)
+    ng = len(starts) - 1
     rng = np.random.default_rng(seed)
     gids = np.sort(rng.choice(ng, min(groups, ng), replace=False)).astype(np.int64)
-    active = np.arange(n, dtype=np.uint32)
     # |a_old| of the sampled members from an opening-angle pass (setup, not timed)
-    gI, gamin = O.groups(active, prm.group_max, sp4, None)
-    boot, _, _ = O.walk(tree, jpos, bj, sp4, active, prm.group_max, gI, gamin, 0, prm.theta,
+    gI, gamin = O.groups(starts, active, sp4, None)
+    boot, _, _ = O.walk(tree, jpos, bj, sp4, active, starts, gI, gamin, 0, prm.theta,
                         prm.delta_acc, prm.eps, prm.G, group_ids=gids)
     aold = np.zeros(n, np.float32)
     rows = np.isfinite(boot[:, 0])
-    aold[rows] = O.amag(boot[rows].astype(np.float32)).astype(np.float32)
-    gI, gamin = O.groups(active, prm.group_max, sp4, aold)
+    aold[rows] = O.aold_of(boot[rows].astype(np.float32))
+    gI, gamin = O.groups(starts, active, sp4, aold)
     t1 = time.perf_counter()
-    acc, inter, _ = O.walk(tree, jpos, bj, sp4, active, prm.group_max, gI, gamin, 1, prm.theta,
+    acc, inter, _ = O.walk(tree, jpos, bj, sp4, active, starts, gI, gamin, 1, prm.theta,
                            prm.delta_acc, prm.eps, prm.G, group_ids=gids)
     t_walk = time.perf_counter() - t1
     n_inter = int(inter[inter >= 0].sum())

@@ -68,11 +68,15 @@ typedef struct gt_params {
     float eps;          /* Plummer softening of Eq. (1)                            */
     float G;            /* gravitational constant of Eq. (1)                       */
     int32_t leaf_max;   /* a cell with more particles than this is split (<= 21 levels) */
-    int32_t group_max;  /* i-particles per group sharing one walk (Sec. 2.3)        */
-    int32_t ij_share;   /* S: threads sharing one i-particle (Sec. 2.5), 1..32, power of 2;
-                           group_max must be <= 32 / ij_share                       */
+    int32_t group_max;  /* at most this many i-particles share one walk (Sec. 2.3), <= 32 */
+    int32_t ij_share;   /* S: threads sharing one i-particle (Sec. 2.5): 1..32, a power of
+                           2 with group_max <= 32 / S; or 0 = per group, 32 / (members
+                           rounded up to a power of two)                           */
     int32_t levels;     /* L: number of block-step levels, 1..30 (Sec. 1)          */
-    int32_t rebuild_every; /* rebuild the tree every n block steps (Sec. 2.6); 1 = always */
+    int32_t rebuild_every; /* rebuild the tree every n block steps (Sec. 2.6); 1 = always;
+                              0 = automatic: the interval model of gt_rebuild_interval fed
+                              with the measured walk and rebuild times (synchronises the
+                              stream once per block step)                             */
     int32_t walk_queue; /* per-warp cell queue capacity, power of 2 (Sec. 2.3); >= 8192
                            leaves room for the depth-first fallback that bounds it */
     int32_t node_factor;   /* tree-cell capacity = node_factor * n + 2048 (>= 1); tight
@@ -80,7 +84,15 @@ typedef struct gt_params {
                               level 21 and may need more than the default 2 */
     double eta;         /* step accuracy: dt_i = sqrt(2 eta eps / |a_i|)           */
     double dt_max;      /* longest step, a power of two; <= 0: derived at gt_start */
+    int32_t group_mode; /* GT_GROUP_CELLS (default): a group is the actives of one tree
+                           cell holding at most group_max of them, so it never straddles
+                           distant regions (Sec. 2.4); GT_GROUP_RUNS: consecutive runs of
+                           group_max actives in the given order                    */
+    int32_t reserved1;
 } gt_params;
+
+#define GT_GROUP_RUNS 0
+#define GT_GROUP_CELLS 1
 
 /* Counters and state read back by gt_get_stats (synchronises the stream). */
 typedef struct gt_stats {
@@ -106,8 +118,8 @@ GT_API const char *gt_strerror(int status);
 
 /* The paper's fiducial parameters: acceleration MAC with Delta_acc = 2^-7
  * (Sec. 3.3), theta = 0.5 for the bootstrap pass, G = 1, eps = 1/64,
- * leaf_max = 16, group_max = 32, S = 1, L = 8, eta = 0.025, queue 16384,
- * node_factor 2. */
+ * leaf_max = 16, group_max = 32, S = 0 (per group), L = 8, eta = 0.025,
+ * queue 16384, node_factor 2, cell grouping, automatic rebuild interval. */
 GT_API int gt_default_params(gt_params *prm);
 
 /* Bytes of device workspace a system of n particles needs (n >= 0). */
@@ -147,7 +159,9 @@ GT_API int gt_build_tree(gt_system *sys, gt_stream stream);
  * lambda r_JI (Eqs. 6-7) and the Plummer-softened sums of Eq. (1) run over the
  * accepted cells and the particles of opened leaves.
  *   d_active  n_active internal indices (uint32), or NULL for all particles
- *             (then n_active must be n).  Groups follow the given order.
+ *             (then n_active must be n).  With cell grouping the list must be
+ *             strictly increasing (else GT_EINVAL is latched); with run grouping
+ *             groups follow the given order.
  *   d_aold    n FP32 |a_old| by internal index (the acceleration MAC needs it),
  *             or NULL to use the system's own.
  *   d_acc     n_active x 4 FP32 output (ax, ay, az, potential), in d_active order.
@@ -217,6 +231,17 @@ GT_API int gt_get_timers(gt_system *sys, double *ms_out, int64_t *launches_out, 
 
 /* Kernels launched by this library since load (all systems). */
 GT_API int gt_kernel_launches(int64_t *count);
+
+/* Tree-rebuild interval model (Sec. 2.6, Eqs. 8-14; Appendix C).  Host only.
+ * t_walk[0..n-1]: measured walk times of the n block steps since the last
+ * rebuild (n >= 3); t_make: the rebuild's time.  Fits the linear, power-law and
+ * parabolic growth models by least squares, keeps the one with the smallest
+ * reduced chi^2 (sigma_i = 1) in *model (0 linear, 1 power law, 2 parabolic),
+ * its coefficients in coef[3] (may be NULL: t1, dt | t1, r | t1, b, a), and the
+ * interval that minimises the mean time per step in *n_opt (1e6 when the model
+ * has no minimum, i.e. no rebuild is due). */
+GT_API int gt_rebuild_interval(const double *t_walk, int n, double t_make, int *model, double *n_opt,
+                               double *coef);
 
 /* Copy the state out in internal order.  Any pointer may be NULL to skip it;
  * any may be host or device memory.  p_pos, p_vel n x 3 FP64 (velocity is the

@@ -73,13 +73,17 @@ def _declare(L):
     L.or_build.restype = I64
     L.or_pseudo_j.argtypes = [I64, P, P, P, P, P, P, P]
     L.or_pseudo_j.restype = I32
-    L.or_groups.argtypes = [I64, P, I32, P, P, P, P]
-    L.or_walk.argtypes = [I64, P, P, P, P, P, P, P, I64, P, I32, P, P, I32, F, F, F, F,
+    L.or_active_prefix.argtypes = [I64, I64, P, P]
+    L.or_group_starts.argtypes = [I64, P, P, P, P, P, I32, P]
+    L.or_group_starts.restype = I64
+    L.or_groups.argtypes = [I64, P, P, P, P, P, P]
+    L.or_walk.argtypes = [I64, P, P, P, P, P, P, P, I64, P, P, P, P, I32, F, F, F, F,
                           I64, P, P, P, P]
     L.or_walk.restype = I32
     L.or_dtmax_exponent.argtypes = [I64, P, D, D]
     L.or_dtmax_exponent.restype = I32
-    L.or_amag.argtypes = [I64, P, P]
+    L.or_a2.argtypes = [I64, P, P]
+    L.or_aold.argtypes = [I64, P, P]
     L.or_init_levels.argtypes = [I64, P, P, D, D, I32, I32, D, P, P, P, P]
     L.or_predict.argtypes = [I64, P, P, P, P, I64, D, P]
     L.or_correct.argtypes = [I64, P, P, I64, D, I32, I32, D, D, P, P, P, P, P, P]
@@ -87,8 +91,8 @@ def _declare(L):
     L.or_morton3.restype = C.c_uint64
     L.or_mac_accept.argtypes = [I32, F, F, F, F, P, P, F]
     L.or_mac_accept.restype = I32
-    L.or_level_from_amag.argtypes = [D, D, D, I32, I32]
-    L.or_level_from_amag.restype = I32
+    L.or_level_from_a2.argtypes = [D, D, D, I32, I32]
+    L.or_level_from_a2.restype = I32
 
 
 def _p(a):
@@ -117,6 +121,7 @@ class Params:
     levels: int = 8
     eta: float = 0.025
     dt_max: float = 0.0        # 0: derived at start as a power of two
+    group_mode: int = 1        # 1: groups bounded by tree cells; 0: runs of group_max actives
 
 
 def f32(x):
@@ -190,25 +195,48 @@ def pseudo_j(tree: dict, sp4: np.ndarray):
     return jpos, bj
 
 
-def groups(active: np.ndarray, gmax: int, sp4: np.ndarray, aold=None):
+def active_prefix(n: int, active) -> np.ndarray:
+    active = _c(active, np.uint32)
+    P = np.zeros(n + 1, np.uint32)
+    lib().or_active_prefix(n, active.shape[0], _p(active), _p(P))
+    return P
+
+
+def group_starts(tree: dict, n: int, active, gmax: int, mode: int = 1) -> np.ndarray:
+    """First active position of every group, plus n_active at the end.
+
+    mode 1: groups bounded by tree cells (Sec. 2.4); mode 0: consecutive runs of gmax."""
+    active = _c(active, np.uint32)
+    na = active.shape[0]
+    if mode == 0 or tree["n_nodes"] == 0:
+        return np.append(np.arange(0, na, gmax, dtype=np.uint32), np.uint32(na))
+    P = active_prefix(n, active)
+    starts = np.zeros(na + 1, np.uint32)
+    ng = lib().or_group_starts(tree["n_nodes"], _p(tree["first"]), _p(tree["count"]), _p(tree["child"]),
+                               _p(tree["parent"]), _p(P), int(gmax), _p(starts))
+    return starts[:ng + 1].copy()
+
+
+def groups(starts, active, sp4: np.ndarray, aold=None):
+    starts = _c(starts, np.uint32)
     active = _c(active, np.uint32)
     sp4 = _c(sp4, np.float32)
-    na = active.shape[0]
-    ng = (na + gmax - 1) // gmax
+    ng = starts.shape[0] - 1
     gI = np.zeros((ng, 4), np.float32)
     gamin = np.zeros(ng, np.float32)
     ao = None if aold is None else _c(aold, np.float32)
-    lib().or_groups(na, _p(active), int(gmax), _p(sp4), _p(ao), _p(gI), _p(gamin))
+    lib().or_groups(ng, _p(starts), _p(active), _p(sp4), _p(ao), _p(gI), _p(gamin))
     return gI, gamin
 
 
-def walk(tree: dict, jpos, bj, sp4, active, gmax: int, gI, gamin, mac: int, theta: float,
+def walk(tree: dict, jpos, bj, sp4, active, starts, gI, gamin, mac: int, theta: float,
          delta_acc: float, eps: float, G: float, group_ids=None):
     """Tree walk for the listed groups (all if None).  Returns (acc, inter, ntest)."""
     active = _c(active, np.uint32)
+    starts = _c(starts, np.uint32)
     sp4 = _c(sp4, np.float32)
     na = active.shape[0]
-    ng = (na + gmax - 1) // gmax
+    ng = starts.shape[0] - 1
     gids = None if group_ids is None else _c(group_ids, np.int64)
     n_eval = ng if gids is None else gids.shape[0]
     acc = np.full((na, 4), np.nan, np.float64)
@@ -216,7 +244,7 @@ def walk(tree: dict, jpos, bj, sp4, active, gmax: int, gI, gamin, mac: int, thet
     ntest = np.zeros(n_eval, np.int64)
     rc = lib().or_walk(tree["n_nodes"], _p(_c(jpos, np.float32)), _p(_c(bj, np.float32)),
                        _p(tree["first"]), _p(tree["count"]), _p(tree["child"]), _p(tree["nchild"]),
-                       _p(sp4), na, _p(active), int(gmax), _p(_c(gI, np.float32)),
+                       _p(sp4), na, _p(active), _p(starts), _p(_c(gI, np.float32)),
                        _p(_c(gamin, np.float32)), int(mac), f32(theta), f32(delta_acc), f32(eps),
                        f32(G), n_eval, _p(gids), _p(acc), _p(inter), _p(ntest))
     if rc != 0:
@@ -232,16 +260,25 @@ def predict(r0, vh, t0, mass, T: int, dt_min: float) -> np.ndarray:
     return p4
 
 
-def amag(acc4) -> np.ndarray:
+def a2(acc4) -> np.ndarray:
+    """|a|^2 in FP64 from FP32 components, (ax^2 + ay^2) + az^2."""
     acc4 = _c(acc4, np.float32)
     out = np.zeros(acc4.shape[0], np.float64)
-    lib().or_amag(acc4.shape[0], _p(acc4), _p(out))
+    lib().or_a2(acc4.shape[0], _p(acc4), _p(out))
     return out
 
 
-def dtmax_exponent(amag_arr, eta: float, eps: float) -> int:
-    a = _c(amag_arr, np.float64)
-    return int(lib().or_dtmax_exponent(a.shape[0], _p(a), float(eta), float(eps)))
+def aold_of(acc4) -> np.ndarray:
+    """|a_old| = sqrtf((float)|a|^2)."""
+    acc4 = _c(acc4, np.float32)
+    out = np.zeros(acc4.shape[0], np.float32)
+    lib().or_aold(acc4.shape[0], _p(acc4), _p(out))
+    return out
+
+
+def dtmax_exponent(acc4, eta: float, eps: float) -> int:
+    acc4 = _c(acc4, np.float32)
+    return int(lib().or_dtmax_exponent(acc4.shape[0], _p(acc4), float(eta), float(eps)))
 
 
 def init_levels(acc4, vel, eta, eps, M, L, dt_max):
@@ -280,8 +317,8 @@ def mac_accept(mac: int, theta: float, delta_acc: float, amin: float, G: float, 
                                     _p(gi), _p(jp), f32(bJ)))
 
 
-def level_from_amag(amag_v: float, eta: float, eps: float, M: int, L: int) -> int:
-    return int(lib().or_level_from_amag(float(amag_v), float(eta), float(eps), int(M), int(L)))
+def level_from_a2(a2: float, eta: float, eps: float, M: int, L: int) -> int:
+    return int(lib().or_level_from_a2(float(a2), float(eta), float(eps), int(M), int(L)))
 
 
 # ------------------------------------------------------------------ pipelines
@@ -304,13 +341,14 @@ def tree_force(p4: np.ndarray, prm: Params, aold=None, active=None, mac=None, th
     if active is None:
         active = np.arange(n, dtype=np.uint32)
     saold = None if aold is None else _c(aold, np.float32)[order]
-    gI, gamin = groups(active, prm.group_max, sp4, saold)
+    starts = group_starts(tree, n, active, prm.group_max, prm.group_mode)
+    gI, gamin = groups(starts, active, sp4, saold)
     m = prm.mac if mac is None else mac
     th = prm.theta if theta is None else theta
-    acc, inter, ntest = walk(tree, jpos, bj, sp4, active, prm.group_max, gI, gamin, m, th,
+    acc, inter, ntest = walk(tree, jpos, bj, sp4, active, starts, gI, gamin, m, th,
                              prm.delta_acc, prm.eps, prm.G, group_ids)
     return {"key": key, "box": box, "order": order, "skey": skey, "sp4": sp4, "tree": tree,
-            "jpos": jpos, "bj": bj, "active": active, "gI": gI, "gamin": gamin,
+            "jpos": jpos, "bj": bj, "active": active, "starts": starts, "gI": gI, "gamin": gamin,
             "acc": acc, "inter": inter, "ntest": ntest}
 
 
@@ -321,8 +359,7 @@ def bootstrap_aold(p4: np.ndarray, prm: Params) -> np.ndarray:
     silent); the first pass uses the opening-angle MAC and its |a| seeds a_old.
     """
     r = tree_force(p4, prm, mac=0)
-    acc32 = r["acc"].astype(np.float32)
-    am = amag(acc32).astype(np.float32)
+    am = aold_of(r["acc"].astype(np.float32))
     out = np.empty_like(am)
     out[r["order"]] = am
     return out
@@ -373,11 +410,10 @@ class BlockStepSim:
         self._permute(r["order"])
         acc32 = r["acc"].astype(np.float32)
         self.interactions += int(r["inter"].sum())
-        am = amag(acc32)
         if prm.dt_max > 0:
             self.M = int(np.frexp(prm.dt_max)[1] - 1)
         else:
-            self.M = dtmax_exponent(am, prm.eta, prm.eps)
+            self.M = dtmax_exponent(acc32, prm.eta, prm.eps)
         self.dt_max = float(np.ldexp(1.0, self.M))
         vel = self.vh
         self.level, self.t0, self.vh, self.aold = init_levels(acc32, vel, prm.eta, prm.eps,
@@ -403,8 +439,9 @@ class BlockStepSim:
         tree = build_tree(skey, prm.leaf_max)
         jpos, bj = pseudo_j(tree, sp4)
         active = np.nonzero(self.t0 + self.ticks(self.level) == T)[0].astype(np.uint32)
-        gI, gamin = groups(active, prm.group_max, sp4, self.aold)
-        acc, inter, _ = walk(tree, jpos, bj, sp4, active, prm.group_max, gI, gamin, prm.mac,
+        starts = group_starts(tree, self.n, active, prm.group_max, prm.group_mode)
+        gI, gamin = groups(starts, active, sp4, self.aold)
+        acc, inter, _ = walk(tree, jpos, bj, sp4, active, starts, gI, gamin, prm.mac,
                              prm.theta, prm.delta_acc, prm.eps, prm.G)
         acc32 = acc.astype(np.float32)
         correct(active, acc32, T, self.dt_max, self.M, self.L, prm.eta, prm.eps, self.r0,

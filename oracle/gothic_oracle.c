@@ -36,12 +36,12 @@ int or_num_threads(void) {
 #endif
 }
 
-/* Smallest float >= v, for v >= 0: an enclosing radius rounded outwards. */
-static float round_up_to_float(double v) {
-    float f = (float)v;
-    if ((double)f < v) f = nextafterf(f, INFINITY);
-    return f;
-}
+/* Enclosing radii are evaluated in FP32 and widened by (1 + 2^-20): an FP32
+ * distance carries a few roundings of at most 2^-24 each, so the widened radius
+ * still holds every particle (P:183 asks only for a sphere that contains them). */
+#define RADIUS_MARGIN (1.0f + 0x1p-20f)
+
+static float norm3f(float dx, float dy, float dz) { return sqrtf((dx * dx + dy * dy) + dz * dz); }
 
 /* ------------------------------------------------------------------------- */
 /* O1. Direct summation, Eq. (1): a_i = sum_{j != i} G m_j (r_j - r_i) /     */
@@ -214,16 +214,15 @@ int64_t or_build(int64_t n, const uint64_t *skey, int leaf_max, int64_t cap,
 /* ------------------------------------------------------------------------- */
 /* A5. Pseudo j-particles (Sec. 2.1, Fig. 1): m_J = sum m, r_J = sum m r /   */
 /* m_J, and b_J the radius of a sphere about r_J that holds every particle   */
-/* of the cell.  Sums are FP64: a leaf adds its particles in sorted order, a */
-/* cell adds its children's sums in child order; r_J and m_J are then        */
-/* rounded to FP32.  b_J (FP64, rounded up to FP32): for a leaf, the largest */
-/* |r - r_J| over its particles; for a cell, the largest |r_c - r_J| + b_c   */
-/* over its children c.  Children have larger node numbers than parents, so  */
-/* a reverse sweep is bottom-up.                                             */
+/* of the cell.  The sums are FP64: a leaf adds its particles in sorted      */
+/* order, a cell adds its children's sums in child order.  m_J = (float)M;   */
+/* r_J is the FP32 quotient (float)S / (float)M (the paper keeps r_J in      */
+/* single precision, Sec. 2); a cell of one particle is that particle. */
+/* b_J (FP32): a leaf's largest |r - r_J|, a cell's largest |r_c - r_J| + b_c */
+/* over its children, times (1 + 2^-20).  Children have larger node numbers  */
+/* than parents, so a reverse sweep is bottom-up.                            */
 /* jpos out: nn x (x, y, z, m) FP32; bj out: nn FP32.                        */
 /* ------------------------------------------------------------------------- */
-static double dist3(double dx, double dy, double dz) { return sqrt((dx * dx + dy * dy) + dz * dz); }
-
 int or_pseudo_j(int64_t nn, const uint32_t *first, const uint32_t *count, const int32_t *child,
                 const uint8_t *nchild, const float *sp4, float *jpos, float *bj) {
     double *sum = (double *)malloc((size_t)(nn > 0 ? nn : 1) * 4 * sizeof(double));
@@ -248,50 +247,97 @@ int or_pseudo_j(int64_t nn, const uint32_t *first, const uint32_t *count, const 
             }
         }
         sum[4 * c + 0] = m; sum[4 * c + 1] = sx; sum[4 * c + 2] = sy; sum[4 * c + 3] = sz;
-        const float jx = (float)(sx / m), jy = (float)(sy / m), jz = (float)(sz / m);
+        float jx, jy, jz;
+        if (count[c] == 1) {
+            const uint32_t i = first[c];
+            jx = sp4[4 * i + 0]; jy = sp4[4 * i + 1]; jz = sp4[4 * i + 2];
+        } else {
+            const float mf = (float)m;
+            jx = (float)sx / mf; jy = (float)sy / mf; jz = (float)sz / mf;
+        }
         jpos[4 * c + 0] = jx; jpos[4 * c + 1] = jy; jpos[4 * c + 2] = jz; jpos[4 * c + 3] = (float)m;
-        double b = 0.0;
+        float b = 0.0f;
         if (child[c] < 0) {
-            double d2max = 0.0;
+            float d2max = 0.0f;
             for (uint32_t i = first[c]; i < first[c] + count[c]; i++) {
-                const double dx = (double)sp4[4 * i + 0] - (double)jx;
-                const double dy = (double)sp4[4 * i + 1] - (double)jy;
-                const double dz = (double)sp4[4 * i + 2] - (double)jz;
-                const double d2 = (dx * dx + dy * dy) + dz * dz;
+                const float dx = sp4[4 * i + 0] - jx, dy = sp4[4 * i + 1] - jy, dz = sp4[4 * i + 2] - jz;
+                const float d2 = (dx * dx + dy * dy) + dz * dz;
                 if (d2 > d2max) d2max = d2;
             }
-            b = sqrt(d2max);
+            b = sqrtf(d2max);
         } else {
             for (int k = 0; k < nchild[c]; k++) {
                 const int64_t ch = child[c] + k;
-                const double e = dist3((double)jpos[4 * ch + 0] - (double)jx,
-                                       (double)jpos[4 * ch + 1] - (double)jy,
-                                       (double)jpos[4 * ch + 2] - (double)jz) + (double)bj[ch];
+                const float e = norm3f(jpos[4 * ch + 0] - jx, jpos[4 * ch + 1] - jy, jpos[4 * ch + 2] - jz) + bj[ch];
                 if (e > b) b = e;
             }
         }
-        bj[c] = round_up_to_float(b);
+        bj[c] = b * RADIUS_MARGIN;
     }
     free(sum);
     return 0;
 }
 
 /* ------------------------------------------------------------------------- */
-/* A6. Groups of i-particles and their pseudo i-particles (Sec. 2.3, Fig. 2; */
-/* the sphere about the geometric centre of the enclosing box, Appendix B    */
-/* "GEO").  Group g holds active[g*G .. min(n_active, (g+1)*G)).             */
-/*   r_I = 0.5f * (min + max) per axis in FP32;                              */
-/*   b_I = max |r_i - r_I| in FP64, rounded up to FP32;                      */
-/*   amin = min |a_old| over the group (the acceleration MAC needs one       */
-/*   |a_old| per group; the smallest is the conservative choice).            */
+/* A6a. Active prefix: P[i] = number of active particles (sorted indices,    */
+/* strictly increasing in `active`) below sorted index i, for i = 0..n.      */
+/* ------------------------------------------------------------------------- */
+void or_active_prefix(int64_t n, int64_t n_active, const uint32_t *active, uint32_t *P) {
+    int64_t k = 0;
+    for (int64_t i = 0; i <= n; i++) {
+        while (k < n_active && (int64_t)active[k] < i) k++;
+        P[i] = (uint32_t)k;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* A6b. Groups of i-particles (Sec. 2.3; Sec. 2.4: i-particles far apart are  */
+/* not unified into one group).  A group never straddles two tree cells: the */
+/* "group cells" are the cells whose active count A is at least 1 and at     */
+/* most gmax (or leaves, whatever A), and whose parent holds more than gmax  */
+/* actives (or that are the root).  Each group cell contributes its actives  */
+/* in key order, cut into runs of gmax.  Returns the number of groups; the   */
+/* first active position of every group, ascending, goes to starts (room    */
+/* for n_active + 1 entries); starts[ng] = P[n] is appended.                 */
+/* ------------------------------------------------------------------------- */
+static int cmp_u32(const void *a, const void *b) {
+    const uint32_t x = *(const uint32_t *)a, y = *(const uint32_t *)b;
+    return (x > y) - (x < y);
+}
+
+int64_t or_group_starts(int64_t nn, const uint32_t *first, const uint32_t *count, const int32_t *child,
+                        const int32_t *parent, const uint32_t *P, int gmax, uint32_t *starts) {
+    int64_t ng = 0;
+    for (int64_t c = 0; c < nn; c++) {
+        const uint32_t a0 = P[first[c]], A = P[first[c] + count[c]] - a0;
+        if (A == 0) continue;
+        if (parent[c] >= 0) {
+            const int32_t p = parent[c];
+            if (P[first[p] + count[p]] - P[first[p]] <= (uint32_t)gmax) continue;  /* inside a group cell */
+        }
+        if (A > (uint32_t)gmax && child[c] >= 0) continue;                          /* split further */
+        for (uint32_t s = a0; s < a0 + A; s += (uint32_t)gmax) starts[ng++] = s;
+    }
+    qsort(starts, (size_t)ng, sizeof(uint32_t), cmp_u32);
+    starts[ng] = nn > 0 ? P[first[0] + count[0]] : 0;
+    return ng;
+}
+
+/* ------------------------------------------------------------------------- */
+/* A6c. Pseudo i-particles (Sec. 2.3, Fig. 2): the sphere about the centre   */
+/* of the members' bounding box (Appendix B, "GEO").  Group g holds          */
+/* active[starts[g] .. starts[g+1]).                                          */
+/*   r_I = 0.5f (min + max) per axis (FP32);                                  */
+/*   b_I = the largest FP32 |r_i - r_I|, times (1 + 2^-20);                   */
+/*   amin = min |a_old| over the group (the acceleration MAC needs one |a_old| */
+/*   per group; the smallest is the conservative choice).                    */
 /* gI out: ng x (x, y, z, b_I); gamin out: ng.                               */
 /* ------------------------------------------------------------------------- */
-void or_groups(int64_t n_active, const uint32_t *active, int gmax, const float *sp4,
+void or_groups(int64_t ng, const uint32_t *starts, const uint32_t *active, const float *sp4,
                const float *aold, float *gI, float *gamin) {
-    const int64_t ng = (n_active + gmax - 1) / gmax;
 #pragma omp parallel for
     for (int64_t g = 0; g < ng; g++) {
-        const int64_t a0 = g * gmax, a1 = (a0 + gmax < n_active) ? a0 + gmax : n_active;
+        const int64_t a0 = starts[g], a1 = starts[g + 1];
         float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
         float am = INFINITY;
         for (int64_t k = a0; k < a1; k++) {
@@ -306,17 +352,15 @@ void or_groups(int64_t n_active, const uint32_t *active, int gmax, const float *
         }
         float c[3];
         for (int a = 0; a < 3; a++) c[a] = 0.5f * (mn[a] + mx[a]);
-        double d2max = 0.0;
+        float d2max = 0.0f;
         for (int64_t k = a0; k < a1; k++) {
             const uint32_t i = active[k];
-            const double dx = (double)sp4[4 * i + 0] - (double)c[0];
-            const double dy = (double)sp4[4 * i + 1] - (double)c[1];
-            const double dz = (double)sp4[4 * i + 2] - (double)c[2];
-            const double d2 = (dx * dx + dy * dy) + dz * dz;
+            const float dx = sp4[4 * i + 0] - c[0], dy = sp4[4 * i + 1] - c[1], dz = sp4[4 * i + 2] - c[2];
+            const float d2 = (dx * dx + dy * dy) + dz * dz;
             if (d2 > d2max) d2max = d2;
         }
         gI[4 * g + 0] = c[0]; gI[4 * g + 1] = c[1]; gI[4 * g + 2] = c[2];
-        gI[4 * g + 3] = round_up_to_float(sqrt(d2max));
+        gI[4 * g + 3] = sqrtf(d2max) * RADIUS_MARGIN;
         gamin[g] = am;
     }
 }
@@ -357,7 +401,8 @@ static int mac_accept(int mac, float theta, float dacc_amin, float G, const floa
 /* The member's own contribution to the potential (-G m_i/eps, present when  */
 /* it appears on its own list) is removed so that phi matches Eq. (1)'s      */
 /* j != i (the acceleration term of j = i is exactly zero).                  */
-/* groups: the ids to evaluate (all ng groups if NULL).                      */
+/* Group g holds active[starts[g] .. starts[g+1]); groups: the ids to       */
+/* evaluate (all ng groups if NULL).                                         */
 /* acc out: n_active x 4 doubles (ax, ay, az, phi) at the active positions   */
 /* of the evaluated groups; inter out: per active particle, list length;     */
 /* ntest out: per evaluated group, MAC tests made.                           */
@@ -365,7 +410,7 @@ static int mac_accept(int mac, float theta, float dacc_amin, float G, const floa
 /* ------------------------------------------------------------------------- */
 int or_walk(int64_t nn, const float *jpos, const float *bj, const uint32_t *first,
             const uint32_t *count, const int32_t *child, const uint8_t *nchild,
-            const float *sp4, int64_t n_active, const uint32_t *active, int gmax,
+            const float *sp4, int64_t n_active, const uint32_t *active, const uint32_t *starts,
             const float *gI, const float *gamin, int mac, float theta, float delta_acc,
             float eps, float G, int64_t n_eval, const int64_t *groups,
             double *acc, int64_t *inter, int64_t *ntest) {
@@ -420,7 +465,7 @@ int or_walk(int64_t nn, const float *jpos, const float *bj, const uint32_t *firs
                 }
             }
             if (ntest) ntest[e] = tests;
-            const int64_t a0 = g * gmax, a1 = (a0 + gmax < n_active) ? a0 + gmax : n_active;
+            const int64_t a0 = starts[g], a1 = starts[g + 1];
             const double eps2 = (double)eps * (double)eps;
             for (int64_t k = a0; k < a1; k++) {
                 const uint32_t i = active[k];
@@ -454,104 +499,120 @@ int or_walk(int64_t nn, const float *jpos, const float *bj, const uint32_t *firs
 }
 
 /* ------------------------------------------------------------------------- */
-/* Block time step (Sec. 1, block steps; Sec. 2.7, Eqs. 15-17).             */
+/* Block time step (Sec. 1; Sec. 2.7, Eqs. 15-17).                          */
 /* Levels k = 0 .. L-1 have steps dt_k = dt_max 2^-k, dt_max = 2^M.  Time is */
 /* an integer count of the finest step dt_{L-1}; level k spans               */
 /* ticks(k) = 2^(L-1-k) ticks.  Step criterion (the paper fixes none; the    */
 /* acceleration form of Springel 2005, whose MAC the paper adopts):          */
-/*   dt_i = sqrt(2 eta eps / |a_i|),  evaluated as sqrt(((2 eta) eps)/|a|).  */
-/* The level is the smallest k with dt_k <= dt_i, clamped to [0, L-1].  With */
-/* dt_i = f 2^e (frexp, f in [0.5, 1)) that is k = M - e + 1, exactly.       */
+/*   dt_i = sqrt(c / |a_i|),  c = 2 eta eps.                                  */
+/* The level is the smallest k with dt_k <= dt_i, clamped to [0, L-1].  Both */
+/* sides are positive, so this is dt_k^4 |a|^2 <= c^2, i.e.                  */
+/*   2^(4(M-k)) A2 <= c2,  A2 = (ax^2 + ay^2) + az^2,  c2 = c c  (FP64),      */
+/* decided exactly from the exponents and fractions (frexp) of A2 and c2.    */
+/* |a_old| = sqrtf((float)A2).                                               */
 /* ------------------------------------------------------------------------- */
-static int level_from_amag(double amag, double eta, double eps, int M, int L) {
-    if (!(amag > 0.0) || !isfinite(amag)) return 0;
-    const double dti = sqrt(((2.0 * eta) * eps) / amag);
-    if (!isfinite(dti)) return 0;
-    int e;
-    (void)frexp(dti, &e);
-    int k = M - e + 1;
+static int64_t floordiv4(int64_t d) { return d >= 0 ? d / 4 : -((-d + 3) / 4); }
+
+static int level_from_a2(double a2, double c2, int M, int L) {
+    if (!(a2 > 0.0) || !isfinite(a2)) return 0;
+    int ea, ec;
+    const double fa = frexp(a2, &ea), fc = frexp(c2, &ec);
+    /* level k qualifies iff 4k > D, or 4k == D and fa <= fc, with D = ea + 4M - ec */
+    const int64_t D = (int64_t)ea + 4 * (int64_t)M - ec;
+    const int64_t q = floordiv4(D);
+    int64_t k = (4 * q == D && fa <= fc) ? q : q + 1;
     if (k < 0) k = 0;
     if (k > L - 1) k = L - 1;
-    return k;
+    return (int)k;
 }
 
-/* log2 of the largest power of two not above the largest dt_i (init). */
-int or_dtmax_exponent(int64_t n, const double *amag, double eta, double eps) {
-    double best = 0.0;
-    for (int64_t i = 0; i < n; i++) {
-        if (!(amag[i] > 0.0)) continue;
-        const double dti = sqrt(((2.0 * eta) * eps) / amag[i]);
-        if (dti > best) best = dti;
-    }
-    if (!(best > 0.0) || !isfinite(best)) return 0;
-    int e;
-    (void)frexp(best, &e);
-    return e - 1;
+static double c2_of(double eta, double eps) {
+    const double c = (2.0 * eta) * eps;
+    return c * c;
 }
 
-/* |a| in FP64 from the FP32 components. */
-static double amag_of(const float *a) {
+static double a2_of(const float *a) {
     const double ax = a[0], ay = a[1], az = a[2];
-    return sqrt((ax * ax + ay * ay) + az * az);
+    return (ax * ax + ay * ay) + az * az;
 }
 
-void or_amag(int64_t n, const float *acc4, double *out) {
-    for (int64_t i = 0; i < n; i++) out[i] = amag_of(acc4 + 4 * i);
+void or_a2(int64_t n, const float *acc4, double *out) {
+    for (int64_t i = 0; i < n; i++) out[i] = a2_of(acc4 + 4 * i);
+}
+
+/* log2 dt_max at the start: the largest M with 2^M <= max_i dt_i, i.e. the   */
+/* largest M with 2^(4M) A2min <= c2 (A2min the smallest positive A2).        */
+int or_dtmax_exponent(int64_t n, const float *acc4, double eta, double eps) {
+    double a2min = INFINITY;
+    for (int64_t i = 0; i < n; i++) {
+        const double a2 = a2_of(acc4 + 4 * i);
+        if (a2 > 0.0 && a2 < a2min) a2min = a2;
+    }
+    if (!isfinite(a2min)) return 0;
+    int ea, ec;
+    const double fa = frexp(a2min, &ea), fc = frexp(c2_of(eta, eps), &ec);
+    /* M qualifies iff 4M < D, or 4M == D and fa <= fc, with D = ec - ea */
+    const int64_t D = (int64_t)ec - ea;
+    const int64_t q = floordiv4(D);
+    if (4 * q == D) return (int)(fa <= fc ? q : q - 1);
+    return (int)q;
 }
 
 /* Initial levels and first half kick (t = 0): v^{1/2} = v + (dt_k/2) a     */
-/* (Eq. 15 at n = 0).  acc4: n x 4 FP32.                                    */
+/* (Eq. 15 at n = 0), as one fused multiply-add.  acc4: n x 4 FP32.         */
 void or_init_levels(int64_t n, const float *acc4, const double *vel, double eta, double eps,
                     int M, int L, double dt_max, uint8_t *level, int64_t *t0, double *vh,
                     float *aold) {
+    const double c2 = c2_of(eta, eps);
     for (int64_t i = 0; i < n; i++) {
-        const double am = amag_of(acc4 + 4 * i);
-        const int k = level_from_amag(am, eta, eps, M, L);
+        const double a2 = a2_of(acc4 + 4 * i);
+        const int k = level_from_a2(a2, c2, M, L);
         const double hdt = 0.5 * ldexp(dt_max, -k);
-        for (int a = 0; a < 3; a++) vh[3 * i + a] = vel[3 * i + a] + hdt * (double)acc4[4 * i + a];
+        for (int a = 0; a < 3; a++) vh[3 * i + a] = fma(hdt, (double)acc4[4 * i + a], vel[3 * i + a]);
         level[i] = (uint8_t)k;
         t0[i] = 0;
-        aold[i] = (float)am;
+        aold[i] = sqrtf((float)a2);
     }
 }
 
 /* A8. Prediction of all j-particles to tick T (Eq. 16 with the elapsed time */
 /* T - t0 in place of dt_j; the stored v^{1/2} already holds the half kick). */
-/*   r(T) = r0 + ((T - t0) dt_min) v^{1/2}, FP64, then rounded to FP32.     */
+/*   r(T) = fma((T - t0) dt_min, v^{1/2}, r0) in FP64, then rounded to FP32. */
 void or_predict(int64_t n, const double *r0, const double *vh, const int64_t *t0,
                 const float *mass, int64_t T, double dt_min, float *p4) {
 #pragma omp parallel for
     for (int64_t i = 0; i < n; i++) {
         const double dt = (double)(T - t0[i]) * dt_min;
-        for (int a = 0; a < 3; a++) p4[4 * i + a] = (float)(r0[3 * i + a] + dt * vh[3 * i + a]);
+        for (int a = 0; a < 3; a++) p4[4 * i + a] = (float)fma(dt, vh[3 * i + a], r0[3 * i + a]);
         p4[4 * i + 3] = mass[i];
     }
 }
 
 /* A9. Correction of the active particles (Eq. 17), new level, and the next  */
 /* half kick.  For active particle i (sorted index active[k]) at tick T:     */
-/*   v     = v^{1/2} + (dt_old/2) a            (Eq. 17)                      */
-/*   k_new = from |a|; a shorter step is always taken; a longer one only by  */
+/*   v     = fma(dt_old/2, a, v^{1/2})          (Eq. 17)                     */
+/*   k_new = from A2; a shorter step is always taken; a longer one only by   */
 /*           one level and only when T is a multiple of the longer step      */
-/*   v^{1/2} <- v + (dt_new/2) a;  r0 <- r(T) (the predicted position);      */
-/*   t0 <- T;  a_old <- |a| (FP32).                                          */
+/*   v^{1/2} <- fma(dt_new/2, a, v);  r0 <- r(T) (the predicted position);   */
+/*   t0 <- T;  |a_old| <- sqrtf((float)A2).                                   */
 void or_correct(int64_t n_active, const uint32_t *active, const float *acc4, int64_t T,
                 double dt_max, int M, int L, double eta, double eps, double *r0, double *vh,
                 int64_t *t0, uint8_t *level, float *aold, float *acc_store) {
     const double dt_min = ldexp(dt_max, -(L - 1));
+    const double c2 = c2_of(eta, eps);
     for (int64_t k = 0; k < n_active; k++) {
         const uint32_t i = active[k];
         const float *a = acc4 + 4 * k;
         const int kold = level[i];
-        const double dt_old = ldexp(dt_max, -kold);
+        const double hold = 0.5 * ldexp(dt_max, -kold);
         const double dtp = (double)(T - t0[i]) * dt_min;
         double v[3];
         for (int c = 0; c < 3; c++) {
-            r0[3 * i + c] = r0[3 * i + c] + dtp * vh[3 * i + c];
-            v[c] = vh[3 * i + c] + (0.5 * dt_old) * (double)a[c];
+            r0[3 * i + c] = fma(dtp, vh[3 * i + c], r0[3 * i + c]);
+            v[c] = fma(hold, (double)a[c], vh[3 * i + c]);
         }
-        const double am = amag_of(a);
-        const int kc = level_from_amag(am, eta, eps, M, L);
+        const double a2 = a2_of(a);
+        const int kc = level_from_a2(a2, c2, M, L);
         int knew = kold;
         if (kc > kold) {
             knew = kc;
@@ -560,10 +621,10 @@ void or_correct(int64_t n_active, const uint32_t *active, const float *acc4, int
             if (T % span == 0) knew = kold - 1;
         }
         const double hdt = 0.5 * ldexp(dt_max, -knew);
-        for (int c = 0; c < 3; c++) vh[3 * i + c] = v[c] + hdt * (double)a[c];
+        for (int c = 0; c < 3; c++) vh[3 * i + c] = fma(hdt, (double)a[c], v[c]);
         level[i] = (uint8_t)knew;
         t0[i] = T;
-        aold[i] = (float)am;
+        aold[i] = sqrtf((float)a2);
         if (acc_store) memcpy(acc_store + 4 * (int64_t)i, a, 4 * sizeof(float));
     }
 }
@@ -576,6 +637,11 @@ int or_mac_accept(int mac, float theta, float delta_acc, float amin, float G, co
     return mac_accept(mac, theta, delta_acc * amin, G, gI, jp[0], jp[1], jp[2], jp[3], bJ);
 }
 
-int or_level_from_amag(double amag, double eta, double eps, int M, int L) {
-    return level_from_amag(amag, eta, eps, M, L);
+int or_level_from_a2(double a2, double eta, double eps, int M, int L) {
+    return level_from_a2(a2, c2_of(eta, eps), M, L);
+}
+
+/* |a_old| from FP32 accelerations: sqrtf((float)A2). */
+void or_aold(int64_t n, const float *acc4, float *out) {
+    for (int64_t i = 0; i < n; i++) out[i] = sqrtf((float)a2_of(acc4 + 4 * i));
 }

@@ -4,7 +4,9 @@
 #include <string.h>
 
 #include <atomic>
+#include <cmath>
 #include <new>
+#include <vector>
 
 #include "gt_internal.cuh"
 
@@ -18,17 +20,32 @@ struct PhaseTimers {
     cudaEvent_t b[GT_NPHASES]{}, e[GT_NPHASES]{};
     bool ran[GT_NPHASES]{};
     double ms[GT_NPHASES]{};
+    double last_ms[GT_NPHASES]{};  // the most recent execution of each phase
     long long cnt[GT_NPHASES]{};
+};
+
+// Automatic tree-rebuild interval (Sec. 2.6): walk times since the last rebuild,
+// normalised to the mean number of i-particles per block step (block steps vary
+// N_i by orders of magnitude; the fit is meant to see the tree ageing, not that).
+struct RebuildTuner {
+    std::vector<double> y;
+    double t_make = 0.0;
+    double nact_sum = 0.0;
+    long long nact_cnt = 0;
+    double n_opt = 1e6;
+    int model = -1;
+    long long since = 0;  // block steps on the current tree
 };
 
 struct gt_system {
     int64_t n = 0;
     PhaseTimers prof;
+    RebuildTuner tune;
     gt_params prm{};
     int dev = 0, nsm = 0;
     int walk_blocks = 0, walk_warps = 0;
     int cur = 0;
-    bool started = false, have_tree = false;
+    bool started = false, have_tree = false, last_rebuilt = false;
     long long steps = 0, rebuilds = 0;
     int64_t cap = 0;        // node capacity
     State st[2]{};
@@ -37,6 +54,10 @@ struct gt_system {
     Nodes nd{};
     unsigned long long *status = nullptr;
     uint32_t *active = nullptr;
+    uint32_t *prefix = nullptr;   // P[i] = actives below internal index i (n + 1 entries)
+    uint8_t *flags = nullptr;     // a caller's active list as flags
+    uint8_t *marks = nullptr;     // first active position of every group
+    uint32_t *gstart = nullptr;   // group starts (cell grouping)
     float4 *acc_out = nullptr;
     float *aold_tmp = nullptr;
     double *scratch3 = nullptr;
@@ -68,10 +89,11 @@ int check_params(const gt_params *p) {
     if (!p) return GT_EINVAL;
     if (p->mac != GT_MAC_OPENING_ANGLE && p->mac != GT_MAC_ACCELERATION) return GT_EINVAL;
     if (p->leaf_max < 1) return GT_EINVAL;
-    if (!pow2(p->ij_share) || p->ij_share > 32) return GT_EINVAL;
-    if (p->group_max < 1 || p->group_max > 32 / p->ij_share) return GT_EINVAL;
+    if (p->ij_share != 0 && (!pow2(p->ij_share) || p->ij_share > 32)) return GT_EINVAL;
+    if (p->group_max < 1 || p->group_max > 32 / (p->ij_share ? p->ij_share : 1)) return GT_EINVAL;
+    if (p->group_mode != GT_GROUP_RUNS && p->group_mode != GT_GROUP_CELLS) return GT_EINVAL;
     if (p->levels < 1 || p->levels > 30) return GT_EINVAL;
-    if (p->rebuild_every < 1 || p->node_factor < 1 || p->node_factor > 64) return GT_EINVAL;
+    if (p->rebuild_every < 0 || p->node_factor < 1 || p->node_factor > 64) return GT_EINVAL;
     if (!pow2(p->walk_queue) || p->walk_queue < 64) return GT_EINVAL;
     if (!(p->eps > 0.0f) || !(p->theta >= 0.0f) || !(p->delta_acc >= 0.0f)) return GT_EINVAL;
     if (!(p->eta > 0.0)) return GT_EINVAL;
@@ -88,14 +110,6 @@ int device_sms(int *dev, int *nsm) {
     return GT_OK;
 }
 
-int max_walk_blocks(int nsm) {
-    int best = 0;
-    for (int s = 1; s <= 32; s <<= 1) {
-        const int b = gt_walk_blocks(s, nsm);
-        best = b > best ? b : best;
-    }
-    return best;
-}
 
 int64_t node_capacity(int64_t n, const gt_params *p) { return (int64_t)p->node_factor * n + 2048; }
 
@@ -140,6 +154,10 @@ size_t carve(gt_system *s, char *base, int64_t n, const gt_params *p, int nsm, i
     const int64_t st_tiles = (cap + 511) / 512 + (n + 4095) / 4096 + 64;
     s->status = L.take<unsigned long long>(base, st_tiles);
     s->active = L.take<uint32_t>(base, N);
+    s->prefix = L.take<uint32_t>(base, N + 1);
+    s->flags = L.take<uint8_t>(base, N);
+    s->marks = L.take<uint8_t>(base, N);
+    s->gstart = L.take<uint32_t>(base, N);
     s->acc_out = L.take<float4>(base, N);
     s->aold_tmp = L.take<float>(base, N);
     s->scratch3 = L.take<double>(base, 3 * N + 8);  // also stages 13 B per particle on resume
@@ -156,12 +174,14 @@ int last_cuda() { return cudaGetLastError() == cudaSuccess ? GT_OK : GT_ECUDA; }
 
 enum { PH_PREDICT = 0, PH_SORT, PH_PERMUTE, PH_BUILD, PH_PSEUDO, PH_ACTIVE, PH_WALK, PH_CORRECT };
 
+bool timing(const gt_system *s) { return s->prof.on || (s->prof.created && s->prm.rebuild_every == 0); }
+
 void ph_begin(gt_system *s, int p, cudaStream_t st) {
-    if (s->prof.on) cudaEventRecord(s->prof.b[p], st);
+    if (timing(s)) cudaEventRecord(s->prof.b[p], st);
 }
 
 void ph_end(gt_system *s, int p, cudaStream_t st) {
-    if (s->prof.on) {
+    if (timing(s)) {
         cudaEventRecord(s->prof.e[p], st);
         s->prof.ran[p] = true;
     }
@@ -169,15 +189,50 @@ void ph_end(gt_system *s, int p, cudaStream_t st) {
 
 // fold the finished phases' times in (the stream must have been synchronised)
 void ph_collect(gt_system *s) {
-    if (!s->prof.on) return;
+    if (!timing(s)) return;
     for (int p = 0; p < GT_NPHASES; p++) {
         if (!s->prof.ran[p]) continue;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, s->prof.b[p], s->prof.e[p]) == cudaSuccess) {
             s->prof.ms[p] += ms;
+            s->prof.last_ms[p] = ms;
             s->prof.cnt[p] += 1;
         }
         s->prof.ran[p] = false;
+    }
+}
+
+int ensure_events(gt_system *s) {
+    if (s->prof.created) return GT_OK;
+    for (int p = 0; p < GT_NPHASES; p++)
+        if (cudaEventCreate(&s->prof.b[p]) || cudaEventCreate(&s->prof.e[p])) return GT_ECUDA;
+    s->prof.created = true;
+    return GT_OK;
+}
+
+// After a synchronised block step: feed its walk time (and, after a rebuild, the
+// rebuild's time) to the interval model.
+void tune_after_step(gt_system *s, bool rebuilt, unsigned n_active) {
+    RebuildTuner &t = s->tune;
+    if (rebuilt) {
+        t.y.clear();
+        t.t_make = s->prof.last_ms[PH_SORT] + s->prof.last_ms[PH_PERMUTE] + s->prof.last_ms[PH_BUILD];
+        t.since = 0;
+        t.n_opt = 1e6;
+    }
+    t.since++;
+    if (n_active == 0) return;
+    t.nact_sum += n_active;
+    t.nact_cnt++;
+    const double mean = t.nact_sum / (double)t.nact_cnt;
+    t.y.push_back(s->prof.last_ms[PH_WALK] * mean / (double)n_active);
+    if (t.y.size() >= 3) {
+        int model = -1;
+        double nopt = 1e6;
+        if (gt_rebuild_interval(t.y.data(), (int)t.y.size(), t.t_make, &model, &nopt, nullptr) == GT_OK) {
+            t.model = model;
+            t.n_opt = nopt;
+        }
     }
 }
 
@@ -219,8 +274,21 @@ void build_tree(gt_system *s, cudaStream_t st, const float4 *posm_src) {
     s->rebuilds++;
 }
 
+double c2_of(const gt_params &p) {
+    const double c = (2.0 * p.eta) * (double)p.eps;
+    return c * c;
+}
+
+// A6 groups + A7 walk over the active list already in s->active / ctl->n_active
+// (cell grouping needs the prefix s->prefix of that list), or over a caller's list.
 void walk(gt_system *s, const uint32_t *active, const float *aold, float4 *acc, int mac, cudaStream_t st) {
     WalkArgs a;
+    a.gstart = nullptr;
+    if (s->prm.group_mode == GT_GROUP_CELLS) {
+        gt_launch_groups(s->nd, s->cap, s->prefix, s->prm.group_max, s->n, s->marks, s->ctl, s->gstart,
+                         s->status, s->nsm, st);
+        a.gstart = s->gstart;
+    }
     a.jpos = s->nd.jpos;
     a.walk = s->nd.walk;
     a.posm = s->posm;
@@ -233,14 +301,22 @@ void walk(gt_system *s, const uint32_t *active, const float *aold, float4 *acc, 
     a.gmax = s->prm.group_max;
     a.qcap = s->prm.walk_queue;
     a.mac = mac;
+    a.ij_share = s->prm.ij_share;
     a.theta = s->prm.theta;
     a.delta_acc = s->prm.delta_acc;
     a.eps2 = s->prm.eps * s->prm.eps;
     a.G = s->prm.G;
     a.inv_eps = 1.0f / s->prm.eps;
     ph_begin(s, PH_WALK, st);
-    gt_launch_walk(a, s->prm.ij_share, s->walk_blocks, st);
+    gt_launch_walk(a, s->walk_blocks, st);
     ph_end(s, PH_WALK, st);
+}
+
+// every particle active (start-up passes, gt_accel_active with no list)
+void walk_all(gt_system *s, const float *aold, float4 *acc, int mac, cudaStream_t st) {
+    gt_launch_prepare(s->ctl, 0, st);
+    gt_launch_active(s->st[s->cur], s->n, s->prm.levels, 1, s->ctl, s->active, s->prefix, s->status, s->nsm, st);
+    walk(s, nullptr, aold, acc, mac, st);
 }
 
 }  // namespace
@@ -273,9 +349,10 @@ int gt_default_params(gt_params *p) {
     p->G = 1.0f;
     p->leaf_max = 16;
     p->group_max = 32;
-    p->ij_share = 1;
+    p->ij_share = 0;
+    p->group_mode = GT_GROUP_CELLS;
     p->levels = 8;
-    p->rebuild_every = 1;
+    p->rebuild_every = 0;
     p->walk_queue = 16384;
     p->node_factor = 2;
     p->eta = 0.025;
@@ -290,7 +367,7 @@ int gt_workspace_bytes(int64_t n, const gt_params *prm, size_t *bytes) {
     int dev, nsm;
     if ((rc = device_sms(&dev, &nsm))) return rc;
     gt_system tmp;
-    *bytes = carve(&tmp, nullptr, n, prm, nsm, max_walk_blocks(nsm));
+    *bytes = carve(&tmp, nullptr, n, prm, nsm, gt_walk_blocks(nsm));
     return GT_OK;
 }
 
@@ -303,11 +380,10 @@ int gt_system_create(gt_system **out, int64_t n, const gt_params *prm, void *d_w
     if (!s) return GT_ENOMEM;
     if ((rc = device_sms(&s->dev, &s->nsm))) { delete s; return rc; }
     gt_sort_init();
-    const int wb = max_walk_blocks(s->nsm);
+    const int wb = gt_walk_blocks(s->nsm);
     const size_t need = carve(s, nullptr, n, prm, s->nsm, wb);
     if (ws_bytes < need) { delete s; return GT_ENOMEM; }
     carve(s, (char *)d_ws, n, prm, s->nsm, wb);
-    s->walk_blocks = gt_walk_blocks(prm->ij_share, s->nsm);
     s->n = n;
     s->prm = *prm;
     // zero the control block, the look-back status words and the arrival counters
@@ -343,7 +419,6 @@ int gt_set_params(gt_system *s, const gt_params *prm) {
     s->prm = *prm;
     s->prm.walk_queue = prm->walk_queue;
     (void)qcap_region;
-    s->walk_blocks = gt_walk_blocks(prm->ij_share, s->nsm);
     return GT_OK;
 }
 
@@ -380,9 +455,19 @@ int gt_accel_active(gt_system *s, const uint32_t *d_active, int64_t n_active, co
     if (!d_active && n_active != s->n) return GT_EINVAL;
     if (!s->have_tree) return GT_ESTATE;
     cudaStream_t st = S(stream);
-    gt_launch_prepare(s->ctl, 0, st);
-    gt_launch_set_nactive(s->ctl, (unsigned)n_active, st);
-    walk(s, d_active, d_aold ? d_aold : s->st[s->cur].aold, (float4 *)d_acc, s->prm.mac, st);
+    const float *aold = d_aold ? d_aold : s->st[s->cur].aold;
+    if (!d_active) {
+        walk_all(s, aold, (float4 *)d_acc, s->prm.mac, st);
+    } else if (s->prm.group_mode == GT_GROUP_CELLS) {
+        gt_launch_prepare(s->ctl, 0, st);
+        gt_launch_active_from_list(d_active, n_active, s->n, s->flags, s->ctl, s->active, s->prefix, s->status,
+                                   s->nsm, st);
+        walk(s, s->active, aold, (float4 *)d_acc, s->prm.mac, st);
+    } else {
+        gt_launch_prepare(s->ctl, 0, st);
+        gt_launch_set_nactive(s->ctl, (unsigned)n_active, st);
+        walk(s, d_active, aold, (float4 *)d_acc, s->prm.mac, st);
+    }
     return last_cuda();
 }
 
@@ -397,15 +482,11 @@ int gt_start(gt_system *s, const float *p_aold_boot, gt_stream stream) {
             return GT_ECUDA;
         gt_launch_gather_f(s->aold_tmp, t.id, n, t.aold, st);
     } else {
-        gt_launch_prepare(s->ctl, 0, st);
-        gt_launch_set_nactive(s->ctl, (unsigned)n, st);
-        walk(s, nullptr, nullptr, s->acc_out, GT_MAC_OPENING_ANGLE, st);
-        gt_launch_amag(s->acc_out, n, t.aold, st);
+        walk_all(s, nullptr, s->acc_out, GT_MAC_OPENING_ANGLE, st);
+        gt_launch_aold(s->acc_out, n, t.aold, st);
         ph_sync_collect(s, st);
     }
-    gt_launch_prepare(s->ctl, 0, st);
-    gt_launch_set_nactive(s->ctl, (unsigned)n, st);
-    walk(s, nullptr, t.aold, s->acc_out, s->prm.mac, st);
+    walk_all(s, t.aold, s->acc_out, s->prm.mac, st);
     int M = 0, have_M = 0;
     if (s->prm.dt_max > 0.0) {
         int e;
@@ -413,10 +494,10 @@ int gt_start(gt_system *s, const float *p_aold_boot, gt_stream stream) {
         M = e - 1;
         have_M = 1;
     }
-    gt_launch_init_levels(t, s->acc_out, n, s->prm.levels, s->prm.eta, (double)s->prm.eps, M, have_M,
-                          s->ctl, s->nsm, st);
+    gt_launch_init_levels(t, s->acc_out, n, s->prm.levels, c2_of(s->prm), M, have_M, s->ctl, s->nsm, st);
     s->started = true;
     s->steps = 0;
+    s->tune = RebuildTuner();
     return last_cuda();
 }
 
@@ -426,8 +507,26 @@ int gt_block_step(gt_system *s, gt_stream stream) {
     cudaStream_t st = S(stream);
     const int64_t n = s->n;
     if (n == 0) return GT_OK;
+    bool rebuild;
+    if (s->prm.rebuild_every == 0) {  // automatic interval (Sec. 2.6)
+        if (ensure_events(s)) return GT_ECUDA;
+        if (s->steps > 0) {
+            unsigned na = 0;
+            if (cudaMemcpyAsync(&na, &s->ctl->n_active, 4, cudaMemcpyDeviceToHost, st) ||
+                cudaStreamSynchronize(st))
+                return GT_ECUDA;
+            const bool was_rebuild = s->last_rebuilt;
+            ph_collect(s);
+            tune_after_step(s, was_rebuild, na);
+        }
+        const double cap = 256.0;
+        const double n_opt = s->tune.n_opt < cap ? s->tune.n_opt : cap;
+        rebuild = s->steps == 0 || (double)s->tune.since >= std::ceil(n_opt);
+    } else {
+        rebuild = s->steps % s->prm.rebuild_every == 0;
+    }
+    s->last_rebuilt = rebuild;
     gt_launch_prepare(s->ctl, 1, st);
-    const bool rebuild = s->steps % s->prm.rebuild_every == 0;
     ph_begin(s, PH_PREDICT, st);
     gt_launch_predict(s->st[s->cur], n, s->ctl, rebuild ? s->posm_tmp : s->posm, st);
     ph_end(s, PH_PREDICT, st);
@@ -440,12 +539,11 @@ int gt_block_step(gt_system *s, gt_stream stream) {
     }
     State &t = s->st[s->cur];
     ph_begin(s, PH_ACTIVE, st);
-    gt_launch_active(t, n, s->prm.levels, 0, s->ctl, s->active, s->status, s->nsm, st);
+    gt_launch_active(t, n, s->prm.levels, 0, s->ctl, s->active, s->prefix, s->status, s->nsm, st);
     ph_end(s, PH_ACTIVE, st);
     walk(s, s->active, t.aold, s->acc_out, s->prm.mac, st);
     ph_begin(s, PH_CORRECT, st);
-    gt_launch_correct(t, s->active, s->acc_out, s->ctl, n, s->prm.levels, s->prm.eta, (double)s->prm.eps,
-                      s->nsm, st);
+    gt_launch_correct(t, s->active, s->acc_out, s->ctl, n, s->prm.levels, c2_of(s->prm), s->nsm, st);
     ph_end(s, PH_CORRECT, st);
     s->steps++;
     return last_cuda();
@@ -500,8 +598,7 @@ int gt_correct(gt_system *s, const uint32_t *d_active, int64_t n_active, const f
     State &t = s->st[s->cur];
     gt_launch_set_tnext(s->ctl, T, st);
     gt_launch_set_nactive(s->ctl, (unsigned)n_active, st);
-    gt_launch_correct(t, d_active, (const float4 *)d_acc, s->ctl, s->n, s->prm.levels, s->prm.eta,
-                      (double)s->prm.eps, s->nsm, st);
+    gt_launch_correct(t, d_active, (const float4 *)d_acc, s->ctl, s->n, s->prm.levels, c2_of(s->prm), s->nsm, st);
     // the next block time over every particle
     gt_launch_prepare(s->ctl, 1, st);
     gt_launch_tnext_all(t, s->n, s->prm.levels, s->ctl, s->nsm, st);
@@ -533,11 +630,7 @@ int gt_advance(gt_system *s, int64_t T_end, int64_t *steps, gt_stream stream) {
 
 int gt_profile(gt_system *s, int enable) {
     if (!s) return GT_EINVAL;
-    if (enable && !s->prof.created) {
-        for (int p = 0; p < GT_NPHASES; p++)
-            if (cudaEventCreate(&s->prof.b[p]) || cudaEventCreate(&s->prof.e[p])) return GT_ECUDA;
-        s->prof.created = true;
-    }
+    if (enable && ensure_events(s)) return GT_ECUDA;
     s->prof.on = enable != 0;
     for (int p = 0; p < GT_NPHASES; p++) {
         s->prof.ms[p] = 0.0;

@@ -10,6 +10,10 @@
 #define GT_TREE_LEVELS 22             // tree levels 0..21
 #define GT_LEAF_FLAG 0x80000000u      // set in a node's second link word for a leaf
 #define GT_SPIN_LIMIT (1u << 22)      // bound on every device spin-wait (iterations)
+// Enclosing radii computed in FP32 are widened by (1 + 2^-20): the few roundings of
+// an FP32 distance (each <= 2^-24 relative) cannot then shrink a radius below the
+// true one.
+#define GT_RADIUS_MARGIN (1.0f + 0x1p-20f)
 
 // Kernel ids recorded with a latched error (diagnostic only).
 enum { GTK_NONE = 0, GTK_BUILD, GTK_PSEUDO, GTK_ACTIVE, GTK_WALK, GTK_SORT, GTK_CORRECT };
@@ -21,11 +25,11 @@ struct DevCtl {
     int err_where;                    // GTK_* of the kernel that latched it
     unsigned int epoch;               // bumped once per tree build / compaction
     unsigned int n_active;            // i-particles of the current force evaluation
+    unsigned int n_groups;            // groups of the current force evaluation (cell grouping)
     unsigned int group_next;          // dynamic group counter of the walk
     unsigned int tile_ticket[GT_TREE_LEVELS + 2];  // dynamic tile ids (build levels, compaction)
     unsigned int level_start[GT_TREE_LEVELS + 2];  // first cell of each level; [22] = node count
     unsigned int sort_done;           // last-block counter of the digit scan
-    unsigned int pad0;
     unsigned long long interactions;  // cumulative
     unsigned long long mac_tests;     // cumulative
     unsigned long long tnext;         // block time of the current step
@@ -195,24 +199,29 @@ void gt_launch_interleave3(const double *x, const double *y, const double *z, in
                            cudaStream_t st);
 void gt_launch_gather_f(const float *in, const uint32_t *id, int64_t n, float *out, cudaStream_t st);
 void gt_launch_active(const State &s, int64_t n, int L, int all, DevCtl *ctl, uint32_t *active,
-                      unsigned long long *status, int nsm, cudaStream_t st);
+                      uint32_t *prefix, unsigned long long *status, int nsm, cudaStream_t st);
+void gt_launch_active_from_list(const uint32_t *list, int64_t n_list, int64_t n, uint8_t *flags, DevCtl *ctl,
+                                uint32_t *active, uint32_t *prefix, unsigned long long *status, int nsm,
+                                cudaStream_t st);
+void gt_launch_groups(Nodes nd, int64_t cap, const uint32_t *prefix, int gmax, int64_t n, uint8_t *marks,
+                      DevCtl *ctl, uint32_t *gstart, unsigned long long *status, int nsm, cudaStream_t st);
 void gt_launch_correct(const State &s, const uint32_t *active, const float4 *acc, DevCtl *ctl,
-                       int64_t n, int L, double eta, double eps, int nsm, cudaStream_t st);
-void gt_launch_amag(const float4 *acc, int64_t n, float *aold, cudaStream_t st);
+                       int64_t n, int L, double c2, int nsm, cudaStream_t st);
+void gt_launch_aold(const float4 *acc, int64_t n, float *aold, cudaStream_t st);
 void gt_launch_set_clock(DevCtl *ctl, int M, int L, long long T, cudaStream_t st);
 void gt_launch_set_tnext(DevCtl *ctl, long long T, cudaStream_t st);
 void gt_launch_tnext_all(const State &s, int64_t n, int L, DevCtl *ctl, int nsm, cudaStream_t st);
 void gt_launch_gather_resume(const uint8_t *lv, const long long *t0, const float *ao, const float4 *acc,
                              const State &s, int64_t n, cudaStream_t st);
-void gt_launch_init_levels(const State &s, const float4 *acc, int64_t n, int L, double eta,
-                           double eps, int M_given, int have_M, DevCtl *ctl, int nsm,
-                           cudaStream_t st);
+void gt_launch_init_levels(const State &s, const float4 *acc, int64_t n, int L, double c2, int M_given,
+                           int have_M, DevCtl *ctl, int nsm, cudaStream_t st);
 // walk.cu
 struct WalkArgs {
     const float4 *jpos;
     const float4 *walk;
     const float4 *posm;
-    const uint32_t *active;  // may be null: identity
+    const uint32_t *active;  // null: identity
+    const uint32_t *gstart;  // first active position of every group; null: runs of gmax
     const float *aold;
     float4 *acc;
     uint32_t *queue;
@@ -221,8 +230,12 @@ struct WalkArgs {
     int gmax;
     int qcap;                // power of two
     int mac;
+    int ij_share;            // lanes per i-particle; 0: 32 / (members rounded up to a power of two)
     float theta, delta_acc, eps2, G, inv_eps;
 };
-int gt_walk_blocks(int ij_share, int nsm);
+int gt_walk_blocks(int nsm);
+// tuner.cu
+extern "C" int gt_rebuild_interval(const double *t_walk, int n, double t_make, int *model_out,
+                                   double *n_opt_out, double *coef_out);
 int gt_walk_warps_per_block();
-void gt_launch_walk(const WalkArgs &a, int ij_share, int nblocks, cudaStream_t st);
+void gt_launch_walk(const WalkArgs &a, int nblocks, cudaStream_t st);

@@ -1,19 +1,24 @@
-// Block time step (Sec. 1; Sec. 2.7, Eqs. 15-17) and the particle-array plumbing:
+// Block time step (Sec. 1; Sec. 2.7, Eqs. 15-17), active sets and groups, and the
+// particle-array plumbing:
 //   k_prepare      per-phase bookkeeping (epoch, tickets, the step's block time)
-//   k_predict      A8: r(T) = r0 + ((T - t0) dt_min) v^{1/2} for every particle, FP64,
+//   k_predict      A8: r(T) = fma((T - t0) dt_min, v^{1/2}, r0) for every particle, FP64,
 //                  rounded to FP32 for the tree                    (HBM: 60 B read, 16 B written)
 //   k_permute      A3: gather every particle array into key order  (HBM: ~100 B each way)
-//   k_active       A6: active = (t0 + ticks(level) == T), compacted in key order with a
-//                  block scan and a bounded decoupled look-back; the inactive particles'
-//                  next step ends are folded into the next block time (HBM: 9 B + 4 B/active)
+//   k_compact      A6: order-preserving compaction with a block scan and a bounded decoupled
+//                  look-back; selects by block time (t0 + ticks(level) == T), by a flag array,
+//                  or all, and writes the active prefix P[i] = #actives below i
+//                  (HBM: 9 B read + 4 B prefix per particle, 4 B per active)
+//   k_group_cells  A6: groups bounded by tree cells (Sec. 2.4): the actives of every maximal
+//                  cell with at most group_max of them (or of a leaf, cut into runs)
 //   k_correct      A9: Eq. (17), the new level, the next half kick; the active particles'
 //                  new step ends are folded into the next block time
 //   k_init_levels  start: dt_max, levels and the first half kick
-// Level of a particle: the smallest k with dt_max 2^-k <= dt_i = sqrt(2 eta eps / |a|),
-// clamped to [0, L-1]; with dt_i = f 2^e (f in [0.5, 1)) this is k = M - e + 1 where
-// dt_max = 2^M.  A shorter step is taken at once; a longer one only by one level and
-// only when T is a multiple of the longer step.  Every FP64 operation is written with
-// an explicit rounding intrinsic (no contraction), so results are reproducible bit for bit.
+// Level of a particle: the smallest k with dt_k = dt_max 2^-k <= dt_i = sqrt(c/|a|),
+// c = 2 eta eps, clamped to [0, L-1]; equivalently 2^(4(M-k)) A2 <= c2 with
+// A2 = (ax^2 + ay^2) + az^2 and c2 = c c in FP64, decided exactly on the exponents
+// (no root, no division: FP64 throughput is low on this GPU).  A shorter step is taken
+// at once; a longer one only by one level and only when T is a multiple of it.  Every
+// FP64 operation carries an explicit rounding, so results are reproducible bit for bit.
 #include "gt_internal.cuh"
 
 namespace {
@@ -37,9 +42,9 @@ __global__ __launch_bounds__(256) void k_predict(State s, long long n, const Dev
     const long long T = (long long)ctl->tnext;
     const double dt_min = ldexp(ctl->dt_max, -ctl->levels_m1);
     const double dt = __dmul_rn((double)(T - s.t0[i]), dt_min);
-    const float x = __double2float_rn(__dadd_rn(s.rx[i], __dmul_rn(dt, s.vx[i])));
-    const float y = __double2float_rn(__dadd_rn(s.ry[i], __dmul_rn(dt, s.vy[i])));
-    const float z = __double2float_rn(__dadd_rn(s.rz[i], __dmul_rn(dt, s.vz[i])));
+    const float x = __double2float_rn(__fma_rn(dt, s.vx[i], s.rx[i]));
+    const float y = __double2float_rn(__fma_rn(dt, s.vy[i], s.ry[i]));
+    const float z = __double2float_rn(__fma_rn(dt, s.vz[i], s.rz[i]));
     posm[i] = make_float4(x, y, z, s.mass[i]);
 }
 
@@ -103,6 +108,20 @@ __global__ __launch_bounds__(256) void k_gather_f(const float *__restrict__ in, 
     if (i < n) out[i] = in[id[i]];
 }
 
+// flags[active[k]] = 1 for a caller's list; a list that is not strictly increasing or
+// holds an index >= n latches GT_EINVAL (the cell grouping needs key order)
+__global__ __launch_bounds__(256) void k_scatter_flags(const uint32_t *__restrict__ active, long long na,
+                                                       long long n, uint8_t *__restrict__ flags, DevCtl *ctl) {
+    const long long k = blockIdx.x * 256ll + threadIdx.x;
+    if (k >= na) return;
+    const uint32_t i = active[k];
+    if ((long long)i >= n || (k > 0 && active[k - 1] >= i)) {
+        gt_set_error(ctl, GT_EINVAL, GTK_ACTIVE);
+        return;
+    }
+    flags[i] = 1;
+}
+
 constexpr int AT = 256, AIPT = 16, ATILE = AT * AIPT;
 
 __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
@@ -114,78 +133,126 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
     return v;
 }
 
-__global__ __launch_bounds__(AT) void k_active(long long n, const long long *__restrict__ t0,
-                                               const uint8_t *__restrict__ level, int L, int all,
-                                               DevCtl *ctl, uint32_t *__restrict__ active,
-                                               unsigned long long *status) {
+enum { CM_TIME = 0, CM_ALL = 1, CM_FLAGS = 2 };
+
+// Order-preserving compaction of [0, n) (n from n_dev if given).  Writes the selected
+// indices to out, the prefix P[i] = #selected below i (i = 0..n) if prefix != null,
+// and the count to *count_out.  CM_TIME also folds the unselected particles' step
+// ends into the next block time.
+__global__ __launch_bounds__(AT) void k_compact(long long n_host, const unsigned int *n_dev, int mode,
+                                                const long long *__restrict__ t0,
+                                                const uint8_t *__restrict__ level, int L,
+                                                const uint8_t *__restrict__ flags, DevCtl *ctl,
+                                                int ticket, uint32_t tag_slot, uint32_t *__restrict__ out,
+                                                uint32_t *__restrict__ prefix, unsigned int *count_out,
+                                                unsigned long long *status) {
     __shared__ uint32_t tmp[AT / 32 + 1];
     __shared__ uint32_t tile_sh, excl_sh;
+    const long long n = n_dev ? (long long)*n_dev : n_host;
     const unsigned long long T = ctl->tnext;
-    const uint32_t tag = ctl->epoch * 32u + 30u;
+    const uint32_t tag = ctl->epoch * 32u + tag_slot;
     const uint32_t ntiles = (uint32_t)((n + ATILE - 1) / ATILE);
     unsigned long long tmin = ~0ull;
+    if (n == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            *count_out = 0;
+            if (prefix) prefix[0] = 0;
+        }
+        return;
+    }
     for (;;) {
-        if (threadIdx.x == 0) tile_sh = atomicAdd(&ctl->tile_ticket[GT_TREE_LEVELS], 1u);
+        if (threadIdx.x == 0) tile_sh = atomicAdd(&ctl->tile_ticket[ticket], 1u);
         __syncthreads();
         const uint32_t tile = tile_sh;
         __syncthreads();
         if (tile >= ntiles) break;
         const long long i0 = (long long)tile * ATILE + threadIdx.x * AIPT;
-        uint32_t flags = 0;
+        uint32_t sel = 0;
 #pragma unroll
         for (int q = 0; q < AIPT; q++) {
             const long long i = i0 + q;
             if (i < n) {
-                if (all) {
-                    flags |= 1u << q;
+                bool on;
+                if (mode == CM_ALL) {
+                    on = true;
+                } else if (mode == CM_FLAGS) {
+                    on = flags[i] != 0;
                 } else {
                     const unsigned long long tend =
                         (unsigned long long)t0[i] + (1ull << (L - 1 - (int)level[i]));
-                    if (tend == T) flags |= 1u << q;
-                    else tmin = tend < tmin ? tend : tmin;
+                    on = tend == T;
+                    if (!on) tmin = tend < tmin ? tend : tmin;
                 }
+                if (on) sel |= 1u << q;
             }
         }
         uint32_t total;
-        const uint32_t excl = block_excl_scan<AT>((uint32_t)__popc(flags), &total, tmp);
+        const uint32_t excl = block_excl_scan<AT>((uint32_t)__popc(sel), &total, tmp);
         if (threadIdx.x == 0) excl_sh = lookback_prefix(status, tile, total, tag, ctl, GTK_ACTIVE);
         __syncthreads();
         uint32_t pos = excl_sh + excl;
 #pragma unroll
-        for (int q = 0; q < AIPT; q++)
-            if (flags & (1u << q)) active[pos++] = (uint32_t)(i0 + q);
-        if (tile == ntiles - 1 && threadIdx.x == AT - 1) ctl->n_active = excl_sh + total;
+        for (int q = 0; q < AIPT; q++) {
+            const long long i = i0 + q;
+            if (i < n && prefix) prefix[i] = pos;
+            if (sel & (1u << q)) out[pos++] = (uint32_t)i;
+        }
+        if (tile == ntiles - 1 && threadIdx.x == AT - 1) {
+            *count_out = excl_sh + total;
+            if (prefix) prefix[n] = excl_sh + total;
+        }
     }
-    if (!all) {
+    if (mode == CM_TIME) {
         tmin = warp_min_u64(tmin);
         if (lane_id() == 0 && tmin != ~0ull) atomicMin(&ctl->tnext_acc, tmin);
     }
 }
 
-__device__ __forceinline__ double amag3(float4 a) {
+// Mark the first active position of every group (Sec. 2.4 reading: groups never
+// straddle two tree cells).  A group cell holds 1..gmax actives (or is a leaf) and its
+// parent holds more than gmax (or it is the root); its actives are cut into runs of gmax.
+__global__ __launch_bounds__(256) void k_group_cells(Nodes nd, long long cap, const uint32_t *__restrict__ P,
+                                                     int gmax, uint8_t *__restrict__ marks, const DevCtl *ctl) {
+    long long nn = ctl->level_start[GT_TREE_LEVELS];
+    if (nn > cap) nn = cap;
+    for (long long c = blockIdx.x * 256ll + threadIdx.x; c < nn; c += (long long)gridDim.x * 256) {
+        const uint32_t f = nd.first[c];
+        const uint32_t a0 = P[f], A = P[f + nd.count[c]] - a0;
+        if (A == 0) continue;
+        const int32_t p = nd.parent[c];
+        if (p >= 0) {
+            const uint32_t fp = nd.first[p];
+            if (P[fp + nd.count[p]] - P[fp] <= (uint32_t)gmax) continue;  // inside a group cell
+        }
+        if (A > (uint32_t)gmax && nd.child[c] >= 0) continue;               // its children decide
+        for (uint32_t s = a0; s < a0 + A; s += (uint32_t)gmax) marks[s] = 1;
+    }
+}
+
+__device__ __forceinline__ double a2_of(float4 a) {
     const double ax = a.x, ay = a.y, az = a.z;
-    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)), __dmul_rn(az, az)));
+    // the squares are exact in FP64, so the fused forms round only at the additions
+    return __fma_rn(az, az, __fma_rn(ay, ay, __dmul_rn(ax, ax)));
 }
 
-__device__ __forceinline__ double dt_crit(double am, double eta, double eps) {
-    return __dsqrt_rn(__ddiv_rn(__dmul_rn(__dmul_rn(2.0, eta), eps), am));
-}
+__device__ __forceinline__ long long floordiv4(long long d) { return d >= 0 ? d / 4 : -((-d + 3) / 4); }
 
-__device__ __forceinline__ int level_from_amag(double am, double eta, double eps, int M, int L) {
-    if (!(am > 0.0) || !isfinite(am)) return 0;
-    const double dti = dt_crit(am, eta, eps);
-    if (!isfinite(dti)) return 0;
-    int e;
-    (void)frexp(dti, &e);
-    int k = M - e + 1;
+__device__ __forceinline__ int level_from_a2(double a2, double c2, int M, int L) {
+    if (!(a2 > 0.0) || !isfinite(a2)) return 0;
+    int ea, ec;
+    const double fa = frexp(a2, &ea), fc = frexp(c2, &ec);
+    // level k qualifies iff 4k > D, or 4k == D and fa <= fc, with D = ea + 4M - ec
+    const long long D = (long long)ea + 4ll * M - ec;
+    const long long q = floordiv4(D);
+    long long k = (4 * q == D && fa <= fc) ? q : q + 1;
     k = k < 0 ? 0 : k;
     k = k > L - 1 ? L - 1 : k;
-    return k;
+    return (int)k;
 }
 
 __global__ __launch_bounds__(256) void k_correct(State s, const uint32_t *__restrict__ active,
                                                  const float4 *__restrict__ acc, DevCtl *ctl, long long n,
-                                                 int L, double eta, double eps) {
+                                                 int L, double c2) {
     const uint32_t na = ctl->n_active;
     const long long T = (long long)ctl->tnext;
     const double dt_max = ctl->dt_max;
@@ -200,17 +267,18 @@ __global__ __launch_bounds__(256) void k_correct(State s, const uint32_t *__rest
         }
         const float4 a = acc[k];
         const int kold = s.level[i];
-        const double hold = __dmul_rn(0.5, ldexp(dt_max, -kold));
+        const double hold = 0.5 * ldexp(dt_max, -kold);
         const double dtp = __dmul_rn((double)(T - s.t0[i]), dt_min);
         const double ax = a.x, ay = a.y, az = a.z;
-        const double vx = __dadd_rn(s.vx[i], __dmul_rn(hold, ax));
-        const double vy = __dadd_rn(s.vy[i], __dmul_rn(hold, ay));
-        const double vz = __dadd_rn(s.vz[i], __dmul_rn(hold, az));
-        s.rx[i] = __dadd_rn(s.rx[i], __dmul_rn(dtp, s.vx[i]));
-        s.ry[i] = __dadd_rn(s.ry[i], __dmul_rn(dtp, s.vy[i]));
-        s.rz[i] = __dadd_rn(s.rz[i], __dmul_rn(dtp, s.vz[i]));
-        const double am = amag3(a);
-        const int kc = level_from_amag(am, eta, eps, M, L);
+        const double vx0 = s.vx[i], vy0 = s.vy[i], vz0 = s.vz[i];
+        s.rx[i] = __fma_rn(dtp, vx0, s.rx[i]);
+        s.ry[i] = __fma_rn(dtp, vy0, s.ry[i]);
+        s.rz[i] = __fma_rn(dtp, vz0, s.rz[i]);
+        const double vx = __fma_rn(hold, ax, vx0);
+        const double vy = __fma_rn(hold, ay, vy0);
+        const double vz = __fma_rn(hold, az, vz0);
+        const double a2 = a2_of(a);
+        const int kc = level_from_a2(a2, c2, M, L);
         int knew = kold;
         if (kc > kold) {
             knew = kc;
@@ -218,13 +286,13 @@ __global__ __launch_bounds__(256) void k_correct(State s, const uint32_t *__rest
             const long long span = 1ll << (L - 1 - (kold - 1));
             if (T % span == 0) knew = kold - 1;
         }
-        const double hnew = __dmul_rn(0.5, ldexp(dt_max, -knew));
-        s.vx[i] = __dadd_rn(vx, __dmul_rn(hnew, ax));
-        s.vy[i] = __dadd_rn(vy, __dmul_rn(hnew, ay));
-        s.vz[i] = __dadd_rn(vz, __dmul_rn(hnew, az));
+        const double hnew = 0.5 * ldexp(dt_max, -knew);
+        s.vx[i] = __fma_rn(hnew, ax, vx);
+        s.vy[i] = __fma_rn(hnew, ay, vy);
+        s.vz[i] = __fma_rn(hnew, az, vz);
         s.level[i] = (uint8_t)knew;
         s.t0[i] = T;
-        s.aold[i] = __double2float_rn(am);
+        s.aold[i] = __fsqrt_rn(__double2float_rn(a2));
         s.acc[i] = a;
         const unsigned long long tend = (unsigned long long)T + (1ull << (L - 1 - knew));
         tmin = tend < tmin ? tend : tmin;
@@ -233,42 +301,39 @@ __global__ __launch_bounds__(256) void k_correct(State s, const uint32_t *__rest
     if (lane_id() == 0 && tmin != ~0ull) atomicMin(&ctl->tnext_acc, tmin);
 }
 
-__global__ __launch_bounds__(256) void k_amag(const float4 *__restrict__ acc, long long n,
+__global__ __launch_bounds__(256) void k_aold(const float4 *__restrict__ acc, long long n,
                                               float *__restrict__ aold) {
     const long long i = blockIdx.x * 256ll + threadIdx.x;
-    if (i < n) aold[i] = __double2float_rn(amag3(acc[i]));
+    if (i < n) aold[i] = __fsqrt_rn(__double2float_rn(a2_of(acc[i])));
 }
 
-// start, phase 1: the largest dt_i over all particles (bit pattern of a positive double)
-__global__ __launch_bounds__(256) void k_max_dt(const float4 *__restrict__ acc, long long n, double eta,
-                                                double eps, DevCtl *ctl) {
-    unsigned long long best = 0;
+// start, phase 1: the smallest positive A2 (bit pattern of a positive double)
+__global__ __launch_bounds__(256) void k_min_a2(const float4 *__restrict__ acc, long long n, DevCtl *ctl) {
+    unsigned long long best = ~0ull;
     for (long long i = blockIdx.x * 256ll + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
-        const double am = amag3(acc[i]);
-        if (!(am > 0.0)) continue;
-        const unsigned long long b = (unsigned long long)__double_as_longlong(dt_crit(am, eta, eps));
-        best = b > best ? b : best;
+        const double a2 = a2_of(acc[i]);
+        if (!(a2 > 0.0) || !isfinite(a2)) continue;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(a2);
+        best = b < best ? b : best;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long t = __shfl_xor_sync(0xffffffffu, best, o);
-        best = t > best ? t : best;
-    }
-    if (lane_id() == 0 && best) atomicMax(&ctl->max_dt_bits, best);
+    best = warp_min_u64(best);
+    if (lane_id() == 0 && best != ~0ull) atomicMin(&ctl->max_dt_bits, best);
 }
 
-// start, phase 2: dt_max, levels, t0 = 0, first half kick v^{1/2} = v + (dt/2) a
+// start, phase 2: dt_max (the largest 2^M with 2^(4M) A2min <= c2), levels, t0 = 0,
+// first half kick v^{1/2} = fma(dt/2, a, v)
 __global__ __launch_bounds__(256) void k_init_levels(State s, const float4 *__restrict__ acc, long long n,
-                                                     int L, double eta, double eps, int M_given,
-                                                     int have_M, DevCtl *ctl) {
+                                                     int L, double c2, int M_given, int have_M, DevCtl *ctl) {
     int M = M_given;
     if (!have_M) {
-        const double best = __longlong_as_double((long long)ctl->max_dt_bits);
         M = 0;
-        if (best > 0.0 && isfinite(best)) {
-            int e;
-            (void)frexp(best, &e);
-            M = e - 1;
+        if (ctl->max_dt_bits != ~0ull) {
+            const double a2min = __longlong_as_double((long long)ctl->max_dt_bits);
+            int ea, ec;
+            const double fa = frexp(a2min, &ea), fc = frexp(c2, &ec);
+            const long long D = (long long)ec - ea;  // M qualifies iff 4M < D, or 4M == D and fa <= fc
+            const long long q = floordiv4(D);
+            M = (int)(4 * q == D ? (fa <= fc ? q : q - 1) : q);
         }
     }
     const double dt_max = ldexp(1.0, M);
@@ -280,15 +345,15 @@ __global__ __launch_bounds__(256) void k_init_levels(State s, const float4 *__re
     unsigned long long tmin = ~0ull;
     for (long long i = blockIdx.x * 256ll + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
         const float4 a = acc[i];
-        const double am = amag3(a);
-        const int k = level_from_amag(am, eta, eps, M, L);
-        const double h = __dmul_rn(0.5, ldexp(dt_max, -k));
-        s.vx[i] = __dadd_rn(s.vx[i], __dmul_rn(h, (double)a.x));
-        s.vy[i] = __dadd_rn(s.vy[i], __dmul_rn(h, (double)a.y));
-        s.vz[i] = __dadd_rn(s.vz[i], __dmul_rn(h, (double)a.z));
+        const double a2 = a2_of(a);
+        const int k = level_from_a2(a2, c2, M, L);
+        const double h = 0.5 * ldexp(dt_max, -k);
+        s.vx[i] = __fma_rn(h, (double)a.x, s.vx[i]);
+        s.vy[i] = __fma_rn(h, (double)a.y, s.vy[i]);
+        s.vz[i] = __fma_rn(h, (double)a.z, s.vz[i]);
         s.level[i] = (uint8_t)k;
         s.t0[i] = 0;
-        s.aold[i] = __double2float_rn(am);
+        s.aold[i] = __fsqrt_rn(__double2float_rn(a2));
         s.acc[i] = a;
         const unsigned long long tend = 1ull << (L - 1 - k);
         tmin = tend < tmin ? tend : tmin;
@@ -333,7 +398,7 @@ __global__ __launch_bounds__(256) void k_gather_resume(const uint8_t *__restrict
 }
 
 __global__ void k_reset_start(DevCtl *ctl) {
-    ctl->max_dt_bits = 0;
+    ctl->max_dt_bits = ~0ull;
     ctl->tnext_acc = ~0ull;
     ctl->tnext = 0;
 }
@@ -378,28 +443,47 @@ void gt_launch_gather_f(const float *in, const uint32_t *id, int64_t n, float *o
 }
 
 void gt_launch_active(const State &s, int64_t n, int L, int all, DevCtl *ctl, uint32_t *active,
-                      unsigned long long *status, int nsm, cudaStream_t st) {
-    if (n <= 0) {
-        { k_set_nactive<<<1, 1, 0, st>>>(ctl, 0u); gt_note_launches(1); }
-        return;
-    }
-    { k_active<<<nsm * 4, AT, 0, st>>>(n, s.t0, s.level, L, all, ctl, active, status); gt_note_launches(1); }
+                      uint32_t *prefix, unsigned long long *status, int nsm, cudaStream_t st) {
+    { k_compact<<<nsm * 4, AT, 0, st>>>(n, nullptr, all ? CM_ALL : CM_TIME, s.t0, s.level, L, nullptr, ctl,
+                                        GT_TREE_LEVELS, 30u, active, prefix, &ctl->n_active, status);
+      gt_note_launches(1); }
+}
+
+void gt_launch_active_from_list(const uint32_t *list, int64_t n_list, int64_t n, uint8_t *flags, DevCtl *ctl,
+                                uint32_t *active, uint32_t *prefix, unsigned long long *status, int nsm,
+                                cudaStream_t st) {
+    if (n > 0) cudaMemsetAsync(flags, 0, (size_t)n, st);
+    if (n_list > 0) { k_scatter_flags<<<nblk(n_list), 256, 0, st>>>(list, n_list, n, flags, ctl); gt_note_launches(1); }
+    { k_compact<<<nsm * 4, AT, 0, st>>>(n, nullptr, CM_FLAGS, nullptr, nullptr, 0, flags, ctl, GT_TREE_LEVELS,
+                                        30u, active, prefix, &ctl->n_active, status);
+      gt_note_launches(1); }
+}
+
+void gt_launch_groups(Nodes nd, int64_t cap, const uint32_t *prefix, int gmax, int64_t n, uint8_t *marks,
+                      DevCtl *ctl, uint32_t *gstart, unsigned long long *status, int nsm, cudaStream_t st) {
+    if (n > 0) cudaMemsetAsync(marks, 0, (size_t)n, st);
+    { k_group_cells<<<nsm * 8, 256, 0, st>>>(nd, cap, prefix, gmax, marks, ctl); gt_note_launches(1); }
+    { k_compact<<<nsm * 4, AT, 0, st>>>(0, &ctl->n_active, CM_FLAGS, nullptr, nullptr, 0, marks, ctl,
+                                        GT_TREE_LEVELS + 1, 31u, gstart, nullptr, &ctl->n_groups, status);
+      gt_note_launches(1); }
 }
 
 void gt_launch_correct(const State &s, const uint32_t *active, const float4 *acc, DevCtl *ctl,
-                       int64_t n, int L, double eta, double eps, int nsm, cudaStream_t st) {
-    if (n > 0) { k_correct<<<nsm * 8, 256, 0, st>>>(s, active, acc, ctl, n, L, eta, eps); gt_note_launches(1); }
+                       int64_t n, int L, double c2, int nsm, cudaStream_t st) {
+    if (n > 0) { k_correct<<<nsm * 8, 256, 0, st>>>(s, active, acc, ctl, n, L, c2); gt_note_launches(1); }
 }
 
-void gt_launch_amag(const float4 *acc, int64_t n, float *aold, cudaStream_t st) {
-    if (n > 0) { k_amag<<<nblk(n), 256, 0, st>>>(acc, n, aold); gt_note_launches(1); }
+void gt_launch_aold(const float4 *acc, int64_t n, float *aold, cudaStream_t st) {
+    if (n > 0) { k_aold<<<nblk(n), 256, 0, st>>>(acc, n, aold); gt_note_launches(1); }
 }
 
 void gt_launch_set_clock(DevCtl *ctl, int M, int L, long long T, cudaStream_t st) {
     { k_set_clock<<<1, 1, 0, st>>>(ctl, M, L, T); gt_note_launches(1); }
 }
 
-void gt_launch_set_tnext(DevCtl *ctl, long long T, cudaStream_t st) { { k_set_tnext<<<1, 1, 0, st>>>(ctl, T); gt_note_launches(1); } }
+void gt_launch_set_tnext(DevCtl *ctl, long long T, cudaStream_t st) {
+    { k_set_tnext<<<1, 1, 0, st>>>(ctl, T); gt_note_launches(1); }
+}
 
 void gt_launch_tnext_all(const State &s, int64_t n, int L, DevCtl *ctl, int nsm, cudaStream_t st) {
     if (n > 0) { k_tnext_all<<<nsm * 4, 256, 0, st>>>(s.t0, s.level, n, L, ctl); gt_note_launches(1); }
@@ -410,10 +494,9 @@ void gt_launch_gather_resume(const uint8_t *lv, const long long *t0, const float
     if (n > 0) { k_gather_resume<<<nblk(n), 256, 0, st>>>(lv, t0, ao, acc, s.id, n, s); gt_note_launches(1); }
 }
 
-void gt_launch_init_levels(const State &s, const float4 *acc, int64_t n, int L, double eta,
-                           double eps, int M_given, int have_M, DevCtl *ctl, int nsm,
-                           cudaStream_t st) {
+void gt_launch_init_levels(const State &s, const float4 *acc, int64_t n, int L, double c2, int M_given,
+                           int have_M, DevCtl *ctl, int nsm, cudaStream_t st) {
     { k_reset_start<<<1, 1, 0, st>>>(ctl); gt_note_launches(1); }
-    if (!have_M && n > 0) { k_max_dt<<<nsm * 4, 256, 0, st>>>(acc, n, eta, eps, ctl); gt_note_launches(1); }
-    { k_init_levels<<<nsm * 8, 256, 0, st>>>(s, acc, n, L, eta, eps, M_given, have_M, ctl); gt_note_launches(1); }
+    if (!have_M && n > 0) { k_min_a2<<<nsm * 4, 256, 0, st>>>(acc, n, ctl); gt_note_launches(1); }
+    { k_init_levels<<<nsm * 8, 256, 0, st>>>(s, acc, n, L, c2, M_given, have_M, ctl); gt_note_launches(1); }
 }

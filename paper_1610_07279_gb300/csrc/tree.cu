@@ -12,11 +12,13 @@
 //
 // A5, one kernel: each leaf sums its particles in FP64 (mass, m x, m y, m z) and
 // climbs; the last child to arrive at a cell (atomic counter, no waiting) sums the
-// children's FP64 sums in child order and continues upward.  r_J and m_J are
-// rounded to FP32; b_J is the largest |r - r_J| of a leaf's particles, or the
-// largest |r_c - r_J| + b_c over a cell's children, in FP64 rounded up to FP32.
-// Every FP64 operation is written with an explicit rounding intrinsic so that no
-// multiply-add is contracted: the result is the same bit for bit on every run.
+// children's FP64 sums in child order and continues upward.  m_J = (float)M and
+// r_J = (float)S / (float)M (a cell of one particle is that particle); b_J is the
+// largest FP32 |r - r_J| of a leaf's particles, or the largest |r_c - r_J| + b_c
+// over a cell's children, widened by (1 + 2^-20) so that FP32 rounding cannot
+// shrink it below the true enclosing radius.  FP64 is kept to the four sums (FP64
+// throughput is low on this GPU).  Every operation carries an explicit rounding,
+// so the result is the same bit for bit on every run.
 #include "gt_internal.cuh"
 
 namespace {
@@ -144,6 +146,10 @@ __device__ __forceinline__ double sq3(double dx, double dy, double dz) {
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
+__device__ __forceinline__ float sq3f(float dx, float dy, float dz) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
 __global__ __launch_bounds__(256) void k_pseudo(Nodes nd, long long cap, const float4 *__restrict__ posm,
                                                 DevCtl *ctl) {
     long long nn = ctl->level_start[GT_TREE_LEVELS];
@@ -154,25 +160,31 @@ __global__ __launch_bounds__(256) void k_pseudo(Nodes nd, long long cap, const f
         double m = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
         for (uint32_t i = f; i < f + k; i++) {
             const float4 p = posm[i];
-            const double mi = (double)p.w;
+            const double mi = (double)p.w;  // m x is exact in FP64, so the fused form rounds once like + does
             m = __dadd_rn(m, mi);
-            sx = __dadd_rn(sx, __dmul_rn(mi, (double)p.x));
-            sy = __dadd_rn(sy, __dmul_rn(mi, (double)p.y));
-            sz = __dadd_rn(sz, __dmul_rn(mi, (double)p.z));
+            sx = __fma_rn(mi, (double)p.x, sx);
+            sy = __fma_rn(mi, (double)p.y, sy);
+            sz = __fma_rn(mi, (double)p.z, sz);
         }
-        float jx = __double2float_rn(__ddiv_rn(sx, m));
-        float jy = __double2float_rn(__ddiv_rn(sy, m));
-        float jz = __double2float_rn(__ddiv_rn(sz, m));
-        double d2max = 0.0;
+        float jx, jy, jz;
+        if (k == 1) {  // a cell of one particle is that particle
+            const float4 p = posm[f];
+            jx = p.x; jy = p.y; jz = p.z;
+        } else {
+            const float mf = __double2float_rn(m);
+            jx = __fdiv_rn(__double2float_rn(sx), mf);
+            jy = __fdiv_rn(__double2float_rn(sy), mf);
+            jz = __fdiv_rn(__double2float_rn(sz), mf);
+        }
+        float d2max = 0.0f;
         for (uint32_t i = f; i < f + k; i++) {
             const float4 p = posm[i];
-            const double d2 = sq3(__dsub_rn((double)p.x, (double)jx), __dsub_rn((double)p.y, (double)jy),
-                                  __dsub_rn((double)p.z, (double)jz));
+            const float d2 = sq3f(__fsub_rn(p.x, jx), __fsub_rn(p.y, jy), __fsub_rn(p.z, jz));
             if (d2 > d2max) d2max = d2;
         }
         nd.sum[c0] = DSum4{m, sx, sy, sz};
         nd.jpos[c0] = make_float4(jx, jy, jz, __double2float_rn(m));
-        nd.walk[c0] = make_float4(__double2float_ru(__dsqrt_rn(d2max)), __uint_as_float(f),
+        nd.walk[c0] = make_float4(__fmul_rn(__fsqrt_rn(d2max), GT_RADIUS_MARGIN), __uint_as_float(f),
                                   __uint_as_float(k | GT_LEAF_FLAG), 0.0f);
         // climb while this thread is the last child to arrive
         long long c = c0;
@@ -194,22 +206,21 @@ __global__ __launch_bounds__(256) void k_pseudo(Nodes nd, long long cap, const f
                 sy = __dadd_rn(sy, s23.x);
                 sz = __dadd_rn(sz, s23.y);
             }
-            jx = __double2float_rn(__ddiv_rn(sx, m));
-            jy = __double2float_rn(__ddiv_rn(sy, m));
-            jz = __double2float_rn(__ddiv_rn(sz, m));
-            double b = 0.0;
+            const float mf = __double2float_rn(m);
+            jx = __fdiv_rn(__double2float_rn(sx), mf);
+            jy = __fdiv_rn(__double2float_rn(sy), mf);
+            jz = __fdiv_rn(__double2float_rn(sz), mf);
+            float b = 0.0f;
             for (uint32_t q = 0; q < nch; q++) {
                 const float4 cj = __ldcg(&nd.jpos[ch0 + q]);
                 const float4 cw = __ldcg(&nd.walk[ch0 + q]);
-                const double e = __dadd_rn(__dsqrt_rn(sq3(__dsub_rn((double)cj.x, (double)jx),
-                                                          __dsub_rn((double)cj.y, (double)jy),
-                                                          __dsub_rn((double)cj.z, (double)jz))),
-                                           (double)cw.x);
+                const float e = __fadd_rn(__fsqrt_rn(sq3f(__fsub_rn(cj.x, jx), __fsub_rn(cj.y, jy),
+                                                          __fsub_rn(cj.z, jz))), cw.x);
                 if (e > b) b = e;
             }
             nd.sum[p] = DSum4{m, sx, sy, sz};
-            nd.jpos[p] = make_float4(jx, jy, jz, __double2float_rn(m));
-            nd.walk[p] = make_float4(__double2float_ru(b), __uint_as_float((uint32_t)ch0),
+            nd.jpos[p] = make_float4(jx, jy, jz, mf);
+            nd.walk[p] = make_float4(__fmul_rn(b, GT_RADIUS_MARGIN), __uint_as_float((uint32_t)ch0),
                                      __uint_as_float(nch), 0.0f);
             nd.arrive[p] = 0;
             c = p;

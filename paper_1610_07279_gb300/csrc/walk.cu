@@ -2,10 +2,14 @@
 // ij-parallelisation of Sec. 2.5.
 //
 // One warp walks one group at a time (a persistent grid; groups are taken from an
-// atomic counter, so slow groups do not hold a fixed share of the GPU).  Per group:
+// atomic counter, so slow groups do not hold a fixed share of the GPU).  A group is a
+// range of the active list: the actives of one tree cell (Sec. 2.4 reading) or a run
+// of group_max.  Per group:
+//   * S lanes per member (Sec. 2.5): fixed, or 32 / (members rounded up to a power of
+//     two) so that small groups still fill the warp;
 //   * pseudo i-particle: the sphere about the centre of the members' bounding box
-//     (Appendix B, "GEO"), radius rounded up to FP32 from an FP64 distance; |a_old| of
-//     the group is the smallest of its members';
+//     (Appendix B, "GEO"), the FP32 radius widened by (1 + 2^-20); |a_old| of the
+//     group is the smallest of its members';
 //   * breadth-first traversal: a ring-buffer queue of cells in a per-warp slice of
 //     global memory (when the queue fills up, the newest cells are taken first, i.e.
 //     depth-first, which bounds its size; the order of the interactions does not change
@@ -13,7 +17,8 @@
 //     distance lambda r_JI (Eqs. 2, 5-7) in FP32 with explicit rounding (so the decision
 //     is reproducible); accepted cells join the shared-memory interaction list,
 //     rejected cells push their children (warp prefix sum), rejected leaves copy their
-//     particles into the list (coalesced);
+//     particles into the list with asynchronous global-to-shared copies (cp.async),
+//     waited for only when the list is flushed;
 //   * the list is flushed through Eq. (1) whenever it fills: each i-particle is held by
 //     S lanes that take every S-th list entry (FP32, rsqrt), summed with xor-shuffles at
 //     the end.  The potential is accumulated too; the member's own term -G m_i/eps is
@@ -28,7 +33,7 @@ namespace {
 
 constexpr int WT = 256;           // threads per block
 constexpr int NWARP = WT / 32;
-constexpr int LIST_CAP = 320;     // interaction-list entries per warp
+constexpr int LIST_CAP = 384;     // interaction-list entries per warp
 constexpr int FLUSH_AT = 256;     // flush once the list holds this many
 // Depth-first reserve of the queue: popping the newest 32 cells and pushing at most
 // 8 children each grows the queue by <= 224 per tree level, <= ~22 x 256 in all.
@@ -47,6 +52,13 @@ __device__ __forceinline__ bool mac_accept(int mac, float theta, float dacc_amin
     return __fmul_rn(__fmul_rn(d2, d2), dacc_amin) >= __fmul_rn(__fmul_rn(G, jp.w), __fmul_rn(bJ, bJ));
 }
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 __device__ __forceinline__ void interact(const float4 s, float xi, float yi, float zi, float eps2,
                                          float &ax, float &ay, float &az, float &ph) {
     const float dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
@@ -60,9 +72,8 @@ __device__ __forceinline__ void interact(const float4 s, float xi, float yi, flo
     ph -= mr;
 }
 
-template <int S>
 __global__ __launch_bounds__(WT, 4) void k_walk(WalkArgs a) {
-    __shared__ float4 list_sm[NWARP][LIST_CAP];
+    __shared__ __align__(16) float4 list_sm[NWARP][LIST_CAP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4 *list = list_sm[warp];
     uint32_t *q = a.queue + (size_t)(blockIdx.x * NWARP + warp) * (size_t)a.qcap;
@@ -70,8 +81,7 @@ __global__ __launch_bounds__(WT, 4) void k_walk(WalkArgs a) {
     const int lifo_at = a.qcap - LIFO_ROOM;
     const uint32_t na = a.ctl->n_active;
     const uint32_t gmax = (uint32_t)a.gmax;
-    const uint32_t ngroups = (na + gmax - 1) / gmax;
-    const int slot = lane / S, sub = lane % S;
+    const uint32_t ngroups = a.gstart ? a.ctl->n_groups : (na + gmax - 1) / gmax;
     const unsigned FULL = 0xffffffffu;
     const unsigned lt = lanemask_lt();
     unsigned long long n_inter = 0, n_tests = 0;
@@ -81,8 +91,22 @@ __global__ __launch_bounds__(WT, 4) void k_walk(WalkArgs a) {
         if (lane == 0) g = atomicAdd(&a.ctl->group_next, 1u);
         g = __shfl_sync(FULL, g, 0);
         if (g >= ngroups) break;
-        const uint32_t a0 = g * gmax;
-        const uint32_t cnt = min(gmax, na - a0);
+        uint32_t a0, a1;
+        if (a.gstart) {
+            a0 = a.gstart[g];
+            a1 = g + 1 < ngroups ? a.gstart[g + 1] : na;
+        } else {
+            a0 = g * gmax;
+            a1 = min(a0 + gmax, na);
+        }
+        const uint32_t cnt = a1 - a0;
+        if (cnt == 0u || cnt > 32u) {  // a malformed group range: report it and skip
+            if (lane == 0) gt_set_error(a.ctl, GT_EINVAL, GTK_WALK);
+            continue;
+        }
+        const int S = a.ij_share ? a.ij_share : 32 >> (cnt <= 1 ? 0 : 32 - __clz(cnt - 1));
+        const int logS = __ffs(S) - 1;
+        const int slot = lane >> logS, sub = lane & (S - 1);
         const bool have = (uint32_t)slot < cnt;
         const uint32_t kk = a0 + (have ? (uint32_t)slot : 0u);
         uint32_t i = a.active ? a.active[kk] : kk;
@@ -108,18 +132,17 @@ __global__ __launch_bounds__(WT, 4) void k_walk(WalkArgs a) {
         const float cx = __fmul_rn(0.5f, __fadd_rn(mnx, mxx));
         const float cy = __fmul_rn(0.5f, __fadd_rn(mny, mxy));
         const float cz = __fmul_rn(0.5f, __fadd_rn(mnz, mxz));
-        const double ddx = __dsub_rn((double)pi.x, (double)cx);
-        const double ddy = __dsub_rn((double)pi.y, (double)cy);
-        const double ddz = __dsub_rn((double)pi.z, (double)cz);
-        double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+        const float ddx = __fsub_rn(pi.x, cx), ddy = __fsub_rn(pi.y, cy), ddz = __fsub_rn(pi.z, cz);
+        float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ddx, ddx), __fmul_rn(ddy, ddy)), __fmul_rn(ddz, ddz));
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) d2 = fmax(d2, __shfl_xor_sync(FULL, d2, o));
-        const float bI = __double2float_ru(__dsqrt_rn(d2));
+        for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(FULL, d2, o));
+        const float bI = __fmul_rn(__fsqrt_rn(d2), GT_RADIUS_MARGIN);
         const float dacc_amin = __fmul_rn(a.delta_acc, ao);
 
         float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f;
         int list_n = 0;
         auto flush = [&]() {
+            cp_async_wait_all();
             __syncwarp();
             int j = sub;
             for (; j + 3 * S < list_n; j += 4 * S) {
@@ -183,20 +206,33 @@ __global__ __launch_bounds__(WT, 4) void k_walk(WalkArgs a) {
                 for (uint32_t k = 0; k < nch; k++) q[(pos + k) & qmask] = l0 + k;
                 tail += tot;
             }
-            // opened leaves -> their particles into the list
-            unsigned lm = __ballot_sync(FULL, valid && !ok && leaf);
-            while (lm) {
-                const int src = __ffs(lm) - 1;
-                lm &= lm - 1;
-                const uint32_t lf = __shfl_sync(FULL, l0, src);
-                const uint32_t lc = __shfl_sync(FULL, l1 & ~GT_LEAF_FLAG, src);
-                uint32_t done = 0;
-                while (done < lc) {
-                    if (list_n == LIST_CAP) flush();
-                    const uint32_t take = min(lc - done, (uint32_t)(LIST_CAP - list_n));
-                    for (uint32_t k = lane; k < take; k += 32) list[list_n + k] = a.posm[lf + done + k];
-                    list_n += (int)take;
-                    done += take;
+            // opened leaves -> their particles into the list (asynchronous copies)
+            const uint32_t lc = (valid && !ok && leaf) ? (l1 & ~GT_LEAF_FLAG) : 0u;
+            const uint32_t lincl = warp_incl_scan(lc);
+            const uint32_t ltot = __shfl_sync(FULL, lincl, 31);
+            if (ltot) {
+                if (list_n + (int)ltot > LIST_CAP) flush();
+                if (ltot <= (uint32_t)LIST_CAP) {
+                    const uint32_t dst = (uint32_t)list_n + lincl - lc;
+                    for (uint32_t k = 0; k < lc; k++) cp_async16(&list[dst + k], &a.posm[l0 + k]);
+                    list_n += (int)ltot;
+                } else {  // leaves holding more particles than the list: one at a time, in chunks
+                    unsigned lm = __ballot_sync(FULL, lc != 0u);
+                    while (lm) {
+                        const int src = __ffs(lm) - 1;
+                        lm &= lm - 1;
+                        const uint32_t lf = __shfl_sync(FULL, l0, src);
+                        const uint32_t lcount = __shfl_sync(FULL, lc, src);
+                        uint32_t done = 0;
+                        while (done < lcount) {
+                            if (list_n == LIST_CAP) flush();
+                            const uint32_t take = min(lcount - done, (uint32_t)(LIST_CAP - list_n));
+                            for (uint32_t k = lane; k < take; k += 32)
+                                cp_async16(&list[list_n + k], &a.posm[lf + done + k]);
+                            list_n += (int)take;
+                            done += take;
+                        }
+                    }
                 }
             }
             if (list_n >= FLUSH_AT) flush();
@@ -204,13 +240,13 @@ __global__ __launch_bounds__(WT, 4) void k_walk(WalkArgs a) {
         }
         if (overflow) {
             if (lane == 0) gt_set_error(a.ctl, GT_EOVERFLOW, GTK_WALK);
+            cp_async_wait_all();
             list_n = 0;
             if (sub == 0 && have) a.acc[kk] = make_float4(NAN, NAN, NAN, NAN);
             __syncwarp();
             continue;
         }
         flush();
-#pragma unroll
         for (int o = 1; o < S; o <<= 1) {
             ax += __shfl_xor_sync(FULL, ax, o);
             ay += __shfl_xor_sync(FULL, ay, o);
@@ -228,38 +264,17 @@ __global__ __launch_bounds__(WT, 4) void k_walk(WalkArgs a) {
     }
 }
 
-template <int S>
-int blocks_for(int nsm) {
+}  // namespace
+
+int gt_walk_blocks(int nsm) {
     int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk<S>, WT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk, WT, 0);
     if (per < 1) per = 1;
     return per * nsm;
 }
 
-}  // namespace
-
-int gt_walk_blocks(int ij_share, int nsm) {
-    switch (ij_share) {
-        case 1: return blocks_for<1>(nsm);
-        case 2: return blocks_for<2>(nsm);
-        case 4: return blocks_for<4>(nsm);
-        case 8: return blocks_for<8>(nsm);
-        case 16: return blocks_for<16>(nsm);
-        case 32: return blocks_for<32>(nsm);
-        default: return -1;
-    }
-}
-
 int gt_walk_warps_per_block() { return NWARP; }
 
-void gt_launch_walk(const WalkArgs &a, int ij_share, int nblocks, cudaStream_t st) {
-    switch (ij_share) {
-        case 1: { k_walk<1><<<nblocks, WT, 0, st>>>(a); gt_note_launches(1); } break;
-        case 2: { k_walk<2><<<nblocks, WT, 0, st>>>(a); gt_note_launches(1); } break;
-        case 4: { k_walk<4><<<nblocks, WT, 0, st>>>(a); gt_note_launches(1); } break;
-        case 8: { k_walk<8><<<nblocks, WT, 0, st>>>(a); gt_note_launches(1); } break;
-        case 16: { k_walk<16><<<nblocks, WT, 0, st>>>(a); gt_note_launches(1); } break;
-        case 32: { k_walk<32><<<nblocks, WT, 0, st>>>(a); gt_note_launches(1); } break;
-        default: break;
-    }
+void gt_launch_walk(const WalkArgs &a, int nblocks, cudaStream_t st) {
+    { k_walk<<<nblocks, WT, 0, st>>>(a); gt_note_launches(1); }
 }

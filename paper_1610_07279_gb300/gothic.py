@@ -36,7 +36,12 @@ class gt_params(C.Structure):
                 ("eps", C.c_float), ("G", C.c_float), ("leaf_max", C.c_int32),
                 ("group_max", C.c_int32), ("ij_share", C.c_int32), ("levels", C.c_int32),
                 ("rebuild_every", C.c_int32), ("walk_queue", C.c_int32), ("node_factor", C.c_int32),
-                ("eta", C.c_double), ("dt_max", C.c_double)]
+                ("eta", C.c_double), ("dt_max", C.c_double), ("group_mode", C.c_int32),
+                ("reserved1", C.c_int32)]
+
+
+GT_GROUP_RUNS = 0
+GT_GROUP_CELLS = 1
 
 
 class gt_stats(C.Structure):
@@ -101,6 +106,8 @@ def load(path: str | None = None):
     L.gt_get_timers.argtypes = [P, C.POINTER(C.c_double), C.POINTER(I64), P]
     L.gt_kernel_launches.argtypes = [C.POINTER(I64)]
     L.gt_sort_pairs_noalloc.argtypes = [P, P, I64, P]
+    L.gt_rebuild_interval.argtypes = [C.POINTER(C.c_double), I32, C.c_double, C.POINTER(I32),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.gt_get_tree.argtypes = [P, P, P, P, P, P, C.POINTER(I64), P]
     L.gt_get_active.argtypes = [P, P, C.POINTER(I64), P]
     L.gt_sync_status.argtypes = [P, P]
@@ -147,6 +154,17 @@ def gt_kernel_launches() -> int:
     c = C.c_int64(0)
     _check(load().gt_kernel_launches(C.byref(c)), "gt_kernel_launches")
     return int(c.value)
+
+
+def gt_rebuild_interval(t_walk, t_make: float):
+    """(model, n_opt, coef) of the rebuild-interval fit (host only, no GPU needed)."""
+    t = np.ascontiguousarray(t_walk, np.float64)
+    model = C.c_int(0)
+    nopt = C.c_double(0.0)
+    coef = (C.c_double * 3)()
+    _check(load().gt_rebuild_interval(t.ctypes.data_as(C.POINTER(C.c_double)), int(t.size), float(t_make),
+                                      C.byref(model), C.byref(nopt), coef), "gt_rebuild_interval")
+    return int(model.value), float(nopt.value), [float(c) for c in coef]
 
 
 GT_NOALLOC_SORT_MAX = 1 << 20

@@ -40,7 +40,8 @@ def test_binding_loads_and_strerror(libpath):
 
 def test_struct_layout_matches_header(libpath):
     from paper_1610_07279_gb300 import gothic
-    assert ctypes.sizeof(gothic.gt_params) == 64 and gothic.gt_params.node_factor.offset == 44
+    assert ctypes.sizeof(gothic.gt_params) == 72 and gothic.gt_params.node_factor.offset == 44
+    assert gothic.gt_params.group_mode.offset == 64
     assert gothic.gt_params.eta.offset == 48
     assert ctypes.sizeof(gothic.gt_stats) == 96
 
@@ -49,7 +50,8 @@ def test_default_params_host_only(libpath):
     from paper_1610_07279_gb300 import gothic
     p = gothic.gt_default_params()
     assert p.mac == gothic.GT_MAC_ACCELERATION and p.delta_acc == 2.0 ** -7
-    assert p.leaf_max == 16 and p.group_max == 32 and p.ij_share == 1
+    assert p.leaf_max == 16 and p.group_max == 32 and p.ij_share == 0
+    assert p.group_mode == gothic.GT_GROUP_CELLS
 
 
 def test_no_cpu_fallback_in_product():

@@ -65,7 +65,7 @@ def _params(g, eps, **kw):
 def _oparams(O, prm):
     return O.Params(mac=prm.mac, theta=prm.theta, delta_acc=prm.delta_acc, eps=prm.eps, G=prm.G,
                     leaf_max=prm.leaf_max, group_max=prm.group_max, levels=prm.levels, eta=prm.eta,
-                    dt_max=prm.dt_max)
+                    dt_max=prm.dt_max, group_mode=prm.group_mode)
 
 
 def _rel(a, r):
@@ -189,23 +189,26 @@ def _walk_case(env, kind, n, seed, mac, S, gmax, active_frac=None, **kw):
 
 
 @pytest.mark.parametrize("mac", [0, 1])
-@pytest.mark.parametrize("S,gmax", [(1, 32), (1, 20), (2, 16), (4, 8), (32, 1)])
-def test_walk_plummer_config(env, mac, S, gmax):
-    _walk_case(env, "plummer", 1 << 13, 1, mac, S, gmax)
+@pytest.mark.parametrize("S,gmax,mode", [(0, 32, 1), (1, 32, 1), (0, 20, 1), (2, 16, 1), (4, 8, 1), (32, 1, 1),
+                                         (1, 32, 0), (0, 32, 0), (0, 13, 0)])
+def test_walk_plummer_config(env, mac, S, gmax, mode):
+    _walk_case(env, "plummer", 1 << 13, 1, mac, S, gmax, group_mode=mode)
 
 
 @pytest.mark.parametrize("kind,n", [("nfw", 40000), ("m31", 1 << 15), ("clustered", 9000)])
 def test_walk_other_models(env, kind, n):
-    _walk_case(env, kind, n, 3, 1, 1, 32)
+    _walk_case(env, kind, n, 3, 1, 0, 32)
 
 
-def test_walk_active_subset(env):
-    _walk_case(env, "nfw", 30011, 4, 1, 1, 32, active_frac=0.17)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_walk_active_subset(env, mode):
+    _walk_case(env, "nfw", 30011, 4, 1, 0, 32, active_frac=0.17, group_mode=mode)
 
 
 def test_walk_small_leaf_and_list(env):
-    _walk_case(env, "plummer", 7000, 5, 1, 1, 32, leaf_max=1)
-    _walk_case(env, "coincident", 700, 5, 1, 1, 32)
+    _walk_case(env, "plummer", 7000, 5, 1, 0, 32, leaf_max=1)
+    _walk_case(env, "coincident", 700, 5, 1, 0, 32)
+    _walk_case(env, "coincident", 700, 5, 1, 0, 32, leaf_max=500)  # leaves larger than the list
 
 
 def test_walk_queue_overflow_is_reported(env):
@@ -269,7 +272,7 @@ def test_start_matches_oracle(env):
     torch, g, O = env
     n = 1 << 14
     pos, vel, mass, eps = ics.nfw(n, seed=12)
-    prm = _params(g, eps, levels=6)
+    prm = _params(g, eps, levels=6, rebuild_every=1)
     oprm = _oparams(O, prm)
     sim = O.BlockStepSim(pos, vel, mass, oprm)
     boot = O.bootstrap_aold(_p4(pos, mass), oprm)
@@ -293,7 +296,7 @@ def test_block_steps_match_oracle(env):
     torch, g, O = env
     n = 1 << 14
     pos, vel, mass, eps = ics.nfw(n, seed=13)
-    prm = _params(g, eps, levels=5)
+    prm = _params(g, eps, levels=5, rebuild_every=1)
     oprm = _oparams(O, prm)
     sim = O.BlockStepSim(pos, vel, mass, oprm)
     boot = O.bootstrap_aold(_p4(pos, mass), oprm)
@@ -326,7 +329,7 @@ def test_checkpoint_resume_bitexact(env):
     torch, g, O = env
     n = 1 << 13
     pos, vel, mass, eps = ics.plummer(n, seed=14)
-    prm = _params(g, eps, levels=5)
+    prm = _params(g, eps, levels=5, rebuild_every=1)
     a = g.System(n, prm)
     a.set_state(pos, vel, mass)
     a.start()
@@ -352,6 +355,35 @@ def test_checkpoint_resume_bitexact(env):
     b.close()
 
 
+def test_automatic_rebuild_interval(env):
+    """rebuild_every = 0 (Sec. 2.6): the tree is reused between rebuilds with refreshed pseudo
+    j-particles; the run rebuilds less often than it steps and stays close to the run that
+    rebuilds every step."""
+    torch, g, O = env
+    n = 1 << 15
+    pos, vel, mass, eps = ics.nfw(n, seed=15)
+    runs = {}
+    for every in (0, 1):
+        s = g.System(n, _params(g, eps, levels=5, rebuild_every=every))
+        s.set_state(pos, vel, mass)
+        s.start()
+        steps = s.advance(3 * 16)  # three longest steps
+        st = s.stats()
+        runs[every] = (steps, st, s.get_state())
+        assert s.status() == g.GT_OK
+        s.close()
+    steps0, st0, end0 = runs[0]
+    steps1, st1, end1 = runs[1]
+    assert steps0 == steps1 and st0["T"] == st1["T"]
+    assert st0["rebuilds"] < st1["rebuilds"]
+    a0 = np.empty_like(end0["acc"])
+    a0[end0["id"]] = end0["acc"]
+    a1 = np.empty_like(end1["acc"])
+    a1[end1["id"]] = end1["acc"]
+    rel = _rel(a0, a1.astype(np.float64))
+    assert np.median(rel) < 5e-3
+
+
 # ------------------------------------------------------------------ full sizes, sampled
 def _full_size_sampled(env, kind, n, seed, ngroups_sample=48):
     torch, g, O = env
@@ -369,15 +401,16 @@ def _full_size_sampled(env, kind, n, seed, ngroups_sample=48):
     acc = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
     s.accel_active(None, torch.from_numpy(aold).cuda(), acc)
     s.sync()
-    ng = -(-n // prm.group_max)
+    active = np.arange(n, dtype=np.uint32)
+    sp4 = ref["p4"][ref["order"]]
+    starts = O.group_starts(ref["tree"], n, active, prm.group_max, prm.group_mode)
+    ng = len(starts) - 1
     gids = np.unique(np.random.default_rng(seed + 1).integers(0, ng, ngroups_sample))
     gids = np.union1d(gids, [0, ng - 1])
-    active = np.arange(n, dtype=np.uint32)
-    gI, gamin = O.groups(active, prm.group_max, ref["p4"][ref["order"]], aold)
-    oacc, inter, _ = O.walk(ref["tree"], ref["jpos"], ref["bj"], ref["p4"][ref["order"]], active,
-                            prm.group_max, gI, gamin, prm.mac, prm.theta, prm.delta_acc, prm.eps, prm.G,
-                            group_ids=gids)
-    rows = np.concatenate([np.arange(gg * prm.group_max, min(n, (gg + 1) * prm.group_max)) for gg in gids])
+    gI, gamin = O.groups(starts, active, sp4, aold)
+    oacc, inter, _ = O.walk(ref["tree"], ref["jpos"], ref["bj"], sp4, active, starts, gI, gamin, prm.mac,
+                            prm.theta, prm.delta_acc, prm.eps, prm.G, group_ids=gids)
+    rows = np.concatenate([np.arange(starts[gg], starts[gg + 1]) for gg in gids])
     rel = _rel(acc.cpu().numpy()[rows], oacc[rows])
     assert np.median(rel) <= MED_TOL and np.percentile(rel, 99) <= P99_TOL, (np.median(rel), np.percentile(rel, 99))
     s.close()

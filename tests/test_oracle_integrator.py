@@ -7,21 +7,39 @@ import pytest
 from paper_1610_07279_gb300 import ics
 
 
-def test_level_from_amag_brute_force(oracle_lib):
+def test_level_from_a2_brute_force(oracle_lib):
+    """Smallest k with dt_max 2^-k <= dt_i = sqrt(c/|a|), c = 2 eta eps, decided exactly
+    (rational arithmetic on the FP64 inputs: dt_k^4 |a|^2 <= c^2, c^2 rounded once)."""
+    from fractions import Fraction as Fr
     O = oracle_lib
     eta, eps, M, L = 0.025, 0.01, 2, 8
+    c = (2.0 * eta) * eps
+    c2 = Fr(c * c)
     rng = np.random.default_rng(3)
-    for am in np.concatenate([10.0 ** rng.uniform(-6, 3, 3000), [0.0, 1e300]]):
+    a2s = list(10.0 ** rng.uniform(-12, 6, 3000)) + [0.0, 1e300]
+    # values sitting exactly on level boundaries: |a|^2 = c2 / dt_k^4
+    a2s += [float(c2 / Fr(2) ** (4 * (M - k))) for k in range(L)]
+    for a2 in a2s:
         want = 0
-        if am > 0:
-            dti = math.sqrt(((2.0 * eta) * eps) / am)
-            # smallest k with dt_max 2^-k <= dt_i, clamped to [0, L-1]
-            want = next((k for k in range(L) if math.ldexp(1.0, M - k) <= dti), L - 1)
-        assert O.level_from_amag(am, eta, eps, M, L) == want, am
-    # exactly on a level boundary: dt_i == dt_k belongs to level k
-    am = (2.0 * eta) * eps / (math.ldexp(1.0, M - 3) ** 2)
-    assert math.sqrt(((2.0 * eta) * eps) / am) == math.ldexp(1.0, M - 3)
-    assert O.level_from_amag(am, eta, eps, M, L) == 3
+        if a2 > 0:
+            want = next((k for k in range(L) if Fr(2) ** (4 * (M - k)) * Fr(a2) <= c2), L - 1)
+        assert O.level_from_a2(a2, eta, eps, M, L) == want, a2
+
+
+def test_dtmax_exponent_brute_force(oracle_lib):
+    from fractions import Fraction as Fr
+    O = oracle_lib
+    eta, eps = 0.025, 1.0 / 64
+    c2 = Fr(((2.0 * eta) * eps) ** 2)
+    rng = np.random.default_rng(4)
+    for _ in range(300):
+        acc = np.zeros((5, 4), np.float32)
+        acc[:, :3] = (rng.standard_normal((5, 3)) * 10.0 ** rng.uniform(-6, 3)).astype(np.float32)
+        a2 = O.a2(acc)
+        a2min = Fr(float(a2[a2 > 0].min()))
+        # largest M with 2^M <= dt_i of the particle with the smallest |a|
+        M = max(m for m in range(-80, 80) if Fr(2) ** (4 * m) * a2min <= c2)
+        assert O.dtmax_exponent(acc, eta, eps) == M
 
 
 def _one(O, kold, kc_amag, T, t0, L=6, M=0, eta=0.025, eps=0.01):
@@ -35,7 +53,7 @@ def _one(O, kold, kc_amag, T, t0, L=6, M=0, eta=0.025, eps=0.01):
     return int(lv[0]), int(t0a[0])
 
 
-def _amag_for_level(k, M=0, eta=0.025, eps=0.01):
+def _amag_for_level(k, M=0, eta=0.025, eps=0.01):  # |a| whose dt_i is 1.5 dt_k
     dti = 1.5 * math.ldexp(1.0, int(M) - int(k))  # level k holds dt in [dt_k, 2 dt_k)
     return float(np.float32((2.0 * eta) * eps / (dti * dti)))
 
@@ -80,7 +98,9 @@ def test_active_counts_closed_form(oracle_lib):
 
 
 def test_shared_step_reduces_to_leapfrog(oracle_lib):
-    """L = 1 (one shared, fixed step): the block-step scheme is the KDK leap-frog."""
+    """L = 1 (one shared, fixed step): the block-step scheme is the KDK leap-frog (P:388-396);
+    the reference here uses separate multiplies and adds, the scheme fused ones, so the two
+    agree to rounding."""
     O = oracle_lib
     n = 512
     pos, vel, m, eps = ics.plummer(n, seed=21)
@@ -109,10 +129,10 @@ def test_shared_step_reduces_to_leapfrog(oracle_lib):
         vh = v + (0.5 * dt) * a
         back = np.empty_like(sim.r0)
         back[sim.id] = sim.r0
-        np.testing.assert_array_equal(back, r)
+        np.testing.assert_allclose(back, r, rtol=1e-13, atol=1e-15)
         bv = np.empty_like(sim.vh)
         bv[sim.id] = sim.vh
-        np.testing.assert_array_equal(bv, vh)
+        np.testing.assert_allclose(bv, vh, rtol=1e-11, atol=1e-14)
         assert sim.T == step + 1
 
 

@@ -121,9 +121,9 @@ def test_pseudo_j_invariants(oracle_lib):
     jpos, bj = O.pseudo_j(t, sp4)
     # equal power-of-two masses: the root mass is exact
     assert jpos[0, 3] == np.float32(sp4[:, 3].astype(np.float64).sum())
-    # root COM = system COM (FP64), within the FP32 rounding of r_J
+    # root COM = system COM (FP64), within the FP32 quotient's rounding (<= 1.5 ulp)
     com = (sp4[:, 3:4].astype(np.float64) * sp4[:, :3]).sum(0) / sp4[:, 3].astype(np.float64).sum()
-    assert np.all(np.abs(jpos[0, :3] - com) <= np.spacing(np.abs(com).astype(np.float32)) + 1e-12)
+    assert np.all(np.abs(jpos[0, :3] - com) <= 2 * np.spacing(np.abs(com).astype(np.float32)) + 1e-12)
     # every particle lies inside the b_J sphere of every cell that holds it
     for c in range(t["n_nodes"]):
         f, k = t["first"][c], t["count"][c]
@@ -133,12 +133,12 @@ def test_pseudo_j_invariants(oracle_lib):
     one = t["count"] == 1
     assert np.all(bj[one] == 0)
     assert np.array_equal(jpos[one, :3], sp4[t["first"][one], :3])
-    # a leaf's b_J is its largest particle distance rounded up to FP32 (tight)
+    # a leaf's b_J is its largest particle distance widened by ~2^-20 (tight)
     leaves = np.nonzero(t["child"] < 0)[0]
     for c in leaves[:500]:
         f, k = t["first"][c], t["count"][c]
         d = np.linalg.norm(sp4[f:f + k, :3].astype(np.float64) - jpos[c, :3].astype(np.float64), axis=1)
-        assert bj[c] >= d.max() and np.nextafter(bj[c], np.float32(0)) < d.max() or bj[c] == 0
+        assert d.max() <= bj[c] <= d.max() * (1 + 2.0 ** -18) + 1e-30
 
 
 def test_pseudo_j_com_per_cell(oracle_lib):
@@ -157,4 +157,4 @@ def test_pseudo_j_com_per_cell(oracle_lib):
         M = m.sum()
         com = (m[:, None] * sp4[f:f + k, :3]).sum(0) / M
         assert abs(jpos[c, 3] - M) <= np.spacing(np.float32(M))
-        assert np.all(np.abs(jpos[c, :3] - com) <= 1.01 * np.spacing(np.abs(com).astype(np.float32)) + 1e-15)
+        assert np.all(np.abs(jpos[c, :3] - com) <= 2 * np.spacing(np.abs(com).astype(np.float32)) + 1e-15)
