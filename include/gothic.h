@@ -287,10 +287,10 @@ GT_API int gt_measure_fp32_peak(double *flops, gt_stream stream);
  * order), with the same radix-sort kernels gt_build_tree uses.  d_keys (n
  * uint64) and d_vals (n uint32) are device arrays owned by the caller; they
  * receive the sorted pairs.  The scratch the sort needs (the alternate key and
- * value buffers, per-tile digit histograms and a control word) lives in one
- * file-scope device array of the library, sized for GT_NOALLOC_SORT_MAX pairs
- * (about 12.3 MiB, held on every GPU that loads the library until the process
- * exits); nothing is allocated or freed by the call.
+ * value buffers, per-tile look-back status words, digit histograms and a control
+ * block) lives in one file-scope device array of the library, sized for
+ * GT_NOALLOC_SORT_MAX pairs (about 13.1 MiB, held on every GPU that loads the
+ * library until the process exits); nothing is allocated or freed by the call.
  *   - n > GT_NOALLOC_SORT_MAX: rejected with GT_EINVAL before any device work.
  *   - The first call on a device looks up the array's device address (once per
  *     device, with that device current); make that first call before any stream

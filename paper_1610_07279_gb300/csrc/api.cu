@@ -44,7 +44,6 @@ struct gt_system {
     gt_params prm{};
     int dev = 0, nsm = 0;
     int walk_blocks = 0, walk_warps = 0;
-    int cur = 0;
     bool started = false, have_tree = false, last_rebuilt = false;
     long long steps = 0, rebuilds = 0;
     int64_t cap = 0;        // node capacity
@@ -137,9 +136,9 @@ size_t carve(gt_system *s, char *base, int64_t n, const gt_params *p, int nsm, i
         s->sb.key[b] = L.take<uint64_t>(base, N);
         s->sb.val[b] = L.take<uint32_t>(base, N);
     }
-    s->sb.tile_hist = (uint32_t *)L.take<char>(base, gt_sort_scratch_bytes(n));
-    s->sb.digit_base = L.take<uint32_t>(base, 256);
-    s->sb.digit_total = L.take<uint32_t>(base, 256);
+    s->sb.status = (unsigned long long *)L.take<char>(base, gt_sort_scratch_bytes(n));
+    s->sb.hist = L.take<uint32_t>(base, 8 * 256);
+    s->sb.digit_base = L.take<uint32_t>(base, 8 * 256);
     const int64_t cap = node_capacity(n, p);
     s->cap = cap;
     s->nd.first = L.take<uint32_t>(base, cap);
@@ -147,10 +146,14 @@ size_t carve(gt_system *s, char *base, int64_t n, const gt_params *p, int nsm, i
     s->nd.child = L.take<int32_t>(base, cap);
     s->nd.nchild = L.take<uint32_t>(base, cap);
     s->nd.parent = L.take<int32_t>(base, cap);
-    s->nd.arrive = L.take<uint32_t>(base, cap);
     s->nd.jpos = L.take<float4>(base, cap);
     s->nd.walk = L.take<float4>(base, cap);
     s->nd.sum = L.take<DSum4>(base, cap);
+    s->nd.leaf_flag = L.take<uint8_t>(base, N);
+    s->nd.node_at = L.take<uint32_t>(base, N);
+    s->nd.leaf_first = L.take<uint32_t>(base, N);
+    s->nd.internal = L.take<uint32_t>(base, cap);
+    s->nd.iprefix = L.take<uint32_t>(base, cap + 1);
     const int64_t st_tiles = (cap + 511) / 512 + (n + 4095) / 4096 + 64;
     s->status = L.take<unsigned long long>(base, st_tiles);
     s->active = L.take<uint32_t>(base, N);
@@ -244,7 +247,10 @@ void ph_sync_collect(gt_system *s, cudaStream_t st) {
 
 cudaStream_t S(gt_stream s) { return (cudaStream_t)s; }
 
-// A1-A5 on the current FP32 positions in s->posm (permutes every array into key order)
+// A1-A5 on FP32 positions posm_src (s->posm or the predicted s->posm_tmp): keys, sort,
+// then every particle array gathered into key order.  Buffer roles never change
+// (state 0 and posm always hold the current data), so the launches can be captured
+// in a CUDA graph and replayed.
 void build_tree(gt_system *s, cudaStream_t st, const float4 *posm_src) {
     const int64_t n = s->n;
     gt_launch_prepare(s->ctl, 0, st);
@@ -253,19 +259,20 @@ void build_tree(gt_system *s, cudaStream_t st, const float4 *posm_src) {
     gt_launch_keys(posm_src, n, s->ctl, s->sb.key[0], s->sb.val[0], st);
     gt_launch_sort(s->sb, n, s->ctl, st);
     ph_end(s, PH_SORT, st);
-    const int nxt = s->cur ^ 1;
-    float4 *dst = posm_src == s->posm ? s->posm_tmp : s->posm;
     ph_begin(s, PH_PERMUTE, st);
-    gt_launch_permute(s->st[s->cur], s->st[nxt], posm_src, dst, s->sb.val[0], n, st);
-    ph_end(s, PH_PERMUTE, st);
-    s->cur = nxt;
-    if (dst != s->posm) {
-        float4 *t = s->posm;
-        s->posm = s->posm_tmp;
-        s->posm_tmp = t;
+    if (posm_src == s->posm_tmp) {
+        gt_launch_permute(s->st[0], s->st[1], posm_src, s->posm, s->sb.val[0], n, st);
+        gt_launch_copy_state(s->st[1], s->st[0], nullptr, nullptr, n, st);
+    } else {
+        gt_launch_permute(s->st[0], s->st[1], posm_src, s->posm_tmp, s->sb.val[0], n, st);
+        gt_launch_copy_state(s->st[1], s->st[0], s->posm_tmp, s->posm, n, st);
     }
+    ph_end(s, PH_PERMUTE, st);
     ph_begin(s, PH_BUILD, st);
+    if (n > 0) cudaMemsetAsync(s->nd.leaf_flag, 0, (size_t)n, st);
     gt_launch_build(s->sb.key[0], n, s->prm.leaf_max, s->nd, s->cap, s->status, s->ctl, s->nsm, st);
+    gt_launch_leaf_list(s->nd, n, s->ctl, s->status, s->nsm, st);
+    gt_launch_internal_list(s->nd, s->ctl, s->status, s->nsm, st);
     ph_end(s, PH_BUILD, st);
     ph_begin(s, PH_PSEUDO, st);
     gt_launch_pseudo(s->nd, s->cap, s->posm, s->ctl, s->nsm, st);
@@ -315,7 +322,7 @@ void walk(gt_system *s, const uint32_t *active, const float *aold, float4 *acc, 
 // every particle active (start-up passes, gt_accel_active with no list)
 void walk_all(gt_system *s, const float *aold, float4 *acc, int mac, cudaStream_t st) {
     gt_launch_prepare(s->ctl, 0, st);
-    gt_launch_active(s->st[s->cur], s->n, s->prm.levels, 1, s->ctl, s->active, s->prefix, s->status, s->nsm, st);
+    gt_launch_active(s->st[0], s->n, s->prm.levels, 1, s->ctl, s->active, s->prefix, s->status, s->nsm, st);
     walk(s, nullptr, aold, acc, mac, st);
 }
 
@@ -386,10 +393,10 @@ int gt_system_create(gt_system **out, int64_t n, const gt_params *prm, void *d_w
     carve(s, (char *)d_ws, n, prm, s->nsm, wb);
     s->n = n;
     s->prm = *prm;
-    // zero the control block, the look-back status words and the arrival counters
+    // zero the control block and the look-back status words
     if (cudaMemset(s->ctl, 0, sizeof(DevCtl)) != cudaSuccess ||
         cudaMemset(s->status, 0, (size_t)((s->cap + 511) / 512 + (n + 4095) / 4096 + 64) * 8) != cudaSuccess ||
-        cudaMemset(s->nd.arrive, 0, (size_t)s->cap * 4) != cudaSuccess ||
+        cudaMemset(s->sb.status, 0, gt_sort_scratch_bytes(n)) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess) {
         delete s;
         return GT_ECUDA;
@@ -427,7 +434,6 @@ int gt_set_state(gt_system *s, const double *p_pos, const double *p_vel, const f
     if (!s || (s->n > 0 && (!p_pos || !p_vel || !p_mass))) return GT_EINVAL;
     cudaStream_t st = S(stream);
     const int64_t n = s->n;
-    s->cur = 0;
     State &t = s->st[0];
     if (n > 0) {
         if (cudaMemcpyAsync(s->scratch3, p_pos, (size_t)n * 24, cudaMemcpyDefault, st) != cudaSuccess) return GT_ECUDA;
@@ -455,7 +461,7 @@ int gt_accel_active(gt_system *s, const uint32_t *d_active, int64_t n_active, co
     if (!d_active && n_active != s->n) return GT_EINVAL;
     if (!s->have_tree) return GT_ESTATE;
     cudaStream_t st = S(stream);
-    const float *aold = d_aold ? d_aold : s->st[s->cur].aold;
+    const float *aold = d_aold ? d_aold : s->st[0].aold;
     if (!d_active) {
         walk_all(s, aold, (float4 *)d_acc, s->prm.mac, st);
     } else if (s->prm.group_mode == GT_GROUP_CELLS) {
@@ -476,7 +482,7 @@ int gt_start(gt_system *s, const float *p_aold_boot, gt_stream stream) {
     cudaStream_t st = S(stream);
     const int64_t n = s->n;
     build_tree(s, st, s->posm);
-    State &t = s->st[s->cur];
+    State &t = s->st[0];
     if (p_aold_boot) {
         if (n > 0 && cudaMemcpyAsync(s->aold_tmp, p_aold_boot, (size_t)n * 4, cudaMemcpyDefault, st) != cudaSuccess)
             return GT_ECUDA;
@@ -528,7 +534,7 @@ int gt_block_step(gt_system *s, gt_stream stream) {
     s->last_rebuilt = rebuild;
     gt_launch_prepare(s->ctl, 1, st);
     ph_begin(s, PH_PREDICT, st);
-    gt_launch_predict(s->st[s->cur], n, s->ctl, rebuild ? s->posm_tmp : s->posm, st);
+    gt_launch_predict(s->st[0], n, s->ctl, rebuild ? s->posm_tmp : s->posm, st);
     ph_end(s, PH_PREDICT, st);
     if (rebuild) {
         build_tree(s, st, s->posm_tmp);
@@ -537,7 +543,7 @@ int gt_block_step(gt_system *s, gt_stream stream) {
         gt_launch_pseudo(s->nd, s->cap, s->posm, s->ctl, s->nsm, st);
         ph_end(s, PH_PSEUDO, st);
     }
-    State &t = s->st[s->cur];
+    State &t = s->st[0];
     ph_begin(s, PH_ACTIVE, st);
     gt_launch_active(t, n, s->prm.levels, 0, s->ctl, s->active, s->prefix, s->status, s->nsm, st);
     ph_end(s, PH_ACTIVE, st);
@@ -558,7 +564,7 @@ int gt_set_integrator_state(gt_system *s, const uint8_t *p_level, const int64_t 
     cudaStream_t st = S(stream);
     const int64_t n = s->n;
     const int L = s->prm.levels;
-    State &t = s->st[s->cur];
+    State &t = s->st[0];
     if (n > 0) {
         // stage the caller-order arrays in scratch (24 B per particle is enough for 1+8+4 B)
         char *base = (char *)s->scratch3;
@@ -585,7 +591,7 @@ int gt_predict(gt_system *s, int64_t T, float *d_posm, gt_stream stream) {
     if (!s->started) return GT_ESTATE;
     cudaStream_t st = S(stream);
     gt_launch_set_tnext(s->ctl, T, st);
-    gt_launch_predict(s->st[s->cur], s->n, s->ctl, (float4 *)d_posm, st);
+    gt_launch_predict(s->st[0], s->n, s->ctl, (float4 *)d_posm, st);
     return last_cuda();
 }
 
@@ -595,7 +601,7 @@ int gt_correct(gt_system *s, const uint32_t *d_active, int64_t n_active, const f
         return GT_EINVAL;
     if (!s->started) return GT_ESTATE;
     cudaStream_t st = S(stream);
-    State &t = s->st[s->cur];
+    State &t = s->st[0];
     gt_launch_set_tnext(s->ctl, T, st);
     gt_launch_set_nactive(s->ctl, (unsigned)n_active, st);
     gt_launch_correct(t, d_active, (const float4 *)d_acc, s->ctl, s->n, s->prm.levels, c2_of(s->prm), s->nsm, st);
@@ -663,7 +669,7 @@ int gt_get_state(gt_system *s, double *p_pos, double *p_vel, float *p_mass, floa
     cudaStream_t st = S(stream);
     const int64_t n = s->n;
     if (n == 0) return GT_OK;
-    const State &t = s->st[s->cur];
+    const State &t = s->st[0];
     if (p_pos) {
         gt_launch_interleave3(t.rx, t.ry, t.rz, n, s->scratch3, st);
         if (cudaMemcpyAsync(p_pos, s->scratch3, (size_t)n * 24, cudaMemcpyDefault, st)) return GT_ECUDA;
@@ -699,7 +705,7 @@ int gt_get_tree(gt_system *s, uint64_t *p_keys, uint32_t *p_order, uint32_t *p_n
     const int64_t capacity = *n_nodes_inout;
     *n_nodes_inout = nn;
     if (n > 0 && p_keys && cudaMemcpyAsync(p_keys, s->sb.key[0], (size_t)n * 8, cudaMemcpyDefault, st)) return GT_ECUDA;
-    if (n > 0 && p_order && cudaMemcpyAsync(p_order, s->st[s->cur].id, (size_t)n * 4, cudaMemcpyDefault, st))
+    if (n > 0 && p_order && cudaMemcpyAsync(p_order, s->st[0].id, (size_t)n * 4, cudaMemcpyDefault, st))
         return GT_ECUDA;
     if (nn > capacity && (p_nodes || p_jpos || p_bj)) return GT_EOVERFLOW;
     if (nn > 0) {

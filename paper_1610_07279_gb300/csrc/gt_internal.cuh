@@ -26,10 +26,14 @@ struct DevCtl {
     unsigned int epoch;               // bumped once per tree build / compaction
     unsigned int n_active;            // i-particles of the current force evaluation
     unsigned int n_groups;            // groups of the current force evaluation (cell grouping)
+    unsigned int n_leaves;            // leaves of the current tree
+    unsigned int n_internal;          // cells with children
+    unsigned int istart[GT_TREE_LEVELS + 2];  // first entry of every level in the internal-cell list
     unsigned int group_next;          // dynamic group counter of the walk
-    unsigned int tile_ticket[GT_TREE_LEVELS + 2];  // dynamic tile ids (build levels, compaction)
+    unsigned int tile_ticket[GT_TREE_LEVELS + 4];  // dynamic tile ids: levels, actives, groups, leaves, cells
     unsigned int level_start[GT_TREE_LEVELS + 2];  // first cell of each level; [22] = node count
-    unsigned int sort_done;           // last-block counter of the digit scan
+    unsigned int sort_ticket[8];      // dynamic tile ids of the 8 sort passes
+    unsigned int sort_epoch;          // look-back epoch of the sort
     unsigned long long interactions;  // cumulative
     unsigned long long mac_tests;     // cumulative
     unsigned long long tnext;         // block time of the current step
@@ -67,11 +71,15 @@ struct Nodes {
     int32_t *child;            // first child, -1 for a leaf
     uint32_t *nchild;
     int32_t *parent;
-    uint32_t *arrive;          // bottom-up arrival counters (zero between passes)
     float4 *jpos;              // pseudo j-particle (x, y, z, m) FP32
     float4 *walk;              // (b_J, link0, link1, 0): link0 = first child or first particle,
                                // link1 = nchild, or count | GT_LEAF_FLAG for a leaf
     DSum4 *sum;                // FP64 (m, m x, m y, m z)
+    uint8_t *leaf_flag;        // per particle: 1 where a leaf starts (build scratch)
+    uint32_t *node_at;         // per particle: the leaf starting there
+    uint32_t *leaf_first;      // first particle of every leaf, in particle order
+    uint32_t *internal;        // cells with children, in node (level) order
+    uint32_t *iprefix;         // per node: cells with children before it (build scratch)
 };
 
 __device__ __forceinline__ void gt_set_error(DevCtl *ctl, int code, int where) {
@@ -84,6 +92,19 @@ __device__ __forceinline__ unsigned int lanemask_lt() {
     unsigned int m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+// Exact FP32 -> FP64 conversion of a normal float by its IEEE-754 fields, on the
+// integer pipe (the FP64 pipe of this GPU is narrow); zero, subnormal, inf and nan
+// take the hardware conversion.
+__device__ __forceinline__ double f2d(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const unsigned long long d = ((unsigned long long)(b >> 31) << 63) |
+                                 ((unsigned long long)(e + (1023u - 127u)) << 52) |
+                                 ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
 }
 
 // Inclusive warp scan of 32-bit counts.
@@ -166,9 +187,9 @@ void gt_note_launches(int k);
 struct SortBufs {
     uint64_t *key[2];
     uint32_t *val[2];
-    uint32_t *tile_hist;     // RADIX x ntiles
-    uint32_t *digit_base;    // RADIX
-    uint32_t *digit_total;   // RADIX
+    unsigned long long *status;  // look-back status, tiles x RADIX
+    uint32_t *hist;              // digit histograms of the 8 passes, 8 x RADIX
+    uint32_t *digit_base;        // digit starts of the 8 passes, 8 x RADIX
 };
 
 // keys.cu
@@ -184,6 +205,8 @@ void gt_sort_init();
 // tree.cu
 void gt_launch_build(const uint64_t *skey, int64_t n, int leaf_max, Nodes nd, int64_t cap,
                      unsigned long long *status, DevCtl *ctl, int nsm, cudaStream_t st);
+void gt_launch_leaf_list(Nodes nd, int64_t n, DevCtl *ctl, unsigned long long *status, int nsm, cudaStream_t st);
+void gt_launch_internal_list(Nodes nd, DevCtl *ctl, unsigned long long *status, int nsm, cudaStream_t st);
 void gt_launch_pseudo(Nodes nd, int64_t cap, const float4 *posm, DevCtl *ctl, int nsm,
                       cudaStream_t st);
 // integrate.cu
@@ -193,6 +216,8 @@ void gt_launch_predict(const State &s, int64_t n, const DevCtl *ctl, float4 *pos
 void gt_launch_load(const State &s, float4 *posm, int64_t n, cudaStream_t st);
 void gt_launch_permute(const State &src, const State &dst, const float4 *posm_in, float4 *posm_out,
                        const uint32_t *perm, int64_t n, cudaStream_t st);
+void gt_launch_copy_state(const State &src, const State &dst, const float4 *posm_in, float4 *posm_out,
+                          int64_t n, cudaStream_t st);
 void gt_launch_deinterleave3(const double *in, int64_t n, double *x, double *y, double *z,
                              cudaStream_t st);
 void gt_launch_interleave3(const double *x, const double *y, const double *z, int64_t n, double *out,

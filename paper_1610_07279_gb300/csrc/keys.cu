@@ -83,11 +83,14 @@ __device__ __forceinline__ unsigned long long spread3(unsigned long long v) {
     return v;
 }
 
-__device__ __forceinline__ unsigned long long quantise(float x, float xmin, double scale) {
-    // floor((x - xmin) * 2^21/side) in FP64 with explicit rounding, clamped to 2^21 - 1
-    double t = floor(__dmul_rn(__dsub_rn((double)x, (double)xmin), scale));
-    t = fmin(t, (double)((1u << GT_KEY_LEVELS) - 1u));
-    return (unsigned long long)t;
+__device__ __forceinline__ unsigned long long quantise(float x, double xmin, double scale) {
+    // floor((x - xmin) * 2^21/side) in FP64 with explicit rounding, clamped to 2^21 - 1.
+    // x is widened exactly on the integer pipe; the floor is the round-down conversion
+    // (the product is >= 0), so the FP64 pipe runs one sub, one mul and one conversion.
+    const double t = __dmul_rn(__dsub_rn(f2d(x), xmin), scale);
+    const unsigned long long q = __double2ull_rd(t);
+    constexpr unsigned long long QMAX = (1ull << GT_KEY_LEVELS) - 1ull;
+    return q < QMAX ? q : QMAX;
 }
 
 __global__ __launch_bounds__(256) void k_keys(const float4 *__restrict__ posm, long long n,
@@ -100,9 +103,9 @@ __global__ __launch_bounds__(256) void k_keys(const float4 *__restrict__ posm, l
     unsigned long long k = 0;
     if (side > 0.0) {
         const float4 p = posm[i];
-        const unsigned long long qx = quantise(p.x, ctl->bbox_min[0], scale);
-        const unsigned long long qy = quantise(p.y, ctl->bbox_min[1], scale);
-        const unsigned long long qz = quantise(p.z, ctl->bbox_min[2], scale);
+        const unsigned long long qx = quantise(p.x, f2d(ctl->bbox_min[0]), scale);
+        const unsigned long long qy = quantise(p.y, f2d(ctl->bbox_min[1]), scale);
+        const unsigned long long qz = quantise(p.z, f2d(ctl->bbox_min[2]), scale);
         k = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
     }
     key[i] = k;

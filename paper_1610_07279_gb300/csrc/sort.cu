@@ -1,14 +1,17 @@
 // Step A2: stable LSD radix sort of (63-bit key, 32-bit index) pairs (Sec. 2.1: the
 // particles are sorted by their space-filling key with a library radix sort).
 //
-// Eight passes of 8-bit digits.  Each pass runs three kernels:
-//   tile_hist   per 4096-key tile, a histogram of the pass digit     (reads 8 B/key)
-//   digit_scan  per digit, an exclusive scan over tiles; the last block to finish
-//               turns the digit totals into digit bases (no waiting)
-//   scatter     per tile, a stable rank of every key inside the tile (warp-striped
-//               match/popc ranking), a local sort in shared memory, then coalesced
-//               writes of each digit run to its global slot       (reads and writes 12 B/key)
-// HBM-bound: 32 B per key per pass plus the small tile histograms.
+// Eight passes of 8-bit digits, one kernel per pass after one histogram pass:
+//   k_hist_all     all eight digit histograms in one read of the keys   (reads 8 B/key)
+//   k_digit_bases  exclusive scans of the histograms -> where every digit starts
+//   k_onesweep     per 2048-key tile taken in ticket order: a stable rank of every key
+//                  inside the tile (warp-striped match/popc), the tile's per-digit counts
+//                  published and each digit's exclusive prefix over earlier tiles found
+//                  by a decoupled look-back (256 digits in parallel, a window of 8 earlier
+//                  tiles per step, every wait bounded), a local sort in shared memory,
+//                  then coalesced writes of each digit run
+//                  (reads and writes 12 B/key; 8 B of status per digit and tile)
+// HBM-bound: ~25 B per key per pass.
 #include <mutex>
 
 #include "gt_internal.cuh"
@@ -16,86 +19,129 @@
 namespace {
 
 constexpr int ST = 256;            // threads per tile
-constexpr int IPT = 16;            // keys per thread
+#ifndef GT_SORT_IPT
+#define GT_SORT_IPT 8
+#endif
+constexpr int IPT = GT_SORT_IPT;   // keys per thread
 constexpr int TILE = ST * IPT;     // keys per tile
 constexpr int RB = 8;              // digit bits
 constexpr int R = 1 << RB;         // digits
 constexpr int NW = ST / 32;
 constexpr int PASSES = 8;          // 64 / RB (bit 63 is always 0; the last pass is cheap)
-constexpr size_t SCATTER_SMEM =
-    TILE * sizeof(unsigned long long) + TILE * sizeof(uint32_t) + (NW * R + R + NW + 1) * sizeof(uint32_t);
+constexpr size_t SCATTER_SMEM = TILE * sizeof(unsigned long long) + TILE * sizeof(uint32_t) +
+                                (NW * R + 2 * R + NW + 1) * sizeof(uint32_t);
 static_assert(ST == R, "one thread per digit in the per-tile scans");
 
-__global__ __launch_bounds__(ST) void k_tile_hist(long long n, int shift,
-                                                  const unsigned long long *__restrict__ key,
-                                                  uint32_t *__restrict__ tile_hist, int ntiles) {
-    __shared__ uint32_t h[R];
-    h[threadIdx.x] = 0;
+__global__ __launch_bounds__(ST) void k_hist_all(long long n, const unsigned long long *__restrict__ key,
+                                                 uint32_t *__restrict__ hist /* PASSES x R */) {
+    __shared__ uint32_t h[PASSES][R];
+    for (int p = 0; p < PASSES; p++) h[p][threadIdx.x] = 0;
     __syncthreads();
-    const long long base = (long long)blockIdx.x * TILE;
-#pragma unroll 4
-    for (int j = 0; j < IPT; j++) {
-        const long long i = base + j * ST + threadIdx.x;
+    // the keys of a tree rebuild arrive nearly sorted (the particles are still in the
+    // previous key order), so a warp's 32 neighbouring keys often share their high digits:
+    // such a digit is counted once for the whole warp, the others by one atomic per lane
+    for (long long i0 = (long long)blockIdx.x * ST; i0 < n; i0 += (long long)gridDim.x * ST) {
+        const long long i = i0 + threadIdx.x;
         const bool ok = i < n;
-        const unsigned int d = ok ? (unsigned int)((key[i] >> shift) & (R - 1)) : (unsigned int)R;
-        const unsigned int peers = __match_any_sync(0xffffffffu, d);
-        if (ok && (peers & lanemask_lt()) == 0) atomicAdd(&h[d], (unsigned int)__popc(peers));
-    }
-    __syncthreads();
-    tile_hist[threadIdx.x * (long long)ntiles + blockIdx.x] = h[threadIdx.x];
-}
-
-__global__ __launch_bounds__(1024) void k_digit_scan(uint32_t *__restrict__ tile_hist, int ntiles,
-                                                     uint32_t *__restrict__ digit_total,
-                                                     uint32_t *__restrict__ digit_base, DevCtl *ctl) {
-    __shared__ uint32_t tmp[1024 / 32 + 1];
-    __shared__ bool last;
-    uint32_t *row = tile_hist + (long long)blockIdx.x * ntiles;
-    const int per = (ntiles + 1023) / 1024;
-    const int t0 = threadIdx.x * per;
-    uint32_t s = 0;
-    for (int k = 0; k < per; k++)
-        if (t0 + k < ntiles) s += row[t0 + k];
-    uint32_t total;
-    uint32_t run = block_excl_scan<1024>(s, &total, tmp);
-    for (int k = 0; k < per; k++)
-        if (t0 + k < ntiles) {
-            const uint32_t v = row[t0 + k];
-            row[t0 + k] = run;
-            run += v;
+        const unsigned long long k = ok ? key[i] : 0ull;
+        const bool full = __all_sync(0xffffffffu, ok);
+#pragma unroll
+        for (int p = 0; p < PASSES; p++) {
+            const unsigned int d = (unsigned int)((k >> (p * RB)) & (R - 1));
+            const unsigned int d0 = __shfl_sync(0xffffffffu, d, 0);
+            if (full && __all_sync(0xffffffffu, d == d0)) {
+                if ((threadIdx.x & 31) == 0) atomicAdd(&h[p][d], 32u);
+            } else if (ok) {
+                atomicAdd(&h[p][d], 1u);
+            }
         }
-    if (threadIdx.x == 0) {
-        digit_total[blockIdx.x] = total;
-        __threadfence();
-        last = atomicAdd(&ctl->sort_done, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (last) {
-        __threadfence();
-        const uint32_t v = threadIdx.x < R ? __ldcg(&digit_total[threadIdx.x]) : 0u;
-        uint32_t tot;
-        const uint32_t b = block_excl_scan<1024>(v, &tot, tmp);
-        if (threadIdx.x < R) digit_base[threadIdx.x] = b;
-        if (threadIdx.x == 0) ctl->sort_done = 0;
-    }
+    for (int p = 0; p < PASSES; p++)
+        if (h[p][threadIdx.x]) atomicAdd(&hist[p * R + threadIdx.x], h[p][threadIdx.x]);
 }
 
-__global__ __launch_bounds__(ST) void k_scatter(long long n, int shift,
-                                                const unsigned long long *__restrict__ kin,
-                                                const uint32_t *__restrict__ vin,
-                                                unsigned long long *__restrict__ kout,
-                                                uint32_t *__restrict__ vout,
-                                                const uint32_t *__restrict__ tile_prefix,
-                                                const uint32_t *__restrict__ digit_base, int ntiles) {
+// one block: digit starts of every pass; also opens a new look-back epoch and resets the tickets
+__global__ __launch_bounds__(ST) void k_digit_bases(const uint32_t *__restrict__ hist,
+                                                    uint32_t *__restrict__ base, DevCtl *ctl) {
+    __shared__ uint32_t tmp[ST / 32 + 1];
+    for (int p = 0; p < PASSES; p++) {
+        uint32_t tot;
+        const uint32_t b = block_excl_scan<ST>(hist[p * R + threadIdx.x], &tot, tmp);
+        base[p * R + threadIdx.x] = b;
+    }
+    if (threadIdx.x < PASSES) ctl->sort_ticket[threadIdx.x] = 0;
+    if (threadIdx.x == 0) ctl->sort_epoch += 1u;
+}
+
+// Look-back of one digit: the count of digit d in all tiles before `tile`.  Status word
+// (tag << 32 | count) of tile t, digit d sits at status[t * R + d], so the 256 threads of a
+// tile read one contiguous row per predecessor; each step reads a window of LB rows at once
+// and adds counts back to the first tile whose inclusive prefix is published.
+__device__ __forceinline__ uint32_t lookback_digit(const unsigned long long *status, int tile, int d,
+                                                   unsigned long long tagA, unsigned long long tagP,
+                                                   DevCtl *ctl) {
+    constexpr int LB = 8;
+    uint32_t excl = 0;
+    int t = tile - 1;
+    unsigned int spins = 0;
+    while (t >= 0) {
+        unsigned long long sv[LB];
+#pragma unroll
+        for (int j = 0; j < LB; j++)
+            sv[j] = t - j >= 0 ? *((const volatile unsigned long long *)&status[(size_t)(t - j) * R + d]) : tagP;
+        int used = 0;
+        bool done = false, stalled = false;
+#pragma unroll
+        for (int j = 0; j < LB; j++) {
+            if (done || stalled) continue;
+            const unsigned long long tag = sv[j] & 0xffffffff00000000ull;
+            if (tag == tagP) {
+                excl += (uint32_t)sv[j];
+                done = true;
+            } else if (tag == tagA) {
+                excl += (uint32_t)sv[j];
+                used = j + 1;
+            } else {
+                stalled = true;
+            }
+        }
+        if (done) break;
+        t -= used;
+        if (stalled) {
+            if (++spins > GT_SPIN_LIMIT) {
+                gt_set_error(ctl, GT_ETIMEOUT, GTK_SORT);
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
+    return excl;
+}
+
+__global__ __launch_bounds__(ST) void k_onesweep(long long n, int pass,
+                                                 const unsigned long long *__restrict__ kin,
+                                                 const uint32_t *__restrict__ vin,
+                                                 unsigned long long *__restrict__ kout,
+                                                 uint32_t *__restrict__ vout,
+                                                 const uint32_t *__restrict__ digit_base,
+                                                 unsigned long long *status /* ntiles x R */, int ntiles,
+                                                 DevCtl *ctl) {
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned long long *skey = (unsigned long long *)smraw;
     uint32_t *sval = (uint32_t *)(skey + TILE);
     uint32_t *wcnt = sval + TILE;     // NW x R: per-warp digit counts, then offsets
     uint32_t *dstart = wcnt + NW * R; // R: tile-local start of every digit
-    uint32_t *scantmp = dstart + R;   // NW + 1
-    const int tile = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *gbase = dstart + R;     // R: global slot of every digit's first key in this tile
+    uint32_t *scantmp = gbase + R;    // NW + 1
+    __shared__ uint32_t tile_sh;
+    const int shift = pass * RB;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) tile_sh = atomicAdd(&ctl->sort_ticket[pass], 1u);
     for (int k = threadIdx.x; k < NW * R; k += ST) wcnt[k] = 0;
     __syncthreads();
+    const int tile = (int)tile_sh;
+    if (tile >= ntiles) return;
 
     // warp w owns keys [base, base + 32*IPT) of the tile, item j of lane l is base + 32 j + l:
     // visiting j in order and lanes in order visits the keys in index order (stability)
@@ -123,34 +169,51 @@ __global__ __launch_bounds__(ST) void k_scatter(long long n, int shift,
         loc[j] = prev + rank;
     }
     __syncthreads();
-    // per digit: exclusive offsets of the warps, then the digit's tile-local start
-    uint32_t tot = 0;
+    // thread d: exclusive offsets of the warps for digit d, the tile's count of digit d
+    const int d = threadIdx.x;
+    uint32_t cnt = 0;
     for (int ww = 0; ww < NW; ww++) {
-        const uint32_t t = wcnt[ww * R + threadIdx.x];
-        wcnt[ww * R + threadIdx.x] = tot;
-        tot += t;
+        const uint32_t t = wcnt[ww * R + d];
+        wcnt[ww * R + d] = cnt;
+        cnt += t;
     }
+    // publish this tile's count of digit d as early as possible
+    const unsigned int epoch = ctl->sort_epoch * PASSES + (unsigned)pass;
+    const unsigned long long tagA = (unsigned long long)(4u * epoch + 1u) << 32;
+    const unsigned long long tagP = (unsigned long long)(4u * epoch + 2u) << 32;
+    unsigned long long *own = status + (size_t)tile * R + d;
+    if (tile == 0)
+        *((volatile unsigned long long *)own) = tagP | cnt;
+    else
+        *((volatile unsigned long long *)own) = tagA | cnt;
     uint32_t total;
-    const uint32_t ds = block_excl_scan<ST>(tot, &total, scantmp);
-    dstart[threadIdx.x] = ds;
+    dstart[d] = block_excl_scan<ST>(cnt, &total, scantmp);
     __syncthreads();
+    // local sort by digit in shared memory (stable: warp offset + rank inside the warp)
 #pragma unroll
     for (int j = 0; j < IPT; j++) {
         const bool ok = base + j * 32 + lane < n;
         if (ok) {
-            const unsigned int d = (unsigned int)((k[j] >> shift) & (R - 1));
-            const uint32_t pos = dstart[d] + wcnt[w * R + d] + loc[j];
+            const unsigned int dj = (unsigned int)((k[j] >> shift) & (R - 1));
+            const uint32_t pos = dstart[dj] + wcnt[w * R + dj] + loc[j];
             skey[pos] = k[j];
             sval[pos] = v[j];
         }
     }
+    // count of digit d in all earlier tiles, then this tile's inclusive prefix
+    uint32_t excl = 0;
+    if (tile > 0) {
+        excl = lookback_digit(status, tile, d, tagA, tagP, ctl);
+        *((volatile unsigned long long *)own) = tagP | (unsigned long long)(excl + cnt);
+    }
+    gbase[d] = digit_base[pass * R + d] + excl - dstart[d];
     __syncthreads();
     const long long rem = n - (long long)tile * TILE;
     const int m = rem < TILE ? (int)rem : TILE;
     for (int p = threadIdx.x; p < m; p += ST) {
         const unsigned long long kk = skey[p];
-        const unsigned int d = (unsigned int)((kk >> shift) & (R - 1));
-        const uint32_t g = digit_base[d] + tile_prefix[d * (long long)ntiles + tile] + (uint32_t)(p - dstart[d]);
+        const unsigned int dk = (unsigned int)((kk >> shift) & (R - 1));
+        const uint32_t g = gbase[dk] + (uint32_t)p;
         kout[g] = kk;
         vout[g] = sval[p];
     }
@@ -161,32 +224,37 @@ __global__ __launch_bounds__(ST) void k_scatter(long long n, int shift,
 int gt_sort_tiles(int64_t n) { return (int)((n + TILE - 1) / TILE); }
 
 size_t gt_sort_scratch_bytes(int64_t n) {
-    return (size_t)R * (size_t)(gt_sort_tiles(n) > 0 ? gt_sort_tiles(n) : 1) * sizeof(uint32_t);
+    // look-back status (R x tiles x 8 B)
+    return (size_t)R * (size_t)(gt_sort_tiles(n) > 0 ? gt_sort_tiles(n) : 1) * sizeof(unsigned long long);
 }
 
 void gt_sort_init() {
-    cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCATTER_SMEM);
+    cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCATTER_SMEM);
 }
 
 void gt_launch_sort(SortBufs &b, int64_t n, DevCtl *ctl, cudaStream_t st) {
     if (n <= 1) return;
     const int ntiles = gt_sort_tiles(n);
+    cudaMemsetAsync(b.hist, 0, PASSES * R * sizeof(uint32_t), st);
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long blocks = (n + ST - 1) / ST;
+    { k_hist_all<<<(unsigned)(blocks < nsm * 8 ? blocks : nsm * 8), ST, 0, st>>>(n, (const unsigned long long *)b.key[0], b.hist); gt_note_launches(1); }
+    { k_digit_bases<<<1, ST, 0, st>>>(b.hist, b.digit_base, ctl); gt_note_launches(1); }
     for (int p = 0; p < PASSES; p++) {
         const int src = p & 1, dst = src ^ 1;
-        const int shift = p * RB;
-        { k_tile_hist<<<ntiles, ST, 0, st>>>(n, shift, (const unsigned long long *)b.key[src],
-                                           b.tile_hist, ntiles); gt_note_launches(1); }
-        { k_digit_scan<<<R, 1024, 0, st>>>(b.tile_hist, ntiles, b.digit_total, b.digit_base, ctl); gt_note_launches(1); }
-        { k_scatter<<<ntiles, ST, SCATTER_SMEM, st>>>(n, shift, (const unsigned long long *)b.key[src],
-                                                    b.val[src], (unsigned long long *)b.key[dst],
-                                                    b.val[dst], b.tile_hist, b.digit_base, ntiles); gt_note_launches(1); }
+        { k_onesweep<<<ntiles, ST, SCATTER_SMEM, st>>>(n, p, (const unsigned long long *)b.key[src], b.val[src],
+                                                       (unsigned long long *)b.key[dst], b.val[dst], b.digit_base,
+                                                       b.status, ntiles, ctl);
+          gt_note_launches(1); }
     }
 }
 
 // ---- sort without allocation (gt_sort_pairs_noalloc) -----------------------------
 // All scratch of one sort of up to GT_NOALLOC_SORT_MAX pairs lives in this array:
-// [control block | alternate keys | alternate values | tile histograms | digit bases |
-// digit totals].  Host code must not use the symbol as an address: the device
+// [control block | alternate keys | alternate values | look-back status | digit
+// histograms | digit bases].  Host code must not use the symbol as an address: the device
 // address is looked up once per device below.
 namespace {
 
@@ -195,10 +263,10 @@ constexpr size_t na_up(size_t b) { return (b + NA_ALIGN - 1) / NA_ALIGN * NA_ALI
 constexpr size_t NA_TILES = (GT_NOALLOC_SORT_MAX + TILE - 1) / TILE;
 constexpr size_t NA_OFF_KEY = na_up(sizeof(DevCtl));
 constexpr size_t NA_OFF_VAL = NA_OFF_KEY + na_up((size_t)GT_NOALLOC_SORT_MAX * sizeof(unsigned long long));
-constexpr size_t NA_OFF_HIST = NA_OFF_VAL + na_up((size_t)GT_NOALLOC_SORT_MAX * sizeof(uint32_t));
-constexpr size_t NA_OFF_BASE = NA_OFF_HIST + na_up(R * NA_TILES * sizeof(uint32_t));
-constexpr size_t NA_OFF_TOTAL = NA_OFF_BASE + na_up(R * sizeof(uint32_t));
-constexpr size_t NA_BYTES = NA_OFF_TOTAL + na_up(R * sizeof(uint32_t));
+constexpr size_t NA_OFF_STATUS = NA_OFF_VAL + na_up((size_t)GT_NOALLOC_SORT_MAX * sizeof(uint32_t));
+constexpr size_t NA_OFF_HIST = NA_OFF_STATUS + na_up(R * NA_TILES * sizeof(unsigned long long));
+constexpr size_t NA_OFF_BASE = NA_OFF_HIST + na_up(PASSES * R * sizeof(uint32_t));
+constexpr size_t NA_BYTES = NA_OFF_BASE + na_up(PASSES * R * sizeof(uint32_t));
 
 __device__ __align__(256) unsigned char g_noalloc_sort_scratch[NA_BYTES];
 
@@ -207,7 +275,8 @@ std::mutex g_na_mu;
 char *g_na_addr[NA_MAX_DEVICES] = {};
 
 // Device address of the scratch array on the current device (looked up once per device).
-int noalloc_scratch(char **out) {
+int noalloc_scratch(char **out, bool *first_use) {
+    *first_use = false;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return GT_ECUDA;
     if (dev < 0 || dev >= NA_MAX_DEVICES) return GT_EINVAL;
@@ -215,8 +284,9 @@ int noalloc_scratch(char **out) {
     if (!g_na_addr[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_sort_scratch) != cudaSuccess || !p) return GT_ECUDA;
-        gt_sort_init();  // the scatter kernel's shared-memory limit, on this device
+        gt_sort_init();  // the sort kernel's shared-memory limit, on this device
         g_na_addr[dev] = (char *)p;
+        *first_use = true;
     }
     *out = g_na_addr[dev];
     return GT_OK;
@@ -228,22 +298,29 @@ extern "C" int gt_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals, int64_t
     if (n < 0 || (n > 0 && (!d_keys || !d_vals))) return GT_EINVAL;
     if (n > GT_NOALLOC_SORT_MAX) return GT_EINVAL;  // larger than the static scratch
     char *base = nullptr;
-    const int rc = noalloc_scratch(&base);
+    bool first_use = false;
+    const int rc = noalloc_scratch(&base, &first_use);
     if (rc != GT_OK) return rc;
     if (n <= 1) return GT_OK;
     cudaStream_t st = (cudaStream_t)stream;
     DevCtl *ctl = (DevCtl *)base;
-    // the digit scan's last-block counter must start at zero (a previous call may
-    // have been cut short); everything else is fully written before it is read
-    if (cudaMemsetAsync(&ctl->sort_done, 0, sizeof(ctl->sort_done), st) != cudaSuccess) return GT_ECUDA;
+    // the histograms are cleared by the sort itself; the look-back status words carry
+    // an epoch that the control block counts, so the control block and the status
+    // must start at zero once (the first call on a device), after which every call
+    // leaves them consistent for the next
+    if (first_use) {
+        if (cudaMemsetAsync(ctl, 0, sizeof(DevCtl), st) != cudaSuccess ||
+            cudaMemsetAsync(base + NA_OFF_STATUS, 0, R * NA_TILES * sizeof(unsigned long long), st) != cudaSuccess)
+            return GT_ECUDA;
+    }
     SortBufs b;
     b.key[0] = d_keys;
     b.val[0] = d_vals;
     b.key[1] = (uint64_t *)(base + NA_OFF_KEY);
     b.val[1] = (uint32_t *)(base + NA_OFF_VAL);
-    b.tile_hist = (uint32_t *)(base + NA_OFF_HIST);
+    b.status = (unsigned long long *)(base + NA_OFF_STATUS);
+    b.hist = (uint32_t *)(base + NA_OFF_HIST);
     b.digit_base = (uint32_t *)(base + NA_OFF_BASE);
-    b.digit_total = (uint32_t *)(base + NA_OFF_TOTAL);
     gt_launch_sort(b, n, ctl, st);  // an even number of passes leaves the result in d_keys/d_vals
     return cudaGetLastError() == cudaSuccess ? GT_OK : GT_ECUDA;
 }

@@ -10,9 +10,10 @@
 // look-back over tiles taken in ticket order (bounded wait).  Numbering is thus
 // level by level and, inside a level, by first particle.
 //
-// A5, one kernel: each leaf sums its particles in FP64 (mass, m x, m y, m z) and
-// climbs; the last child to arrive at a cell (atomic counter, no waiting) sums the
-// children's FP64 sums in child order and continues upward.  m_J = (float)M and
+// A5: one lane per leaf sums its particles in FP64 (mass, m x, m y, m z), then one
+// pass per level, deepest first, over the cells with children (a list compacted at
+// build time) sums the children's FP64 sums in child order -- every FP64 instruction
+// runs with full warps, which matters on this GPU's narrow FP64 pipe.  m_J = (float)M and
 // r_J = (float)S / (float)M (a cell of one particle is that particle); b_J is the
 // largest FP32 |r - r_J| of a leaf's particles, or the largest |r_c - r_J| + b_c
 // over a cell's children, widened by (1 + 2^-20) so that FP32 rounding cannot
@@ -35,7 +36,6 @@ __global__ void k_build_init(long long n, Nodes nd, DevCtl *ctl) {
         nd.first[0] = 0;
         nd.count[0] = (uint32_t)n;
         nd.parent[0] = -1;
-        nd.arrive[0] = 0;
     }
 }
 
@@ -104,15 +104,20 @@ __global__ __launch_bounds__(BT) void k_build_level(int lvl, const unsigned long
         for (int q = 0; q < NPT; q++) {
             const uint32_t c = lo + tile * BTILE + threadIdx.x * NPT + q;
             if (c >= hi) continue;
-            if (nc[q] == 0) {
+            if (nc[q] == 0) {  // a leaf: record where it starts, for the per-step leaf list
                 nd.child[c] = -1;
                 nd.nchild[c] = 0;
+                const uint32_t f = nd.first[c];
+                nd.leaf_flag[f] = 1;
+                nd.node_at[f] = c;
                 continue;
             }
             if ((long long)next + nc[q] > cap) {
                 gt_set_error(ctl, GT_EOVERFLOW, GTK_BUILD);
                 nd.child[c] = -1;
                 nd.nchild[c] = 0;
+                nd.leaf_flag[nd.first[c]] = 1;
+                nd.node_at[nd.first[c]] = c;
                 next += nc[q];
                 continue;
             }
@@ -126,7 +131,6 @@ __global__ __launch_bounds__(BT) void k_build_level(int lvl, const unsigned long
                     nd.parent[next] = (int32_t)c;
                     nd.child[next] = -1;
                     nd.nchild[next] = 0;
-                    nd.arrive[next] = 0;
                     next++;
                 }
             }
@@ -142,29 +146,26 @@ __global__ __launch_bounds__(BT) void k_build_level(int lvl, const unsigned long
     }
 }
 
-__device__ __forceinline__ double sq3(double dx, double dy, double dz) {
-    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-}
-
 __device__ __forceinline__ float sq3f(float dx, float dy, float dz) {
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
 
-__global__ __launch_bounds__(256) void k_pseudo(Nodes nd, long long cap, const float4 *__restrict__ posm,
-                                                DevCtl *ctl) {
-    long long nn = ctl->level_start[GT_TREE_LEVELS];
-    if (nn > cap) nn = cap;
-    for (long long c0 = blockIdx.x * 256ll + threadIdx.x; c0 < nn; c0 += (long long)gridDim.x * 256) {
-        if (nd.child[c0] >= 0) continue;  // cells are finished by their last arriving child
-        const uint32_t f = nd.first[c0], k = nd.count[c0];
+// leaves: one lane per leaf, leaves in particle order (neighbouring lanes read
+// neighbouring particles)
+__global__ __launch_bounds__(256) void k_pseudo_leaves(Nodes nd, const float4 *__restrict__ posm, DevCtl *ctl) {
+    const long long nl = ctl->n_leaves;
+    for (long long t = blockIdx.x * 256ll + threadIdx.x; t < nl; t += (long long)gridDim.x * 256) {
+        const uint32_t f = nd.leaf_first[t];
+        const uint32_t c = nd.node_at[f];
+        const uint32_t k = nd.count[c];
         double m = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
         for (uint32_t i = f; i < f + k; i++) {
             const float4 p = posm[i];
-            const double mi = (double)p.w;  // m x is exact in FP64, so the fused form rounds once like + does
+            const double mi = f2d(p.w);  // m x is exact in FP64, so the fused form rounds once like + does
             m = __dadd_rn(m, mi);
-            sx = __fma_rn(mi, (double)p.x, sx);
-            sy = __fma_rn(mi, (double)p.y, sy);
-            sz = __fma_rn(mi, (double)p.z, sz);
+            sx = __fma_rn(mi, f2d(p.x), sx);
+            sy = __fma_rn(mi, f2d(p.y), sy);
+            sz = __fma_rn(mi, f2d(p.z), sz);
         }
         float jx, jy, jz;
         if (k == 1) {  // a cell of one particle is that particle
@@ -182,49 +183,45 @@ __global__ __launch_bounds__(256) void k_pseudo(Nodes nd, long long cap, const f
             const float d2 = sq3f(__fsub_rn(p.x, jx), __fsub_rn(p.y, jy), __fsub_rn(p.z, jz));
             if (d2 > d2max) d2max = d2;
         }
-        nd.sum[c0] = DSum4{m, sx, sy, sz};
-        nd.jpos[c0] = make_float4(jx, jy, jz, __double2float_rn(m));
-        nd.walk[c0] = make_float4(__fmul_rn(__fsqrt_rn(d2max), GT_RADIUS_MARGIN), __uint_as_float(f),
-                                  __uint_as_float(k | GT_LEAF_FLAG), 0.0f);
-        // climb while this thread is the last child to arrive
-        long long c = c0;
-        for (;;) {
-            const int32_t p = nd.parent[c];
-            if (p < 0) break;
-            __threadfence();
-            const uint32_t nch = nd.nchild[p];
-            const uint32_t old = atomicAdd(&nd.arrive[p], 1u);
-            if (old != nch - 1) break;
-            __threadfence();
-            const int32_t ch0 = nd.child[p];
-            m = 0.0; sx = 0.0; sy = 0.0; sz = 0.0;
-            for (uint32_t q = 0; q < nch; q++) {
-                const double2 *sp = (const double2 *)&nd.sum[ch0 + q];
-                const double2 s01 = __ldcg(sp), s23 = __ldcg(sp + 1);
-                m = __dadd_rn(m, s01.x);
-                sx = __dadd_rn(sx, s01.y);
-                sy = __dadd_rn(sy, s23.x);
-                sz = __dadd_rn(sz, s23.y);
-            }
-            const float mf = __double2float_rn(m);
-            jx = __fdiv_rn(__double2float_rn(sx), mf);
-            jy = __fdiv_rn(__double2float_rn(sy), mf);
-            jz = __fdiv_rn(__double2float_rn(sz), mf);
-            float b = 0.0f;
-            for (uint32_t q = 0; q < nch; q++) {
-                const float4 cj = __ldcg(&nd.jpos[ch0 + q]);
-                const float4 cw = __ldcg(&nd.walk[ch0 + q]);
-                const float e = __fadd_rn(__fsqrt_rn(sq3f(__fsub_rn(cj.x, jx), __fsub_rn(cj.y, jy),
-                                                          __fsub_rn(cj.z, jz))), cw.x);
-                if (e > b) b = e;
-            }
-            nd.sum[p] = DSum4{m, sx, sy, sz};
-            nd.jpos[p] = make_float4(jx, jy, jz, mf);
-            nd.walk[p] = make_float4(__fmul_rn(b, GT_RADIUS_MARGIN), __uint_as_float((uint32_t)ch0),
-                                     __uint_as_float(nch), 0.0f);
-            nd.arrive[p] = 0;
-            c = p;
+        nd.sum[c] = DSum4{m, sx, sy, sz};
+        nd.jpos[c] = make_float4(jx, jy, jz, __double2float_rn(m));
+        nd.walk[c] = make_float4(__fmul_rn(__fsqrt_rn(d2max), GT_RADIUS_MARGIN), __uint_as_float(f),
+                                 __uint_as_float(k | GT_LEAF_FLAG), 0.0f);
+    }
+}
+
+// cells with children of one level, after the deeper levels: sums of the children's
+// sums in child order
+__global__ __launch_bounds__(256) void k_pseudo_level(int lvl, Nodes nd, const DevCtl *ctl) {
+    const long long i0 = ctl->istart[lvl], i1 = ctl->istart[lvl + 1];
+    for (long long t = i0 + blockIdx.x * 256ll + threadIdx.x; t < i1; t += (long long)gridDim.x * 256) {
+        const uint32_t p = nd.internal[t];
+        const int32_t ch0 = nd.child[p];
+        const uint32_t nch = nd.nchild[p];
+        double m = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+        for (uint32_t q = 0; q < nch; q++) {
+            const DSum4 s = nd.sum[ch0 + q];
+            m = __dadd_rn(m, s.m);
+            sx = __dadd_rn(sx, s.x);
+            sy = __dadd_rn(sy, s.y);
+            sz = __dadd_rn(sz, s.z);
         }
+        const float mf = __double2float_rn(m);
+        const float jx = __fdiv_rn(__double2float_rn(sx), mf);
+        const float jy = __fdiv_rn(__double2float_rn(sy), mf);
+        const float jz = __fdiv_rn(__double2float_rn(sz), mf);
+        float b = 0.0f;
+        for (uint32_t q = 0; q < nch; q++) {
+            const float4 cj = nd.jpos[ch0 + q];
+            const float bc = nd.walk[ch0 + q].x;
+            const float e = __fadd_rn(__fsqrt_rn(sq3f(__fsub_rn(cj.x, jx), __fsub_rn(cj.y, jy),
+                                                      __fsub_rn(cj.z, jz))), bc);
+            if (e > b) b = e;
+        }
+        nd.sum[p] = DSum4{m, sx, sy, sz};
+        nd.jpos[p] = make_float4(jx, jy, jz, mf);
+        nd.walk[p] = make_float4(__fmul_rn(b, GT_RADIUS_MARGIN), __uint_as_float((uint32_t)ch0),
+                                 __uint_as_float(nch), 0.0f);
     }
 }
 
@@ -240,5 +237,9 @@ void gt_launch_build(const uint64_t *skey, int64_t n, int leaf_max, Nodes nd, in
 
 void gt_launch_pseudo(Nodes nd, int64_t cap, const float4 *posm, DevCtl *ctl, int nsm,
                       cudaStream_t st) {
-    { k_pseudo<<<nsm * 8, 256, 0, st>>>(nd, cap, posm, ctl); gt_note_launches(1); }
+    (void)cap;
+    { k_pseudo_leaves<<<nsm * 8, 256, 0, st>>>(nd, posm, ctl); gt_note_launches(1); }
+    for (int l = GT_TREE_LEVELS - 2; l >= 0; l--) {
+        { k_pseudo_level<<<nsm * 4, 256, 0, st>>>(l, nd, ctl); gt_note_launches(1); }
+    }
 }

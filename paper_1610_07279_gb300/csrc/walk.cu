@@ -59,11 +59,19 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// 1/sqrt(r2) on the special-function unit; r2 >= eps^2 > 0 is never subnormal, so the
+// flush-to-zero form needs no range handling
+__device__ __forceinline__ float rsqrt_sfu(float r2) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(r2));
+    return r;
+}
+
 __device__ __forceinline__ void interact(const float4 s, float xi, float yi, float zi, float eps2,
                                          float &ax, float &ay, float &az, float &ph) {
     const float dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
     const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-    const float rinv = rsqrtf(r2);
+    const float rinv = rsqrt_sfu(r2);
     const float mr = s.w * rinv;
     const float mr3 = mr * rinv * rinv;
     ax = fmaf(mr3, dx, ax);
