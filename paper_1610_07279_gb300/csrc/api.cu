@@ -149,11 +149,7 @@ size_t carve(gt_system *s, char *base, int64_t n, const gt_params *p, int nsm, i
     s->nd.jpos = L.take<float4>(base, cap);
     s->nd.walk = L.take<float4>(base, cap);
     s->nd.sum = L.take<DSum4>(base, cap);
-    s->nd.leaf_flag = L.take<uint8_t>(base, N);
-    s->nd.node_at = L.take<uint32_t>(base, N);
-    s->nd.leaf_first = L.take<uint32_t>(base, N);
-    s->nd.internal = L.take<uint32_t>(base, cap);
-    s->nd.iprefix = L.take<uint32_t>(base, cap + 1);
+    s->nd.cells = L.take<uint32_t>(base, cap);
     const int64_t st_tiles = (cap + 511) / 512 + (n + 4095) / 4096 + 64;
     s->status = L.take<unsigned long long>(base, st_tiles);
     s->active = L.take<uint32_t>(base, N);
@@ -269,10 +265,8 @@ void build_tree(gt_system *s, cudaStream_t st, const float4 *posm_src) {
     }
     ph_end(s, PH_PERMUTE, st);
     ph_begin(s, PH_BUILD, st);
-    if (n > 0) cudaMemsetAsync(s->nd.leaf_flag, 0, (size_t)n, st);
     gt_launch_build(s->sb.key[0], n, s->prm.leaf_max, s->nd, s->cap, s->status, s->ctl, s->nsm, st);
-    gt_launch_leaf_list(s->nd, n, s->ctl, s->status, s->nsm, st);
-    gt_launch_internal_list(s->nd, s->ctl, s->status, s->nsm, st);
+    gt_launch_cell_lists(s->nd, s->cap, s->ctl, s->nsm, st);
     ph_end(s, PH_BUILD, st);
     ph_begin(s, PH_PSEUDO, st);
     gt_launch_pseudo(s->nd, s->cap, s->posm, s->ctl, s->nsm, st);

@@ -8,6 +8,8 @@
 
 #define GT_KEY_LEVELS 21              // 21 bits per axis -> 63-bit Morton keys
 #define GT_TREE_LEVELS 22             // tree levels 0..21
+#define GT_LEAF_BUCKETS 17            // leaves bucketed by particle count: 1..16, then larger
+#define GT_CELL_BUCKETS (GT_LEAF_BUCKETS + GT_TREE_LEVELS * 8)  // + (level, children) buckets
 #define GT_LEAF_FLAG 0x80000000u      // set in a node's second link word for a leaf
 #define GT_SPIN_LIMIT (1u << 22)      // bound on every device spin-wait (iterations)
 // Enclosing radii computed in FP32 are widened by (1 + 2^-20): the few roundings of
@@ -27,8 +29,8 @@ struct DevCtl {
     unsigned int n_active;            // i-particles of the current force evaluation
     unsigned int n_groups;            // groups of the current force evaluation (cell grouping)
     unsigned int n_leaves;            // leaves of the current tree
-    unsigned int n_internal;          // cells with children
-    unsigned int istart[GT_TREE_LEVELS + 2];  // first entry of every level in the internal-cell list
+    unsigned int istart[GT_TREE_LEVELS + 2];  // where every level's cells with children start in the cell list
+    unsigned int cell_bucket[GT_CELL_BUCKETS];  // bucket sizes, then fill cursors, of the cell list
     unsigned int group_next;          // dynamic group counter of the walk
     unsigned int tile_ticket[GT_TREE_LEVELS + 4];  // dynamic tile ids: levels, actives, groups, leaves, cells
     unsigned int level_start[GT_TREE_LEVELS + 2];  // first cell of each level; [22] = node count
@@ -75,11 +77,9 @@ struct Nodes {
     float4 *walk;              // (b_J, link0, link1, 0): link0 = first child or first particle,
                                // link1 = nchild, or count | GT_LEAF_FLAG for a leaf
     DSum4 *sum;                // FP64 (m, m x, m y, m z)
-    uint8_t *leaf_flag;        // per particle: 1 where a leaf starts (build scratch)
-    uint32_t *node_at;         // per particle: the leaf starting there
-    uint32_t *leaf_first;      // first particle of every leaf, in particle order
-    uint32_t *internal;        // cells with children, in node (level) order
-    uint32_t *iprefix;         // per node: cells with children before it (build scratch)
+    uint32_t *cells;           // every node once: the leaves bucketed by particle count, then
+                               // the cells with children by level (deepest last) and, inside
+                               // a level, by number of children
 };
 
 __device__ __forceinline__ void gt_set_error(DevCtl *ctl, int code, int where) {
@@ -139,44 +139,55 @@ __device__ __forceinline__ unsigned int block_excl_scan(unsigned int v, unsigned
     return r;
 }
 
-// Decoupled look-back (single thread): publish this tile's aggregate, gather
-// the exclusive prefix from its predecessors, publish the inclusive prefix.
-// Status words pack (tag << 32 | value); tag = 4*epoch + {1: aggregate, 2: prefix}.
-// Tiles are taken in increasing order from a ticket, so every predecessor is
-// held by a running block and the wait ends; it is still bounded, and a wait
-// that runs out latches GT_ETIMEOUT and returns the partial prefix.
-__device__ __forceinline__ unsigned int lookback_prefix(unsigned long long *status, unsigned int tile,
-                                                        unsigned int aggregate, unsigned int epoch,
-                                                        DevCtl *ctl, int where) {
+// Decoupled look-back, by one full warp: publish this tile's aggregate, gather the
+// exclusive prefix from its predecessors, publish the inclusive prefix.  Status
+// words pack (tag << 32 | value); tag = 4*epoch + {1: aggregate, 2: prefix}.  Lane
+// i reads predecessor tile - 1 - i, so each step covers 32 tiles: once every tile
+// up to the nearest published prefix has published at least its aggregate, the
+// values up to and including that prefix are summed by shuffles; with no prefix in
+// the window the 32 aggregates are added and the window moves back.  Tiles are taken
+// in increasing order from a ticket, so every predecessor is held by a running block
+// and the wait ends; it is still bounded, and a wait that runs out latches
+// GT_ETIMEOUT and returns the partial prefix.  Every lane gets the result.
+__device__ __forceinline__ unsigned int lookback_warp(unsigned long long *status, unsigned int tile,
+                                                      unsigned int aggregate, unsigned int epoch,
+                                                      DevCtl *ctl, int where) {
     const unsigned long long tagA = (unsigned long long)(4u * epoch + 1u) << 32;
     const unsigned long long tagP = (unsigned long long)(4u * epoch + 2u) << 32;
+    const int lane = (int)(threadIdx.x & 31u);
     if (tile == 0) {
-        atomicExch(&status[0], tagP | aggregate);
+        if (lane == 0) atomicExch(&status[0], tagP | aggregate);
         return 0u;
     }
-    atomicExch(&status[tile], tagA | aggregate);
+    if (lane == 0) atomicExch(&status[tile], tagA | aggregate);
     unsigned int excl = 0;
-    int t = (int)tile - 1;
+    int base = (int)tile - 1;
     unsigned int spins = 0;
-    while (t >= 0) {
-        const unsigned long long s = *((volatile unsigned long long *)&status[t]);
-        const unsigned long long tag = s & 0xffffffff00000000ull;
-        if (tag == tagP) {
-            excl += (unsigned int)s;
-            break;
-        }
-        if (tag == tagA) {
-            excl += (unsigned int)s;
-            --t;
+    for (;;) {
+        const int t = base - lane;
+        // a slot before tile 0 reads as a published prefix of 0
+        const unsigned long long sv = t >= 0 ? *((volatile unsigned long long *)&status[t]) : tagP;
+        const unsigned long long tag = sv & 0xffffffff00000000ull;
+        const unsigned int pmask = __ballot_sync(0xffffffffu, tag == tagP);
+        const unsigned int vmask = __ballot_sync(0xffffffffu, tag == tagP || tag == tagA);
+        const int firstP = pmask ? __ffs(pmask) - 1 : 32;
+        const unsigned int need = firstP >= 31 ? 0xffffffffu : ((1u << (firstP + 1)) - 1u);
+        if ((vmask & need) != need) {
+            if (++spins > GT_SPIN_LIMIT) {
+                if (lane == 0) gt_set_error(ctl, GT_ETIMEOUT, where);
+                break;
+            }
+            __nanosleep(32);
             continue;
         }
-        if (++spins > GT_SPIN_LIMIT) {
-            gt_set_error(ctl, GT_ETIMEOUT, where);
-            break;
-        }
-        __nanosleep(32);
+        unsigned int v = lane <= firstP ? (unsigned int)sv : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (firstP < 32) break;
+        base -= 32;
     }
-    atomicExch(&status[tile], tagP | (unsigned long long)(excl + aggregate));
+    if (lane == 0) atomicExch(&status[tile], tagP | (unsigned long long)(excl + aggregate));
     return excl;
 }
 
@@ -205,8 +216,7 @@ void gt_sort_init();
 // tree.cu
 void gt_launch_build(const uint64_t *skey, int64_t n, int leaf_max, Nodes nd, int64_t cap,
                      unsigned long long *status, DevCtl *ctl, int nsm, cudaStream_t st);
-void gt_launch_leaf_list(Nodes nd, int64_t n, DevCtl *ctl, unsigned long long *status, int nsm, cudaStream_t st);
-void gt_launch_internal_list(Nodes nd, DevCtl *ctl, unsigned long long *status, int nsm, cudaStream_t st);
+void gt_launch_cell_lists(Nodes nd, int64_t cap, DevCtl *ctl, int nsm, cudaStream_t st);
 void gt_launch_pseudo(Nodes nd, int64_t cap, const float4 *posm, DevCtl *ctl, int nsm,
                       cudaStream_t st);
 // integrate.cu

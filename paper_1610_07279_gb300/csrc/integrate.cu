@@ -153,7 +153,7 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
     return v;
 }
 
-enum { CM_TIME = 0, CM_ALL = 1, CM_FLAGS = 2, CM_NONNEG = 3 };
+enum { CM_TIME = 0, CM_ALL = 1, CM_FLAGS = 2 };
 
 // Order-preserving compaction of [0, n) (n from n_dev if given).  Writes the selected
 // indices to out, the prefix P[i] = #selected below i (i = 0..n) if prefix != null,
@@ -162,8 +162,7 @@ enum { CM_TIME = 0, CM_ALL = 1, CM_FLAGS = 2, CM_NONNEG = 3 };
 __global__ __launch_bounds__(AT) void k_compact(long long n_host, const unsigned int *n_dev, int mode,
                                                 const long long *__restrict__ t0,
                                                 const uint8_t *__restrict__ level, int L,
-                                                const uint8_t *__restrict__ flags,
-                                                const int32_t *__restrict__ ivals, DevCtl *ctl,
+                                                const uint8_t *__restrict__ flags, DevCtl *ctl,
                                                 int ticket, uint32_t tag_slot, uint32_t *__restrict__ out,
                                                 uint32_t *__restrict__ prefix, unsigned int *count_out,
                                                 unsigned long long *status) {
@@ -198,8 +197,6 @@ __global__ __launch_bounds__(AT) void k_compact(long long n_host, const unsigned
                     on = true;
                 } else if (mode == CM_FLAGS) {
                     on = flags[i] != 0;
-                } else if (mode == CM_NONNEG) {
-                    on = ivals[i] >= 0;
                 } else {
                     const unsigned long long tend =
                         (unsigned long long)t0[i] + (1ull << (L - 1 - (int)level[i]));
@@ -211,7 +208,10 @@ __global__ __launch_bounds__(AT) void k_compact(long long n_host, const unsigned
         }
         uint32_t total;
         const uint32_t excl = block_excl_scan<AT>((uint32_t)__popc(sel), &total, tmp);
-        if (threadIdx.x == 0) excl_sh = lookback_prefix(status, tile, total, tag, ctl, GTK_ACTIVE);
+        if (threadIdx.x < 32) {
+            const uint32_t e = lookback_warp(status, tile, total, tag, ctl, GTK_ACTIVE);
+            if (threadIdx.x == 0) excl_sh = e;
+        }
         __syncthreads();
         uint32_t pos = excl_sh + excl;
 #pragma unroll
@@ -472,7 +472,7 @@ void gt_launch_gather_f(const float *in, const uint32_t *id, int64_t n, float *o
 
 void gt_launch_active(const State &s, int64_t n, int L, int all, DevCtl *ctl, uint32_t *active,
                       uint32_t *prefix, unsigned long long *status, int nsm, cudaStream_t st) {
-    { k_compact<<<nsm * 4, AT, 0, st>>>(n, nullptr, all ? CM_ALL : CM_TIME, s.t0, s.level, L, nullptr, nullptr, ctl,
+    { k_compact<<<nsm * 4, AT, 0, st>>>(n, nullptr, all ? CM_ALL : CM_TIME, s.t0, s.level, L, nullptr, ctl,
                                         GT_TREE_LEVELS, 30u, active, prefix, &ctl->n_active, status);
       gt_note_launches(1); }
 }
@@ -482,39 +482,16 @@ void gt_launch_active_from_list(const uint32_t *list, int64_t n_list, int64_t n,
                                 cudaStream_t st) {
     if (n > 0) cudaMemsetAsync(flags, 0, (size_t)n, st);
     if (n_list > 0) { k_scatter_flags<<<nblk(n_list), 256, 0, st>>>(list, n_list, n, flags, ctl); gt_note_launches(1); }
-    { k_compact<<<nsm * 4, AT, 0, st>>>(n, nullptr, CM_FLAGS, nullptr, nullptr, 0, flags, nullptr, ctl, GT_TREE_LEVELS,
+    { k_compact<<<nsm * 4, AT, 0, st>>>(n, nullptr, CM_FLAGS, nullptr, nullptr, 0, flags, ctl, GT_TREE_LEVELS,
                                         30u, active, prefix, &ctl->n_active, status);
       gt_note_launches(1); }
-}
-
-void gt_launch_leaf_list(Nodes nd, int64_t n, DevCtl *ctl, unsigned long long *status, int nsm, cudaStream_t st) {
-    { k_compact<<<nsm * 4, AT, 0, st>>>(n, nullptr, CM_FLAGS, nullptr, nullptr, 0, nd.leaf_flag, nullptr, ctl,
-                                        GT_TREE_LEVELS + 2, 29u, nd.leaf_first, nullptr, &ctl->n_leaves, status);
-      gt_note_launches(1); }
-}
-
-// where every level starts in the internal-cell list
-__global__ void k_set_istart(const uint32_t *__restrict__ iprefix, DevCtl *ctl) {
-    const unsigned nn = ctl->level_start[GT_TREE_LEVELS];
-    for (int l = threadIdx.x; l <= GT_TREE_LEVELS; l += blockDim.x) {
-        const unsigned ls = ctl->level_start[l] < nn ? ctl->level_start[l] : nn;
-        ctl->istart[l] = iprefix[ls];
-    }
-}
-
-void gt_launch_internal_list(Nodes nd, DevCtl *ctl, unsigned long long *status, int nsm, cudaStream_t st) {
-    { k_compact<<<nsm * 4, AT, 0, st>>>(0, &ctl->level_start[GT_TREE_LEVELS], CM_NONNEG, nullptr, nullptr, 0,
-                                        nullptr, nd.child, ctl, GT_TREE_LEVELS + 3, 28u, nd.internal, nd.iprefix,
-                                        &ctl->n_internal, status);
-      gt_note_launches(1); }
-    { k_set_istart<<<1, 32, 0, st>>>(nd.iprefix, ctl); gt_note_launches(1); }
 }
 
 void gt_launch_groups(Nodes nd, int64_t cap, const uint32_t *prefix, int gmax, int64_t n, uint8_t *marks,
                       DevCtl *ctl, uint32_t *gstart, unsigned long long *status, int nsm, cudaStream_t st) {
     if (n > 0) cudaMemsetAsync(marks, 0, (size_t)n, st);
     { k_group_cells<<<nsm * 8, 256, 0, st>>>(nd, cap, prefix, gmax, marks, ctl); gt_note_launches(1); }
-    { k_compact<<<nsm * 4, AT, 0, st>>>(0, &ctl->n_active, CM_FLAGS, nullptr, nullptr, 0, marks, nullptr, ctl,
+    { k_compact<<<nsm * 4, AT, 0, st>>>(0, &ctl->n_active, CM_FLAGS, nullptr, nullptr, 0, marks, ctl,
                                         GT_TREE_LEVELS + 1, 31u, gstart, nullptr, &ctl->n_groups, status);
       gt_note_launches(1); }
 }

@@ -25,7 +25,7 @@
 namespace {
 
 constexpr int BT = 256;         // threads per build block
-constexpr int NPT = 2;          // cells per thread
+constexpr int NPT = 1;          // cells per thread
 constexpr int BTILE = BT * NPT; // cells per tile
 
 __global__ void k_build_init(long long n, Nodes nd, DevCtl *ctl) {
@@ -97,27 +97,25 @@ __global__ __launch_bounds__(BT) void k_build_level(int lvl, const unsigned long
         }
         uint32_t total;
         uint32_t excl = block_excl_scan<BT>(tsum, &total, tmp);
-        if (threadIdx.x == 0) excl_sh = lookback_prefix(status, tile, total, tag, ctl, GTK_BUILD);
+        if (threadIdx.x < 32) {
+            const uint32_t e = lookback_warp(status, tile, total, tag, ctl, GTK_BUILD);
+            if (threadIdx.x == 0) excl_sh = e;
+        }
         __syncthreads();
         uint32_t next = hi + excl_sh + excl;  // node id of this thread's first child
 #pragma unroll
         for (int q = 0; q < NPT; q++) {
             const uint32_t c = lo + tile * BTILE + threadIdx.x * NPT + q;
             if (c >= hi) continue;
-            if (nc[q] == 0) {  // a leaf: record where it starts, for the per-step leaf list
+            if (nc[q] == 0) {  // a leaf
                 nd.child[c] = -1;
                 nd.nchild[c] = 0;
-                const uint32_t f = nd.first[c];
-                nd.leaf_flag[f] = 1;
-                nd.node_at[f] = c;
                 continue;
             }
             if ((long long)next + nc[q] > cap) {
                 gt_set_error(ctl, GT_EOVERFLOW, GTK_BUILD);
                 nd.child[c] = -1;
                 nd.nchild[c] = 0;
-                nd.leaf_flag[nd.first[c]] = 1;
-                nd.node_at[nd.first[c]] = c;
                 next += nc[q];
                 continue;
             }
@@ -150,13 +148,83 @@ __device__ __forceinline__ float sq3f(float dx, float dy, float dz) {
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
 
-// leaves: one lane per leaf, leaves in particle order (neighbouring lanes read
-// neighbouring particles)
+// ---- cell lists for the per-step pseudo j-particle passes -----------------------
+// Every node goes once into nd.cells: the leaves first, bucketed by particle count
+// (1..16, then all larger), then the cells with children, level by level and inside a
+// level by number of children.  A warp of the pseudo-j passes then takes cells of one
+// size, so the FP64 sums run with all lanes busy.  The order inside a bucket is free:
+// every cell's result depends on its own particles or children only.
+
+// bucket of node p, given the level ranges ls[0..GT_TREE_LEVELS]
+__device__ __forceinline__ int cell_bucket_of(const Nodes &nd, uint32_t p, const uint32_t *ls) {
+    if (nd.child[p] < 0) {
+        const uint32_t k = nd.count[p];
+        return (k >= GT_LEAF_BUCKETS ? GT_LEAF_BUCKETS : (int)k) - 1;
+    }
+    int lvl = 0;  // the last level starting at or before p
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+        if (lvl + step < GT_TREE_LEVELS && ls[lvl + step] <= p) lvl += step;
+    return GT_LEAF_BUCKETS + lvl * 8 + (int)nd.nchild[p] - 1;
+}
+
+__global__ __launch_bounds__(256) void k_cell_count(Nodes nd, long long cap, DevCtl *ctl) {
+    __shared__ uint32_t ls[GT_TREE_LEVELS + 1];
+    __shared__ uint32_t h[GT_CELL_BUCKETS];
+    for (int i = threadIdx.x; i <= GT_TREE_LEVELS; i += 256) ls[i] = ctl->level_start[i];
+    for (int i = threadIdx.x; i < GT_CELL_BUCKETS; i += 256) h[i] = 0;
+    __syncthreads();
+    long long nn = ls[GT_TREE_LEVELS];
+    if (nn > cap) nn = cap;
+    for (long long p = blockIdx.x * 256ll + threadIdx.x; p < nn; p += (long long)gridDim.x * 256)
+        atomicAdd(&h[cell_bucket_of(nd, (uint32_t)p, ls)], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < GT_CELL_BUCKETS; i += 256)
+        if (h[i]) atomicAdd(&ctl->cell_bucket[i], h[i]);
+}
+
+// one block: bucket sizes -> fill cursors; the leaf count and where every level starts
+__global__ __launch_bounds__(256) void k_cell_scan(DevCtl *ctl) {
+    static_assert(GT_CELL_BUCKETS <= 256, "one thread per bucket");
+    __shared__ uint32_t tmp[256 / 32 + 1];
+    const int b = threadIdx.x;
+    const uint32_t v = b < GT_CELL_BUCKETS ? ctl->cell_bucket[b] : 0u;
+    uint32_t total;
+    const uint32_t start = block_excl_scan<256>(v, &total, tmp);
+    if (b < GT_CELL_BUCKETS) ctl->cell_bucket[b] = start;
+    if (b == GT_LEAF_BUCKETS) ctl->n_leaves = start;
+    if (b >= GT_LEAF_BUCKETS && b < GT_CELL_BUCKETS && (b - GT_LEAF_BUCKETS) % 8 == 0)
+        ctl->istart[(b - GT_LEAF_BUCKETS) / 8] = start;
+    if (b == 0) ctl->istart[GT_TREE_LEVELS] = total;
+}
+
+__global__ __launch_bounds__(256) void k_cell_fill(Nodes nd, long long cap, DevCtl *ctl) {
+    __shared__ uint32_t ls[GT_TREE_LEVELS + 1];
+    for (int i = threadIdx.x; i <= GT_TREE_LEVELS; i += 256) ls[i] = ctl->level_start[i];
+    __syncthreads();
+    long long nn = ls[GT_TREE_LEVELS];
+    if (nn > cap) nn = cap;
+    const unsigned lt = lanemask_lt();
+    // the loop bound is warp-uniform, so every lane takes part in the match
+    for (long long p0 = blockIdx.x * 256ll + (threadIdx.x & ~31u); p0 < nn; p0 += (long long)gridDim.x * 256) {
+        const long long p = p0 + (threadIdx.x & 31);
+        const bool ok = p < nn;
+        const int b = ok ? cell_bucket_of(nd, (uint32_t)p, ls) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(peers) - 1;
+        uint32_t pos0 = 0;
+        if (ok && (peers & lt) == 0) pos0 = atomicAdd(&ctl->cell_bucket[b], (uint32_t)__popc(peers));
+        pos0 = __shfl_sync(0xffffffffu, pos0, leader);
+        if (ok) nd.cells[pos0 + __popc(peers & lt)] = (uint32_t)p;
+    }
+}
+
+// leaves: one lane per leaf, a warp's leaves of one particle count
 __global__ __launch_bounds__(256) void k_pseudo_leaves(Nodes nd, const float4 *__restrict__ posm, DevCtl *ctl) {
     const long long nl = ctl->n_leaves;
     for (long long t = blockIdx.x * 256ll + threadIdx.x; t < nl; t += (long long)gridDim.x * 256) {
-        const uint32_t f = nd.leaf_first[t];
-        const uint32_t c = nd.node_at[f];
+        const uint32_t c = nd.cells[t];
+        const uint32_t f = nd.first[c];
         const uint32_t k = nd.count[c];
         double m = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
         for (uint32_t i = f; i < f + k; i++) {
@@ -195,7 +263,7 @@ __global__ __launch_bounds__(256) void k_pseudo_leaves(Nodes nd, const float4 *_
 __global__ __launch_bounds__(256) void k_pseudo_level(int lvl, Nodes nd, const DevCtl *ctl) {
     const long long i0 = ctl->istart[lvl], i1 = ctl->istart[lvl + 1];
     for (long long t = i0 + blockIdx.x * 256ll + threadIdx.x; t < i1; t += (long long)gridDim.x * 256) {
-        const uint32_t p = nd.internal[t];
+        const uint32_t p = nd.cells[t];
         const int32_t ch0 = nd.child[p];
         const uint32_t nch = nd.nchild[p];
         double m = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
@@ -233,6 +301,13 @@ void gt_launch_build(const uint64_t *skey, int64_t n, int leaf_max, Nodes nd, in
     for (int l = 0; l < GT_TREE_LEVELS; l++)
         { k_build_level<<<nsm * 4, BT, 0, st>>>(l, (const unsigned long long *)skey, leaf_max, nd, cap,
                                               status, ctl); gt_note_launches(1); }
+}
+
+void gt_launch_cell_lists(Nodes nd, int64_t cap, DevCtl *ctl, int nsm, cudaStream_t st) {
+    cudaMemsetAsync(ctl->cell_bucket, 0, sizeof(ctl->cell_bucket), st);
+    { k_cell_count<<<nsm * 4, 256, 0, st>>>(nd, cap, ctl); gt_note_launches(1); }
+    { k_cell_scan<<<1, 256, 0, st>>>(ctl); gt_note_launches(1); }
+    { k_cell_fill<<<nsm * 4, 256, 0, st>>>(nd, cap, ctl); gt_note_launches(1); }
 }
 
 void gt_launch_pseudo(Nodes nd, int64_t cap, const float4 *posm, DevCtl *ctl, int nsm,
