@@ -302,6 +302,79 @@ GT_API int gt_measure_fp32_peak(double *flops, gt_stream stream);
 #define GT_NOALLOC_SORT_MAX (1 << 20)
 GT_API int gt_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals, int64_t n, gt_stream stream);
 
+/* ---- batches: many independent systems, one walk launch (Sec. 2.3, 2.5) -------
+ *
+ * A batch holds nsys systems of any sizes in one caller workspace.  One force
+ * evaluation of the batch rebuilds every system's tree (A1-A5), makes every particle
+ * active and cuts the groups (A6), on forked streams so that the small systems'
+ * kernels overlap, then walks the groups of ALL systems in one persistent launch
+ * (A7): warps take global group numbers from one counter and find their system from
+ * a device-side prefix of the systems' group counts.  Each system's forces are the
+ * same, bit for bit, as gt_build_tree + gt_accel_active of that system alone with the
+ * same parameters.  The whole evaluation can be captured once into a CUDA graph and
+ * replayed.  Batch members share one walk queue and the batch's streams: their own
+ * entry points (gt_set_state, gt_get_state, gt_accel_active, ...) may be called
+ * between batch evaluations, one at a time.
+ */
+typedef struct gt_batch gt_batch;
+
+/* Bytes of workspace for a batch of nsys systems of n[k] particles and parameters
+ * prm[k] (prm may hold 1 entry used for all).  The queue depth of the batch is the
+ * largest walk_queue. */
+GT_API int gt_batch_workspace_bytes(int nsys, const int64_t *n, const gt_params *prm, int n_prm,
+                                    size_t *bytes);
+/* Create the batch inside d_ws (256-byte aligned, gt_batch_workspace_bytes long).
+ * The library creates up to 32 streams of its own for the forked builds.  Every
+ * system starts empty: load each with gt_set_state(gt_batch_system(...)). */
+GT_API int gt_batch_create(gt_batch **batch, int nsys, const int64_t *n, const gt_params *prm, int n_prm,
+                           void *d_ws, size_t ws_bytes);
+GT_API int gt_batch_destroy(gt_batch *batch);
+/* The k-th member (owned by the batch; do not destroy it). */
+GT_API int gt_batch_system(gt_batch *batch, int k, gt_system **sys);
+/* The walk's tuning knobs of every member: leaf_max (tree leaf size), group_max
+ * (i-particles per group), walk_queue (node-queue depth per warp, a power of two no
+ * larger than the depth fixed at create; 0 keeps each).  Drops a captured graph. */
+GT_API int gt_batch_set_knobs(gt_batch *batch, int leaf_max, int group_max, int walk_queue);
+/* One force evaluation of every member with all particles active, enqueued on
+ * stream.  bootstrap != 0 first walks with the opening-angle MAC (theta of each
+ * member) and takes |a| as a_old, then walks with each member's own MAC (the
+ * acceleration MAC needs a_old, Sec. 2.2); bootstrap == 0 uses the a_old each member
+ * already holds.  The accelerations stay in each member's force buffer: read them
+ * with gt_batch_get_acc. */
+GT_API int gt_batch_accel(gt_batch *batch, int bootstrap, gt_stream stream);
+/* Capture the same evaluation into a CUDA graph (replaces a previous one);
+ * gt_batch_launch replays it on stream. */
+GT_API int gt_batch_capture(gt_batch *batch, int bootstrap, gt_stream stream);
+GT_API int gt_batch_launch(gt_batch *batch, gt_stream stream);
+/* Accelerations (x, y, z, potential; n x 4 FP32) of member k in internal order, and
+ * optionally the original index of every internal slot (n uint32); host or device
+ * pointers.  Synchronises stream. */
+GT_API int gt_batch_get_acc(gt_batch *batch, int k, float *p_acc, uint32_t *p_id, gt_stream stream);
+/* Error words of all members (the first non-zero status; each word is cleared) and
+ * the interactions counted so far per member (n_out[k], may be NULL).  Synchronises. */
+GT_API int gt_batch_sync_status(gt_batch *batch, int64_t *interactions_out, gt_stream stream);
+
+/* Autotuner of the batch's walk knobs.  Every combination of the candidate leaf
+ * sizes, group sizes and queue depths is run reps times as a captured evaluation
+ * (bootstrap == 0, so every member must hold a_old, e.g. after one bootstrap
+ * evaluation) and timed with CUDA events; the fastest is kept (set on the batch) and
+ * returned with every candidate's mean time.  Zero-length candidate lists keep the
+ * current value. */
+typedef struct gt_tune_space {
+    int32_t n_leaf, leaf_max[8];
+    int32_t n_group, group_max[8];
+    int32_t n_queue, walk_queue[4];
+    int32_t reps;                 /* timed replays per candidate (>= 1) */
+} gt_tune_space;
+typedef struct gt_tune_result {
+    int32_t leaf_max, group_max, walk_queue;
+    int32_t n_tried;
+    double best_ms;               /* mean time of one evaluation with the kept knobs */
+    double ms[256];               /* per candidate, leaf-major, then group, then queue */
+} gt_tune_result;
+GT_API int gt_batch_autotune(gt_batch *batch, const gt_tune_space *space, gt_tune_result *result,
+                             gt_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

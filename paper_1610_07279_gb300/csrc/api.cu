@@ -8,68 +8,15 @@
 #include <new>
 #include <vector>
 
-#include "gt_internal.cuh"
+#include "gt_system.cuh"
 
 static std::atomic<long long> g_launches{0};
 
 void gt_note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
-// Per-phase event timers of one system.
-struct PhaseTimers {
-    bool on = false, created = false;
-    cudaEvent_t b[GT_NPHASES]{}, e[GT_NPHASES]{};
-    bool ran[GT_NPHASES]{};
-    double ms[GT_NPHASES]{};
-    double last_ms[GT_NPHASES]{};  // the most recent execution of each phase
-    long long cnt[GT_NPHASES]{};
-};
-
-// Automatic tree-rebuild interval (Sec. 2.6): walk times since the last rebuild,
-// normalised to the mean number of i-particles per block step (block steps vary
-// N_i by orders of magnitude; the fit is meant to see the tree ageing, not that).
-struct RebuildTuner {
-    std::vector<double> y;
-    double t_make = 0.0;
-    double nact_sum = 0.0;
-    long long nact_cnt = 0;
-    double n_opt = 1e6;
-    int model = -1;
-    long long since = 0;  // block steps on the current tree
-};
-
-struct gt_system {
-    int64_t n = 0;
-    PhaseTimers prof;
-    RebuildTuner tune;
-    gt_params prm{};
-    int dev = 0, nsm = 0;
-    int walk_blocks = 0, walk_warps = 0;
-    bool started = false, have_tree = false, last_rebuilt = false;
-    long long steps = 0, rebuilds = 0;
-    int64_t cap = 0;        // node capacity
-    State st[2]{};
-    float4 *posm = nullptr, *posm_tmp = nullptr;
-    SortBufs sb{};
-    Nodes nd{};
-    unsigned long long *status = nullptr;
-    uint32_t *active = nullptr;
-    uint32_t *prefix = nullptr;   // P[i] = actives below internal index i (n + 1 entries)
-    uint8_t *flags = nullptr;     // a caller's active list as flags
-    uint8_t *marks = nullptr;     // first active position of every group
-    uint32_t *gstart = nullptr;   // group starts (cell grouping)
-    float4 *acc_out = nullptr;
-    float *aold_tmp = nullptr;
-    double *scratch3 = nullptr;
-    float *bbox_partial = nullptr;
-    int bbox_blocks = 0;
-    uint32_t *queue = nullptr;
-    int64_t queue_entries = 0;
-    DevCtl *ctl = nullptr;
-};
-
 namespace {
 
-constexpr size_t ALIGN = 256;
+constexpr size_t ALIGN = GT_WS_ALIGN;
 
 struct Layout {
     size_t off = 0;
@@ -113,7 +60,8 @@ int device_sms(int *dev, int *nsm) {
 int64_t node_capacity(int64_t n, const gt_params *p) { return (int64_t)p->node_factor * n + 2048; }
 
 // Carve every buffer out of base (or only measure when base == nullptr).
-size_t carve(gt_system *s, char *base, int64_t n, const gt_params *p, int nsm, int walk_blocks) {
+size_t carve(gt_system *s, char *base, int64_t n, const gt_params *p, int nsm, int walk_blocks,
+             bool own_queue = true) {
     Layout L;
     const size_t N = (size_t)(n > 0 ? n : 1);
     s->ctl = L.take<DevCtl>(base, 1);
@@ -164,8 +112,8 @@ size_t carve(gt_system *s, char *base, int64_t n, const gt_params *p, int nsm, i
     s->bbox_partial = L.take<float>(base, 6 * (size_t)s->bbox_blocks);
     s->walk_blocks = walk_blocks;
     s->walk_warps = walk_blocks * gt_walk_warps_per_block();
-    s->queue_entries = (int64_t)s->walk_warps * p->walk_queue;
-    s->queue = L.take<uint32_t>(base, (size_t)s->queue_entries);
+    s->queue_entries = own_queue ? (int64_t)s->walk_warps * p->walk_queue : 0;
+    s->queue = own_queue ? L.take<uint32_t>(base, (size_t)s->queue_entries) : nullptr;
     return (L.off + ALIGN - 1) / ALIGN * ALIGN;
 }
 
@@ -283,13 +231,66 @@ double c2_of(const gt_params &p) {
 // A6 groups + A7 walk over the active list already in s->active / ctl->n_active
 // (cell grouping needs the prefix s->prefix of that list), or over a caller's list.
 void walk(gt_system *s, const uint32_t *active, const float *aold, float4 *acc, int mac, cudaStream_t st) {
-    WalkArgs a;
-    a.gstart = nullptr;
-    if (s->prm.group_mode == GT_GROUP_CELLS) {
+    if (s->prm.group_mode == GT_GROUP_CELLS)
         gt_launch_groups(s->nd, s->cap, s->prefix, s->prm.group_max, s->n, s->marks, s->ctl, s->gstart,
                          s->status, s->nsm, st);
-        a.gstart = s->gstart;
-    }
+    const WalkArgs a = gt_sys_walk_args(s, active, aold, acc, mac);
+    ph_begin(s, PH_WALK, st);
+    gt_launch_walk(a, s->walk_blocks, st);
+    ph_end(s, PH_WALK, st);
+}
+
+// every particle active (start-up passes, gt_accel_active with no list)
+void walk_all(gt_system *s, const float *aold, float4 *acc, int mac, cudaStream_t st) {
+    gt_launch_prepare(s->ctl, 0, st);
+    gt_launch_active(s->st[0], s->n, s->prm.levels, 1, s->ctl, s->active, s->prefix, s->status, s->nsm, st);
+    walk(s, nullptr, aold, acc, mac, st);
+}
+
+}  // namespace
+
+// ---- helpers shared with the batch and the server ------------------------------
+int gt_sys_check_params(const gt_params *p) { return check_params(p); }
+
+int gt_sys_device_sms(int *dev, int *nsm) { return device_sms(dev, nsm); }
+
+size_t gt_sys_carve(gt_system *s, char *base, int64_t n, const gt_params *p, int nsm, int walk_blocks,
+                    bool own_queue) {
+    return carve(s, base, n, p, nsm, walk_blocks, own_queue);
+}
+
+int gt_sys_init(gt_system *s, int64_t n, const gt_params *p, void *ws, size_t ws_bytes, bool own_queue) {
+    int rc = device_sms(&s->dev, &s->nsm);
+    if (rc) return rc;
+    gt_sort_init();
+    const int wb = gt_walk_blocks(s->nsm);
+    const size_t need = carve(s, nullptr, n, p, s->nsm, wb, own_queue);
+    if (ws_bytes < need) return GT_ENOMEM;
+    carve(s, (char *)ws, n, p, s->nsm, wb, own_queue);
+    s->n = n;
+    s->prm = *p;
+    // zero the control block and the look-back status words
+    if (cudaMemset(s->ctl, 0, sizeof(DevCtl)) != cudaSuccess ||
+        cudaMemset(s->status, 0, (size_t)((s->cap + 511) / 512 + (n + 4095) / 4096 + 64) * 8) != cudaSuccess ||
+        cudaMemset(s->sb.status, 0, gt_sort_scratch_bytes(n)) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
+        return GT_ECUDA;
+    return GT_OK;
+}
+
+void gt_sys_build_tree(gt_system *s, cudaStream_t st, const float4 *posm_src) { build_tree(s, st, posm_src); }
+
+void gt_sys_groups_all(gt_system *s, cudaStream_t st) {
+    gt_launch_prepare(s->ctl, 0, st);
+    gt_launch_active(s->st[0], s->n, s->prm.levels, 1, s->ctl, s->active, s->prefix, s->status, s->nsm, st);
+    if (s->prm.group_mode == GT_GROUP_CELLS)
+        gt_launch_groups(s->nd, s->cap, s->prefix, s->prm.group_max, s->n, s->marks, s->ctl, s->gstart,
+                         s->status, s->nsm, st);
+}
+
+WalkArgs gt_sys_walk_args(const gt_system *s, const uint32_t *active, const float *aold, float4 *acc, int mac) {
+    WalkArgs a;
+    a.gstart = s->prm.group_mode == GT_GROUP_CELLS ? s->gstart : nullptr;
     a.jpos = s->nd.jpos;
     a.walk = s->nd.walk;
     a.posm = s->posm;
@@ -308,19 +309,10 @@ void walk(gt_system *s, const uint32_t *active, const float *aold, float4 *acc, 
     a.eps2 = s->prm.eps * s->prm.eps;
     a.G = s->prm.G;
     a.inv_eps = 1.0f / s->prm.eps;
-    ph_begin(s, PH_WALK, st);
-    gt_launch_walk(a, s->walk_blocks, st);
-    ph_end(s, PH_WALK, st);
+    return a;
 }
 
-// every particle active (start-up passes, gt_accel_active with no list)
-void walk_all(gt_system *s, const float *aold, float4 *acc, int mac, cudaStream_t st) {
-    gt_launch_prepare(s->ctl, 0, st);
-    gt_launch_active(s->st[0], s->n, s->prm.levels, 1, s->ctl, s->active, s->prefix, s->status, s->nsm, st);
-    walk(s, nullptr, aold, acc, mac, st);
-}
-
-}  // namespace
+void gt_sys_aold_from_acc(gt_system *s, cudaStream_t st) { gt_launch_aold(s->acc_out, s->n, s->st[0].aold, st); }
 
 extern "C" {
 
@@ -379,21 +371,9 @@ int gt_system_create(gt_system **out, int64_t n, const gt_params *prm, void *d_w
     if (rc) return rc;
     gt_system *s = new (std::nothrow) gt_system();
     if (!s) return GT_ENOMEM;
-    if ((rc = device_sms(&s->dev, &s->nsm))) { delete s; return rc; }
-    gt_sort_init();
-    const int wb = gt_walk_blocks(s->nsm);
-    const size_t need = carve(s, nullptr, n, prm, s->nsm, wb);
-    if (ws_bytes < need) { delete s; return GT_ENOMEM; }
-    carve(s, (char *)d_ws, n, prm, s->nsm, wb);
-    s->n = n;
-    s->prm = *prm;
-    // zero the control block and the look-back status words
-    if (cudaMemset(s->ctl, 0, sizeof(DevCtl)) != cudaSuccess ||
-        cudaMemset(s->status, 0, (size_t)((s->cap + 511) / 512 + (n + 4095) / 4096 + 64) * 8) != cudaSuccess ||
-        cudaMemset(s->sb.status, 0, gt_sort_scratch_bytes(n)) != cudaSuccess ||
-        cudaDeviceSynchronize() != cudaSuccess) {
+    if ((rc = gt_sys_init(s, n, prm, d_ws, ws_bytes, true))) {
         delete s;
-        return GT_ECUDA;
+        return rc;
     }
     *out = s;
     return GT_OK;

@@ -274,3 +274,7 @@ extern "C" int gt_rebuild_interval(const double *t_walk, int n, double t_make, i
                                    double *n_opt_out, double *coef_out);
 int gt_walk_warps_per_block();
 void gt_launch_walk(const WalkArgs &a, int nblocks, cudaStream_t st);
+// one launch over the groups of nsys systems (args, ctls: device arrays of nsys entries)
+void gt_launch_walk_batch(DevCtl *const *ctls, const WalkArgs *args, int nsys, uint32_t *gprefix,
+                          unsigned int *group_next, uint32_t *queue, int qcap, int mac, int nblocks,
+                          cudaStream_t st);

@@ -1,0 +1,79 @@
+// Host-side definition of gt_system and the helpers that string its kernels
+// together; shared by the single-system entry points, the batch and the server.
+#pragma once
+
+#include <vector>
+
+#include "gt_internal.cuh"
+
+// Per-phase event timers of one system.
+struct PhaseTimers {
+    bool on = false, created = false;
+    cudaEvent_t b[GT_NPHASES]{}, e[GT_NPHASES]{};
+    bool ran[GT_NPHASES]{};
+    double ms[GT_NPHASES]{};
+    double last_ms[GT_NPHASES]{};  // the most recent execution of each phase
+    long long cnt[GT_NPHASES]{};
+};
+
+// Automatic tree-rebuild interval (Sec. 2.6): walk times since the last rebuild,
+// normalised to the mean number of i-particles per block step (block steps vary
+// N_i by orders of magnitude; the fit is meant to see the tree ageing, not that).
+struct RebuildTuner {
+    std::vector<double> y;
+    double t_make = 0.0;
+    double nact_sum = 0.0;
+    long long nact_cnt = 0;
+    double n_opt = 1e6;
+    int model = -1;
+    long long since = 0;  // block steps on the current tree
+};
+
+struct gt_system {
+    int64_t n = 0;
+    PhaseTimers prof;
+    RebuildTuner tune;
+    gt_params prm{};
+    int dev = 0, nsm = 0;
+    int walk_blocks = 0, walk_warps = 0;
+    bool started = false, have_tree = false, last_rebuilt = false;
+    long long steps = 0, rebuilds = 0;
+    int64_t cap = 0;        // node capacity
+    State st[2]{};
+    float4 *posm = nullptr, *posm_tmp = nullptr;
+    SortBufs sb{};
+    Nodes nd{};
+    unsigned long long *status = nullptr;
+    uint32_t *active = nullptr;
+    uint32_t *prefix = nullptr;   // P[i] = actives below internal index i (n + 1 entries)
+    uint8_t *flags = nullptr;     // a caller's active list as flags
+    uint8_t *marks = nullptr;     // first active position of every group
+    uint32_t *gstart = nullptr;   // group starts (cell grouping)
+    float4 *acc_out = nullptr;
+    float *aold_tmp = nullptr;
+    double *scratch3 = nullptr;
+    float *bbox_partial = nullptr;
+    int bbox_blocks = 0;
+    uint32_t *queue = nullptr;    // the walk queue (a batch's shared queue for batch members)
+    int64_t queue_entries = 0;
+    DevCtl *ctl = nullptr;
+};
+
+constexpr size_t GT_WS_ALIGN = 256;
+
+int gt_sys_check_params(const gt_params *p);
+int gt_sys_device_sms(int *dev, int *nsm);
+// Carve every buffer of a system out of base (or only measure when base == nullptr);
+// own_queue == false leaves the walk queue to the caller (a batch).
+size_t gt_sys_carve(gt_system *s, char *base, int64_t n, const gt_params *p, int nsm, int walk_blocks,
+                    bool own_queue);
+// Carve a system into ws (ws_bytes from gt_sys_carve) and zero its control words (synchronous).
+int gt_sys_init(gt_system *s, int64_t n, const gt_params *p, void *ws, size_t ws_bytes, bool own_queue);
+// A1-A5 on FP32 positions posm_src
+void gt_sys_build_tree(gt_system *s, cudaStream_t st, const float4 *posm_src);
+// A6 with every particle active: the active list and, for cell grouping, the groups
+void gt_sys_groups_all(gt_system *s, cudaStream_t st);
+// arguments of one walk over the current active list / groups
+WalkArgs gt_sys_walk_args(const gt_system *s, const uint32_t *active, const float *aold, float4 *acc, int mac);
+// |a| of the last walk over every particle -> a_old (start-up pass)
+void gt_sys_aold_from_acc(gt_system *s, cudaStream_t st);

@@ -80,195 +80,282 @@ __device__ __forceinline__ void interact(const float4 s, float xi, float yi, flo
     ph -= mr;
 }
 
+// One group g of system a (Sec. 2.3): pseudo i-particle, traversal, force loop.  The
+// warp's interaction and MAC-test counts are added to n_inter and n_tests.
+__device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32_t ngroups, float4 *list,
+                                           uint32_t *q, unsigned long long &n_inter,
+                                           unsigned long long &n_tests) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t qmask = (uint32_t)a.qcap - 1u;
+    const int lifo_at = a.qcap - LIFO_ROOM;
+    const uint32_t na = a.ctl->n_active;
+    const uint32_t gmax = (uint32_t)a.gmax;
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lt = lanemask_lt();
+    uint32_t a0, a1;
+    if (a.gstart) {
+        a0 = a.gstart[g];
+        a1 = g + 1 < ngroups ? a.gstart[g + 1] : na;
+    } else {
+        a0 = g * gmax;
+        a1 = min(a0 + gmax, na);
+    }
+    const uint32_t cnt = a1 - a0;
+    if (cnt == 0u || cnt > 32u) {  // a malformed group range: report it and skip
+        if (lane == 0) gt_set_error(a.ctl, GT_EINVAL, GTK_WALK);
+        return;
+    }
+    const int S = a.ij_share ? a.ij_share : 32 >> (cnt <= 1 ? 0 : 32 - __clz(cnt - 1));
+    const int logS = __ffs(S) - 1;
+    const int slot = lane >> logS, sub = lane & (S - 1);
+    const bool have = (uint32_t)slot < cnt;
+    const uint32_t kk = a0 + (have ? (uint32_t)slot : 0u);
+    uint32_t i = a.active ? a.active[kk] : kk;
+    if (i >= a.n) {  // an index outside the system: report it, walk particle 0 instead
+        gt_set_error(a.ctl, GT_EINVAL, GTK_WALK);
+        i = 0;
+    }
+    const float4 pi = a.posm[i];
+    float ao = have ? (a.aold ? a.aold[i] : 0.0f) : INFINITY;
+
+    // pseudo i-particle (lanes without a member repeat member 0: no effect on the box)
+    float mnx = pi.x, mny = pi.y, mnz = pi.z, mxx = pi.x, mxy = pi.y, mxz = pi.z;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mnx = fminf(mnx, __shfl_xor_sync(FULL, mnx, o));
+        mny = fminf(mny, __shfl_xor_sync(FULL, mny, o));
+        mnz = fminf(mnz, __shfl_xor_sync(FULL, mnz, o));
+        mxx = fmaxf(mxx, __shfl_xor_sync(FULL, mxx, o));
+        mxy = fmaxf(mxy, __shfl_xor_sync(FULL, mxy, o));
+        mxz = fmaxf(mxz, __shfl_xor_sync(FULL, mxz, o));
+        ao = fminf(ao, __shfl_xor_sync(FULL, ao, o));
+    }
+    const float cx = __fmul_rn(0.5f, __fadd_rn(mnx, mxx));
+    const float cy = __fmul_rn(0.5f, __fadd_rn(mny, mxy));
+    const float cz = __fmul_rn(0.5f, __fadd_rn(mnz, mxz));
+    const float ddx = __fsub_rn(pi.x, cx), ddy = __fsub_rn(pi.y, cy), ddz = __fsub_rn(pi.z, cz);
+    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ddx, ddx), __fmul_rn(ddy, ddy)), __fmul_rn(ddz, ddz));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(FULL, d2, o));
+    const float bI = __fmul_rn(__fsqrt_rn(d2), GT_RADIUS_MARGIN);
+    const float dacc_amin = __fmul_rn(a.delta_acc, ao);
+
+    float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f;
+    int list_n = 0;
+    auto flush = [&]() {
+        cp_async_wait_all();
+        __syncwarp();
+        int j = sub;
+        for (; j + 3 * S < list_n; j += 4 * S) {
+            const float4 s0 = list[j], s1 = list[j + S], s2 = list[j + 2 * S], s3 = list[j + 3 * S];
+            interact(s0, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
+            interact(s1, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
+            interact(s2, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
+            interact(s3, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
+        }
+        for (; j < list_n; j += S) interact(list[j], pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
+        n_inter += (unsigned long long)list_n * cnt;
+        list_n = 0;
+        __syncwarp();
+    };
+
+    uint32_t head = 0, tail = 1;
+    if (lane == 0) q[0] = 0u;  // the root
+    __syncwarp();
+    bool overflow = false;
+    while (head != tail) {
+        const uint32_t live = tail - head;
+        const uint32_t nb = min(live, 32u);
+        const bool valid = (uint32_t)lane < nb;
+        // breadth-first from the head while there is room, depth-first from the tail after
+        uint32_t base;
+        if ((int)live > lifo_at) {
+            tail -= nb;
+            base = tail;
+        } else {
+            base = head;
+            head += nb;
+        }
+        float4 jp = make_float4(0.f, 0.f, 0.f, 0.f), wk = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid) {
+            const uint32_t node = q[(base + lane) & qmask];
+            jp = a.jpos[node];
+            wk = a.walk[node];
+        }
+        n_tests += nb;
+        const bool ok = valid && mac_accept(a.mac, a.theta, dacc_amin, a.G, cx, cy, cz, bI, jp, wk.x);
+        const uint32_t l0 = __float_as_uint(wk.y), l1 = __float_as_uint(wk.z);
+        const bool leaf = (l1 & GT_LEAF_FLAG) != 0u;
+        // accepted cells -> list
+        const unsigned am = __ballot_sync(FULL, ok);
+        if (am) {
+            const int nacc = __popc(am);
+            if (list_n + nacc > LIST_CAP) flush();
+            if (ok) list[list_n + __popc(am & lt)] = jp;
+            list_n += nacc;
+        }
+        // opened cells -> queue their children
+        const uint32_t nch = (valid && !ok && !leaf) ? l1 : 0u;
+        const uint32_t incl = warp_incl_scan(nch);
+        const uint32_t tot = __shfl_sync(FULL, incl, 31);
+        if (tot) {
+            if (tail - head + tot > (uint32_t)a.qcap) {
+                overflow = true;
+                break;
+            }
+            const uint32_t pos = tail + incl - nch;
+            for (uint32_t k = 0; k < nch; k++) q[(pos + k) & qmask] = l0 + k;
+            tail += tot;
+        }
+        // opened leaves -> their particles into the list (asynchronous copies)
+        const uint32_t lc = (valid && !ok && leaf) ? (l1 & ~GT_LEAF_FLAG) : 0u;
+        const uint32_t lincl = warp_incl_scan(lc);
+        const uint32_t ltot = __shfl_sync(FULL, lincl, 31);
+        if (ltot) {
+            if (list_n + (int)ltot > LIST_CAP) flush();
+            if (ltot <= (uint32_t)LIST_CAP) {
+                const uint32_t dst = (uint32_t)list_n + lincl - lc;
+                for (uint32_t k = 0; k < lc; k++) cp_async16(&list[dst + k], &a.posm[l0 + k]);
+                list_n += (int)ltot;
+            } else {  // leaves holding more particles than the list: one at a time, in chunks
+                unsigned lm = __ballot_sync(FULL, lc != 0u);
+                while (lm) {
+                    const int src = __ffs(lm) - 1;
+                    lm &= lm - 1;
+                    const uint32_t lf = __shfl_sync(FULL, l0, src);
+                    const uint32_t lcount = __shfl_sync(FULL, lc, src);
+                    uint32_t done = 0;
+                    while (done < lcount) {
+                        if (list_n == LIST_CAP) flush();
+                        const uint32_t take = min(lcount - done, (uint32_t)(LIST_CAP - list_n));
+                        for (uint32_t k = lane; k < take; k += 32)
+                            cp_async16(&list[list_n + k], &a.posm[lf + done + k]);
+                        list_n += (int)take;
+                        done += take;
+                    }
+                }
+            }
+        }
+        if (list_n >= FLUSH_AT) flush();
+        __syncwarp();
+    }
+    if (overflow) {
+        if (lane == 0) gt_set_error(a.ctl, GT_EOVERFLOW, GTK_WALK);
+        cp_async_wait_all();
+        list_n = 0;
+        if (sub == 0 && have) a.acc[kk] = make_float4(NAN, NAN, NAN, NAN);
+        __syncwarp();
+        return;
+    }
+    flush();
+    for (int o = 1; o < S; o <<= 1) {
+        ax += __shfl_xor_sync(FULL, ax, o);
+        ay += __shfl_xor_sync(FULL, ay, o);
+        az += __shfl_xor_sync(FULL, az, o);
+        ph += __shfl_xor_sync(FULL, ph, o);
+    }
+    if (sub == 0 && have) {
+        const float phi = fmaf(pi.w, a.inv_eps, ph);
+        a.acc[kk] = make_float4(a.G * ax, a.G * ay, a.G * az, a.G * phi);
+    }
+}
+
+// groups of one system in a list of the systems' group counts: gprefix[s] is the first
+// global group of system s, gprefix[nsys] the total
+__device__ __forceinline__ int system_of(const uint32_t *gprefix, int nsys, uint32_t gg) {
+    int lo = 0, hi = nsys - 1;  // the last s with gprefix[s] <= gg
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (gprefix[mid] <= gg) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 __global__ __launch_bounds__(WT, 4) void k_walk(WalkArgs a) {
     __shared__ __align__(16) float4 list_sm[NWARP][LIST_CAP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4 *list = list_sm[warp];
     uint32_t *q = a.queue + (size_t)(blockIdx.x * NWARP + warp) * (size_t)a.qcap;
-    const uint32_t qmask = (uint32_t)a.qcap - 1u;
-    const int lifo_at = a.qcap - LIFO_ROOM;
     const uint32_t na = a.ctl->n_active;
     const uint32_t gmax = (uint32_t)a.gmax;
     const uint32_t ngroups = a.gstart ? a.ctl->n_groups : (na + gmax - 1) / gmax;
-    const unsigned FULL = 0xffffffffu;
-    const unsigned lt = lanemask_lt();
     unsigned long long n_inter = 0, n_tests = 0;
-
     for (;;) {
         uint32_t g = 0;
         if (lane == 0) g = atomicAdd(&a.ctl->group_next, 1u);
-        g = __shfl_sync(FULL, g, 0);
+        g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= ngroups) break;
-        uint32_t a0, a1;
-        if (a.gstart) {
-            a0 = a.gstart[g];
-            a1 = g + 1 < ngroups ? a.gstart[g + 1] : na;
-        } else {
-            a0 = g * gmax;
-            a1 = min(a0 + gmax, na);
-        }
-        const uint32_t cnt = a1 - a0;
-        if (cnt == 0u || cnt > 32u) {  // a malformed group range: report it and skip
-            if (lane == 0) gt_set_error(a.ctl, GT_EINVAL, GTK_WALK);
-            continue;
-        }
-        const int S = a.ij_share ? a.ij_share : 32 >> (cnt <= 1 ? 0 : 32 - __clz(cnt - 1));
-        const int logS = __ffs(S) - 1;
-        const int slot = lane >> logS, sub = lane & (S - 1);
-        const bool have = (uint32_t)slot < cnt;
-        const uint32_t kk = a0 + (have ? (uint32_t)slot : 0u);
-        uint32_t i = a.active ? a.active[kk] : kk;
-        if (i >= a.n) {  // an index outside the system: report it, walk particle 0 instead
-            gt_set_error(a.ctl, GT_EINVAL, GTK_WALK);
-            i = 0;
-        }
-        const float4 pi = a.posm[i];
-        float ao = have ? (a.aold ? a.aold[i] : 0.0f) : INFINITY;
-
-        // pseudo i-particle (lanes without a member repeat member 0: no effect on the box)
-        float mnx = pi.x, mny = pi.y, mnz = pi.z, mxx = pi.x, mxy = pi.y, mxz = pi.z;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            mnx = fminf(mnx, __shfl_xor_sync(FULL, mnx, o));
-            mny = fminf(mny, __shfl_xor_sync(FULL, mny, o));
-            mnz = fminf(mnz, __shfl_xor_sync(FULL, mnz, o));
-            mxx = fmaxf(mxx, __shfl_xor_sync(FULL, mxx, o));
-            mxy = fmaxf(mxy, __shfl_xor_sync(FULL, mxy, o));
-            mxz = fmaxf(mxz, __shfl_xor_sync(FULL, mxz, o));
-            ao = fminf(ao, __shfl_xor_sync(FULL, ao, o));
-        }
-        const float cx = __fmul_rn(0.5f, __fadd_rn(mnx, mxx));
-        const float cy = __fmul_rn(0.5f, __fadd_rn(mny, mxy));
-        const float cz = __fmul_rn(0.5f, __fadd_rn(mnz, mxz));
-        const float ddx = __fsub_rn(pi.x, cx), ddy = __fsub_rn(pi.y, cy), ddz = __fsub_rn(pi.z, cz);
-        float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ddx, ddx), __fmul_rn(ddy, ddy)), __fmul_rn(ddz, ddz));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(FULL, d2, o));
-        const float bI = __fmul_rn(__fsqrt_rn(d2), GT_RADIUS_MARGIN);
-        const float dacc_amin = __fmul_rn(a.delta_acc, ao);
-
-        float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f;
-        int list_n = 0;
-        auto flush = [&]() {
-            cp_async_wait_all();
-            __syncwarp();
-            int j = sub;
-            for (; j + 3 * S < list_n; j += 4 * S) {
-                const float4 s0 = list[j], s1 = list[j + S], s2 = list[j + 2 * S], s3 = list[j + 3 * S];
-                interact(s0, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
-                interact(s1, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
-                interact(s2, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
-                interact(s3, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
-            }
-            for (; j < list_n; j += S) interact(list[j], pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
-            n_inter += (unsigned long long)list_n * cnt;
-            list_n = 0;
-            __syncwarp();
-        };
-
-        uint32_t head = 0, tail = 1;
-        if (lane == 0) q[0] = 0u;  // the root
-        __syncwarp();
-        bool overflow = false;
-        while (head != tail) {
-            const uint32_t live = tail - head;
-            const uint32_t nb = min(live, 32u);
-            const bool valid = (uint32_t)lane < nb;
-            // breadth-first from the head while there is room, depth-first from the tail after
-            uint32_t base;
-            if ((int)live > lifo_at) {
-                tail -= nb;
-                base = tail;
-            } else {
-                base = head;
-                head += nb;
-            }
-            float4 jp = make_float4(0.f, 0.f, 0.f, 0.f), wk = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (valid) {
-                const uint32_t node = q[(base + lane) & qmask];
-                jp = a.jpos[node];
-                wk = a.walk[node];
-            }
-            n_tests += nb;
-            const bool ok = valid && mac_accept(a.mac, a.theta, dacc_amin, a.G, cx, cy, cz, bI, jp, wk.x);
-            const uint32_t l0 = __float_as_uint(wk.y), l1 = __float_as_uint(wk.z);
-            const bool leaf = (l1 & GT_LEAF_FLAG) != 0u;
-            // accepted cells -> list
-            const unsigned am = __ballot_sync(FULL, ok);
-            if (am) {
-                const int nacc = __popc(am);
-                if (list_n + nacc > LIST_CAP) flush();
-                if (ok) list[list_n + __popc(am & lt)] = jp;
-                list_n += nacc;
-            }
-            // opened cells -> queue their children
-            const uint32_t nch = (valid && !ok && !leaf) ? l1 : 0u;
-            const uint32_t incl = warp_incl_scan(nch);
-            const uint32_t tot = __shfl_sync(FULL, incl, 31);
-            if (tot) {
-                if (tail - head + tot > (uint32_t)a.qcap) {
-                    overflow = true;
-                    break;
-                }
-                const uint32_t pos = tail + incl - nch;
-                for (uint32_t k = 0; k < nch; k++) q[(pos + k) & qmask] = l0 + k;
-                tail += tot;
-            }
-            // opened leaves -> their particles into the list (asynchronous copies)
-            const uint32_t lc = (valid && !ok && leaf) ? (l1 & ~GT_LEAF_FLAG) : 0u;
-            const uint32_t lincl = warp_incl_scan(lc);
-            const uint32_t ltot = __shfl_sync(FULL, lincl, 31);
-            if (ltot) {
-                if (list_n + (int)ltot > LIST_CAP) flush();
-                if (ltot <= (uint32_t)LIST_CAP) {
-                    const uint32_t dst = (uint32_t)list_n + lincl - lc;
-                    for (uint32_t k = 0; k < lc; k++) cp_async16(&list[dst + k], &a.posm[l0 + k]);
-                    list_n += (int)ltot;
-                } else {  // leaves holding more particles than the list: one at a time, in chunks
-                    unsigned lm = __ballot_sync(FULL, lc != 0u);
-                    while (lm) {
-                        const int src = __ffs(lm) - 1;
-                        lm &= lm - 1;
-                        const uint32_t lf = __shfl_sync(FULL, l0, src);
-                        const uint32_t lcount = __shfl_sync(FULL, lc, src);
-                        uint32_t done = 0;
-                        while (done < lcount) {
-                            if (list_n == LIST_CAP) flush();
-                            const uint32_t take = min(lcount - done, (uint32_t)(LIST_CAP - list_n));
-                            for (uint32_t k = lane; k < take; k += 32)
-                                cp_async16(&list[list_n + k], &a.posm[lf + done + k]);
-                            list_n += (int)take;
-                            done += take;
-                        }
-                    }
-                }
-            }
-            if (list_n >= FLUSH_AT) flush();
-            __syncwarp();
-        }
-        if (overflow) {
-            if (lane == 0) gt_set_error(a.ctl, GT_EOVERFLOW, GTK_WALK);
-            cp_async_wait_all();
-            list_n = 0;
-            if (sub == 0 && have) a.acc[kk] = make_float4(NAN, NAN, NAN, NAN);
-            __syncwarp();
-            continue;
-        }
-        flush();
-        for (int o = 1; o < S; o <<= 1) {
-            ax += __shfl_xor_sync(FULL, ax, o);
-            ay += __shfl_xor_sync(FULL, ay, o);
-            az += __shfl_xor_sync(FULL, az, o);
-            ph += __shfl_xor_sync(FULL, ph, o);
-        }
-        if (sub == 0 && have) {
-            const float phi = fmaf(pi.w, a.inv_eps, ph);
-            a.acc[kk] = make_float4(a.G * ax, a.G * ay, a.G * az, a.G * phi);
-        }
+        walk_group(a, g, ngroups, list, q, n_inter, n_tests);
     }
     if (lane == 0) {
         if (n_inter) atomicAdd(&a.ctl->interactions, n_inter);
         if (n_tests) atomicAdd(&a.ctl->mac_tests, n_tests);
+    }
+}
+
+// Many systems in one persistent launch: global group numbers run over the systems
+// in order (gprefix), every warp takes the next one from one counter and walks it
+// with that system's arguments (copied to shared memory).  mac >= 0 overrides every
+// system's MAC (the opening-angle start-up pass).
+__global__ __launch_bounds__(WT, 4) void k_walk_batch(const WalkArgs *__restrict__ args, int nsys,
+                                                      const uint32_t *__restrict__ gprefix,
+                                                      unsigned int *group_next, uint32_t *queue, int qcap,
+                                                      int mac) {
+    __shared__ __align__(16) float4 list_sm[NWARP][LIST_CAP];
+    __shared__ WalkArgs sargs[NWARP];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4 *list = list_sm[warp];
+    uint32_t *q = queue + (size_t)(blockIdx.x * NWARP + warp) * (size_t)qcap;
+    const uint32_t total = gprefix[nsys];
+    for (;;) {
+        uint32_t gg = 0;
+        if (lane == 0) gg = atomicAdd(group_next, 1u);
+        gg = __shfl_sync(0xffffffffu, gg, 0);
+        if (gg >= total) break;
+        int sys = 0;
+        if (lane == 0) sys = system_of(gprefix, nsys, gg);
+        sys = __shfl_sync(0xffffffffu, sys, 0);
+        static_assert(sizeof(WalkArgs) % 4 == 0, "copied as words");
+        const uint32_t *src = (const uint32_t *)&args[sys];
+        uint32_t *dst = (uint32_t *)&sargs[warp];
+        for (int w = lane; w < (int)(sizeof(WalkArgs) / 4); w += 32) dst[w] = src[w];
+        __syncwarp();
+        if (mac >= 0 && lane == 0) sargs[warp].mac = mac;
+        __syncwarp();
+        const WalkArgs &a = sargs[warp];
+        const uint32_t g = gg - gprefix[sys];
+        const uint32_t ngroups = gprefix[sys + 1] - gprefix[sys];
+        unsigned long long n_inter = 0, n_tests = 0;
+        // the batch queue replaces the system's own
+        walk_group(a, g, ngroups, list, q, n_inter, n_tests);
+        if (lane == 0) {
+            if (n_inter) atomicAdd(&a.ctl->interactions, n_inter);
+            if (n_tests) atomicAdd(&a.ctl->mac_tests, n_tests);
+        }
+        __syncwarp();
+    }
+}
+
+// gprefix over the systems' group counts (one warp; also resets the batch counter)
+__global__ void k_batch_prefix(DevCtl *const *__restrict__ ctls, const WalkArgs *__restrict__ args, int nsys,
+                               uint32_t *gprefix, unsigned int *group_next) {
+    uint32_t carry = 0;
+    for (int s0 = 0; s0 < nsys; s0 += 32) {
+        const int s = s0 + (int)threadIdx.x;
+        uint32_t ng = 0;
+        if (s < nsys) {
+            const DevCtl *c = ctls[s];
+            const uint32_t na = c->n_active;
+            const uint32_t gm = (uint32_t)args[s].gmax;
+            ng = args[s].gstart ? c->n_groups : (na + gm - 1) / gm;
+        }
+        const uint32_t incl = warp_incl_scan(ng);
+        if (s < nsys) gprefix[s] = carry + incl - ng;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (threadIdx.x == 0) {
+        gprefix[nsys] = carry;
+        *group_next = 0u;
     }
 }
 
@@ -285,4 +372,12 @@ int gt_walk_warps_per_block() { return NWARP; }
 
 void gt_launch_walk(const WalkArgs &a, int nblocks, cudaStream_t st) {
     { k_walk<<<nblocks, WT, 0, st>>>(a); gt_note_launches(1); }
+}
+
+void gt_launch_walk_batch(DevCtl *const *ctls, const WalkArgs *args, int nsys, uint32_t *gprefix,
+                          unsigned int *group_next, uint32_t *queue, int qcap, int mac, int nblocks,
+                          cudaStream_t st) {
+    if (nsys <= 0) return;
+    { k_batch_prefix<<<1, 32, 0, st>>>(ctls, args, nsys, gprefix, group_next); gt_note_launches(1); }
+    { k_walk_batch<<<nblocks, WT, 0, st>>>(args, nsys, gprefix, group_next, queue, qcap, mac); gt_note_launches(1); }
 }

@@ -61,6 +61,18 @@ class GothicError(RuntimeError):
         self.status = status
 
 
+class gt_tune_space(C.Structure):
+    _fields_ = [("n_leaf", C.c_int32), ("leaf_max", C.c_int32 * 8),
+                ("n_group", C.c_int32), ("group_max", C.c_int32 * 8),
+                ("n_queue", C.c_int32), ("walk_queue", C.c_int32 * 4),
+                ("reps", C.c_int32)]
+
+
+class gt_tune_result(C.Structure):
+    _fields_ = [("leaf_max", C.c_int32), ("group_max", C.c_int32), ("walk_queue", C.c_int32),
+                ("n_tried", C.c_int32), ("best_ms", C.c_double), ("ms", C.c_double * 256)]
+
+
 _lib = None
 
 
@@ -113,6 +125,17 @@ def load(path: str | None = None):
     L.gt_sync_status.argtypes = [P, P]
     L.gt_get_stats.argtypes = [P, C.POINTER(gt_stats), P]
     L.gt_measure_fp32_peak.argtypes = [C.POINTER(C.c_double), P]
+    L.gt_batch_workspace_bytes.argtypes = [I32, P, P, I32, C.POINTER(C.c_size_t)]
+    L.gt_batch_create.argtypes = [C.POINTER(P), I32, P, P, I32, P, C.c_size_t]
+    L.gt_batch_destroy.argtypes = [P]
+    L.gt_batch_system.argtypes = [P, I32, C.POINTER(P)]
+    L.gt_batch_set_knobs.argtypes = [P, I32, I32, I32]
+    L.gt_batch_accel.argtypes = [P, I32, P]
+    L.gt_batch_capture.argtypes = [P, I32, P]
+    L.gt_batch_launch.argtypes = [P, P]
+    L.gt_batch_get_acc.argtypes = [P, I32, P, P, P]
+    L.gt_batch_sync_status.argtypes = [P, P, P]
+    L.gt_batch_autotune.argtypes = [P, C.POINTER(gt_tune_space), C.POINTER(gt_tune_result), P]
     for name in declared_symbols():
         getattr(L, name).restype = C.c_char_p if name == "gt_strerror" else C.c_int
     _lib = L
@@ -211,11 +234,21 @@ class System:
         _check(load().gt_system_create(C.byref(self._h), self.n, C.byref(self.params),
                                        self.ws.data_ptr(), self.ws.numel()), "gt_system_create")
 
+    @classmethod
+    def _member(cls, handle, n: int, params: gt_params, owner, stream):
+        """A view of a batch member (owned and destroyed by the batch)."""
+        s = cls.__new__(cls)
+        s.n, s.params, s.ws, s.stream, s._h, s._owner = int(n), params, None, stream, handle, owner
+        return s
+
     # stream defaults to torch's current stream at call time
     def _s(self):
         return self.stream if self.stream is not None else _current_stream()
 
     def close(self):
+        if getattr(self, "_owner", None) is not None:  # a batch member: the batch destroys it
+            self._h = C.c_void_p()
+            return
         if self._h:
             load().gt_system_destroy(self._h)
             self._h = C.c_void_p()
@@ -341,3 +374,94 @@ class System:
         st = gt_stats()
         _check(load().gt_get_stats(self._h, C.byref(st), self._s()), "gt_get_stats")
         return st.as_dict()
+
+
+class Batch:
+    """Many independent systems: forked tree builds and one walk launch over all of
+    them (gt_batch_*).  The batch runs on a stream of its own (capture needs a stream
+    other than the legacy default one); its members use the same stream."""
+
+    def __init__(self, ns, params, stream: int | None = None):
+        import torch
+        self.ns = [int(n) for n in ns]
+        k = len(self.ns)
+        plist = list(params) if isinstance(params, (list, tuple)) else [params]
+        if len(plist) not in (1, k):
+            raise ValueError("one params for all systems, or one per system")
+        self.params = plist
+        self._nn = np.ascontiguousarray(self.ns, np.int64)
+        self._pp = (gt_params * len(plist))(*plist)
+        b = C.c_size_t(0)
+        _check(load().gt_batch_workspace_bytes(k, self._nn.ctypes.data, C.addressof(self._pp), len(plist),
+                                               C.byref(b)), "gt_batch_workspace_bytes")
+        self.ws = torch.empty(max(int(b.value), 256), dtype=torch.uint8, device="cuda")
+        if stream is None:
+            self._torch_stream = torch.cuda.Stream()
+            stream = self._torch_stream.cuda_stream
+        self.stream = stream
+        self._h = C.c_void_p()
+        _check(load().gt_batch_create(C.byref(self._h), k, self._nn.ctypes.data, C.addressof(self._pp),
+                                      len(plist), self.ws.data_ptr(), self.ws.numel()), "gt_batch_create")
+        self.systems = []
+        for i in range(k):
+            h = C.c_void_p()
+            _check(load().gt_batch_system(self._h, i, C.byref(h)), "gt_batch_system")
+            self.systems.append(System._member(h, self.ns[i], plist[0 if len(plist) == 1 else i], self, stream))
+
+    def close(self):
+        if self._h:
+            for s in self.systems:
+                s.close()
+            load().gt_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.ns)
+
+    def set_knobs(self, leaf_max: int = 0, group_max: int = 0, walk_queue: int = 0):
+        _check(load().gt_batch_set_knobs(self._h, int(leaf_max), int(group_max), int(walk_queue)),
+               "gt_batch_set_knobs")
+
+    def accel(self, bootstrap: bool = False):
+        _check(load().gt_batch_accel(self._h, int(bool(bootstrap)), self.stream), "gt_batch_accel")
+
+    def capture(self, bootstrap: bool = False):
+        _check(load().gt_batch_capture(self._h, int(bool(bootstrap)), self.stream), "gt_batch_capture")
+
+    def launch(self):
+        _check(load().gt_batch_launch(self._h, self.stream), "gt_batch_launch")
+
+    def get_acc(self, k: int, out=None, ids=None):
+        """(acc (n, 4) float32, id (n,) uint32) of member k in internal order."""
+        n = self.ns[k]
+        acc = out if out is not None else np.zeros((max(n, 1), 4), np.float32)
+        idv = ids if ids is not None else np.zeros(max(n, 1), np.uint32)
+        _check(load().gt_batch_get_acc(self._h, int(k), _ptr(acc), _ptr(idv), self.stream), "gt_batch_get_acc")
+        return acc, idv
+
+    def sync(self) -> np.ndarray:
+        """Raise on any member's device error; interactions counted so far per member."""
+        inter = np.zeros(len(self.ns), np.int64)
+        _check(load().gt_batch_sync_status(self._h, inter.ctypes.data, self.stream), "device")
+        return inter
+
+    def autotune(self, leaf_max=(), group_max=(), walk_queue=(), reps: int = 3) -> dict:
+        sp = gt_tune_space()
+        sp.n_leaf, sp.n_group, sp.n_queue, sp.reps = len(leaf_max), len(group_max), len(walk_queue), int(reps)
+        for i, v in enumerate(leaf_max):
+            sp.leaf_max[i] = int(v)
+        for i, v in enumerate(group_max):
+            sp.group_max[i] = int(v)
+        for i, v in enumerate(walk_queue):
+            sp.walk_queue[i] = int(v)
+        r = gt_tune_result()
+        _check(load().gt_batch_autotune(self._h, C.byref(sp), C.byref(r), self.stream), "gt_batch_autotune")
+        return {"leaf_max": r.leaf_max, "group_max": r.group_max, "walk_queue": r.walk_queue,
+                "best_ms": r.best_ms, "ms": [float(r.ms[i]) for i in range(r.n_tried)]}
+

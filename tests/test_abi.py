@@ -44,6 +44,8 @@ def test_struct_layout_matches_header(libpath):
     assert gothic.gt_params.group_mode.offset == 64
     assert gothic.gt_params.eta.offset == 48
     assert ctypes.sizeof(gothic.gt_stats) == 96
+    assert ctypes.sizeof(gothic.gt_tune_space) == 96 and ctypes.sizeof(gothic.gt_tune_result) == 2072
+    assert gothic.gt_tune_result.best_ms.offset == 16 and gothic.gt_tune_space.reps.offset == 92
 
 
 def test_default_params_host_only(libpath):

@@ -1,0 +1,173 @@
+"""Batches of independent systems (gt_batch_*): forked builds and one walk launch.
+
+Each member's forces must equal, bit for bit, the single-system path with the same
+parameters (same tree, same groups, same walk per group); one member is also checked
+against the oracle's tree code.  The captured graph must replay the eager result and
+the autotuner must keep a working candidate.
+"""
+import numpy as np
+import pytest
+
+from paper_1610_07279_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+MED_TOL, P99_TOL = 1e-5, 1e-4
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1610_07279_gb300 import build
+    build.build()
+    import oracle as O
+    O.build()
+    from paper_1610_07279_gb300 import gothic as g
+    g.load()
+    return torch, g, O
+
+
+def _members(count, seed, lo, hi):
+    return ics.batch_systems(count, seed=seed, log2_lo=lo, log2_hi=hi)
+
+
+def _params(g, eps, **kw):
+    prm = g.gt_default_params()
+    prm.eps = eps
+    for k, v in kw.items():
+        setattr(prm, k, v)
+    return prm
+
+
+def _load(b, mem):
+    for s, m in zip(b.systems, mem):
+        s.set_state(m["pos"], m["vel"], m["mass"])
+
+
+def _single_forces(env, m, prm, aold_internal):
+    """The single-system path: build, then one walk of every particle with a_old."""
+    torch, g, O = env
+    s = g.System(m["n"], prm)
+    s.set_state(m["pos"], m["vel"], m["mass"])
+    s.build_tree()
+    acc = torch.zeros((m["n"], 4), dtype=torch.float32, device="cuda")
+    s.accel_active(None, torch.from_numpy(aold_internal).cuda(), acc)
+    s.sync()
+    out = acc.cpu().numpy()
+    inter = s.stats()["interactions"]
+    s.close()
+    return out, inter
+
+
+def test_batch_matches_single_system(env):
+    torch, g, O = env
+    mem = _members(7, seed=11, lo=9.0, hi=13.5)
+    prms = [_params(g, m["eps"]) for m in mem]
+    b = g.Batch([m["n"] for m in mem], prms)
+    _load(b, mem)
+    b.accel(bootstrap=True)
+    inter_b = b.sync()
+    for k, m in enumerate(mem):
+        acc_b, id_b = b.get_acc(k)
+        aold_b = b.systems[k].get_state()["aold"]
+        # the start-up pass: |a| of the opening-angle walk of the same tree
+        bh, _ = _single_forces(env, m, _params(g, m["eps"], mac=0), np.zeros(m["n"], np.float32))
+        assert np.array_equal(O.aold_of(bh).view(np.uint32), aold_b.view(np.uint32)), k
+        acc_s, inter_s = _single_forces(env, m, prms[k], aold_b)
+        assert np.array_equal(acc_s.view(np.uint32), acc_b.view(np.uint32)), k
+    # interactions: the bootstrap and the acceleration passes are both counted
+    assert np.all(inter_b > 0)
+    b.close()
+
+
+def test_batch_member_matches_oracle(env):
+    torch, g, O = env
+    mem = _members(3, seed=12, lo=11.0, hi=12.5)
+    prms = [_params(g, m["eps"]) for m in mem]
+    b = g.Batch([m["n"] for m in mem], prms)
+    _load(b, mem)
+    b.accel(bootstrap=True)
+    b.sync()
+    for k, m in enumerate(mem):
+        p4 = np.zeros((m["n"], 4), np.float32)
+        p4[:, :3] = m["pos"]
+        p4[:, 3] = m["mass"]
+        prm = prms[k]
+        oprm = O.Params(mac=prm.mac, theta=prm.theta, delta_acc=prm.delta_acc, eps=prm.eps, G=prm.G,
+                        leaf_max=prm.leaf_max, group_max=prm.group_max, levels=prm.levels, eta=prm.eta,
+                        dt_max=prm.dt_max, group_mode=prm.group_mode)
+        aold = O.bootstrap_aold(p4, oprm)
+        ref = O.tree_force(p4, oprm, aold=aold)
+        acc, ids = b.get_acc(k)
+        assert np.array_equal(ids, ref["order"])
+        a = acc.astype(np.float64)
+        r = ref["acc"]
+        rel = np.linalg.norm(a[:, :3] - r[:, :3], axis=1) / np.linalg.norm(r[:, :3], axis=1)
+        assert np.median(rel) <= MED_TOL and np.percentile(rel, 99) <= P99_TOL, (k, np.median(rel))
+    b.close()
+
+
+def test_batch_graph_replays_eager_result(env):
+    torch, g, O = env
+    mem = _members(9, seed=13, lo=9.0, hi=12.0)
+    b = g.Batch([m["n"] for m in mem], [_params(g, m["eps"]) for m in mem])
+    _load(b, mem)
+    b.accel(bootstrap=True)
+    b.sync()
+    eager = [b.get_acc(k)[0].copy() for k in range(len(mem))]
+    before = g.gt_kernel_launches()
+    b.capture(bootstrap=False)
+    assert g.gt_kernel_launches() == before  # capturing launches nothing
+    for _ in range(3):
+        b.launch()
+    b.sync()
+    assert g.gt_kernel_launches() > before
+    for k in range(len(mem)):
+        assert np.array_equal(b.get_acc(k)[0].view(np.uint32), eager[k].view(np.uint32)), k
+    b.close()
+
+
+def test_batch_with_empty_and_tiny_members(env):
+    torch, g, O = env
+    mem = _members(3, seed=14, lo=10.0, hi=11.0)
+    one = {"n": 1, "pos": np.zeros((1, 3)), "vel": np.zeros((1, 3)), "mass": np.ones(1, np.float32),
+           "eps": 1.0 / 64}
+    empty = {"n": 0, "pos": np.zeros((0, 3)), "vel": np.zeros((0, 3)), "mass": np.zeros(0, np.float32),
+             "eps": 1.0 / 64}
+    mem = [mem[0], empty, one, mem[1], mem[2]]
+    b = g.Batch([m["n"] for m in mem], [_params(g, m["eps"]) for m in mem])
+    _load(b, mem)
+    b.accel(bootstrap=True)
+    b.sync()
+    acc1, _ = b.get_acc(2)
+    assert np.all(acc1[0, :3] == 0.0)  # a lone particle feels no force
+    for k in (0, 3, 4):
+        acc, _ = b.get_acc(k)
+        assert np.all(np.isfinite(acc))
+    b.close()
+
+
+def test_batch_autotune_keeps_a_working_choice(env):
+    torch, g, O = env
+    mem = _members(6, seed=15, lo=10.0, hi=13.0)
+    prms = [_params(g, m["eps"]) for m in mem]
+    b = g.Batch([m["n"] for m in mem], prms)
+    _load(b, mem)
+    b.accel(bootstrap=True)
+    b.sync()
+    res = b.autotune(leaf_max=(8, 16), group_max=(16, 32), walk_queue=(8192, 16384), reps=2)
+    assert len(res["ms"]) == 8 and np.isfinite(res["best_ms"]) and res["best_ms"] == min(res["ms"])
+    assert res["leaf_max"] in (8, 16) and res["group_max"] in (16, 32)
+    # the kept knobs still give the single-system forces of those knobs
+    b.accel(bootstrap=False)
+    b.sync()
+    k = 2
+    m = mem[k]
+    aold = b.systems[k].get_state()["aold"]
+    tuned = _params(g, m["eps"], leaf_max=res["leaf_max"], group_max=res["group_max"],
+                    walk_queue=res["walk_queue"])
+    acc_s, _ = _single_forces(env, m, tuned, aold)
+    assert np.array_equal(acc_s.view(np.uint32), b.get_acc(k)[0].view(np.uint32))
+    b.close()
