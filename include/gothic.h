@@ -375,6 +375,76 @@ typedef struct gt_tune_result {
 GT_API int gt_batch_autotune(gt_batch *batch, const gt_tune_space *space, gt_tune_result *result,
                              gt_stream stream);
 
+/* ---- serving: continuous batching of block-step requests ----------------------
+ *
+ * A server keeps admitted systems resident in device memory and advances them with
+ * iteration-level batching.  Each server tick enqueues, for every resident request, one
+ * unit of work: the start-up (tree, opening-angle pass, a_old, first force, levels;
+ * Sec. 2.2, 2.7) for a new request, one block step (predict, rebuild or pseudo j, active
+ * set, correct; Sec. 2.6-2.7) for a running one.  The per-request parts run on forked
+ * streams; the tree walks of all requests in the tick run in one persistent launch.
+ * Requests join and leave at tick boundaries: one submitted while others are on the
+ * GPU is admitted as soon as a slot and memory are free and its work overlaps theirs.
+ * A request's result does not depend on the other requests (separate buffers, the
+ * same kernels and order per system): it is the same bit for bit alone and in a mix.
+ *
+ * Memory comes from the caller's callbacks only: one region at create (the shared walk
+ * queue and the per-tick tables) and one workspace per admitted request, returned
+ * through free_fn when the request's result has been collected (or at destroy).
+ * Admission keeps the sum of those blocks within hbm_cap bytes.  Not thread-safe: one
+ * host thread drives a server (single producer).
+ */
+#define GT_SERVER_MAX_SLOTS 256
+typedef void *(*gt_alloc_fn)(size_t bytes, void *ctx);  /* device memory, 256-byte aligned; NULL on failure */
+typedef void (*gt_free_fn)(void *ptr, void *ctx);
+typedef struct gt_server gt_server;
+
+typedef struct gt_request {
+    int64_t n;                 /* particles */
+    const double *p_pos;       /* n x 3 FP64, host or device; copied in by gt_submit */
+    const double *p_vel;       /* n x 3 FP64 */
+    const float *p_mass;       /* n FP32 */
+    gt_params params;          /* rebuild_every 0 means every 4 block steps here (the
+                                  automatic interval needs a host sync per step) */
+    int32_t nsteps;            /* block steps after the start-up (>= 0) */
+    int32_t reserved;
+} gt_request;
+
+enum { GT_REQ_UNKNOWN = 0, GT_REQ_RUNNING = 1, GT_REQ_DONE = 2 };
+
+typedef struct gt_server_stats {
+    int64_t ticks;             /* ticks enqueued */
+    int64_t admitted, completed;
+    int64_t slots_used;
+    int64_t hbm_used;          /* bytes held through alloc_fn */
+    int64_t hbm_cap;
+    int64_t walk_launches;     /* batched walk launches */
+    int64_t reserved;
+} gt_server_stats;
+
+/* max_slots <= GT_SERVER_MAX_SLOTS resident requests; walk_queue: the per-warp walk
+ * queue depth of the server (a power of two; requests asking for more are clamped). */
+GT_API int gt_server_create(gt_server **srv, size_t hbm_cap, int max_slots, int walk_queue,
+                            gt_alloc_fn alloc_fn, gt_free_fn free_fn, void *ctx);
+/* Waits for the device, returns every block through free_fn. */
+GT_API int gt_server_destroy(gt_server *srv);
+/* Admit a request: GT_EAGAIN when no slot is free or its workspace would pass hbm_cap
+ * (retry after collecting results), GT_EINVAL for bad arguments, GT_ENOMEM when
+ * alloc_fn fails.  The inputs are copied before the call returns.  Non-blocking
+ * otherwise; *ticket identifies the request. */
+GT_API int gt_submit(gt_server *srv, const gt_request *req, uint64_t *ticket);
+/* Enqueue ticks while there is work and fewer than two ticks are in flight; never
+ * waits for the device.  *running = requests resident (may be NULL). */
+GT_API int gt_server_progress(gt_server *srv, int *running);
+/* Drive the server (as gt_server_progress) and report a request: GT_EPENDING while it
+ * runs; GT_OK with *state = GT_REQ_DONE once finished, after writing its final state in
+ * the caller's particle order -- positions at each particle's last correction and the
+ * stored half-step velocities (Sec. 2.7), n x 3 FP64 each, host or device, either may be
+ * NULL -- and releasing its slot (a later poll reports GT_REQ_UNKNOWN / GT_EINVAL).  A
+ * device error of the request is returned instead of GT_OK (its slot is released). */
+GT_API int gt_poll(gt_server *srv, uint64_t ticket, int *state, double *p_pos_out, double *p_vel_out);
+GT_API int gt_server_get_stats(gt_server *srv, gt_server_stats *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -259,7 +259,8 @@ size_t gt_sys_carve(gt_system *s, char *base, int64_t n, const gt_params *p, int
     return carve(s, base, n, p, nsm, walk_blocks, own_queue);
 }
 
-int gt_sys_init(gt_system *s, int64_t n, const gt_params *p, void *ws, size_t ws_bytes, bool own_queue) {
+int gt_sys_init(gt_system *s, int64_t n, const gt_params *p, void *ws, size_t ws_bytes, bool own_queue,
+                cudaStream_t st) {
     int rc = device_sms(&s->dev, &s->nsm);
     if (rc) return rc;
     gt_sort_init();
@@ -269,11 +270,13 @@ int gt_sys_init(gt_system *s, int64_t n, const gt_params *p, void *ws, size_t ws
     carve(s, (char *)ws, n, p, s->nsm, wb, own_queue);
     s->n = n;
     s->prm = *p;
-    // zero the control block and the look-back status words
-    if (cudaMemset(s->ctl, 0, sizeof(DevCtl)) != cudaSuccess ||
-        cudaMemset(s->status, 0, (size_t)((s->cap + 511) / 512 + (n + 4095) / 4096 + 64) * 8) != cudaSuccess ||
-        cudaMemset(s->sb.status, 0, gt_sort_scratch_bytes(n)) != cudaSuccess ||
-        cudaDeviceSynchronize() != cudaSuccess)
+    // zero the control block and the look-back status words (on st, then wait for it;
+    // without a stream, on the default stream and wait for the device)
+    const size_t st_bytes = (size_t)((s->cap + 511) / 512 + (n + 4095) / 4096 + 64) * 8;
+    if (cudaMemsetAsync(s->ctl, 0, sizeof(DevCtl), st) != cudaSuccess ||
+        cudaMemsetAsync(s->status, 0, st_bytes, st) != cudaSuccess ||
+        cudaMemsetAsync(s->sb.status, 0, gt_sort_scratch_bytes(n), st) != cudaSuccess ||
+        (st ? cudaStreamSynchronize(st) : cudaDeviceSynchronize()) != cudaSuccess)
         return GT_ECUDA;
     return GT_OK;
 }
@@ -313,6 +316,51 @@ WalkArgs gt_sys_walk_args(const gt_system *s, const uint32_t *active, const floa
 }
 
 void gt_sys_aold_from_acc(gt_system *s, cudaStream_t st) { gt_launch_aold(s->acc_out, s->n, s->st[0].aold, st); }
+
+void gt_sys_step_pre(gt_system *s, cudaStream_t st, bool rebuild) {
+    const int64_t n = s->n;
+    gt_launch_prepare(s->ctl, 1, st);
+    ph_begin(s, PH_PREDICT, st);
+    gt_launch_predict(s->st[0], n, s->ctl, rebuild ? s->posm_tmp : s->posm, st);
+    ph_end(s, PH_PREDICT, st);
+    if (rebuild) {
+        build_tree(s, st, s->posm_tmp);
+    } else {
+        ph_begin(s, PH_PSEUDO, st);
+        gt_launch_pseudo(s->nd, s->cap, s->posm, s->ctl, s->nsm, st);
+        ph_end(s, PH_PSEUDO, st);
+    }
+    ph_begin(s, PH_ACTIVE, st);
+    gt_launch_active(s->st[0], n, s->prm.levels, 0, s->ctl, s->active, s->prefix, s->status, s->nsm, st);
+    ph_end(s, PH_ACTIVE, st);
+}
+
+void gt_sys_step_groups(gt_system *s, cudaStream_t st) {
+    if (s->prm.group_mode == GT_GROUP_CELLS)
+        gt_launch_groups(s->nd, s->cap, s->prefix, s->prm.group_max, s->n, s->marks, s->ctl, s->gstart,
+                         s->status, s->nsm, st);
+}
+
+void gt_sys_step_post(gt_system *s, cudaStream_t st) {
+    ph_begin(s, PH_CORRECT, st);
+    gt_launch_correct(s->st[0], s->active, s->acc_out, s->ctl, s->n, s->prm.levels, c2_of(s->prm), s->nsm, st);
+    ph_end(s, PH_CORRECT, st);
+    s->steps++;
+}
+
+void gt_sys_start_levels(gt_system *s, cudaStream_t st) {
+    int M = 0, have_M = 0;
+    if (s->prm.dt_max > 0.0) {
+        int e;
+        frexp(s->prm.dt_max, &e);
+        M = e - 1;
+        have_M = 1;
+    }
+    gt_launch_init_levels(s->st[0], s->acc_out, s->n, s->prm.levels, c2_of(s->prm), M, have_M, s->ctl, s->nsm, st);
+    s->started = true;
+    s->steps = 0;
+    s->tune = RebuildTuner();
+}
 
 extern "C" {
 
@@ -371,7 +419,7 @@ int gt_system_create(gt_system **out, int64_t n, const gt_params *prm, void *d_w
     if (rc) return rc;
     gt_system *s = new (std::nothrow) gt_system();
     if (!s) return GT_ENOMEM;
-    if ((rc = gt_sys_init(s, n, prm, d_ws, ws_bytes, true))) {
+    if ((rc = gt_sys_init(s, n, prm, d_ws, ws_bytes, true, nullptr))) {
         delete s;
         return rc;
     }
@@ -467,17 +515,7 @@ int gt_start(gt_system *s, const float *p_aold_boot, gt_stream stream) {
         ph_sync_collect(s, st);
     }
     walk_all(s, t.aold, s->acc_out, s->prm.mac, st);
-    int M = 0, have_M = 0;
-    if (s->prm.dt_max > 0.0) {
-        int e;
-        frexp(s->prm.dt_max, &e);
-        M = e - 1;
-        have_M = 1;
-    }
-    gt_launch_init_levels(t, s->acc_out, n, s->prm.levels, c2_of(s->prm), M, have_M, s->ctl, s->nsm, st);
-    s->started = true;
-    s->steps = 0;
-    s->tune = RebuildTuner();
+    gt_sys_start_levels(s, st);
     return last_cuda();
 }
 
@@ -506,26 +544,10 @@ int gt_block_step(gt_system *s, gt_stream stream) {
         rebuild = s->steps % s->prm.rebuild_every == 0;
     }
     s->last_rebuilt = rebuild;
-    gt_launch_prepare(s->ctl, 1, st);
-    ph_begin(s, PH_PREDICT, st);
-    gt_launch_predict(s->st[0], n, s->ctl, rebuild ? s->posm_tmp : s->posm, st);
-    ph_end(s, PH_PREDICT, st);
-    if (rebuild) {
-        build_tree(s, st, s->posm_tmp);
-    } else {
-        ph_begin(s, PH_PSEUDO, st);
-        gt_launch_pseudo(s->nd, s->cap, s->posm, s->ctl, s->nsm, st);
-        ph_end(s, PH_PSEUDO, st);
-    }
+    gt_sys_step_pre(s, st, rebuild);
     State &t = s->st[0];
-    ph_begin(s, PH_ACTIVE, st);
-    gt_launch_active(t, n, s->prm.levels, 0, s->ctl, s->active, s->prefix, s->status, s->nsm, st);
-    ph_end(s, PH_ACTIVE, st);
     walk(s, s->active, t.aold, s->acc_out, s->prm.mac, st);
-    ph_begin(s, PH_CORRECT, st);
-    gt_launch_correct(t, s->active, s->acc_out, s->ctl, n, s->prm.levels, c2_of(s->prm), s->nsm, st);
-    ph_end(s, PH_CORRECT, st);
-    s->steps++;
+    gt_sys_step_post(s, st);
     return last_cuda();
 }
 

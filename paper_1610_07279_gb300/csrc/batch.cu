@@ -195,7 +195,7 @@ int gt_batch_create(gt_batch **out, int nsys, const int64_t *n, const gt_params 
         gt_system *s = new (std::nothrow) gt_system();
         if (!s) { gt_batch_destroy(b); return GT_ENOMEM; }
         b->sys[k] = s;
-        if ((rc = gt_sys_init(s, n[k], &prm_of(prm, n_prm, k), base + off, mb[k], false))) {
+        if ((rc = gt_sys_init(s, n[k], &prm_of(prm, n_prm, k), base + off, mb[k], false, nullptr))) {
             gt_batch_destroy(b);
             return rc;
         }

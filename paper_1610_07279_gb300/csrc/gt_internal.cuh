@@ -232,6 +232,7 @@ void gt_launch_deinterleave3(const double *in, int64_t n, double *x, double *y, 
                              cudaStream_t st);
 void gt_launch_interleave3(const double *x, const double *y, const double *z, int64_t n, double *out,
                            cudaStream_t st);
+void gt_launch_state_out(const State &t, int64_t n, double *pos, double *vel, cudaStream_t st);
 void gt_launch_gather_f(const float *in, const uint32_t *id, int64_t n, float *out, cudaStream_t st);
 void gt_launch_active(const State &s, int64_t n, int L, int all, DevCtl *ctl, uint32_t *active,
                       uint32_t *prefix, unsigned long long *status, int nsm, cudaStream_t st);

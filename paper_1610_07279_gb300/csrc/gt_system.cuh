@@ -67,8 +67,10 @@ int gt_sys_device_sms(int *dev, int *nsm);
 // own_queue == false leaves the walk queue to the caller (a batch).
 size_t gt_sys_carve(gt_system *s, char *base, int64_t n, const gt_params *p, int nsm, int walk_blocks,
                     bool own_queue);
-// Carve a system into ws (ws_bytes from gt_sys_carve) and zero its control words (synchronous).
-int gt_sys_init(gt_system *s, int64_t n, const gt_params *p, void *ws, size_t ws_bytes, bool own_queue);
+// Carve a system into ws (ws_bytes from gt_sys_carve) and zero its control words; waits
+// for stream st (or, with st == nullptr, for the device).
+int gt_sys_init(gt_system *s, int64_t n, const gt_params *p, void *ws, size_t ws_bytes, bool own_queue,
+                cudaStream_t st);
 // A1-A5 on FP32 positions posm_src
 void gt_sys_build_tree(gt_system *s, cudaStream_t st, const float4 *posm_src);
 // A6 with every particle active: the active list and, for cell grouping, the groups
@@ -77,3 +79,10 @@ void gt_sys_groups_all(gt_system *s, cudaStream_t st);
 WalkArgs gt_sys_walk_args(const gt_system *s, const uint32_t *active, const float *aold, float4 *acc, int mac);
 // |a| of the last walk over every particle -> a_old (start-up pass)
 void gt_sys_aold_from_acc(gt_system *s, cudaStream_t st);
+// after the start-up walks: levels and block time of every particle (the system is started)
+void gt_sys_start_levels(gt_system *s, cudaStream_t st);
+// One block step in three parts around the walk: predict, rebuild or pseudo j, active set
+// (pre); the groups of the active set (groups); correct, levels, next block time (post).
+void gt_sys_step_pre(gt_system *s, cudaStream_t st, bool rebuild);
+void gt_sys_step_groups(gt_system *s, cudaStream_t st);
+void gt_sys_step_post(gt_system *s, cudaStream_t st);

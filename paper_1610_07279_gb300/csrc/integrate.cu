@@ -122,6 +122,24 @@ __global__ __launch_bounds__(256) void k_interleave3(const double *__restrict__ 
     out[3 * i + 2] = z[i];
 }
 
+// state out in the caller's particle order: row id[i] of pos/vel (n x 3) <- slot i
+__global__ __launch_bounds__(256) void k_state_out(State t, long long n, double *__restrict__ pos,
+                                                   double *__restrict__ vel) {
+    const long long i = blockIdx.x * 256ll + threadIdx.x;
+    if (i >= n) return;
+    const long long j = t.id[i];
+    if (pos) {
+        pos[3 * j] = t.rx[i];
+        pos[3 * j + 1] = t.ry[i];
+        pos[3 * j + 2] = t.rz[i];
+    }
+    if (vel) {
+        vel[3 * j] = t.vx[i];
+        vel[3 * j + 1] = t.vy[i];
+        vel[3 * j + 2] = t.vz[i];
+    }
+}
+
 __global__ __launch_bounds__(256) void k_gather_f(const float *__restrict__ in, const uint32_t *__restrict__ id,
                                                   long long n, float *__restrict__ out) {
     const long long i = blockIdx.x * 256ll + threadIdx.x;
@@ -464,6 +482,10 @@ void gt_launch_deinterleave3(const double *in, int64_t n, double *x, double *y, 
 void gt_launch_interleave3(const double *x, const double *y, const double *z, int64_t n, double *out,
                            cudaStream_t st) {
     if (n > 0) { k_interleave3<<<nblk(n), 256, 0, st>>>(x, y, z, n, out); gt_note_launches(1); }
+}
+
+void gt_launch_state_out(const State &t, int64_t n, double *pos, double *vel, cudaStream_t st) {
+    if (n > 0) { k_state_out<<<nblk(n), 256, 0, st>>>(t, n, pos, vel); gt_note_launches(1); }
 }
 
 void gt_launch_gather_f(const float *in, const uint32_t *id, int64_t n, float *out, cudaStream_t st) {

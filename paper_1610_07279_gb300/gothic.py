@@ -73,6 +73,22 @@ class gt_tune_result(C.Structure):
                 ("n_tried", C.c_int32), ("best_ms", C.c_double), ("ms", C.c_double * 256)]
 
 
+GT_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+GT_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+GT_SERVER_MAX_SLOTS = 256
+GT_REQ_UNKNOWN, GT_REQ_RUNNING, GT_REQ_DONE = 0, 1, 2
+
+
+class gt_request(C.Structure):
+    _fields_ = [("n", C.c_int64), ("p_pos", C.c_void_p), ("p_vel", C.c_void_p), ("p_mass", C.c_void_p),
+                ("params", gt_params), ("nsteps", C.c_int32), ("reserved", C.c_int32)]
+
+
+class gt_server_stats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("ticks", "admitted", "completed", "slots_used", "hbm_used",
+                                         "hbm_cap", "walk_launches", "reserved")]
+
+
 _lib = None
 
 
@@ -136,6 +152,12 @@ def load(path: str | None = None):
     L.gt_batch_get_acc.argtypes = [P, I32, P, P, P]
     L.gt_batch_sync_status.argtypes = [P, P, P]
     L.gt_batch_autotune.argtypes = [P, C.POINTER(gt_tune_space), C.POINTER(gt_tune_result), P]
+    L.gt_server_create.argtypes = [C.POINTER(P), C.c_size_t, I32, I32, GT_ALLOC_FN, GT_FREE_FN, P]
+    L.gt_server_destroy.argtypes = [P]
+    L.gt_submit.argtypes = [P, C.POINTER(gt_request), C.POINTER(C.c_uint64)]
+    L.gt_server_progress.argtypes = [P, C.POINTER(I32)]
+    L.gt_poll.argtypes = [P, C.c_uint64, C.POINTER(I32), P, P]
+    L.gt_server_get_stats.argtypes = [P, C.POINTER(gt_server_stats)]
     for name in declared_symbols():
         getattr(L, name).restype = C.c_char_p if name == "gt_strerror" else C.c_int
     _lib = L
@@ -464,4 +486,76 @@ class Batch:
         _check(load().gt_batch_autotune(self._h, C.byref(sp), C.byref(r), self.stream), "gt_batch_autotune")
         return {"leaf_max": r.leaf_max, "group_max": r.group_max, "walk_queue": r.walk_queue,
                 "best_ms": r.best_ms, "ms": [float(r.ms[i]) for i in range(r.n_tried)]}
+
+
+class Server:
+    """Continuous batching of block-step requests (gt_server_*), device memory from
+    torch's caching allocator through the library's allocation callbacks."""
+
+    def __init__(self, hbm_cap: int, max_slots: int = 64, walk_queue: int = 16384):
+        import torch
+        self._blocks = {}
+
+        def _alloc(nbytes, ctx):
+            try:
+                t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+            except RuntimeError:
+                return None
+            self._blocks[t.data_ptr()] = t
+            return t.data_ptr()
+
+        def _free(ptr, ctx):
+            self._blocks.pop(int(ptr), None)
+
+        self._alloc_cb, self._free_cb = GT_ALLOC_FN(_alloc), GT_FREE_FN(_free)
+        self._h = C.c_void_p()
+        _check(load().gt_server_create(C.byref(self._h), int(hbm_cap), int(max_slots), int(walk_queue),
+                                       self._alloc_cb, self._free_cb, None), "gt_server_create")
+
+    def close(self):
+        if self._h:
+            load().gt_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, pos, vel, mass, params: gt_params, nsteps: int):
+        """Ticket of the admitted request, or None when it must wait (no slot / memory)."""
+        pos = np.ascontiguousarray(pos, np.float64) if isinstance(pos, np.ndarray) else pos
+        vel = np.ascontiguousarray(vel, np.float64) if isinstance(vel, np.ndarray) else vel
+        mass = np.ascontiguousarray(mass, np.float32) if isinstance(mass, np.ndarray) else mass
+        r = gt_request()
+        r.n = int(mass.shape[0])
+        r.p_pos, r.p_vel, r.p_mass = _ptr(pos), _ptr(vel), _ptr(mass)
+        r.params = params
+        r.nsteps = int(nsteps)
+        t = C.c_uint64(0)
+        rc = load().gt_submit(self._h, C.byref(r), C.byref(t))
+        if rc == GT_EAGAIN:
+            return None
+        _check(rc, "gt_submit")
+        return int(t.value)
+
+    def progress(self) -> int:
+        running = C.c_int32(0)
+        _check(load().gt_server_progress(self._h, C.byref(running)), "gt_server_progress")
+        return int(running.value)
+
+    def poll(self, ticket: int, pos_out=None, vel_out=None):
+        """True once the request is done (its state written to the outputs), else False."""
+        state = C.c_int32(0)
+        rc = load().gt_poll(self._h, C.c_uint64(ticket), C.byref(state), _ptr(pos_out), _ptr(vel_out))
+        if rc == GT_EPENDING:
+            return False
+        _check(rc, "gt_poll")
+        return state.value == GT_REQ_DONE
+
+    def stats(self) -> dict:
+        st = gt_server_stats()
+        _check(load().gt_server_get_stats(self._h, C.byref(st)), "gt_server_get_stats")
+        return {k: int(getattr(st, k)) for k, _ in gt_server_stats._fields_ if k != "reserved"}
 

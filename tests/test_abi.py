@@ -46,6 +46,8 @@ def test_struct_layout_matches_header(libpath):
     assert ctypes.sizeof(gothic.gt_stats) == 96
     assert ctypes.sizeof(gothic.gt_tune_space) == 96 and ctypes.sizeof(gothic.gt_tune_result) == 2072
     assert gothic.gt_tune_result.best_ms.offset == 16 and gothic.gt_tune_space.reps.offset == 92
+    assert ctypes.sizeof(gothic.gt_request) == 112 and gothic.gt_request.nsteps.offset == 104
+    assert ctypes.sizeof(gothic.gt_server_stats) == 64
 
 
 def test_default_params_host_only(libpath):
