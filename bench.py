@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-groups", type=int, default=2048, help="groups walked by the CPU baseline sample")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-system batch workload")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
+    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-rho", type=str, default="0.5,0.8,1.0,1.2,2.0,burst",
+                    help="load levels as multiples of the serial capacity; 'burst' = all requests at t = 0")
     return ap.parse_args()
 
 
@@ -199,6 +204,203 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+
+# ------------------------------------------------------------------ batch workload
+def direct_fp64(pos, mass, eps, G, targets):
+    """Eq. (1) in FP64 for the target rows (plain numpy, chunked): the accuracy yardstick
+    of the batch report."""
+    pos = np.asarray(pos, np.float64)
+    m = np.asarray(mass, np.float64)
+    out = np.zeros((len(targets), 3))
+    e2 = float(eps) ** 2
+    for a in range(0, len(targets), 16):
+        t = targets[a:a + 16]
+        d = pos[None, :, :] - pos[t][:, None, :]
+        r2 = (d * d).sum(-1) + e2
+        w = m[None, :] / (r2 * np.sqrt(r2))
+        out[a:a + 16] = G * (w[:, :, None] * d).sum(1)
+    return out
+
+
+def run_batch(g, torch, steps: int):
+    """64 independent systems (Plummer or NFW, N log-uniform in [2^12, 2^18]): one force
+    evaluation of all of them per step, as a captured graph of forked builds and one
+    walk launch, knobs from the autotuner; against the same members through the
+    single-system calls one after another."""
+    from paper_1610_07279_gb300 import ics
+    mem = ics.batch_systems(64, seed=4)
+    prms = []
+    for m in mem:
+        p = g.gt_default_params()
+        p.eps = m["eps"]
+        prms.append(p)
+    b = g.Batch([m["n"] for m in mem], prms)
+    for s, m in zip(b.systems, mem):
+        s.set_state(m["pos"], m["vel"], m["mass"])
+    b.accel(bootstrap=True)
+    b.sync()
+    tune = b.autotune(leaf_max=(8, 16, 32), group_max=(16, 32), walk_queue=(8192, 16384), reps=3)
+    b.capture(bootstrap=False)
+    b.launch()
+    b.sync()
+    st = torch.cuda.ExternalStream(b.stream)
+    reps = max(10, steps)
+    i0 = int(b.sync().sum())
+    l0 = g.gt_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        b.launch()
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    inter = (int(b.sync().sum()) - i0) / reps
+    launches = (g.gt_kernel_launches() - l0) / reps
+    # serial: the same members, build + walk of every particle, one system after another
+    accs = [torch.empty((max(m["n"], 1), 4), dtype=torch.float32, device="cuda") for m in mem]
+    for s, a in zip(b.systems, accs):  # warm-up
+        s.build_tree()
+        s.accel_active(None, None, a)
+    b.sync()
+    i0 = int(b.sync().sum())
+    e0.record(st)
+    for _ in range(reps):
+        for s, a in zip(b.systems, accs):
+            s.build_tree()
+            s.accel_active(None, None, a)
+    e1.record(st)
+    e1.synchronize()
+    ms_serial = e0.elapsed_time(e1) / reps
+    inter_serial = (int(b.sync().sum()) - i0) / reps
+    # accuracy: FP32 forces of the batch vs FP64 direct sums on 128 random particles per system
+    b.launch()
+    b.sync()
+    rng = np.random.default_rng(40)
+    per = []
+    for k, m in enumerate(mem):
+        acc, ids = b.get_acc(k)
+        rows = rng.choice(m["n"], min(128, m["n"]), replace=False)
+        ref = direct_fp64(m["pos"], m["mass"], m["eps"], 1.0, ids[rows].astype(np.int64))
+        rel = np.linalg.norm(acc[rows, :3] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        per.append({"kind": m["kind"], "n": m["n"], "median": float(np.median(rel)),
+                    "p99": float(np.percentile(rel, 99))})
+    b.close()
+    return {"workload": "64 systems, Plummer or NFW by seeded coin, N = round(2^(12 + 6u)), own eps; "
+                        "one force evaluation of every system per step (tree build + every particle "
+                        "active, acceleration MAC with a_old from an opening-angle start-up pass)",
+            "total_particles": int(sum(m["n"] for m in mem)),
+            "autotuned": {"leaf_max": tune["leaf_max"], "group_max": tune["group_max"],
+                          "walk_queue": tune["walk_queue"], "candidates_ms": tune["ms"]},
+            "batched": {"ms_per_step": ms, "interactions_per_s": inter / (ms * 1e-3),
+                        "systems_per_s": 64 / (ms * 1e-3), "gpu_launches_per_step": launches,
+                        "path": "captured CUDA graph: forked builds + one persistent walk launch"},
+            "serial": {"ms_per_step": ms_serial, "interactions_per_s": inter_serial / (ms_serial * 1e-3),
+                       "systems_per_s": 64 / (ms_serial * 1e-3),
+                       "path": "gt_build_tree + gt_accel_active per system, one after another"},
+            "speedup_vs_serial": ms_serial / ms,
+            "error_vs_fp64_direct": {"sample": "128 random particles per system vs FP64 direct summation",
+                                     "median_of_medians": float(np.median([p["median"] for p in per])),
+                                     "max_median": float(max(p["median"] for p in per)),
+                                     "max_p99": float(max(p["p99"] for p in per)), "per_system": per}}
+
+
+# ------------------------------------------------------------------ serving workload
+class RequestSource:
+    """Inputs of the serving stream: one 2^20-particle sample per model, a request of N
+    particles takes its first N (the samples are iid, so a prefix is a sample of the
+    model; masses rescaled to total 1)."""
+
+    def __init__(self):
+        from paper_1610_07279_gb300 import ics
+        self.master = {"plummer": ics.plummer(1 << 20, seed=51), "nfw": ics.nfw(1 << 20, seed=52)}
+
+    def get(self, req):
+        pos, vel, mass, eps = self.master[req["kind"]]
+        n = req["n"]
+        m = np.full(n, np.float32(1.0 / n))
+        return np.ascontiguousarray(pos[:n]), np.ascontiguousarray(vel[:n]), m, eps
+
+
+def serve_params(g, eps):
+    p = g.gt_default_params()
+    p.eps = eps
+    p.rebuild_every = 4
+    p.walk_queue = 8192
+    return p
+
+
+def run_serving(g, torch, nreq: int, rhos):
+    from paper_1610_07279_gb300 import ics
+    src = RequestSource()
+    # serial capacity: requests alone through the single-system path, one after another
+    probe = ics.serving_requests(48, seed=55, rate=1.0)
+    t_serial = []
+    for r in probe:
+        pos, vel, mass, eps = src.get(r)
+        t0 = time.perf_counter()
+        s = g.System(r["n"], serve_params(g, eps))
+        s.set_state(pos, vel, mass)
+        s.start()
+        for _ in range(r["steps"]):
+            s.block_step()
+        out = s.get_state()
+        s.close()
+        t_serial.append(time.perf_counter() - t0)
+    cap = 1.0 / float(np.mean(t_serial[4:]))  # requests/s, first few are warm-up
+    runs = []
+    for rho in rhos:
+        burst = rho == "burst"
+        reqs = ics.serving_requests(nreq, seed=5, rate=cap if burst else float(rho) * cap)
+        if burst:
+            for r in reqs:
+                r["arrival"] = 0.0
+        srv = g.Server(150 * 10**9, max_slots=128, walk_queue=8192)
+        outs = {}
+        lat_arr, lat_sub = [], []
+        nxt, pending, tickets = 0, [], {}
+        t_start = time.perf_counter()
+        while nxt < len(reqs) or pending or tickets:
+            now = time.perf_counter() - t_start
+            while nxt < len(reqs) and reqs[nxt]["arrival"] <= now:
+                pending.append(nxt)
+                nxt += 1
+            while pending:
+                r = reqs[pending[0]]
+                pos, vel, mass, eps = src.get(r)
+                t = srv.submit(pos, vel, mass, serve_params(g, eps), r["steps"])
+                if t is None:
+                    break
+                tickets[t] = (pending.pop(0), time.perf_counter() - t_start)
+            for t in list(tickets):
+                k, t_sub = tickets[t]
+                if srv.poll(t):
+                    done = time.perf_counter() - t_start
+                    lat_arr.append(done - reqs[k]["arrival"])
+                    lat_sub.append(done - t_sub)
+                    del tickets[t]
+            if not tickets and pending == [] and nxt < len(reqs):
+                time.sleep(max(0.0, min(0.002, reqs[nxt]["arrival"] - (time.perf_counter() - t_start))))
+        span = time.perf_counter() - t_start
+        st = srv.stats()
+        srv.close()
+        runs.append({"rho": rho, "arrival_rate_per_s": None if burst else float(rho) * cap, "requests": len(reqs),
+                     "p50_latency_s": float(np.percentile(lat_arr, 50)),
+                     "p99_latency_s": float(np.percentile(lat_arr, 99)),
+                     "p50_submit_to_done_s": float(np.percentile(lat_sub, 50)),
+                     "p99_submit_to_done_s": float(np.percentile(lat_sub, 99)),
+                     "throughput_req_per_s": len(reqs) / span, "makespan_s": span,
+                     "ticks": st["ticks"], "batched_walk_launches": st["walk_launches"]})
+    return {"workload": f"Poisson arrivals of Plummer/NFW systems, N log-uniform in [2^12, 2^20], 4-32 block "
+                        f"steps each (8 levels, acceleration MAC, rebuild every 4 steps), {nreq} requests per "
+                        f"load level, HBM admission cap 150 GB, up to 128 resident",
+            "serial_capacity_req_per_s": cap,
+            "serial_path": "gt_system_create + gt_set_state + gt_start + block steps + gt_get_state, one "
+                           "request at a time (48 sampled requests)",
+            "latency": "from arrival (queueing included); submit-to-done also given",
+            "runs": runs,
+            "max_throughput_vs_serial": max(r["throughput_req_per_s"] for r in runs) / cap}
+
+
 # ------------------------------------------------------------------ our arm
 def walk_traffic_entry():
     """DRAM bytes per walk launch from the committed ncu summary, if the kernel is unchanged."""
@@ -338,6 +540,14 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline_entry(pos, mass, eps, args.cpu_groups)
+    sysm.close()
+    del sysm
+    batch = serving = None
+    if not args.no_batch:
+        batch = run_batch(g, torch, args.steps)
+    if not args.no_serve:
+        serving = run_serving(g, torch, args.serve_requests,
+                              [x if x == "burst" else float(x) for x in args.serve_rho.split(",")])
 
     if rank == 0:
         breakdown = {k: {"ms_total": v[0], "launches": v[1]} for k, v in timers.items()}
@@ -349,10 +559,10 @@ def run_ours(args):
                 "rebuilds": st1["rebuilds"] - st0["rebuilds"],
                 "interactions": inter, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "cpu_baseline": cpu, "clocks": clk, "phase_ms": breakdown,
+                "batch": batch, "serving": serving,
                 "gflops_paper_convention": {str(f): inter_all * f / (ms_max * 1e-3) / 1e9
                                             for f in (20, 24, 28, 38)}}
         print(json.dumps(line), flush=True)
-    sysm.close()
     if world > 1:
         dist.destroy_process_group()
 

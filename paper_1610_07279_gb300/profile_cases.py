@@ -1,0 +1,105 @@
+"""Small, fixed cases for profiling single kernels under a profiler.
+
+    python -m paper_1610_07279_gb300.profile_cases walk  --model m31 --n 4194304
+    python -m paper_1610_07279_gb300.profile_cases build --model m31 --n 2097152 --repeat 3
+    python -m paper_1610_07279_gb300.profile_cases steps --model m31 --n 2097152 --steps 16
+
+walk:  tree build, one opening-angle walk of every particle (the start-up pass), then
+       one acceleration-MAC walk of every particle (the second k_walk launch).
+build: the tree build (keys, sort, permute, octree, cell lists, pseudo j) repeated.
+steps: start-up and block steps with the automatic rebuild interval.
+Each case prints one line with its timings and counts; inputs are the seeded models of
+``ics`` (the same generators the benchmark uses).
+"""
+from __future__ import annotations
+
+import argparse
+import time
+
+from . import build as _build
+from . import gothic as g
+from . import ics
+
+MODELS = {"m31": ics.andromeda_like, "nfw": ics.nfw, "plummer": ics.plummer}
+
+
+def _system(model: str, n: int, seed: int):
+    pos, vel, mass, eps = MODELS[model](n, seed=seed)
+    prm = g.gt_default_params()
+    prm.eps = eps
+    s = g.System(n, prm)
+    s.set_state(pos, vel, mass)
+    return s, prm
+
+
+def case_walk(model: str, n: int, seed: int) -> str:
+    import torch
+    s, prm = _system(model, n, seed)
+    s.build_tree()
+    acc = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+    boot = g.gt_params.from_buffer_copy(prm)
+    boot.mac = g.GT_MAC_OPENING_ANGLE
+    s.set_params(boot)
+    s.accel_active(None, None, acc)
+    s.sync()
+    aold = torch.linalg.norm(acc[:, :3].double(), dim=1).float().contiguous()
+    s.set_params(prm)
+    st0 = s.stats()
+    t = time.perf_counter()
+    s.accel_active(None, aold, acc)
+    s.sync()
+    dt = time.perf_counter() - t
+    st1 = s.stats()
+    inter = st1["interactions"] - st0["interactions"]
+    tests = st1["mac_tests"] - st0["mac_tests"]
+    s.close()
+    return (f"walk {model} n={n} nodes={st1['n_nodes']} depth={st1['depth']} interactions={inter} "
+            f"mac_tests={tests} acc_walk_ms={dt * 1e3:.3f}")
+
+
+def case_build(model: str, n: int, seed: int, repeat: int) -> str:
+    s, _ = _system(model, n, seed)
+    s.profile(True)
+    for _ in range(repeat):
+        s.build_tree()
+    s.sync()
+    tm = s.timers()
+    s.close()
+    return f"build {model} n={n} " + " ".join(f"{k}_ms={v[0] / max(v[1], 1):.3f}" for k, v in tm.items() if v[1])
+
+
+def case_steps(model: str, n: int, seed: int, steps: int) -> str:
+    s, _ = _system(model, n, seed)
+    s.start()
+    s.profile(True)
+    for _ in range(steps):
+        s.block_step()
+    s.sync()
+    tm = s.timers()
+    st = s.stats()
+    s.close()
+    return (f"steps {model} n={n} block_steps={st['block_steps']} rebuilds={st['rebuilds']} "
+            + " ".join(f"{k}_ms={v[0]:.3f}" for k, v in tm.items() if v[1]))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["walk", "build", "steps"])
+    ap.add_argument("--model", choices=sorted(MODELS), default="m31")
+    ap.add_argument("--n", type=int, default=1 << 21)
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--repeat", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=16)
+    a = ap.parse_args(argv)
+    _build.build()
+    g.load()
+    if a.case == "walk":
+        print(case_walk(a.model, a.n, a.seed), flush=True)
+    elif a.case == "build":
+        print(case_build(a.model, a.n, a.seed, a.repeat), flush=True)
+    else:
+        print(case_steps(a.model, a.n, a.seed, a.steps), flush=True)
+
+
+if __name__ == "__main__":
+    main()
