@@ -402,15 +402,17 @@ def run_serving(g, torch, nreq: int, rhos):
 
 
 # ------------------------------------------------------------------ our arm
-def walk_traffic_entry():
-    """DRAM bytes per walk launch from the committed ncu summary, if the kernel is unchanged."""
+def walk_traffic_entry(interactions_per_launch: float):
+    """DRAM bytes of an average walk launch: the bytes per interaction of the committed ncu
+    capture (profiles/walk_traffic.json) scaled by the interactions one launch does here,
+    or None once walk.cu has changed since the capture."""
     path = os.path.join(ROOT, "profiles", "walk_traffic.json")
     src = os.path.join(ROOT, "paper_1610_07279_gb300", "csrc", "walk.cu")
     try:
         rec = json.load(open(path))
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
         if rec.get("walk_cu_sha256") == h:
-            return rec.get("dram_bytes_per_launch")
+            return rec["dram_bytes_per_interaction"] * interactions_per_launch
     except Exception:
         pass
     return None
@@ -490,9 +492,12 @@ def run_ours(args):
     sm_max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
     peak = nsm * 128 * 2 * sm_max_mhz * 1e6 / 1e12  # FP32 lanes x FMA x clock
     measured_ffma = g.gt_measure_fp32_peak(stream.cuda_stream) / 1e12
-    traffic = walk_traffic_entry()
+    traffic = walk_traffic_entry(inter / max(walk_launches, 1))
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "k_walk (tree walk + force loop)",
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_basis": "DRAM bytes per interaction of the committed ncu capture of k_walk "
+                                 "(profiles/walk_traffic.json) x interactions per launch here",
+                "kernel": "k_walk (tree walk + force loop)",
                 "flops_per_interaction": FLOPS_PER_INTERACTION,
                 "peak_basis": f"{nsm} SMs x 128 FP32 lanes x 2 flops x {sm_max_mhz:.0f} MHz (derived)",
                 "measured_ffma_tflops": measured_ffma,

@@ -68,10 +68,12 @@ typedef struct gt_params {
     float eps;          /* Plummer softening of Eq. (1)                            */
     float G;            /* gravitational constant of Eq. (1)                       */
     int32_t leaf_max;   /* a cell with more particles than this is split (<= 21 levels) */
-    int32_t group_max;  /* at most this many i-particles share one walk (Sec. 2.3), <= 32 */
+    int32_t group_max;  /* at most this many i-particles share one walk (Sec. 2.3):
+                           <= 32 / S for S > 1, else <= 64 (a group of more than 32
+                           gives each lane of the warp two i-particles)            */
     int32_t ij_share;   /* S: threads sharing one i-particle (Sec. 2.5): 1..32, a power of
-                           2 with group_max <= 32 / S; or 0 = per group, 32 / (members
-                           rounded up to a power of two)                           */
+                           2; or 0 = per group, 32 / (members rounded up to a power of
+                           two), one lane per two members above 32                 */
     int32_t levels;     /* L: number of block-step levels, 1..30 (Sec. 1)          */
     int32_t rebuild_every; /* rebuild the tree every n block steps (Sec. 2.6); 1 = always;
                               0 = automatic: the interval model of gt_rebuild_interval fed

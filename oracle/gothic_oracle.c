@@ -38,7 +38,7 @@ int or_num_threads(void) {
 
 /* Enclosing radii are evaluated in FP32 and widened by (1 + 2^-20): an FP32
  * distance carries a few roundings of at most 2^-24 each, so the widened radius
- * still holds every particle (P:183 asks only for a sphere that contains them). */
+ * still holds every particle (Sec. 2.1 asks only for a sphere that contains them). */
 #define RADIUS_MARGIN (1.0f + 0x1p-20f)
 
 static float norm3f(float dx, float dy, float dz) { return sqrtf((dx * dx + dy * dy) + dz * dz); }
@@ -217,7 +217,7 @@ int64_t or_build(int64_t n, const uint64_t *skey, int leaf_max, int64_t cap,
 /* of the cell.  The sums are FP64: a leaf adds its particles in sorted      */
 /* order, a cell adds its children's sums in child order.  m_J = (float)M;   */
 /* r_J is the FP32 quotient (float)S / (float)M (the paper keeps r_J in      */
-/* single precision, Sec. 2); a cell of one particle is that particle. */
+/* single precision, Sec. 2); a cell of one particle is that particle.       */
 /* b_J (FP32): a leaf's largest |r - r_J|, a cell's largest |r_c - r_J| + b_c */
 /* over its children, times (1 + 2^-20).  Children have larger node numbers  */
 /* than parents, so a reverse sweep is bottom-up.                            */

@@ -36,7 +36,8 @@ int check_params(const gt_params *p) {
     if (p->mac != GT_MAC_OPENING_ANGLE && p->mac != GT_MAC_ACCELERATION) return GT_EINVAL;
     if (p->leaf_max < 1) return GT_EINVAL;
     if (p->ij_share != 0 && (!pow2(p->ij_share) || p->ij_share > 32)) return GT_EINVAL;
-    if (p->group_max < 1 || p->group_max > 32 / (p->ij_share ? p->ij_share : 1)) return GT_EINVAL;
+    // up to 32 members with ij_share lanes each, or up to 64 with one lane per two members
+    if (p->group_max < 1 || p->group_max > (p->ij_share > 1 ? 32 / p->ij_share : 64)) return GT_EINVAL;
     if (p->group_mode != GT_GROUP_RUNS && p->group_mode != GT_GROUP_CELLS) return GT_EINVAL;
     if (p->levels < 1 || p->levels > 30) return GT_EINVAL;
     if (p->rebuild_every < 0 || p->node_factor < 1 || p->node_factor > 64) return GT_EINVAL;

@@ -101,25 +101,34 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
         a1 = min(a0 + gmax, na);
     }
     const uint32_t cnt = a1 - a0;
-    if (cnt == 0u || cnt > 32u) {  // a malformed group range: report it and skip
+    // a group of more than 32 gives every lane a second member (lane + 32), one lane each
+    const bool two = cnt > 32u;
+    if (cnt == 0u || cnt > 64u || (two && a.ij_share > 1)) {  // a malformed group: report it, skip
         if (lane == 0) gt_set_error(a.ctl, GT_EINVAL, GTK_WALK);
         return;
     }
-    const int S = a.ij_share ? a.ij_share : 32 >> (cnt <= 1 ? 0 : 32 - __clz(cnt - 1));
+    const int S = two ? 1 : (a.ij_share ? a.ij_share : 32 >> (cnt <= 1 ? 0 : 32 - __clz(cnt - 1)));
     const int logS = __ffs(S) - 1;
     const int slot = lane >> logS, sub = lane & (S - 1);
     const bool have = (uint32_t)slot < cnt;
+    const bool have2 = two && (uint32_t)(lane + 32) < cnt;
     const uint32_t kk = a0 + (have ? (uint32_t)slot : 0u);
+    const uint32_t kk2 = a0 + (have2 ? (uint32_t)(lane + 32) : 0u);
     uint32_t i = a.active ? a.active[kk] : kk;
-    if (i >= a.n) {  // an index outside the system: report it, walk particle 0 instead
+    uint32_t i2 = have2 ? (a.active ? a.active[kk2] : kk2) : i;
+    if (i >= a.n || i2 >= a.n) {  // an index outside the system: report it, walk particle 0 instead
         gt_set_error(a.ctl, GT_EINVAL, GTK_WALK);
-        i = 0;
+        i = i >= a.n ? 0u : i;
+        i2 = i2 >= a.n ? 0u : i2;
     }
     const float4 pi = a.posm[i];
+    const float4 pi2 = have2 ? a.posm[i2] : pi;
     float ao = have ? (a.aold ? a.aold[i] : 0.0f) : INFINITY;
+    if (have2) ao = fminf(ao, a.aold ? a.aold[i2] : 0.0f);
 
     // pseudo i-particle (lanes without a member repeat member 0: no effect on the box)
-    float mnx = pi.x, mny = pi.y, mnz = pi.z, mxx = pi.x, mxy = pi.y, mxz = pi.z;
+    float mnx = fminf(pi.x, pi2.x), mny = fminf(pi.y, pi2.y), mnz = fminf(pi.z, pi2.z);
+    float mxx = fmaxf(pi.x, pi2.x), mxy = fmaxf(pi.y, pi2.y), mxz = fmaxf(pi.z, pi2.z);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         mnx = fminf(mnx, __shfl_xor_sync(FULL, mnx, o));
@@ -135,17 +144,37 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
     const float cz = __fmul_rn(0.5f, __fadd_rn(mnz, mxz));
     const float ddx = __fsub_rn(pi.x, cx), ddy = __fsub_rn(pi.y, cy), ddz = __fsub_rn(pi.z, cz);
     float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ddx, ddx), __fmul_rn(ddy, ddy)), __fmul_rn(ddz, ddz));
+    {
+        const float ex = __fsub_rn(pi2.x, cx), ey = __fsub_rn(pi2.y, cy), ez = __fsub_rn(pi2.z, cz);
+        d2 = fmaxf(d2, __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez)));
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(FULL, d2, o));
     const float bI = __fmul_rn(__fsqrt_rn(d2), GT_RADIUS_MARGIN);
     const float dacc_amin = __fmul_rn(a.delta_acc, ao);
 
     float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f;
+    float bx = 0.f, by = 0.f, bz = 0.f, qh = 0.f;  // the second member's sums
     int list_n = 0;
     auto flush = [&]() {
         cp_async_wait_all();
         __syncwarp();
         int j = sub;
+        if (two) {  // every list entry read once for both members of the lane
+            for (; j + 1 < list_n; j += 2) {
+                const float4 s0 = list[j], s1 = list[j + 1];
+                interact(s0, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
+                interact(s0, pi2.x, pi2.y, pi2.z, a.eps2, bx, by, bz, qh);
+                interact(s1, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
+                interact(s1, pi2.x, pi2.y, pi2.z, a.eps2, bx, by, bz, qh);
+            }
+            if (j < list_n) {
+                const float4 s0 = list[j];
+                interact(s0, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
+                interact(s0, pi2.x, pi2.y, pi2.z, a.eps2, bx, by, bz, qh);
+            }
+            j = list_n;
+        }
         for (; j + 3 * S < list_n; j += 4 * S) {
             const float4 s0 = list[j], s1 = list[j + S], s2 = list[j + 2 * S], s3 = list[j + 3 * S];
             interact(s0, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
@@ -244,6 +273,7 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
         cp_async_wait_all();
         list_n = 0;
         if (sub == 0 && have) a.acc[kk] = make_float4(NAN, NAN, NAN, NAN);
+        if (have2) a.acc[kk2] = make_float4(NAN, NAN, NAN, NAN);
         __syncwarp();
         return;
     }
@@ -257,6 +287,10 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
     if (sub == 0 && have) {
         const float phi = fmaf(pi.w, a.inv_eps, ph);
         a.acc[kk] = make_float4(a.G * ax, a.G * ay, a.G * az, a.G * phi);
+    }
+    if (have2) {
+        const float phi = fmaf(pi2.w, a.inv_eps, qh);
+        a.acc[kk2] = make_float4(a.G * bx, a.G * by, a.G * bz, a.G * phi);
     }
 }
 

@@ -1,0 +1,35 @@
+"""Work partitioning across GPUs (one process per GPU).
+
+Independent systems (a batch, a serving stream) shard with no exchange at all: each
+rank takes whole systems, balanced by the device memory they need.  A single system
+does not shard in the paper's design (one GPU); the split available to it is over
+the groups of i-particles of a replicated tree (Sec. 2.3: groups are independent),
+which needs one gather of the ranks' accelerations per force evaluation.
+"""
+from __future__ import annotations
+
+
+def assign_systems(nbytes, world: int) -> list[list[int]]:
+    """Whole systems to ranks, largest first onto the least-loaded rank (greedy
+    longest-processing-time); returns, per rank, its system indices in ascending
+    order.  Deterministic: ties go to the lower rank and the lower index."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    order = sorted(range(len(nbytes)), key=lambda k: (-int(nbytes[k]), k))
+    load = [0] * world
+    out = [[] for _ in range(world)]
+    for k in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        out[r].append(k)
+        load[r] += int(nbytes[k])
+    return [sorted(v) for v in out]
+
+
+def group_slice(n_groups: int, rank: int, world: int) -> tuple[int, int]:
+    """Contiguous groups [g0, g1) of one rank: the first n_groups % world ranks take
+    one group more."""
+    if not 0 <= rank < world:
+        raise ValueError("rank out of range")
+    base, extra = divmod(int(n_groups), world)
+    g0 = rank * base + min(rank, extra)
+    return g0, g0 + base + (1 if rank < extra else 0)

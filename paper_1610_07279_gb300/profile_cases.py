@@ -23,10 +23,15 @@ from . import ics
 MODELS = {"m31": ics.andromeda_like, "nfw": ics.nfw, "plummer": ics.plummer}
 
 
+KNOBS = {}  # parameter overrides from the command line
+
+
 def _system(model: str, n: int, seed: int):
     pos, vel, mass, eps = MODELS[model](n, seed=seed)
     prm = g.gt_default_params()
     prm.eps = eps
+    for k, v in KNOBS.items():
+        setattr(prm, k, v)
     s = g.System(n, prm)
     s.set_state(pos, vel, mass)
     return s, prm
@@ -90,7 +95,13 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--steps", type=int, default=16)
+    ap.add_argument("--group-max", type=int, default=0)
+    ap.add_argument("--leaf-max", type=int, default=0)
     a = ap.parse_args(argv)
+    if a.group_max:
+        KNOBS["group_max"] = a.group_max
+    if a.leaf_max:
+        KNOBS["leaf_max"] = a.leaf_max
     _build.build()
     g.load()
     if a.case == "walk":

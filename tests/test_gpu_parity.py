@@ -190,14 +190,27 @@ def _walk_case(env, kind, n, seed, mac, S, gmax, active_frac=None, **kw):
 
 @pytest.mark.parametrize("mac", [0, 1])
 @pytest.mark.parametrize("S,gmax,mode", [(0, 32, 1), (1, 32, 1), (0, 20, 1), (2, 16, 1), (4, 8, 1), (32, 1, 1),
-                                         (1, 32, 0), (0, 32, 0), (0, 13, 0)])
+                                         (1, 32, 0), (0, 32, 0), (0, 13, 0), (0, 64, 1), (1, 48, 1),
+                                         (0, 64, 0), (0, 40, 0)])
 def test_walk_plummer_config(env, mac, S, gmax, mode):
     _walk_case(env, "plummer", 1 << 13, 1, mac, S, gmax, group_mode=mode)
 
 
 @pytest.mark.parametrize("kind,n", [("nfw", 40000), ("m31", 1 << 15), ("clustered", 9000)])
-def test_walk_other_models(env, kind, n):
-    _walk_case(env, kind, n, 3, 1, 0, 32)
+@pytest.mark.parametrize("gmax", [32, 64])
+def test_walk_other_models(env, kind, n, gmax):
+    _walk_case(env, kind, n, 3, 1, 0, gmax)
+
+
+def test_group_max_limits(env):
+    torch, g, O = env
+    for S, gmax, ok in [(0, 64, True), (1, 64, True), (0, 65, False), (2, 16, True), (2, 17, False)]:
+        prm = _params(g, 1.0 / 64, ij_share=S, group_max=gmax)
+        if ok:
+            g.gt_workspace_bytes(1024, prm)
+        else:
+            with pytest.raises(g.GothicError):
+                g.gt_workspace_bytes(1024, prm)
 
 
 @pytest.mark.parametrize("mode", [0, 1])

@@ -98,7 +98,7 @@ def test_active_counts_closed_form(oracle_lib):
 
 
 def test_shared_step_reduces_to_leapfrog(oracle_lib):
-    """L = 1 (one shared, fixed step): the block-step scheme is the KDK leap-frog (P:388-396);
+    """L = 1 (one shared, fixed step): the block-step scheme is the KDK leap-frog (Sec. 2.7);
     the reference here uses separate multiplies and adds, the scheme fused ones, so the two
     agree to rounding."""
     O = oracle_lib
