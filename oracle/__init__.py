@@ -74,7 +74,7 @@ def _declare(L):
     L.or_pseudo_j.argtypes = [I64, P, P, P, P, P, P, P]
     L.or_pseudo_j.restype = I32
     L.or_active_prefix.argtypes = [I64, I64, P, P]
-    L.or_group_starts.argtypes = [I64, P, P, P, P, P, I32, P]
+    L.or_group_starts.argtypes = [I64, P, P, P, P, P, I32, P, F, P]
     L.or_group_starts.restype = I64
     L.or_groups.argtypes = [I64, P, P, P, P, P, P]
     L.or_walk.argtypes = [I64, P, P, P, P, P, P, P, I64, P, P, P, P, I32, F, F, F, F,
@@ -122,6 +122,7 @@ class Params:
     eta: float = 0.025
     dt_max: float = 0.0        # 0: derived at start as a power of two
     group_mode: int = 1        # 1: groups bounded by tree cells; 0: runs of group_max actives
+    r_crit: float = 0.0        # critical separation of a group cell's radius (Sec. 2.4); <= 0: none
 
 
 def f32(x):
@@ -202,18 +203,21 @@ def active_prefix(n: int, active) -> np.ndarray:
     return P
 
 
-def group_starts(tree: dict, n: int, active, gmax: int, mode: int = 1) -> np.ndarray:
+def group_starts(tree: dict, n: int, active, gmax: int, mode: int = 1, bj=None, r_crit: float = 0.0) -> np.ndarray:
     """First active position of every group, plus n_active at the end.
 
-    mode 1: groups bounded by tree cells (Sec. 2.4); mode 0: consecutive runs of gmax."""
+    mode 1: groups bounded by tree cells (Sec. 2.4): the cells holding at most gmax
+    actives that are leaves or have b_J <= r_crit (r_crit <= 0: no radius limit);
+    mode 0: consecutive runs of gmax."""
     active = _c(active, np.uint32)
     na = active.shape[0]
     if mode == 0 or tree["n_nodes"] == 0:
         return np.append(np.arange(0, na, gmax, dtype=np.uint32), np.uint32(na))
     P = active_prefix(n, active)
     starts = np.zeros(na + 1, np.uint32)
+    bjv = None if bj is None else _c(bj, np.float32)
     ng = lib().or_group_starts(tree["n_nodes"], _p(tree["first"]), _p(tree["count"]), _p(tree["child"]),
-                               _p(tree["parent"]), _p(P), int(gmax), _p(starts))
+                               _p(tree["parent"]), _p(P), int(gmax), _p(bjv), f32(r_crit), _p(starts))
     return starts[:ng + 1].copy()
 
 
@@ -341,7 +345,7 @@ def tree_force(p4: np.ndarray, prm: Params, aold=None, active=None, mac=None, th
     if active is None:
         active = np.arange(n, dtype=np.uint32)
     saold = None if aold is None else _c(aold, np.float32)[order]
-    starts = group_starts(tree, n, active, prm.group_max, prm.group_mode)
+    starts = group_starts(tree, n, active, prm.group_max, prm.group_mode, bj, prm.r_crit)
     gI, gamin = groups(starts, active, sp4, saold)
     m = prm.mac if mac is None else mac
     th = prm.theta if theta is None else theta
@@ -439,7 +443,7 @@ class BlockStepSim:
         tree = build_tree(skey, prm.leaf_max)
         jpos, bj = pseudo_j(tree, sp4)
         active = np.nonzero(self.t0 + self.ticks(self.level) == T)[0].astype(np.uint32)
-        starts = group_starts(tree, self.n, active, prm.group_max, prm.group_mode)
+        starts = group_starts(tree, self.n, active, prm.group_max, prm.group_mode, bj, prm.r_crit)
         gI, gamin = groups(starts, active, sp4, self.aold)
         acc, inter, _ = walk(tree, jpos, bj, sp4, active, starts, gI, gamin, prm.mac,
                              prm.theta, prm.delta_acc, prm.eps, prm.G)

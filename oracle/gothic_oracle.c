@@ -292,30 +292,41 @@ void or_active_prefix(int64_t n, int64_t n_active, const uint32_t *active, uint3
 
 /* ------------------------------------------------------------------------- */
 /* A6b. Groups of i-particles (Sec. 2.3; Sec. 2.4: i-particles far apart are  */
-/* not unified into one group).  A group never straddles two tree cells: the */
-/* "group cells" are the cells whose active count A is at least 1 and at     */
-/* most gmax (or leaves, whatever A), and whose parent holds more than gmax  */
-/* actives (or that are the root).  Each group cell contributes its actives  */
-/* in key order, cut into runs of gmax.  Returns the number of groups; the   */
-/* first active position of every group, ascending, goes to starts (room    */
-/* for n_active + 1 entries); starts[ng] = P[n] is appended.                 */
+/* not unified into one group).  A group never straddles two tree cells.  A  */
+/* cell "qualifies" when it holds at most gmax actives and is a leaf or has  */
+/* an enclosing radius b_J <= r_crit (the critical separation of Sec. 2.4;   */
+/* r_crit <= 0 means no such limit).  Both counts and radii only shrink from  */
+/* a cell to its children, so along every root-to-leaf path the qualifying   */
+/* cells are a tail: the group cells are the qualifying cells whose parent   */
+/* does not qualify (or the root), plus the leaves on paths where nothing    */
+/* qualifies.  Each group cell with at least one active contributes its      */
+/* actives in key order, cut into runs of gmax.  Returns the number of       */
+/* groups; the first active position of every group, ascending, goes to      */
+/* starts (room for n_active + 1 entries); starts[ng] = P[n] is appended.    */
 /* ------------------------------------------------------------------------- */
 static int cmp_u32(const void *a, const void *b) {
     const uint32_t x = *(const uint32_t *)a, y = *(const uint32_t *)b;
     return (x > y) - (x < y);
 }
 
+static int qualifies(int64_t c, const uint32_t *first, const uint32_t *count, const int32_t *child,
+                     const uint32_t *P, int gmax, const float *bj, float r_crit) {
+    const uint32_t A = P[first[c] + count[c]] - P[first[c]];
+    if (A > (uint32_t)gmax) return 0;
+    if (child[c] < 0 || r_crit <= 0.0f || !bj) return 1;
+    return bj[c] <= r_crit;
+}
+
 int64_t or_group_starts(int64_t nn, const uint32_t *first, const uint32_t *count, const int32_t *child,
-                        const int32_t *parent, const uint32_t *P, int gmax, uint32_t *starts) {
+                        const int32_t *parent, const uint32_t *P, int gmax, const float *bj, float r_crit,
+                        uint32_t *starts) {
     int64_t ng = 0;
     for (int64_t c = 0; c < nn; c++) {
         const uint32_t a0 = P[first[c]], A = P[first[c] + count[c]] - a0;
         if (A == 0) continue;
-        if (parent[c] >= 0) {
-            const int32_t p = parent[c];
-            if (P[first[p] + count[p]] - P[first[p]] <= (uint32_t)gmax) continue;  /* inside a group cell */
-        }
-        if (A > (uint32_t)gmax && child[c] >= 0) continue;                          /* split further */
+        if (parent[c] >= 0 && qualifies(parent[c], first, count, child, P, gmax, bj, r_crit))
+            continue;                                                                  /* inside a group cell */
+        if (!qualifies(c, first, count, child, P, gmax, bj, r_crit) && child[c] >= 0) continue;  /* split */
         for (uint32_t s = a0; s < a0 + A; s += (uint32_t)gmax) starts[ng++] = s;
     }
     qsort(starts, (size_t)ng, sizeof(uint32_t), cmp_u32);

@@ -61,9 +61,10 @@ def _sorted_tree(O, n, seed, kind="nfw", leaf=16):
     return p4[order], O.build_tree(skey, leaf)
 
 
-def _brute_group_starts(tree, n, active, gmax):
+def _brute_group_starts(tree, n, active, gmax, bj=None, r_crit=0.0):
     """Recursive descent from the root: a cell is a group cell when it holds at most
-    gmax actives or is a leaf; its actives are cut into runs of gmax."""
+    gmax actives and is a leaf or has b_J <= r_crit (no radius test when r_crit <= 0),
+    or when it is a leaf; its actives are cut into runs of gmax."""
     pos = {int(a): k for k, a in enumerate(active)}
     act = np.zeros(n + 1, bool)
     act[active] = True
@@ -74,7 +75,8 @@ def _brute_group_starts(tree, n, active, gmax):
         mine = [pos[i] for i in range(f, f + k) if act[i]]
         if not mine:
             return
-        if len(mine) <= gmax or tree["child"][c] < 0:
+        small = len(mine) <= gmax and (r_crit <= 0 or bj[c] <= np.float32(r_crit))
+        if small or tree["child"][c] < 0:
             out.extend(mine[::gmax])
             return
         for ch in range(tree["child"][c], tree["child"][c] + tree["nchild"][c]):
@@ -96,6 +98,30 @@ def test_group_starts_match_recursive_definition(oracle_lib, frac, gmax):
     assert np.array_equal(starts, _brute_group_starts(tree, n, active, gmax))
     assert starts[0] == 0 and starts[-1] == active.size and np.all(np.diff(starts.astype(int)) >= 1)
     assert np.all(np.diff(starts.astype(int)) <= gmax)
+
+
+@pytest.mark.parametrize("frac,gmax", [(1.0, 32), (0.2, 64), (0.02, 16)])
+def test_group_starts_with_rcrit_match_recursive_definition(oracle_lib, frac, gmax):
+    """Sec. 2.4: a cell wider than r_crit is not one group even when it holds few actives."""
+    O = oracle_lib
+    n = 4000
+    sp4, tree = _sorted_tree(O, n, 12)
+    jpos, bj = O.pseudo_j(tree, sp4)
+    rng = np.random.default_rng(3)
+    active = np.sort(rng.choice(n, max(1, int(frac * n)), replace=False)).astype(np.uint32)
+    base = O.group_starts(tree, n, active, gmax)
+    inner = bj[tree["child"][:tree["n_nodes"]] >= 0]
+    prev = len(base)
+    for q in (1.0, 0.9, 0.6, 0.3, 0.0):
+        r_crit = float(np.float32(np.quantile(inner, q))) if q > 0 else 1e-30
+        starts = O.group_starts(tree, n, active, gmax, 1, bj, r_crit)
+        assert np.array_equal(starts, _brute_group_starts(tree, n, active, gmax, bj, r_crit)), q
+        assert len(starts) >= prev  # a tighter limit only splits groups
+        prev = len(starts)
+        assert starts[0] == 0 and starts[-1] == active.size and np.all(np.diff(starts.astype(int)) <= gmax)
+    # no limit, and a limit above every radius, leave the groups of the cell rule unchanged
+    assert np.array_equal(O.group_starts(tree, n, active, gmax, 1, bj, 0.0), base)
+    assert np.array_equal(O.group_starts(tree, n, active, gmax, 1, bj, float(bj.max()) * 2), base)
 
 
 def test_groups_enclose_members(oracle_lib):
