@@ -123,6 +123,7 @@ class Params:
     dt_max: float = 0.0        # 0: derived at start as a power of two
     group_mode: int = 1        # 1: groups bounded by tree cells; 0: runs of group_max actives
     r_crit: float = 0.0        # critical separation of a group cell's radius (Sec. 2.4); <= 0: none
+    rebuild_every: int = 1     # block steps per tree build (Sec. 2.6); the topology is kept between
 
 
 def f32(x):
@@ -372,8 +373,10 @@ def bootstrap_aold(p4: np.ndarray, prm: Params) -> np.ndarray:
 class BlockStepSim:
     """Block time-step integration (Sec. 1; Sec. 2.7) driving the oracle tree force.
 
-    State is kept in sorted (key) order, re-sorted at every step from the predicted
-    positions, exactly as the tree is rebuilt every step.
+    State is kept in sorted (key) order.  Every rebuild_every block steps (Sec. 2.6) the
+    predicted positions are keyed and sorted and the tree is built anew; at the other
+    steps the previous order and topology are kept and only the pseudo j-particles are
+    formed again from the predicted positions.
     """
 
     def __init__(self, pos, vel, mass, prm: Params):
@@ -436,11 +439,16 @@ class BlockStepSim:
         T = self.next_time()
         dt_min = float(np.ldexp(self.dt_max, -(self.L - 1)))
         p4 = predict(self.r0, self.vh, self.t0, self.mass, T, dt_min)
-        key, _ = keys(p4)
-        order, skey = sort(key)
-        self._permute(order)
-        sp4 = np.ascontiguousarray(p4[order])
-        tree = build_tree(skey, prm.leaf_max)
+        if self.steps % max(1, int(prm.rebuild_every)) == 0 or getattr(self, "tree", None) is None:
+            key, _ = keys(p4)
+            order, skey = sort(key)
+            self._permute(order)
+            sp4 = np.ascontiguousarray(p4[order])
+            tree = build_tree(skey, prm.leaf_max)
+            self.tree, self.skey = tree, skey
+        else:
+            order = np.arange(self.n, dtype=np.uint32)
+            sp4, tree, skey = p4, self.tree, self.skey
         jpos, bj = pseudo_j(tree, sp4)
         active = np.nonzero(self.t0 + self.ticks(self.level) == T)[0].astype(np.uint32)
         starts = group_starts(tree, self.n, active, prm.group_max, prm.group_mode, bj, prm.r_crit)

@@ -176,3 +176,33 @@ def test_block_step_runs_and_levels_spread(oracle_lib):
     assert all(b > a for a, b in zip(Ts, Ts[1:]))
     assert np.all(sim.t0 <= sim.T)
     assert np.all((sim.t0 % np.left_shift(1, (prm.levels - 1 - sim.level.astype(np.int64)))) == 0)
+
+
+def test_tree_reused_between_rebuilds(oracle_lib):
+    """Sec. 2.6: between builds the order and topology are kept; the pseudo j-particles
+    follow the predicted particles, so every particle stays inside its ancestors'
+    spheres and the forces keep the tree accuracy against direct summation."""
+    O = oracle_lib
+    n = 3000
+    pos, vel, mass, eps = ics.plummer(n, seed=41)
+    prm = O.Params(eps=O.f32(eps), levels=4, rebuild_every=4)
+    sim = O.BlockStepSim(pos, vel, mass, prm)
+    sim.start()
+    prev = None
+    for k in range(9):
+        r = sim.step()
+        if k % 4 != 0:
+            assert r["tree"] is prev["tree"] and np.array_equal(r["order"], np.arange(n))
+            assert np.array_equal(r["skey"], prev["skey"])
+        prev = r
+        p4 = O.predict(sim.r0, sim.vh, sim.t0, sim.mass, sim.T, float(np.ldexp(sim.dt_max, -(sim.L - 1))))
+        tree = r["tree"]
+        jpos, bj = O.pseudo_j(tree, p4)
+        for c in range(0, tree["n_nodes"], 7):  # enclosure by the refreshed spheres
+            f, cnt = int(tree["first"][c]), int(tree["count"][c])
+            d = np.linalg.norm(p4[f:f + cnt, :3].astype(np.float64) - jpos[c, :3].astype(np.float64), axis=1)
+            assert d.max() <= bj[c] * (1 + 1e-6) + 1e-12
+        act = r["active"]
+        ref = O.direct(p4, prm.eps, prm.G, idx=act.astype(np.int64))
+        rel = np.linalg.norm(r["acc"][:, :3] - ref[:, :3], axis=1) / np.linalg.norm(ref[:, :3], axis=1)
+        assert np.median(rel) < 5e-3, (k, np.median(rel))
