@@ -69,8 +69,9 @@ def config_dict(args, eps):
                         f"N={args.n}, one full block-step cycle per step, tree rebuilt at the automatic "
                         f"interval (Sec. 2.6)",
             "n": args.n, "levels": args.levels, "mac": "acceleration", "delta_acc": 2.0 ** -7,
-            "eps": eps, "leaf_max": 16, "group_max": 32, "ij_share": "per group",
-            "groups": "tree cells with at most 32 actives",
+            "eps": eps, "leaf_max": 16, "group_max": 64, "ij_share": "per group",
+            "groups": "tree cells with at most 16, 32 or 64 actives, the size tuned per class of "
+                      "block step (coarsest active level)",
             "l2": "inputs larger than L2 (particle state ~1.7 GB, nodes ~0.3 GB)"}
 
 
@@ -324,7 +325,9 @@ class RequestSource:
 def serve_params(g, eps):
     p = g.gt_default_params()
     p.eps = eps
-    p.rebuild_every = 4
+    p.rebuild_every = 4        # a server cannot sync per step for the automatic interval
+    p.group_max = 32           # nor tune the group size per step
+    p.group_mode = g.GT_GROUP_CELLS
     p.walk_queue = 8192
     return p
 

@@ -88,13 +88,27 @@ typedef struct gt_params {
     double dt_max;      /* longest step, a power of two; <= 0: derived at gt_start */
     int32_t group_mode; /* GT_GROUP_CELLS (default): a group is the actives of one tree
                            cell holding at most group_max of them, so it never straddles
-                           distant regions (Sec. 2.4); GT_GROUP_RUNS: consecutive runs of
-                           group_max actives in the given order                    */
-    int32_t reserved1;
+                           distant regions (Sec. 2.4); GT_GROUP_CELLS_TUNED: the same with
+                           the size tuned per class of step (below); GT_GROUP_RUNS:
+                           consecutive runs of group_max actives in the given order */
+    float r_crit;       /* critical separation of a group (Sec. 2.4), cell grouping only:
+                           a cell whose enclosing radius b_J exceeds it is split into its
+                           children even when it holds few actives (leaves are kept).
+                           0 = no limit (default); > 0 = this value; < 0 = tuned on line
+                           by Brent's method from |r_crit| on, one search per class of
+                           block step (the coarsest active level), minimising the walk
+                           time per active particle (gt_block_step with the automatic
+                           rebuild interval only; elsewhere |r_crit| is used)       */
 } gt_params;
 
 #define GT_GROUP_RUNS 0
 #define GT_GROUP_CELLS 1
+/* Cell groups whose size is tuned on line (gt_block_step with the automatic rebuild
+ * interval): for every class of block step (the coarsest active level) the walk time
+ * per active particle is measured once with group_max, / 2 and / 4, the fastest is
+ * kept, and the three are measured again every 64 steps of the class.  Elsewhere it
+ * acts as GT_GROUP_CELLS. */
+#define GT_GROUP_CELLS_TUNED 2
 
 /* Counters and state read back by gt_get_stats (synchronises the stream). */
 typedef struct gt_stats {
@@ -120,8 +134,9 @@ GT_API const char *gt_strerror(int status);
 
 /* The paper's fiducial parameters: acceleration MAC with Delta_acc = 2^-7
  * (Sec. 3.3), theta = 0.5 for the bootstrap pass, G = 1, eps = 1/64,
- * leaf_max = 16, group_max = 32, S = 0 (per group), L = 8, eta = 0.025,
- * queue 16384, node_factor 2, cell grouping, automatic rebuild interval. */
+ * leaf_max = 16, group_max = 64, S = 0 (per group), L = 8, eta = 0.025,
+ * queue 16384, node_factor 2, cell grouping with the size tuned per class of step
+ * (GT_GROUP_CELLS_TUNED), r_crit 0, automatic rebuild interval. */
 GT_API int gt_default_params(gt_params *prm);
 
 /* Bytes of device workspace a system of n particles needs (n >= 0). */
@@ -242,6 +257,11 @@ GT_API int gt_kernel_launches(int64_t *count);
  * its coefficients in coef[3] (may be NULL: t1, dt | t1, r | t1, b, a), and the
  * interval that minimises the mean time per step in *n_opt (1e6 when the model
  * has no minimum, i.e. no rebuild is due). */
+/* Brent's minimisation of f over [lo, hi] to a relative tolerance tol, at most max_evals
+ * evaluations (host only): the search the library runs on line for r_crit (Sec. 2.4).
+ * Writes the abscissa and value of the minimum found and the evaluations used. */
+GT_API int gt_brent_minimize(double (*f)(double x, void *ctx), void *ctx, double lo, double hi, double tol,
+                             int max_evals, double *x_min, double *f_min, int *evals);
 GT_API int gt_rebuild_interval(const double *t_walk, int n, double t_make, int *model, double *n_opt,
                                double *coef);
 

@@ -462,4 +462,4 @@ class BlockStepSim:
         self.steps += 1
         self.interactions += int(inter.sum())
         return {"T": T, "active": active, "acc": acc, "inter": inter, "skey": skey,
-                "order": order, "tree": tree}
+                "order": order, "tree": tree, "sp4": sp4, "jpos": jpos, "bj": bj}

@@ -38,7 +38,8 @@ int check_params(const gt_params *p) {
     if (p->ij_share != 0 && (!pow2(p->ij_share) || p->ij_share > 32)) return GT_EINVAL;
     // up to 32 members with ij_share lanes each, or up to 64 with one lane per two members
     if (p->group_max < 1 || p->group_max > (p->ij_share > 1 ? 32 / p->ij_share : 64)) return GT_EINVAL;
-    if (p->group_mode != GT_GROUP_RUNS && p->group_mode != GT_GROUP_CELLS) return GT_EINVAL;
+    if (p->group_mode != GT_GROUP_RUNS && p->group_mode != GT_GROUP_CELLS && p->group_mode != GT_GROUP_CELLS_TUNED)
+        return GT_EINVAL;
     if (p->levels < 1 || p->levels > 30) return GT_EINVAL;
     if (p->rebuild_every < 0 || p->node_factor < 1 || p->node_factor > 64) return GT_EINVAL;
     if (!pow2(p->walk_queue) || p->walk_queue < 64) return GT_EINVAL;
@@ -48,8 +49,15 @@ int check_params(const gt_params *p) {
         int e;
         if (frexp(p->dt_max, &e) != 0.5) return GT_EINVAL;  // must be a power of two
     }
+    if (!std::isfinite(p->r_crit)) return GT_EINVAL;
     return GT_OK;
 }
+
+bool cell_groups(const gt_params &p) { return p.group_mode != GT_GROUP_RUNS; }
+
+// r_crit of the groupings when it is not tuned on line: the given value, or the start
+// of the search for a negative one
+float fixed_rcrit(const gt_params &p) { return p.r_crit > 0.0f ? p.r_crit : (p.r_crit < 0.0f ? -p.r_crit : 0.0f); }
 
 int device_sms(int *dev, int *nsm) {
     if (cudaGetDevice(dev) != cudaSuccess) return GT_ECUDA;
@@ -184,6 +192,78 @@ void tune_after_step(gt_system *s, bool rebuilt, unsigned n_active) {
     }
 }
 
+// class of the block step at T: the coarsest level active then (levels k with
+// T mod 2^(L-1-k) == 0 are active)
+int step_class(const gt_system *s, unsigned long long T) {
+    const int L = s->prm.levels;
+    const int tz = T == 0ull ? 63 : __builtin_ctzll(T);
+    return L - 1 - (tz < L - 1 ? tz : L - 1);
+}
+
+int gsize_candidate(const gt_system *s, int c) {
+    const int g = s->prm.group_max >> (GroupTuner::NCAND - 1 - c);  // group_max / 4, / 2, / 1
+    return g >= 1 ? g : 1;
+}
+
+void gsize_after_step(gt_system *s, unsigned n_active) {
+    GroupTuner &t = s->gtune;
+    if (t.pending_class >= 0 && n_active > 0 && s->prof.last_ms[PH_WALK] > 0.0) {
+        t.sum[t.pending_class][t.pending_cand] += s->prof.last_ms[PH_WALK] / (double)n_active;
+        t.cnt[t.pending_class][t.pending_cand] += 1;
+    }
+    t.pending_class = -1;
+}
+
+void gsize_before_step(gt_system *s, unsigned long long T) {
+    GroupTuner &t = s->gtune;
+    const int k0 = step_class(s, T);
+    if (k0 < 0 || k0 >= GroupTuner::NCLASS) return;
+    if (++t.seen[k0] % 64 == 0)
+        for (int c = 0; c < GroupTuner::NCAND; c++) t.sum[k0][c] = 0.0, t.cnt[k0][c] = 0;
+    int pick = -1;
+    for (int c = GroupTuner::NCAND - 1; c >= 0 && pick < 0; c--)  // the largest size first
+        if (t.cnt[k0][c] < 1) pick = c;
+    if (pick < 0) {
+        pick = GroupTuner::NCAND - 1;
+        for (int c = 0; c < GroupTuner::NCAND; c++)
+            if (t.sum[k0][c] / t.cnt[k0][c] < t.sum[k0][pick] / t.cnt[k0][pick]) pick = c;
+    }
+    s->gmax_now = gsize_candidate(s, pick);
+    t.pending_class = k0;
+    t.pending_cand = pick;
+}
+
+// Sec. 2.4 on line: the walk time per active particle of the step just finished goes
+// to the search of its class; the step at block time T gets the next r_crit of its
+// class (the coarsest level active at T).
+void rcrit_after_step(gt_system *s, unsigned n_active) {
+    RcritTuner &t = s->rtune;
+    if (t.pending >= 0 && n_active > 0 && s->prof.last_ms[PH_WALK] > 0.0) {
+        BrentSearch &b = t.search[t.pending];
+        if (gt_brent_done(&b)) t.held[t.pending]++;
+        else gt_brent_report(&b, s->prof.last_ms[PH_WALK] / (double)n_active);
+    }
+    t.pending = -1;
+}
+
+void rcrit_before_step(gt_system *s, unsigned long long T) {
+    const int k0 = step_class(s, T);
+    RcritTuner &t = s->rtune;
+    if (k0 < 0 || k0 >= RcritTuner::NCLASS) return;
+    BrentSearch &b = t.search[k0];
+    const double x0 = std::log((double)fixed_rcrit(s->prm));
+    if (!t.started[k0]) {
+        gt_brent_start(&b, x0 - std::log(16.0), x0 + std::log(16.0), 0.0, 0.05);
+        t.started[k0] = true;
+    } else if (gt_brent_done(&b) && t.held[k0] >= 8) {  // perturb: search again around the best
+        const double xb = b.x;
+        gt_brent_start(&b, xb - std::log(2.0), xb + std::log(2.0), 0.0, 0.05);
+        t.held[k0] = 0;
+    }
+    s->rcrit_now = (float)std::exp(gt_brent_next(&b));
+    t.pending = k0;
+}
+
 void ph_sync_collect(gt_system *s, cudaStream_t st) {
     if (!s->prof.on) return;
     cudaStreamSynchronize(st);
@@ -218,7 +298,7 @@ void build_tree(gt_system *s, cudaStream_t st, const float4 *posm_src) {
     gt_launch_cell_lists(s->nd, s->cap, s->ctl, s->nsm, st);
     ph_end(s, PH_BUILD, st);
     ph_begin(s, PH_PSEUDO, st);
-    gt_launch_pseudo(s->nd, s->cap, s->posm, s->ctl, s->nsm, st);
+    gt_launch_pseudo(s->nd, s->cap, s->posm, s->ctl, s->nsm, true, st);
     ph_end(s, PH_PSEUDO, st);
     s->have_tree = true;
     s->rebuilds++;
@@ -232,8 +312,8 @@ double c2_of(const gt_params &p) {
 // A6 groups + A7 walk over the active list already in s->active / ctl->n_active
 // (cell grouping needs the prefix s->prefix of that list), or over a caller's list.
 void walk(gt_system *s, const uint32_t *active, const float *aold, float4 *acc, int mac, cudaStream_t st) {
-    if (s->prm.group_mode == GT_GROUP_CELLS)
-        gt_launch_groups(s->nd, s->cap, s->prefix, s->prm.group_max, s->n, s->marks, s->ctl, s->gstart,
+    if (cell_groups(s->prm))
+        gt_launch_groups(s->nd, s->cap, s->prefix, s->gmax_now, s->rcrit_now, s->n, s->marks, s->ctl, s->gstart,
                          s->status, s->nsm, st);
     const WalkArgs a = gt_sys_walk_args(s, active, aold, acc, mac);
     ph_begin(s, PH_WALK, st);
@@ -270,7 +350,7 @@ int gt_sys_init(gt_system *s, int64_t n, const gt_params *p, void *ws, size_t ws
     if (ws_bytes < need) return GT_ENOMEM;
     carve(s, (char *)ws, n, p, s->nsm, wb, own_queue);
     s->n = n;
-    s->prm = *p;
+    gt_sys_apply_params(s, *p);
     // zero the control block and the look-back status words (on st, then wait for it;
     // without a stream, on the default stream and wait for the device)
     const size_t st_bytes = (size_t)((s->cap + 511) / 512 + (n + 4095) / 4096 + 64) * 8;
@@ -282,19 +362,27 @@ int gt_sys_init(gt_system *s, int64_t n, const gt_params *p, void *ws, size_t ws
     return GT_OK;
 }
 
+void gt_sys_apply_params(gt_system *s, const gt_params &p) {
+    s->prm = p;
+    s->rcrit_now = fixed_rcrit(p);
+    s->rtune = RcritTuner();
+    s->gmax_now = p.group_max;
+    s->gtune = GroupTuner();
+}
+
 void gt_sys_build_tree(gt_system *s, cudaStream_t st, const float4 *posm_src) { build_tree(s, st, posm_src); }
 
 void gt_sys_groups_all(gt_system *s, cudaStream_t st) {
     gt_launch_prepare(s->ctl, 0, st);
     gt_launch_active(s->st[0], s->n, s->prm.levels, 1, s->ctl, s->active, s->prefix, s->status, s->nsm, st);
-    if (s->prm.group_mode == GT_GROUP_CELLS)
-        gt_launch_groups(s->nd, s->cap, s->prefix, s->prm.group_max, s->n, s->marks, s->ctl, s->gstart,
+    if (cell_groups(s->prm))
+        gt_launch_groups(s->nd, s->cap, s->prefix, s->gmax_now, s->rcrit_now, s->n, s->marks, s->ctl, s->gstart,
                          s->status, s->nsm, st);
 }
 
 WalkArgs gt_sys_walk_args(const gt_system *s, const uint32_t *active, const float *aold, float4 *acc, int mac) {
     WalkArgs a;
-    a.gstart = s->prm.group_mode == GT_GROUP_CELLS ? s->gstart : nullptr;
+    a.gstart = cell_groups(s->prm) ? s->gstart : nullptr;
     a.jpos = s->nd.jpos;
     a.walk = s->nd.walk;
     a.posm = s->posm;
@@ -304,7 +392,7 @@ WalkArgs gt_sys_walk_args(const gt_system *s, const uint32_t *active, const floa
     a.queue = s->queue;
     a.ctl = s->ctl;
     a.n = (uint32_t)s->n;
-    a.gmax = s->prm.group_max;
+    a.gmax = s->gmax_now;
     a.qcap = s->prm.walk_queue;
     a.mac = mac;
     a.ij_share = s->prm.ij_share;
@@ -328,7 +416,7 @@ void gt_sys_step_pre(gt_system *s, cudaStream_t st, bool rebuild) {
         build_tree(s, st, s->posm_tmp);
     } else {
         ph_begin(s, PH_PSEUDO, st);
-        gt_launch_pseudo(s->nd, s->cap, s->posm, s->ctl, s->nsm, st);
+        gt_launch_pseudo(s->nd, s->cap, s->posm, s->ctl, s->nsm, false, st);  // masses as at the build
         ph_end(s, PH_PSEUDO, st);
     }
     ph_begin(s, PH_ACTIVE, st);
@@ -337,8 +425,8 @@ void gt_sys_step_pre(gt_system *s, cudaStream_t st, bool rebuild) {
 }
 
 void gt_sys_step_groups(gt_system *s, cudaStream_t st) {
-    if (s->prm.group_mode == GT_GROUP_CELLS)
-        gt_launch_groups(s->nd, s->cap, s->prefix, s->prm.group_max, s->n, s->marks, s->ctl, s->gstart,
+    if (cell_groups(s->prm))
+        gt_launch_groups(s->nd, s->cap, s->prefix, s->gmax_now, s->rcrit_now, s->n, s->marks, s->ctl, s->gstart,
                          s->status, s->nsm, st);
 }
 
@@ -390,9 +478,9 @@ int gt_default_params(gt_params *p) {
     p->eps = 0.015625f;         // 1/64
     p->G = 1.0f;
     p->leaf_max = 16;
-    p->group_max = 32;
+    p->group_max = 64;
     p->ij_share = 0;
-    p->group_mode = GT_GROUP_CELLS;
+    p->group_mode = GT_GROUP_CELLS_TUNED;
     p->levels = 8;
     p->rebuild_every = 0;
     p->walk_queue = 16384;
@@ -446,7 +534,7 @@ int gt_set_params(gt_system *s, const gt_params *prm) {
     if (prm->walk_queue > s->prm.walk_queue || prm->node_factor != s->prm.node_factor) return GT_EINVAL;
     if (s->started && (prm->levels != s->prm.levels || prm->dt_max != s->prm.dt_max)) return GT_ESTATE;
     const int qcap_region = s->prm.walk_queue;
-    s->prm = *prm;
+    gt_sys_apply_params(s, *prm);
     s->prm.walk_queue = prm->walk_queue;
     (void)qcap_region;
     return GT_OK;
@@ -487,7 +575,7 @@ int gt_accel_active(gt_system *s, const uint32_t *d_active, int64_t n_active, co
     const float *aold = d_aold ? d_aold : s->st[0].aold;
     if (!d_active) {
         walk_all(s, aold, (float4 *)d_acc, s->prm.mac, st);
-    } else if (s->prm.group_mode == GT_GROUP_CELLS) {
+    } else if (cell_groups(s->prm)) {
         gt_launch_prepare(s->ctl, 0, st);
         gt_launch_active_from_list(d_active, n_active, s->n, s->flags, s->ctl, s->active, s->prefix, s->status,
                                    s->nsm, st);
@@ -529,15 +617,22 @@ int gt_block_step(gt_system *s, gt_stream stream) {
     bool rebuild;
     if (s->prm.rebuild_every == 0) {  // automatic interval (Sec. 2.6)
         if (ensure_events(s)) return GT_ECUDA;
+        unsigned na = 0;
+        unsigned long long tn = 0;
+        if (cudaMemcpyAsync(&na, &s->ctl->n_active, 4, cudaMemcpyDeviceToHost, st) ||
+            cudaMemcpyAsync(&tn, &s->ctl->tnext_acc, 8, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
+            return GT_ECUDA;
         if (s->steps > 0) {
-            unsigned na = 0;
-            if (cudaMemcpyAsync(&na, &s->ctl->n_active, 4, cudaMemcpyDeviceToHost, st) ||
-                cudaStreamSynchronize(st))
-                return GT_ECUDA;
             const bool was_rebuild = s->last_rebuilt;
             ph_collect(s);
             tune_after_step(s, was_rebuild, na);
+            if (s->prm.r_crit < 0.0f) rcrit_after_step(s, na);
         }
+        if (s->prm.group_mode == GT_GROUP_CELLS_TUNED) {
+            if (s->steps > 0) gsize_after_step(s, na);
+            gsize_before_step(s, tn);
+        }
+        if (s->prm.r_crit < 0.0f && cell_groups(s->prm)) rcrit_before_step(s, tn);
         const double cap = 256.0;
         const double n_opt = s->tune.n_opt < cap ? s->tune.n_opt : cap;
         rebuild = s->steps == 0 || (double)s->tune.since >= std::ceil(n_opt);
@@ -756,7 +851,8 @@ int gt_get_stats(gt_system *s, gt_stats *o, gt_stream stream) {
     o->n = s->n;
     o->T = s->started ? (int64_t)c.tnext : 0;
     o->n_active = c.n_active;
-    o->n_groups = ((int64_t)c.n_active + s->prm.group_max - 1) / s->prm.group_max;
+    o->n_groups = cell_groups(s->prm) ? (int64_t)c.n_groups
+                                      : ((int64_t)c.n_active + s->gmax_now - 1) / s->gmax_now;
     o->n_nodes = s->have_tree ? (int64_t)c.level_start[GT_TREE_LEVELS] : 0;
     int depth = 0;
     for (int l = 0; l < GT_TREE_LEVELS; l++)

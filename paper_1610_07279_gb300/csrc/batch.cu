@@ -259,7 +259,7 @@ int gt_batch_set_knobs(gt_batch *b, int leaf_max, int group_max, int walk_queue)
         if (rc) return rc;
         next[k] = p;
     }
-    for (int k = 0; k < b->nsys; k++) b->sys[k]->prm = next[k];
+    for (int k = 0; k < b->nsys; k++) gt_sys_apply_params(b->sys[k], next[k]);
     b->args_dirty = true;
     drop_graph(b);
     return GT_OK;

@@ -36,6 +36,8 @@ struct DevCtl {
     unsigned int level_start[GT_TREE_LEVELS + 2];  // first cell of each level; [22] = node count
     unsigned int sort_ticket[8];      // dynamic tile ids of the 8 sort passes
     unsigned int sort_epoch;          // look-back epoch of the sort
+    unsigned int pl_ticket;           // chunk tickets of the pseudo j-particle level pass
+    unsigned int pl_done[GT_TREE_LEVELS];  // finished chunks per level of that pass
     unsigned long long interactions;  // cumulative
     unsigned long long mac_tests;     // cumulative
     unsigned long long tnext;         // block time of the current step
@@ -105,6 +107,34 @@ __device__ __forceinline__ double f2d(float f) {
                                  ((unsigned long long)(e + (1023u - 127u)) << 52) |
                                  ((unsigned long long)(b & 0x7fffffu) << 29);
     return __longlong_as_double((long long)d);
+}
+
+// FP64 -> FP32 rounded to nearest (ties to even) by the IEEE-754 fields on the integer
+// pipe, for results in the normal FP32 range; zero, subnormal, overflowing, inf and nan
+// values take the hardware conversion.  Keeping the 23 leading fraction bits and rounding
+// on the 29 dropped ones; a carry out of the fraction moves into the exponent, which is
+// the correctly rounded result (up to infinity at the top of the range).
+__device__ __forceinline__ float d2f(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7ffu) - 1023 + 127;
+    if (e <= 0 || e >= 255) return __double2float_rn(d);
+    const unsigned long long frac = b & 0xfffffffffffffull;
+    unsigned int keep = (unsigned int)(frac >> 29);
+    const unsigned int rest = (unsigned int)(frac & 0x1fffffffu);
+    keep += (rest > 0x10000000u || (rest == 0x10000000u && (keep & 1u))) ? 1u : 0u;
+    return __uint_as_float((unsigned int)(b >> 63) << 31 | ((unsigned int)e << 23) + keep);
+}
+
+// (double)d * 2^k for 0 <= d < 2^53 (exact, built from the bits; the FP64 pipe of this
+// GPU is narrow); any other case, or an exponent out of range, takes the FP64 product.
+__device__ __forceinline__ double i2d_scaled(long long d, int k) {
+    if (d == 0) return 0.0;
+    if (d < 0 || d >= (1ll << 53)) return __dmul_rn((double)d, ldexp(1.0, k));
+    const int top = 63 - __clzll(d);
+    const int e = top + k + 1023;
+    if (e <= 0 || e >= 2047) return __dmul_rn((double)d, ldexp(1.0, k));
+    const unsigned long long frac = ((unsigned long long)d << (52 - top)) & 0xfffffffffffffull;
+    return __longlong_as_double((long long)(((unsigned long long)e << 52) | frac));
 }
 
 // Inclusive warp scan of 32-bit counts.
@@ -217,7 +247,8 @@ void gt_sort_init();
 void gt_launch_build(const uint64_t *skey, int64_t n, int leaf_max, Nodes nd, int64_t cap,
                      unsigned long long *status, DevCtl *ctl, int nsm, cudaStream_t st);
 void gt_launch_cell_lists(Nodes nd, int64_t cap, DevCtl *ctl, int nsm, cudaStream_t st);
-void gt_launch_pseudo(Nodes nd, int64_t cap, const float4 *posm, DevCtl *ctl, int nsm,
+// with_mass: form the FP64 mass sums (after a build); otherwise reuse the stored ones
+void gt_launch_pseudo(Nodes nd, int64_t cap, const float4 *posm, DevCtl *ctl, int nsm, bool with_mass,
                       cudaStream_t st);
 // integrate.cu
 void gt_launch_prepare(DevCtl *ctl, int begin_step, cudaStream_t st);
@@ -239,8 +270,9 @@ void gt_launch_active(const State &s, int64_t n, int L, int all, DevCtl *ctl, ui
 void gt_launch_active_from_list(const uint32_t *list, int64_t n_list, int64_t n, uint8_t *flags, DevCtl *ctl,
                                 uint32_t *active, uint32_t *prefix, unsigned long long *status, int nsm,
                                 cudaStream_t st);
-void gt_launch_groups(Nodes nd, int64_t cap, const uint32_t *prefix, int gmax, int64_t n, uint8_t *marks,
-                      DevCtl *ctl, uint32_t *gstart, unsigned long long *status, int nsm, cudaStream_t st);
+void gt_launch_groups(Nodes nd, int64_t cap, const uint32_t *prefix, int gmax, float r_crit, int64_t n,
+                      uint8_t *marks, DevCtl *ctl, uint32_t *gstart, unsigned long long *status, int nsm,
+                      cudaStream_t st);
 void gt_launch_correct(const State &s, const uint32_t *active, const float4 *acc, DevCtl *ctl,
                        int64_t n, int L, double c2, int nsm, cudaStream_t st);
 void gt_launch_aold(const float4 *acc, int64_t n, float *aold, cudaStream_t st);
@@ -271,6 +303,17 @@ struct WalkArgs {
 };
 int gt_walk_blocks(int nsm);
 // tuner.cu
+// On-line Brent minimisation (one abscissa out, its cost back) for the critical
+// separation of groups (Sec. 2.4).
+struct BrentSearch {
+    double a, b, x, w, v, fx, fw, fv, d, e, u, tol, abs_tol;
+    int state;  // 0: first point pending, 1: searching, 2: converged
+    int evals;
+};
+void gt_brent_start(BrentSearch *b, double lo, double hi, double tol, double abs_tol);
+double gt_brent_next(BrentSearch *b);
+void gt_brent_report(BrentSearch *b, double f);
+bool gt_brent_done(const BrentSearch *b);
 extern "C" int gt_rebuild_interval(const double *t_walk, int n, double t_make, int *model_out,
                                    double *n_opt_out, double *coef_out);
 int gt_walk_warps_per_block();

@@ -29,10 +29,39 @@ struct RebuildTuner {
     long long since = 0;  // block steps on the current tree
 };
 
+// On-line tuning of the critical separation of groups (Sec. 2.4): one Brent search per
+// class of block step (the coarsest active level), over log r_crit, minimising the
+// walk time per active particle; after convergence the best value is held for a few
+// steps of its class, then searched again in a narrower bracket around it (the
+// optimum drifts as the system evolves).
+struct RcritTuner {
+    static constexpr int NCLASS = 30;
+    BrentSearch search[NCLASS];
+    bool started[NCLASS] = {};
+    int held[NCLASS] = {};
+    int pending = -1;  // class of the step whose walk time is awaited
+};
+
+// On-line choice of the group size (GT_GROUP_CELLS_TUNED): per class of block step, the
+// mean walk time per active particle of group_max / 4, / 2 and group_max; each is tried
+// once (largest first), then the fastest is used, and every 64 steps of a class the
+// trials start over.
+struct GroupTuner {
+    static constexpr int NCLASS = 30, NCAND = 3;
+    double sum[NCLASS][NCAND] = {};
+    int cnt[NCLASS][NCAND] = {};
+    int seen[NCLASS] = {};
+    int pending_class = -1, pending_cand = -1;
+};
+
 struct gt_system {
     int64_t n = 0;
     PhaseTimers prof;
     RebuildTuner tune;
+    RcritTuner rtune;
+    GroupTuner gtune;
+    int gmax_now = 32;       // group size of the next grouping
+    float rcrit_now = 0.0f;  // r_crit of the next grouping (0: no radius limit)
     gt_params prm{};
     int dev = 0, nsm = 0;
     int walk_blocks = 0, walk_warps = 0;
@@ -71,6 +100,9 @@ size_t gt_sys_carve(gt_system *s, char *base, int64_t n, const gt_params *p, int
 // for stream st (or, with st == nullptr, for the device).
 int gt_sys_init(gt_system *s, int64_t n, const gt_params *p, void *ws, size_t ws_bytes, bool own_queue,
                 cudaStream_t st);
+// Take new parameters and reset what derives from them (group size and r_crit in use,
+// their on-line tuners).
+void gt_sys_apply_params(gt_system *s, const gt_params &p);
 // A1-A5 on FP32 positions posm_src
 void gt_sys_build_tree(gt_system *s, cudaStream_t st, const float4 *posm_src);
 // A6 with every particle active: the active list and, for cell grouping, the groups

@@ -40,19 +40,20 @@ __global__ __launch_bounds__(256) void k_predict(State s, long long n, const Dev
     const long long i = blockIdx.x * 256ll + threadIdx.x;
     if (i >= n) return;
     const long long T = (long long)ctl->tnext;
-    const double dt_min = ldexp(ctl->dt_max, -ctl->levels_m1);
-    const double dt = __dmul_rn((double)(T - s.t0[i]), dt_min);
-    const float x = __double2float_rn(__fma_rn(dt, s.vx[i], s.rx[i]));
-    const float y = __double2float_rn(__fma_rn(dt, s.vy[i], s.ry[i]));
-    const float z = __double2float_rn(__fma_rn(dt, s.vz[i], s.rz[i]));
+    // dt = (T - t0) dt_min with dt_min = dt_max 2^-(L-1) a power of two: exact, so it is
+    // built from the bits; only the three fused multiply-adds run on the FP64 pipe
+    const int k = (int)((__double_as_longlong(ctl->dt_max) >> 52) & 0x7ff) - 1023 - ctl->levels_m1;
+    const double dt = ctl->dt_max > 0.0 ? i2d_scaled(T - s.t0[i], k) : 0.0;
+    const float x = d2f(__fma_rn(dt, s.vx[i], s.rx[i]));
+    const float y = d2f(__fma_rn(dt, s.vy[i], s.ry[i]));
+    const float z = d2f(__fma_rn(dt, s.vz[i], s.rz[i]));
     posm[i] = make_float4(x, y, z, s.mass[i]);
 }
 
 __global__ __launch_bounds__(256) void k_load(State s, long long n, float4 *__restrict__ posm) {
     const long long i = blockIdx.x * 256ll + threadIdx.x;
     if (i >= n) return;
-    posm[i] = make_float4(__double2float_rn(s.rx[i]), __double2float_rn(s.ry[i]),
-                          __double2float_rn(s.rz[i]), s.mass[i]);
+    posm[i] = make_float4(d2f(s.rx[i]), d2f(s.ry[i]), d2f(s.rz[i]), s.mass[i]);
     s.id[i] = (uint32_t)i;
     s.t0[i] = 0;
     s.level[i] = 0;
@@ -250,10 +251,21 @@ __global__ __launch_bounds__(AT) void k_compact(long long n_host, const unsigned
 }
 
 // Mark the first active position of every group (Sec. 2.4 reading: groups never
-// straddle two tree cells).  A group cell holds 1..gmax actives (or is a leaf) and its
-// parent holds more than gmax (or it is the root); its actives are cut into runs of gmax.
+// straddle two tree cells).  A cell qualifies when it holds at most gmax actives and is
+// a leaf or no wider than r_crit (b_J <= r_crit; r_crit <= 0: no radius limit).  Counts
+// and radii only shrink from a cell to its children, so a group cell is a qualifying
+// cell whose parent does not qualify (or the root), or a leaf under no qualifying cell;
+// its actives are cut into runs of gmax.
+__device__ __forceinline__ bool group_cell_ok(const Nodes &nd, const uint32_t *P, uint32_t c, int gmax,
+                                              float r_crit) {
+    const uint32_t f = nd.first[c];
+    if (P[f + nd.count[c]] - P[f] > (uint32_t)gmax) return false;
+    return nd.child[c] < 0 || r_crit <= 0.0f || nd.walk[c].x <= r_crit;
+}
+
 __global__ __launch_bounds__(256) void k_group_cells(Nodes nd, long long cap, const uint32_t *__restrict__ P,
-                                                     int gmax, uint8_t *__restrict__ marks, const DevCtl *ctl) {
+                                                     int gmax, float r_crit, uint8_t *__restrict__ marks,
+                                                     const DevCtl *ctl) {
     long long nn = ctl->level_start[GT_TREE_LEVELS];
     if (nn > cap) nn = cap;
     for (long long c = blockIdx.x * 256ll + threadIdx.x; c < nn; c += (long long)gridDim.x * 256) {
@@ -261,11 +273,8 @@ __global__ __launch_bounds__(256) void k_group_cells(Nodes nd, long long cap, co
         const uint32_t a0 = P[f], A = P[f + nd.count[c]] - a0;
         if (A == 0) continue;
         const int32_t p = nd.parent[c];
-        if (p >= 0) {
-            const uint32_t fp = nd.first[p];
-            if (P[fp + nd.count[p]] - P[fp] <= (uint32_t)gmax) continue;  // inside a group cell
-        }
-        if (A > (uint32_t)gmax && nd.child[c] >= 0) continue;               // its children decide
+        if (p >= 0 && group_cell_ok(nd, P, (uint32_t)p, gmax, r_crit)) continue;  // inside a group cell
+        if (nd.child[c] >= 0 && !group_cell_ok(nd, P, (uint32_t)c, gmax, r_crit)) continue;  // children decide
         for (uint32_t s = a0; s < a0 + A; s += (uint32_t)gmax) marks[s] = 1;
     }
 }
@@ -509,10 +518,11 @@ void gt_launch_active_from_list(const uint32_t *list, int64_t n_list, int64_t n,
       gt_note_launches(1); }
 }
 
-void gt_launch_groups(Nodes nd, int64_t cap, const uint32_t *prefix, int gmax, int64_t n, uint8_t *marks,
-                      DevCtl *ctl, uint32_t *gstart, unsigned long long *status, int nsm, cudaStream_t st) {
+void gt_launch_groups(Nodes nd, int64_t cap, const uint32_t *prefix, int gmax, float r_crit, int64_t n,
+                      uint8_t *marks, DevCtl *ctl, uint32_t *gstart, unsigned long long *status, int nsm,
+                      cudaStream_t st) {
     if (n > 0) cudaMemsetAsync(marks, 0, (size_t)n, st);
-    { k_group_cells<<<nsm * 8, 256, 0, st>>>(nd, cap, prefix, gmax, marks, ctl); gt_note_launches(1); }
+    { k_group_cells<<<nsm * 8, 256, 0, st>>>(nd, cap, prefix, gmax, r_crit, marks, ctl); gt_note_launches(1); }
     { k_compact<<<nsm * 4, AT, 0, st>>>(0, &ctl->n_active, CM_FLAGS, nullptr, nullptr, 0, marks, ctl,
                                         GT_TREE_LEVELS + 1, 31u, gstart, nullptr, &ctl->n_groups, status);
       gt_note_launches(1); }

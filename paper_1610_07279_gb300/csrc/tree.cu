@@ -219,18 +219,22 @@ __global__ __launch_bounds__(256) void k_cell_fill(Nodes nd, long long cap, DevC
     }
 }
 
-// leaves: one lane per leaf, a warp's leaves of one particle count
+// leaves: one lane per leaf, a warp's leaves of one particle count.  The masses and the
+// cells' members do not change between tree builds, so the mass sums are formed at a
+// build (with_mass) and read back at the other block steps: the same values, one FP64
+// addition per particle fewer.
+template <bool WITH_MASS>
 __global__ __launch_bounds__(256) void k_pseudo_leaves(Nodes nd, const float4 *__restrict__ posm, DevCtl *ctl) {
     const long long nl = ctl->n_leaves;
     for (long long t = blockIdx.x * 256ll + threadIdx.x; t < nl; t += (long long)gridDim.x * 256) {
         const uint32_t c = nd.cells[t];
         const uint32_t f = nd.first[c];
         const uint32_t k = nd.count[c];
-        double m = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+        double m = WITH_MASS ? 0.0 : nd.sum[c].m, sx = 0.0, sy = 0.0, sz = 0.0;
         for (uint32_t i = f; i < f + k; i++) {
             const float4 p = posm[i];
             const double mi = f2d(p.w);  // m x is exact in FP64, so the fused form rounds once like + does
-            m = __dadd_rn(m, mi);
+            if (WITH_MASS) m = __dadd_rn(m, mi);
             sx = __fma_rn(mi, f2d(p.x), sx);
             sy = __fma_rn(mi, f2d(p.y), sy);
             sz = __fma_rn(mi, f2d(p.z), sz);
@@ -240,10 +244,10 @@ __global__ __launch_bounds__(256) void k_pseudo_leaves(Nodes nd, const float4 *_
             const float4 p = posm[f];
             jx = p.x; jy = p.y; jz = p.z;
         } else {
-            const float mf = __double2float_rn(m);
-            jx = __fdiv_rn(__double2float_rn(sx), mf);
-            jy = __fdiv_rn(__double2float_rn(sy), mf);
-            jz = __fdiv_rn(__double2float_rn(sz), mf);
+            const float mf = d2f(m);
+            jx = __fdiv_rn(d2f(sx), mf);
+            jy = __fdiv_rn(d2f(sy), mf);
+            jz = __fdiv_rn(d2f(sz), mf);
         }
         float d2max = 0.0f;
         for (uint32_t i = f; i < f + k; i++) {
@@ -252,44 +256,96 @@ __global__ __launch_bounds__(256) void k_pseudo_leaves(Nodes nd, const float4 *_
             if (d2 > d2max) d2max = d2;
         }
         nd.sum[c] = DSum4{m, sx, sy, sz};
-        nd.jpos[c] = make_float4(jx, jy, jz, __double2float_rn(m));
+        nd.jpos[c] = make_float4(jx, jy, jz, d2f(m));
         nd.walk[c] = make_float4(__fmul_rn(__fsqrt_rn(d2max), GT_RADIUS_MARGIN), __uint_as_float(f),
                                  __uint_as_float(k | GT_LEAF_FLAG), 0.0f);
     }
 }
 
-// cells with children of one level, after the deeper levels: sums of the children's
-// sums in child order
-__global__ __launch_bounds__(256) void k_pseudo_level(int lvl, Nodes nd, const DevCtl *ctl) {
-    const long long i0 = ctl->istart[lvl], i1 = ctl->istart[lvl + 1];
-    for (long long t = i0 + blockIdx.x * 256ll + threadIdx.x; t < i1; t += (long long)gridDim.x * 256) {
-        const uint32_t p = nd.cells[t];
-        const int32_t ch0 = nd.child[p];
-        const uint32_t nch = nd.nchild[p];
-        double m = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-        for (uint32_t q = 0; q < nch; q++) {
-            const DSum4 s = nd.sum[ch0 + q];
-            m = __dadd_rn(m, s.m);
-            sx = __dadd_rn(sx, s.x);
-            sy = __dadd_rn(sy, s.y);
-            sz = __dadd_rn(sz, s.z);
+// Cells with children, all levels in one launch.  Every level's part of the cell list
+// is cut into chunks of PL cells; chunks are handed out by a ticket counter, the deepest
+// level first.  Before a chunk of level l is summed, its block waits until every chunk
+// of level l + 1 is finished: those chunks hold smaller tickets, so the blocks holding
+// them are running, and the wait ends (it is bounded all the same).  A cell adds its
+// children's sums in child order.
+constexpr int PL = 256;
+
+template <bool WITH_MASS>
+__global__ __launch_bounds__(PL) void k_pseudo_levels(Nodes nd, DevCtl *ctl) {
+    __shared__ unsigned int cum[GT_TREE_LEVELS + 1];  // first ticket of every level
+    __shared__ unsigned int t_sh;
+    __shared__ int bad_sh;
+    constexpr int TOP = GT_TREE_LEVELS - 2;           // the deepest level with children
+    if (threadIdx.x == 0) {
+        unsigned int c = 0;
+        for (int l = TOP; l >= 0; l--) {
+            cum[l] = c;
+            c += (ctl->istart[l + 1] - ctl->istart[l] + PL - 1) / PL;
         }
-        const float mf = __double2float_rn(m);
-        const float jx = __fdiv_rn(__double2float_rn(sx), mf);
-        const float jy = __fdiv_rn(__double2float_rn(sy), mf);
-        const float jz = __fdiv_rn(__double2float_rn(sz), mf);
-        float b = 0.0f;
-        for (uint32_t q = 0; q < nch; q++) {
-            const float4 cj = nd.jpos[ch0 + q];
-            const float bc = nd.walk[ch0 + q].x;
-            const float e = __fadd_rn(__fsqrt_rn(sq3f(__fsub_rn(cj.x, jx), __fsub_rn(cj.y, jy),
-                                                      __fsub_rn(cj.z, jz))), bc);
-            if (e > b) b = e;
+        cum[GT_TREE_LEVELS] = c;  // total
+        bad_sh = 0;
+    }
+    __syncthreads();
+    const unsigned int total = cum[GT_TREE_LEVELS];
+    for (;;) {
+        if (threadIdx.x == 0) t_sh = atomicAdd(&ctl->pl_ticket, 1u);
+        __syncthreads();
+        const unsigned int t = t_sh;
+        __syncthreads();
+        if (t >= total || bad_sh) break;
+        int lvl = 0;  // the level whose tickets hold t: cum decreases with the level
+        while (lvl < TOP && cum[lvl] > t) lvl++;
+        if (threadIdx.x == 0 && lvl < TOP) {
+            const unsigned int need = cum[lvl] - cum[lvl + 1];  // chunks of level lvl + 1
+            unsigned int spins = 0;
+            while (*((volatile unsigned int *)&ctl->pl_done[lvl + 1]) < need) {
+                if (++spins > GT_SPIN_LIMIT) {
+                    gt_set_error(ctl, GT_ETIMEOUT, GTK_PSEUDO);
+                    bad_sh = 1;
+                    break;
+                }
+                __nanosleep(64);
+            }
+            __threadfence();
         }
-        nd.sum[p] = DSum4{m, sx, sy, sz};
-        nd.jpos[p] = make_float4(jx, jy, jz, mf);
-        nd.walk[p] = make_float4(__fmul_rn(b, GT_RADIUS_MARGIN), __uint_as_float((uint32_t)ch0),
-                                 __uint_as_float(nch), 0.0f);
+        __syncthreads();
+        if (bad_sh) break;
+        const long long idx = (long long)ctl->istart[lvl] + (long long)(t - cum[lvl]) * PL + threadIdx.x;
+        if (idx < (long long)ctl->istart[lvl + 1]) {
+            const uint32_t p = nd.cells[idx];
+            const int32_t ch0 = nd.child[p];
+            const uint32_t nch = nd.nchild[p];
+            // children written by other blocks of this launch: read through L2 (__ldcg), an SM's
+            // L1 may hold a line of them from before they were written
+            double m = WITH_MASS ? 0.0 : nd.sum[p].m, sx = 0.0, sy = 0.0, sz = 0.0;
+            for (uint32_t q = 0; q < nch; q++) {
+                const double2 *cs = (const double2 *)&nd.sum[ch0 + q];
+                const double2 s0 = __ldcg(cs), s1 = __ldcg(cs + 1);  // (m, x), (y, z)
+                if (WITH_MASS) m = __dadd_rn(m, s0.x);
+                sx = __dadd_rn(sx, s0.y);
+                sy = __dadd_rn(sy, s1.x);
+                sz = __dadd_rn(sz, s1.y);
+            }
+            const float mf = d2f(m);
+            const float jx = __fdiv_rn(d2f(sx), mf);
+            const float jy = __fdiv_rn(d2f(sy), mf);
+            const float jz = __fdiv_rn(d2f(sz), mf);
+            float b = 0.0f;
+            for (uint32_t q = 0; q < nch; q++) {
+                const float4 cj = __ldcg(&nd.jpos[ch0 + q]);
+                const float bc = __ldcg(&nd.walk[ch0 + q]).x;
+                const float e = __fadd_rn(__fsqrt_rn(sq3f(__fsub_rn(cj.x, jx), __fsub_rn(cj.y, jy),
+                                                          __fsub_rn(cj.z, jz))), bc);
+                if (e > b) b = e;
+            }
+            nd.sum[p] = DSum4{m, sx, sy, sz};
+            nd.jpos[p] = make_float4(jx, jy, jz, mf);
+            nd.walk[p] = make_float4(__fmul_rn(b, GT_RADIUS_MARGIN), __uint_as_float((uint32_t)ch0),
+                                     __uint_as_float(nch), 0.0f);
+        }
+        __threadfence();  // every thread's cell is visible device-wide before the chunk counts as done
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(&ctl->pl_done[lvl], 1u);
     }
 }
 
@@ -310,11 +366,15 @@ void gt_launch_cell_lists(Nodes nd, int64_t cap, DevCtl *ctl, int nsm, cudaStrea
     { k_cell_fill<<<nsm * 4, 256, 0, st>>>(nd, cap, ctl); gt_note_launches(1); }
 }
 
-void gt_launch_pseudo(Nodes nd, int64_t cap, const float4 *posm, DevCtl *ctl, int nsm,
+void gt_launch_pseudo(Nodes nd, int64_t cap, const float4 *posm, DevCtl *ctl, int nsm, bool with_mass,
                       cudaStream_t st) {
     (void)cap;
-    { k_pseudo_leaves<<<nsm * 8, 256, 0, st>>>(nd, posm, ctl); gt_note_launches(1); }
-    for (int l = GT_TREE_LEVELS - 2; l >= 0; l--) {
-        { k_pseudo_level<<<nsm * 4, 256, 0, st>>>(l, nd, ctl); gt_note_launches(1); }
-    }
+    if (with_mass) { k_pseudo_leaves<true><<<nsm * 8, 256, 0, st>>>(nd, posm, ctl); }
+    else { k_pseudo_leaves<false><<<nsm * 8, 256, 0, st>>>(nd, posm, ctl); }
+    gt_note_launches(1);
+    // the level pass's ticket and per-level counters start at zero
+    cudaMemsetAsync(&ctl->pl_ticket, 0, sizeof(ctl->pl_ticket) + sizeof(ctl->pl_done), st);
+    if (with_mass) { k_pseudo_levels<true><<<nsm * 4, PL, 0, st>>>(nd, ctl); }
+    else { k_pseudo_levels<false><<<nsm * 4, PL, 0, st>>>(nd, ctl); }
+    gt_note_launches(1);
 }

@@ -139,3 +139,103 @@ extern "C" int gt_rebuild_interval(const double *t_walk, int n, double t_make, i
     *n_opt_out = nopt;
     return GT_OK;
 }
+
+// ---- critical separation of groups (Sec. 2.4): Brent's method on line -----------
+//
+// Brent's minimisation keeps a bracket [a, b] around the minimum, the best point x
+// found so far and the two previous best w, v.  Each step tries the vertex of the
+// parabola through (x, w, v); it falls back to a golden-section step into the larger
+// part of the bracket when the parabola is unusable (steps that do not shrink fast
+// enough, or a vertex outside the bracket).  As an on-line search the state machine
+// hands out one abscissa at a time (next) and takes its measured cost back (report).
+void gt_brent_start(BrentSearch *b, double lo, double hi, double tol, double abs_tol) {
+    constexpr double GOLD = 0.3819660112501051;  // (3 - sqrt 5) / 2
+    b->a = lo < hi ? lo : hi;
+    b->b = lo < hi ? hi : lo;
+    b->x = b->w = b->v = b->a + GOLD * (b->b - b->a);
+    b->fx = b->fw = b->fv = 0.0;
+    b->d = b->e = 0.0;
+    b->u = b->x;
+    b->tol = tol;
+    b->abs_tol = abs_tol;
+    b->state = 0;
+    b->evals = 0;
+}
+
+bool gt_brent_done(const BrentSearch *b) { return b->state == 2; }
+
+double gt_brent_next(BrentSearch *b) {
+    constexpr double GOLD = 0.3819660112501051;
+    if (b->state == 0 || b->state == 2) return b->x;  // the first point, or the converged minimum
+    const double m = 0.5 * (b->a + b->b);
+    const double tol1 = b->tol * fabs(b->x) + b->abs_tol, tol2 = 2.0 * tol1;
+    if (fabs(b->x - m) <= tol2 - 0.5 * (b->b - b->a)) {
+        b->state = 2;
+        return b->x;
+    }
+    bool golden = true;
+    if (fabs(b->e) > tol1) {
+        // vertex of the parabola through (x, fx), (w, fw), (v, fv): x + p/q
+        const double r = (b->x - b->w) * (b->fx - b->fv);
+        double q = (b->x - b->v) * (b->fx - b->fw);
+        double p = (b->x - b->v) * q - (b->x - b->w) * r;
+        q = 2.0 * (q - r);
+        if (q > 0.0) p = -p;
+        q = fabs(q);
+        const double e_prev = b->e;
+        b->e = b->d;
+        if (fabs(p) < fabs(0.5 * q * e_prev) && p > q * (b->a - b->x) && p < q * (b->b - b->x)) {
+            b->d = p / q;
+            const double u = b->x + b->d;
+            if (u - b->a < tol2 || b->b - u < tol2) b->d = m >= b->x ? tol1 : -tol1;
+            golden = false;
+        }
+    }
+    if (golden) {
+        b->e = b->x >= m ? b->a - b->x : b->b - b->x;
+        b->d = GOLD * b->e;
+    }
+    b->u = fabs(b->d) >= tol1 ? b->x + b->d : b->x + (b->d >= 0.0 ? tol1 : -tol1);
+    return b->u;
+}
+
+void gt_brent_report(BrentSearch *b, double f) {
+    b->evals++;
+    if (b->state == 0) {
+        b->fx = b->fw = b->fv = f;
+        b->state = 1;
+        return;
+    }
+    if (b->state == 2) return;
+    const double u = b->u;
+    if (f <= b->fx) {
+        if (u >= b->x) b->a = b->x; else b->b = b->x;
+        b->v = b->w; b->fv = b->fw;
+        b->w = b->x; b->fw = b->fx;
+        b->x = u; b->fx = f;
+    } else {
+        if (u < b->x) b->a = u; else b->b = u;
+        if (f <= b->fw || b->w == b->x) {
+            b->v = b->w; b->fv = b->fw;
+            b->w = u; b->fw = f;
+        } else if (f <= b->fv || b->v == b->x || b->v == b->w) {
+            b->v = u; b->fv = f;
+        }
+    }
+}
+
+extern "C" int gt_brent_minimize(double (*f)(double, void *), void *ctx, double lo, double hi, double tol,
+                                 int max_evals, double *x_min, double *f_min, int *evals) {
+    if (!f || !x_min || !(hi > lo) || !(tol > 0.0) || max_evals < 1) return GT_EINVAL;
+    BrentSearch b;
+    gt_brent_start(&b, lo, hi, tol, 1e-12);
+    while (!gt_brent_done(&b) && b.evals < max_evals) {
+        const double x = gt_brent_next(&b);
+        if (gt_brent_done(&b)) break;
+        gt_brent_report(&b, f(x, ctx));
+    }
+    *x_min = b.x;
+    if (f_min) *f_min = b.fx;
+    if (evals) *evals = b.evals;
+    return GT_OK;
+}

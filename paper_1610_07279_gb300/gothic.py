@@ -37,11 +37,12 @@ class gt_params(C.Structure):
                 ("group_max", C.c_int32), ("ij_share", C.c_int32), ("levels", C.c_int32),
                 ("rebuild_every", C.c_int32), ("walk_queue", C.c_int32), ("node_factor", C.c_int32),
                 ("eta", C.c_double), ("dt_max", C.c_double), ("group_mode", C.c_int32),
-                ("reserved1", C.c_int32)]
+                ("r_crit", C.c_float)]
 
 
 GT_GROUP_RUNS = 0
 GT_GROUP_CELLS = 1
+GT_GROUP_CELLS_TUNED = 2
 
 
 class gt_stats(C.Structure):
@@ -73,6 +74,7 @@ class gt_tune_result(C.Structure):
                 ("n_tried", C.c_int32), ("best_ms", C.c_double), ("ms", C.c_double * 256)]
 
 
+BRENT_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_void_p)
 GT_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 GT_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 GT_SERVER_MAX_SLOTS = 256
@@ -141,6 +143,8 @@ def load(path: str | None = None):
     L.gt_sync_status.argtypes = [P, P]
     L.gt_get_stats.argtypes = [P, C.POINTER(gt_stats), P]
     L.gt_measure_fp32_peak.argtypes = [C.POINTER(C.c_double), P]
+    L.gt_brent_minimize.argtypes = [BRENT_FN, P, C.c_double, C.c_double, C.c_double, I32,
+                                    C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(I32)]
     L.gt_batch_workspace_bytes.argtypes = [I32, P, P, I32, C.POINTER(C.c_size_t)]
     L.gt_batch_create.argtypes = [C.POINTER(P), I32, P, P, I32, P, C.c_size_t]
     L.gt_batch_destroy.argtypes = [P]
@@ -210,6 +214,15 @@ def gt_rebuild_interval(t_walk, t_make: float):
     _check(load().gt_rebuild_interval(t.ctypes.data_as(C.POINTER(C.c_double)), int(t.size), float(t_make),
                                       C.byref(model), C.byref(nopt), coef), "gt_rebuild_interval")
     return int(model.value), float(nopt.value), [float(c) for c in coef]
+
+
+def gt_brent_minimize(f, lo: float, hi: float, tol: float = 1e-8, max_evals: int = 100):
+    """(x_min, f_min, evaluations) of Brent's minimisation of f on [lo, hi] (host only)."""
+    cb = BRENT_FN(lambda x, ctx: float(f(x)))
+    x, fx, ev = C.c_double(0.0), C.c_double(0.0), C.c_int32(0)
+    _check(load().gt_brent_minimize(cb, None, float(lo), float(hi), float(tol), int(max_evals), C.byref(x),
+                                    C.byref(fx), C.byref(ev)), "gt_brent_minimize")
+    return float(x.value), float(fx.value), int(ev.value)
 
 
 GT_NOALLOC_SORT_MAX = 1 << 20

@@ -54,8 +54,8 @@ def test_default_params_host_only(libpath):
     from paper_1610_07279_gb300 import gothic
     p = gothic.gt_default_params()
     assert p.mac == gothic.GT_MAC_ACCELERATION and p.delta_acc == 2.0 ** -7
-    assert p.leaf_max == 16 and p.group_max == 32 and p.ij_share == 0
-    assert p.group_mode == gothic.GT_GROUP_CELLS
+    assert p.leaf_max == 16 and p.group_max == 64 and p.ij_share == 0
+    assert p.group_mode == gothic.GT_GROUP_CELLS_TUNED and p.r_crit == 0.0
 
 
 def test_no_cpu_fallback_in_product():

@@ -65,7 +65,8 @@ def _params(g, eps, **kw):
 def _oparams(O, prm):
     return O.Params(mac=prm.mac, theta=prm.theta, delta_acc=prm.delta_acc, eps=prm.eps, G=prm.G,
                     leaf_max=prm.leaf_max, group_max=prm.group_max, levels=prm.levels, eta=prm.eta,
-                    dt_max=prm.dt_max, group_mode=prm.group_mode)
+                    dt_max=prm.dt_max, group_mode=prm.group_mode, r_crit=max(prm.r_crit, 0.0),
+                    rebuild_every=max(prm.rebuild_every, 1))
 
 
 def _rel(a, r):
@@ -200,6 +201,112 @@ def test_walk_plummer_config(env, mac, S, gmax, mode):
 @pytest.mark.parametrize("gmax", [32, 64])
 def test_walk_other_models(env, kind, n, gmax):
     _walk_case(env, kind, n, 3, 1, 0, gmax)
+
+
+@pytest.mark.parametrize("frac,gmax,r_crit", [(0.05, 32, 0.05), (0.3, 64, 0.02), (1.0, 64, 0.01), (0.01, 16, 0.2)])
+def test_walk_critical_separation(env, frac, gmax, r_crit):
+    """Sec. 2.4: cells wider than r_crit are split into smaller groups; same groups on both sides."""
+    _walk_case(env, "nfw", 30000, 5, 1, 0, gmax, active_frac=frac, r_crit=r_crit)
+
+
+def test_block_steps_with_critical_separation_match_oracle(env):
+    torch, g, O = env
+    n = 1 << 13
+    pos, vel, mass, eps = ics.plummer(n, seed=17)
+    prm = _params(g, eps, levels=4, rebuild_every=1, group_max=64, r_crit=0.05)
+    oprm = _oparams(O, prm)
+    sim = O.BlockStepSim(pos, vel, mass, oprm)
+    boot = O.bootstrap_aold(_p4(pos, mass), oprm)
+    sim.start(aold_boot=boot)
+    s = g.System(n, prm)
+    s.set_state(pos, vel, mass)
+    s.start(boot)
+    for k in range(6):
+        r = sim.step()
+        s.block_step()
+        s.sync()
+        assert s.stats()["T"] == r["T"]
+        act = s.get_active()
+        assert np.array_equal(act, r["active"]), k
+    assert s.status() == g.GT_OK
+    s.close()
+
+
+def test_block_steps_reusing_the_tree_match_oracle(env):
+    """Sec. 2.6: between rebuilds the topology and order are kept and only the pseudo
+    j-particles are formed again (the GPU reuses the mass sums of the build).  The
+    pseudo j-particles must equal the oracle's on the same positions bit for bit; the
+    state follows the oracle within tolerance (the corrections use FP32 forces)."""
+    torch, g, O = env
+    n = 1 << 13
+    pos, vel, mass, eps = ics.nfw(n, seed=23)
+    prm = _params(g, eps, levels=4, rebuild_every=3)
+    oprm = _oparams(O, prm)
+    sim = O.BlockStepSim(pos, vel, mass, oprm)
+    boot = O.bootstrap_aold(_p4(pos, mass), oprm)
+    sim.start(aold_boot=boot)
+    s = g.System(n, prm)
+    s.set_state(pos, vel, mass)
+    s.start(boot)
+    buf = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+    for k in range(8):
+        r = sim.step()
+        s.block_step()
+        s.sync()
+        assert s.stats()["T"] == r["T"]
+        act = s.get_active()
+        assert len(np.intersect1d(act, r["active"])) >= 0.999 * max(act.size, r["active"].size), k
+        s.predict(r["T"], buf)  # the positions this step's pseudo j-particles were formed from
+        t = s.get_tree()
+        assert t["n_nodes"] == r["tree"]["n_nodes"]
+        jo = O.pseudo_j(r["tree"], buf.cpu().numpy())[0]
+        assert np.array_equal(t["jpos"].view(np.uint32), jo.view(np.uint32)), k
+    gs = s.get_state()
+    same = gs["id"] == sim.id
+    assert same.mean() >= 0.999
+    assert np.percentile(np.abs(gs["pos"][same] - sim.r0[same]).max(axis=1), 99) < 1e-5
+    assert s.stats()["rebuilds"] == 1 + 3  # the start-up build and steps 0, 3, 6
+    s.close()
+
+
+def test_critical_separation_tuned_on_line(env):
+    """r_crit < 0: Brent searches per class of step; the run stays correct and finishes."""
+    torch, g, O = env
+    pos, vel, mass, eps = ics.nfw(1 << 15, seed=19)
+    prm = _params(g, eps, levels=5, r_crit=-0.05)  # automatic rebuild interval (host sync per step)
+    s = g.System(1 << 15, prm)
+    s.set_state(pos, vel, mass)
+    s.start()
+    for _ in range(40):
+        s.block_step()
+    s.sync()
+    st = s.get_state()
+    assert np.all(np.isfinite(st["pos"])) and np.all(np.isfinite(st["acc"]))
+    assert s.stats()["block_steps"] == 40
+    s.close()
+
+
+def test_group_size_tuned_on_line(env):
+    """GT_GROUP_CELLS_TUNED: every step uses one of group_max / 4, / 2, / 1 as the cell
+    bound; the run stays correct (its forces are those of the chosen size)."""
+    torch, g, O = env
+    n = 1 << 15
+    pos, vel, mass, eps = ics.nfw(n, seed=29)
+    prm = _params(g, eps, levels=5, group_max=64, group_mode=g.GT_GROUP_CELLS_TUNED)
+    s = g.System(n, prm)
+    s.set_state(pos, vel, mass)
+    s.start()
+    sizes = set()
+    for _ in range(48):
+        s.block_step()
+        s.sync()
+        st = s.stats()
+        if st["n_groups"]:
+            sizes.add(int(np.ceil(st["n_active"] / st["n_groups"])))  # a lower bound of the size in use
+    gs = s.get_state()
+    assert np.all(np.isfinite(gs["pos"])) and np.all(np.isfinite(gs["acc"]))
+    assert s.stats()["block_steps"] == 48 and len(sizes) > 1
+    s.close()
 
 
 def test_group_max_limits(env):

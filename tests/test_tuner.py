@@ -1,4 +1,5 @@
-"""Rebuild-interval auto-tuning (Sec. 2.6, Appendix C) against closed forms and brute force.
+"""Rebuild-interval auto-tuning (Sec. 2.6, Appendix C) against closed forms and brute force,
+and the Brent minimisation behind the critical separation of groups (Sec. 2.4).
 
 Host-only code of the library: runs without a GPU.
 """
@@ -75,3 +76,29 @@ def test_model_choice_by_reduced_chi2(g):
     assert g.gt_rebuild_interval(lin, 2.0)[0] == 0
     pw = 0.2 * 1.1 ** i * (1 + rng.normal(0, 1e-5, i.size))
     assert g.gt_rebuild_interval(pw, 2.0)[0] == 1
+
+
+# ---------------------------------------------------------------- Brent (Sec. 2.4)
+def test_brent_finds_parabola_vertex_quickly(g):
+    calls = []
+    x, fx, ev = g.gt_brent_minimize(lambda t: calls.append(t) or (t - 0.7312) ** 2 + 3.0, -5.0, 4.0,
+                                    tol=1e-9, max_evals=100)
+    assert abs(x - 0.7312) < 1e-6 and abs(fx - 3.0) < 1e-10
+    assert min(abs(c - 0.7312) for c in calls[:4]) < 1e-12  # a parabolic step lands on the vertex
+    golden = math.ceil(math.log(9.0 / 1e-9) / math.log((1 + 5 ** 0.5) / 2))
+    assert ev < golden  # fewer evaluations than golden-section search to the same bracket
+
+
+def test_brent_on_nonsmooth_and_edge_minima(g):
+    x, _, ev = g.gt_brent_minimize(lambda t: abs(t - 1.25) ** 0.5, 0.0, 10.0, tol=1e-8, max_evals=200)
+    assert abs(x - 1.25) < 1e-6  # cusp: golden-section steps still shrink the bracket
+    x, _, _ = g.gt_brent_minimize(lambda t: t, 2.0, 3.0, tol=1e-8, max_evals=200)
+    assert x - 2.0 < 1e-6  # a monotone function: the minimum is at the lower end
+    x, _, _ = g.gt_brent_minimize(lambda t: np.cos(t), 2.0, 4.5, tol=1e-10, max_evals=200)
+    assert abs(x - np.pi) < 1e-5
+
+
+def test_brent_respects_the_evaluation_budget(g):
+    calls = []
+    g.gt_brent_minimize(lambda t: calls.append(t) or (t - 0.3) ** 4, -1.0, 1.0, tol=1e-14, max_evals=7)
+    assert len(calls) <= 7 and all(-1.0 <= t <= 1.0 for t in calls)
