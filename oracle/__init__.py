@@ -76,7 +76,7 @@ def _declare(L):
     L.or_active_prefix.argtypes = [I64, I64, P, P]
     L.or_group_starts.argtypes = [I64, P, P, P, P, P, I32, P, F, P]
     L.or_group_starts.restype = I64
-    L.or_groups.argtypes = [I64, P, P, P, P, P, P]
+    L.or_groups.argtypes = [I64, P, P, P, P, I32, P, P]
     L.or_walk.argtypes = [I64, P, P, P, P, P, P, P, I64, P, P, P, P, I32, F, F, F, F,
                           I64, P, P, P, P]
     L.or_walk.restype = I32
@@ -124,6 +124,7 @@ class Params:
     group_mode: int = 1        # 1: groups bounded by tree cells; 0: runs of group_max actives
     r_crit: float = 0.0        # critical separation of a group cell's radius (Sec. 2.4); <= 0: none
     rebuild_every: int = 1     # block steps per tree build (Sec. 2.6); the topology is kept between
+    sphere: int = 0            # pseudo i-particle: 0 GEO, 1 Ritter's efficient bounding sphere (App. B)
 
 
 def f32(x):
@@ -222,7 +223,9 @@ def group_starts(tree: dict, n: int, active, gmax: int, mode: int = 1, bj=None, 
     return starts[:ng + 1].copy()
 
 
-def groups(starts, active, sp4: np.ndarray, aold=None):
+def groups(starts, active, sp4: np.ndarray, aold=None, sphere: int = 0):
+    """Pseudo i-particles (x, y, z, b_I) and min |a_old| per group; sphere 0: GEO centre,
+    1: the centre of Ritter's efficient bounding sphere (Appendix B)."""
     starts = _c(starts, np.uint32)
     active = _c(active, np.uint32)
     sp4 = _c(sp4, np.float32)
@@ -230,7 +233,7 @@ def groups(starts, active, sp4: np.ndarray, aold=None):
     gI = np.zeros((ng, 4), np.float32)
     gamin = np.zeros(ng, np.float32)
     ao = None if aold is None else _c(aold, np.float32)
-    lib().or_groups(ng, _p(starts), _p(active), _p(sp4), _p(ao), _p(gI), _p(gamin))
+    lib().or_groups(ng, _p(starts), _p(active), _p(sp4), _p(ao), int(sphere), _p(gI), _p(gamin))
     return gI, gamin
 
 
@@ -347,7 +350,7 @@ def tree_force(p4: np.ndarray, prm: Params, aold=None, active=None, mac=None, th
         active = np.arange(n, dtype=np.uint32)
     saold = None if aold is None else _c(aold, np.float32)[order]
     starts = group_starts(tree, n, active, prm.group_max, prm.group_mode, bj, prm.r_crit)
-    gI, gamin = groups(starts, active, sp4, saold)
+    gI, gamin = groups(starts, active, sp4, saold, prm.sphere)
     m = prm.mac if mac is None else mac
     th = prm.theta if theta is None else theta
     acc, inter, ntest = walk(tree, jpos, bj, sp4, active, starts, gI, gamin, m, th,
@@ -452,7 +455,7 @@ class BlockStepSim:
         jpos, bj = pseudo_j(tree, sp4)
         active = np.nonzero(self.t0 + self.ticks(self.level) == T)[0].astype(np.uint32)
         starts = group_starts(tree, self.n, active, prm.group_max, prm.group_mode, bj, prm.r_crit)
-        gI, gamin = groups(starts, active, sp4, self.aold)
+        gI, gamin = groups(starts, active, sp4, self.aold, prm.sphere)
         acc, inter, _ = walk(tree, jpos, bj, sp4, active, starts, gI, gamin, prm.mac,
                              prm.theta, prm.delta_acc, prm.eps, prm.G)
         acc32 = acc.astype(np.float32)

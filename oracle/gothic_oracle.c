@@ -342,10 +342,51 @@ int64_t or_group_starts(int64_t nn, const uint32_t *first, const uint32_t *count
 /*   b_I = the largest FP32 |r_i - r_I|, times (1 + 2^-20);                   */
 /*   amin = min |a_old| over the group (the acceleration MAC needs one |a_old| */
 /*   per group; the smallest is the conservative choice).                    */
+/* sphere 0: GEO as above; sphere 1: the centre of Ritter's efficient        */
+/* bounding sphere (below), the radius taken the same way.                   */
 /* gI out: ng x (x, y, z, b_I); gamin out: ng.                               */
 /* ------------------------------------------------------------------------- */
+/* The efficient bounding sphere of Ritter (1990), the pseudo i-particle the paper uses  */
+/* on its newest GPU (Appendix B): a first diameter between the extreme points of the     */
+/* axis whose pair is farthest apart, then the sphere is grown towards the first member    */
+/* outside it (half the way from its far side to the point) until every member is inside */
+/* (at most one growth per member).  FP32, every operation in this order; only the centre */
+/* is kept, the radius is the largest member distance as for GEO.  m: member positions.   */
+static void ebs_centre(int64_t cnt, const float (*m)[3], float c[3]) {
+    int64_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int64_t k = 1; k < cnt; k++)
+        for (int a = 0; a < 3; a++) {
+            if (m[k][a] < m[lo[a]][a]) lo[a] = k;
+            if (m[k][a] > m[hi[a]][a]) hi[a] = k;
+        }
+    int best = 0;
+    float bd2 = -1.0f;
+    for (int a = 0; a < 3; a++) {
+        const float dx = m[hi[a]][0] - m[lo[a]][0], dy = m[hi[a]][1] - m[lo[a]][1], dz = m[hi[a]][2] - m[lo[a]][2];
+        const float d2 = (dx * dx + dy * dy) + dz * dz;
+        if (d2 > bd2) { bd2 = d2; best = a; }
+    }
+    for (int a = 0; a < 3; a++) c[a] = 0.5f * (m[lo[best]][a] + m[hi[best]][a]);
+    float r = 0.5f * sqrtf(bd2);
+    for (int64_t it = 0; it < cnt; it++) {
+        int64_t out = -1;
+        float od2 = 0.0f;
+        for (int64_t k = 0; k < cnt && out < 0; k++) {
+            const float dx = m[k][0] - c[0], dy = m[k][1] - c[1], dz = m[k][2] - c[2];
+            const float d2 = (dx * dx + dy * dy) + dz * dz;
+            if (d2 > r * r) { out = k; od2 = d2; }
+        }
+        if (out < 0) break;
+        const float d = sqrtf(od2);
+        const float rn = 0.5f * (r + d);
+        const float f = (d - rn) / d;
+        for (int a = 0; a < 3; a++) c[a] = c[a] + f * (m[out][a] - c[a]);
+        r = rn;
+    }
+}
+
 void or_groups(int64_t ng, const uint32_t *starts, const uint32_t *active, const float *sp4,
-               const float *aold, float *gI, float *gamin) {
+               const float *aold, int sphere, float *gI, float *gamin) {
 #pragma omp parallel for
     for (int64_t g = 0; g < ng; g++) {
         const int64_t a0 = starts[g], a1 = starts[g + 1];
@@ -362,7 +403,15 @@ void or_groups(int64_t ng, const uint32_t *starts, const uint32_t *active, const
             if (ao < am) am = ao;
         }
         float c[3];
-        for (int a = 0; a < 3; a++) c[a] = 0.5f * (mn[a] + mx[a]);
+        if (sphere == 1 && a1 > a0) {
+            float (*m)[3] = malloc((size_t)(a1 - a0) * sizeof *m);
+            for (int64_t k = a0; k < a1; k++)
+                for (int a = 0; a < 3; a++) m[k - a0][a] = sp4[4 * active[k] + a];
+            ebs_centre(a1 - a0, (const float (*)[3])m, c);
+            free(m);
+        } else {
+            for (int a = 0; a < 3; a++) c[a] = 0.5f * (mn[a] + mx[a]);
+        }
         float d2max = 0.0f;
         for (int64_t k = a0; k < a1; k++) {
             const uint32_t i = active[k];

@@ -227,3 +227,84 @@ def test_walk_single_and_empty(oracle_lib):
     assert np.all(r["acc"] == 0.0) and r["inter"][0] == 1
     r = O.tree_force(np.zeros((0, 4), np.float32), prm)
     assert r["acc"].shape == (0, 4)
+
+
+def _seb_radius(pts, iters=4000):
+    """Smallest enclosing ball by Badoiu-Clarkson: step towards the farthest point by
+    1/(k+1); the radius converges to the optimum (error ~ 1/sqrt(iters))."""
+    c = pts.mean(0)
+    for k in range(iters):
+        far = pts[np.argmax(((pts - c) ** 2).sum(1))]
+        c = c + (far - c) / (k + 1.0)
+    return np.sqrt(((pts - c) ** 2).sum(1).max())
+
+
+def _one_group_sphere(O, pts, sphere):
+    n = len(pts)
+    sp4 = np.zeros((n, 4), np.float32)
+    sp4[:, :3] = pts
+    active = np.arange(n, dtype=np.uint32)
+    gI, _ = O.groups(np.array([0, n], np.uint32), active, sp4, None, sphere)
+    return gI[0]
+
+
+def test_ebs_sphere_special_cases(oracle_lib):
+    """Appendix B, Ritter's efficient bounding sphere: exact on a segment (two points,
+    collinear points), near the circumscribed sphere for points on a sphere, always
+    enclosing, and no worse than the box-centred (GEO) sphere there."""
+    O = oracle_lib
+    two = np.array([[0.25, -1.0, 2.0], [1.25, 0.5, -1.0]], np.float32)
+    s = _one_group_sphere(O, two, 1)
+    half = 0.5 * np.linalg.norm(two[1].astype(np.float64) - two[0])
+    np.testing.assert_allclose(s[:3], 0.5 * (two[0] + two[1]), rtol=0, atol=1e-6)
+    assert half <= s[3] <= half * (1 + 2e-6)
+    t = np.linspace(0, 1, 23)[:, None]
+    line = (np.array([1.0, 2.0, -0.5]) + t * np.array([2.0, -1.0, 0.25])).astype(np.float32)
+    s = _one_group_sphere(O, line, 1)
+    half = 0.5 * np.linalg.norm(line[-1].astype(np.float64) - line[0])
+    assert half <= s[3] <= half * (1 + 1e-5)
+    rng = np.random.default_rng(4)
+    worse = []
+    for _ in range(20):
+        v = rng.normal(size=(48, 3))
+        pts = (3.0 + 2.0 * v / np.linalg.norm(v, axis=1, keepdims=True)).astype(np.float32)
+        se, sg = _one_group_sphere(O, pts, 1), _one_group_sphere(O, pts, 0)
+        d = np.linalg.norm(pts.astype(np.float64) - se[:3].astype(np.float64), axis=1)
+        assert d.max() <= se[3]
+        assert se[3] <= 2.0 * 1.15  # within 15 % of the circumscribed radius
+        worse.append(se[3] / sg[3])
+    assert np.median(worse) <= 1.02
+
+
+def _seb_radius(pts, iters=4000):
+    """Smallest enclosing ball by Badoiu-Clarkson: step towards the farthest point by
+    1/(k+1); the radius converges to the optimum (error ~ 1/sqrt(iters))."""
+    c = pts.mean(0)
+    for k in range(iters):
+        far = pts[np.argmax(((pts - c) ** 2).sum(1))]
+        c = c + (far - c) / (k + 1.0)
+    return np.sqrt(((pts - c) ** 2).sum(1).max())
+
+
+def test_ebs_and_geo_spheres_against_the_smallest_ball(oracle_lib):
+    """Both pseudo i-particle spheres enclose their group and stay within ~1.5x of the
+    smallest enclosing ball on tree-cell groups (the paper reports ~1.1-1.15 on its
+    groups; cell-bounded groups are compact)."""
+    O = oracle_lib
+    n = 8192
+    sp4, tree = _sorted_tree(O, n, 21)
+    active = np.arange(n, dtype=np.uint32)
+    starts = O.group_starts(tree, n, active, 64, 1)
+    rng = np.random.default_rng(1)
+    for sphere in (0, 1):
+        gI, _ = O.groups(starts, active, sp4, None, sphere)
+        ratios = []
+        for g in rng.choice(len(starts) - 1, 40, replace=False):
+            mem = active[starts[g]:starts[g + 1]]
+            if len(mem) < 4:
+                continue
+            pts = sp4[mem, :3].astype(np.float64)
+            d = np.linalg.norm(pts - gI[g, :3].astype(np.float64), axis=1)
+            assert d.max() <= gI[g, 3]
+            ratios.append(gI[g, 3] / _seb_radius(pts))
+        assert min(ratios) >= 0.999 and np.median(ratios) < 1.2 and max(ratios) < 1.6, (sphere, ratios)
