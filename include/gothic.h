@@ -109,6 +109,11 @@ typedef struct gt_params {
  * kept, and the three are measured again every 64 steps of the class.  Elsewhere it
  * acts as GT_GROUP_CELLS. */
 #define GT_GROUP_CELLS_TUNED 2
+/* Flag added to group_mode: the pseudo i-particle of a group is centred on Ritter's
+ * efficient bounding sphere of its members (Appendix B; the paper's choice on its
+ * newest GPU) instead of the centre of their bounding box (GEO, the default); the
+ * radius is the largest member distance either way. */
+#define GT_SPHERE_EBS 0x100
 
 /* Counters and state read back by gt_get_stats (synchronises the stream). */
 typedef struct gt_stats {

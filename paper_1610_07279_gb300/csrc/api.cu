@@ -38,8 +38,9 @@ int check_params(const gt_params *p) {
     if (p->ij_share != 0 && (!pow2(p->ij_share) || p->ij_share > 32)) return GT_EINVAL;
     // up to 32 members with ij_share lanes each, or up to 64 with one lane per two members
     if (p->group_max < 1 || p->group_max > (p->ij_share > 1 ? 32 / p->ij_share : 64)) return GT_EINVAL;
-    if (p->group_mode != GT_GROUP_RUNS && p->group_mode != GT_GROUP_CELLS && p->group_mode != GT_GROUP_CELLS_TUNED)
-        return GT_EINVAL;
+    const int gm = p->group_mode & 0xff;
+    if ((p->group_mode & ~(0xff | GT_SPHERE_EBS)) != 0) return GT_EINVAL;
+    if (gm != GT_GROUP_RUNS && gm != GT_GROUP_CELLS && gm != GT_GROUP_CELLS_TUNED) return GT_EINVAL;
     if (p->levels < 1 || p->levels > 30) return GT_EINVAL;
     if (p->rebuild_every < 0 || p->node_factor < 1 || p->node_factor > 64) return GT_EINVAL;
     if (!pow2(p->walk_queue) || p->walk_queue < 64) return GT_EINVAL;
@@ -53,7 +54,8 @@ int check_params(const gt_params *p) {
     return GT_OK;
 }
 
-bool cell_groups(const gt_params &p) { return p.group_mode != GT_GROUP_RUNS; }
+bool cell_groups(const gt_params &p) { return (p.group_mode & 0xff) != GT_GROUP_RUNS; }
+bool tuned_groups(const gt_params &p) { return (p.group_mode & 0xff) == GT_GROUP_CELLS_TUNED; }
 
 // r_crit of the groupings when it is not tuned on line: the given value, or the start
 // of the search for a negative one
@@ -396,6 +398,7 @@ WalkArgs gt_sys_walk_args(const gt_system *s, const uint32_t *active, const floa
     a.qcap = s->prm.walk_queue;
     a.mac = mac;
     a.ij_share = s->prm.ij_share;
+    a.sphere = (s->prm.group_mode & GT_SPHERE_EBS) ? 1 : 0;
     a.theta = s->prm.theta;
     a.delta_acc = s->prm.delta_acc;
     a.eps2 = s->prm.eps * s->prm.eps;
@@ -628,7 +631,7 @@ int gt_block_step(gt_system *s, gt_stream stream) {
             tune_after_step(s, was_rebuild, na);
             if (s->prm.r_crit < 0.0f) rcrit_after_step(s, na);
         }
-        if (s->prm.group_mode == GT_GROUP_CELLS_TUNED) {
+        if (tuned_groups(s->prm)) {
             if (s->steps > 0) gsize_after_step(s, na);
             gsize_before_step(s, tn);
         }

@@ -299,6 +299,7 @@ struct WalkArgs {
     int qcap;                // power of two
     int mac;
     int ij_share;            // lanes per i-particle; 0: 32 / (members rounded up to a power of two)
+    int sphere;              // pseudo i-particle: 0 GEO centre, 1 Ritter's efficient bounding sphere
     float theta, delta_acc, eps2, G, inv_eps;
 };
 int gt_walk_blocks(int nsm);

@@ -80,6 +80,85 @@ __device__ __forceinline__ void interact(const float4 s, float xi, float yi, flo
     ph -= mr;
 }
 
+// (value, member) of the extreme member on one axis: the smallest (want_max false) or
+// largest value, the lowest member index on ties
+__device__ __forceinline__ void warp_arg_ext(float &v, int &m, bool want_max) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        const int m2 = __shfl_xor_sync(0xffffffffu, m, o);
+        const bool take = want_max ? (v2 > v || (v2 == v && m2 < m)) : (v2 < v || (v2 == v && m2 < m));
+        if (take) { v = v2; m = m2; }
+    }
+}
+
+// Centre of Ritter's efficient bounding sphere of the group's members (Appendix B): the
+// first diameter joins the extreme members of the axis whose pair is farthest apart; the
+// sphere then grows towards the first member outside it (member order) until none is,
+// at most cnt times.  FP32, every operation rounded as written.  Member k < 32 is the
+// first member of the lane holding slot k (pi), member 32 + l the second of lane l (pi2).
+__device__ __forceinline__ void ebs_centre(float4 pi, float4 pi2, bool mine1, bool mine2, int slot, int lane,
+                                           int logS, uint32_t cnt, float &cx, float &cy, float &cz) {
+    const unsigned FULL = 0xffffffffu;
+    const float INF = __int_as_float(0x7f800000);
+    auto coord = [](const float4 &p, int a) { return a == 0 ? p.x : (a == 1 ? p.y : p.z); };
+    // the member's position, fetched from the lane that holds it
+    auto fetch = [&](int m, float &x, float &y, float &z) {
+        const bool second = m >= 32;
+        const int src = second ? m - 32 : (m << logS);
+        const float4 a1 = make_float4(__shfl_sync(FULL, pi.x, src), __shfl_sync(FULL, pi.y, src),
+                                      __shfl_sync(FULL, pi.z, src), 0.f);
+        const float4 a2 = make_float4(__shfl_sync(FULL, pi2.x, src), __shfl_sync(FULL, pi2.y, src),
+                                      __shfl_sync(FULL, pi2.z, src), 0.f);
+        x = second ? a2.x : a1.x; y = second ? a2.y : a1.y; z = second ? a2.z : a1.z;
+    };
+    float bd2 = -1.0f, lx = 0.f, ly = 0.f, lz = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
+    for (int ax = 0; ax < 3; ax++) {
+        float vmin = mine1 ? coord(pi, ax) : INF, vmax = mine1 ? coord(pi, ax) : -INF;
+        int mmin = mine1 ? slot : 1 << 20, mmax = mmin;
+        if (mine2) {
+            const float v2 = coord(pi2, ax);
+            if (v2 < vmin) { vmin = v2; mmin = lane + 32; }  // the second member has the larger index
+            if (v2 > vmax) { vmax = v2; mmax = lane + 32; }
+        }
+        warp_arg_ext(vmin, mmin, false);
+        warp_arg_ext(vmax, mmax, true);
+        float ax0, ay0, az0, ax1, ay1, az1;
+        fetch(mmin, ax0, ay0, az0);
+        fetch(mmax, ax1, ay1, az1);
+        const float dx = __fsub_rn(ax1, ax0), dy = __fsub_rn(ay1, ay0), dz = __fsub_rn(az1, az0);
+        const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+        if (d2 > bd2) { bd2 = d2; lx = ax0; ly = ay0; lz = az0; hx = ax1; hy = ay1; hz = az1; }
+    }
+    cx = __fmul_rn(0.5f, __fadd_rn(lx, hx));
+    cy = __fmul_rn(0.5f, __fadd_rn(ly, hy));
+    cz = __fmul_rn(0.5f, __fadd_rn(lz, hz));
+    float r = __fmul_rn(0.5f, __fsqrt_rn(bd2));
+    for (uint32_t it = 0; it < cnt; it++) {
+        const float r2 = __fmul_rn(r, r);
+        auto outside = [&](const float4 &p) {
+            const float dx = __fsub_rn(p.x, cx), dy = __fsub_rn(p.y, cy), dz = __fsub_rn(p.z, cz);
+            return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) > r2;
+        };
+        const unsigned b1 = __ballot_sync(FULL, mine1 && outside(pi));
+        const unsigned b2 = __ballot_sync(FULL, mine2 && outside(pi2));
+        int m;
+        if (b1) m = (__ffs(b1) - 1) >> logS;
+        else if (b2) m = 32 + __ffs(b2) - 1;
+        else break;
+        float px, py, pz;
+        fetch(m, px, py, pz);
+        const float dx = __fsub_rn(px, cx), dy = __fsub_rn(py, cy), dz = __fsub_rn(pz, cz);
+        const float d = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)));
+        const float rn = __fmul_rn(0.5f, __fadd_rn(r, d));
+        const float f = __fdiv_rn(__fsub_rn(d, rn), d);
+        cx = __fadd_rn(cx, __fmul_rn(f, dx));
+        cy = __fadd_rn(cy, __fmul_rn(f, dy));
+        cz = __fadd_rn(cz, __fmul_rn(f, dz));
+        r = rn;
+    }
+}
+
 // One group g of system a (Sec. 2.3): pseudo i-particle, traversal, force loop.  The
 // warp's interaction and MAC-test counts are added to n_inter and n_tests.
 __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32_t ngroups, float4 *list,
@@ -139,9 +218,10 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
         mxz = fmaxf(mxz, __shfl_xor_sync(FULL, mxz, o));
         ao = fminf(ao, __shfl_xor_sync(FULL, ao, o));
     }
-    const float cx = __fmul_rn(0.5f, __fadd_rn(mnx, mxx));
-    const float cy = __fmul_rn(0.5f, __fadd_rn(mny, mxy));
-    const float cz = __fmul_rn(0.5f, __fadd_rn(mnz, mxz));
+    float cx = __fmul_rn(0.5f, __fadd_rn(mnx, mxx));
+    float cy = __fmul_rn(0.5f, __fadd_rn(mny, mxy));
+    float cz = __fmul_rn(0.5f, __fadd_rn(mnz, mxz));
+    if (a.sphere == 1) ebs_centre(pi, pi2, have && sub == 0, have2, slot, lane, logS, cnt, cx, cy, cz);
     const float ddx = __fsub_rn(pi.x, cx), ddy = __fsub_rn(pi.y, cy), ddz = __fsub_rn(pi.z, cz);
     float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ddx, ddx), __fmul_rn(ddy, ddy)), __fmul_rn(ddz, ddz));
     {

@@ -43,6 +43,7 @@ class gt_params(C.Structure):
 GT_GROUP_RUNS = 0
 GT_GROUP_CELLS = 1
 GT_GROUP_CELLS_TUNED = 2
+GT_SPHERE_EBS = 0x100
 
 
 class gt_stats(C.Structure):

@@ -65,8 +65,8 @@ def _params(g, eps, **kw):
 def _oparams(O, prm):
     return O.Params(mac=prm.mac, theta=prm.theta, delta_acc=prm.delta_acc, eps=prm.eps, G=prm.G,
                     leaf_max=prm.leaf_max, group_max=prm.group_max, levels=prm.levels, eta=prm.eta,
-                    dt_max=prm.dt_max, group_mode=prm.group_mode, r_crit=max(prm.r_crit, 0.0),
-                    rebuild_every=max(prm.rebuild_every, 1))
+                    dt_max=prm.dt_max, group_mode=prm.group_mode & 0xff, r_crit=max(prm.r_crit, 0.0),
+                    rebuild_every=max(prm.rebuild_every, 1), sphere=1 if prm.group_mode & 0x100 else 0)
 
 
 def _rel(a, r):
@@ -307,6 +307,14 @@ def test_group_size_tuned_on_line(env):
     assert np.all(np.isfinite(gs["pos"])) and np.all(np.isfinite(gs["acc"]))
     assert s.stats()["block_steps"] == 48 and len(sizes) > 1
     s.close()
+
+
+@pytest.mark.parametrize("S,gmax,frac", [(0, 32, None), (0, 64, None), (2, 16, None), (0, 64, 0.1), (4, 8, 0.3)])
+def test_walk_ebs_pseudo_particle(env, S, gmax, frac):
+    """Appendix B: the pseudo i-particle centred on Ritter's efficient bounding sphere."""
+    torch, g, O = env
+    _walk_case(env, "nfw", 20000, 7, 1, S, gmax, active_frac=frac,
+               group_mode=g.GT_GROUP_CELLS | g.GT_SPHERE_EBS)
 
 
 def test_group_max_limits(env):
