@@ -71,14 +71,14 @@ def _declare(L):
     L.or_sort.restype = I32
     L.or_build.argtypes = [I64, P, I32, I64, P, P, P, P, P, P, P]
     L.or_build.restype = I64
-    L.or_pseudo_j.argtypes = [I64, P, P, P, P, P, P, P]
+    L.or_pseudo_j.argtypes = [I64, P, P, P, P, P, P, P, P]
     L.or_pseudo_j.restype = I32
     L.or_active_prefix.argtypes = [I64, I64, P, P]
     L.or_group_starts.argtypes = [I64, P, P, P, P, P, I32, P, F, P]
     L.or_group_starts.restype = I64
     L.or_groups.argtypes = [I64, P, P, P, P, I32, P, P]
     L.or_walk.argtypes = [I64, P, P, P, P, P, P, P, I64, P, P, P, P, I32, F, F, F, F,
-                          I64, P, P, P, P]
+                          I64, P, P, P, P, P]
     L.or_walk.restype = I32
     L.or_dtmax_exponent.argtypes = [I64, P, D, D]
     L.or_dtmax_exponent.restype = I32
@@ -89,7 +89,7 @@ def _declare(L):
     L.or_correct.argtypes = [I64, P, P, I64, D, I32, I32, D, D, P, P, P, P, P, P]
     L.or_morton3.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
     L.or_morton3.restype = C.c_uint64
-    L.or_mac_accept.argtypes = [I32, F, F, F, F, P, P, F]
+    L.or_mac_accept.argtypes = [I32, F, F, F, F, P, P, F, F]
     L.or_mac_accept.restype = I32
     L.or_level_from_a2.argtypes = [D, D, D, I32, I32]
     L.or_level_from_a2.restype = I32
@@ -111,7 +111,7 @@ def num_threads() -> int:
 @dataclass
 class Params:
     """Method parameters (the oracle's own copy; mirrors the library's struct)."""
-    mac: int = 1               # 0 opening angle (Eq. 2), 1 acceleration (Eq. 5)
+    mac: int = 1               # 0 opening angle (Eq. 2), 1 acceleration (Eq. 5), 2 multipole (Warren-Salmon)
     theta: float = 0.5         # opening angle; also the bootstrap pass's angle
     delta_acc: float = 2.0 ** -7
     eps: float = 1.0 / 64.0
@@ -186,16 +186,18 @@ def build_tree(skey: np.ndarray, leaf_max: int, cap: int | None = None) -> dict:
             "level": level[:nn].copy(), "parent": parent[:nn].copy(), "level_start": lstart}
 
 
-def pseudo_j(tree: dict, sp4: np.ndarray):
+def pseudo_j(tree: dict, sp4: np.ndarray, with_b2: bool = False):
+    """(jpos, bj), or (jpos, bj, b2) with the second moments B_2 of the multipole MAC."""
     sp4 = _c(sp4, np.float32)
     nn = tree["n_nodes"]
     jpos = np.zeros((nn, 4), np.float32)
     bj = np.zeros(nn, np.float32)
+    b2 = np.zeros(nn, np.float32) if with_b2 else None
     rc = lib().or_pseudo_j(nn, _p(tree["first"]), _p(tree["count"]), _p(tree["child"]),
-                           _p(tree["nchild"]), _p(sp4), _p(jpos), _p(bj))
+                           _p(tree["nchild"]), _p(sp4), _p(jpos), _p(bj), _p(b2))
     if rc != 0:
         raise MemoryError("oracle pseudo_j")
-    return jpos, bj
+    return (jpos, bj, b2) if with_b2 else (jpos, bj)
 
 
 def active_prefix(n: int, active) -> np.ndarray:
@@ -238,8 +240,11 @@ def groups(starts, active, sp4: np.ndarray, aold=None, sphere: int = 0):
 
 
 def walk(tree: dict, jpos, bj, sp4, active, starts, gI, gamin, mac: int, theta: float,
-         delta_acc: float, eps: float, G: float, group_ids=None):
-    """Tree walk for the listed groups (all if None).  Returns (acc, inter, ntest)."""
+         delta_acc: float, eps: float, G: float, group_ids=None, b2=None):
+    """Tree walk for the listed groups (all if None).  Returns (acc, inter, ntest).
+    mac 2 (multipole) needs b2 and takes Delta_mul in delta_acc."""
+    if mac == 2 and b2 is None:
+        raise ValueError("the multipole MAC needs the B_2 moments")
     active = _c(active, np.uint32)
     starts = _c(starts, np.uint32)
     sp4 = _c(sp4, np.float32)
@@ -254,7 +259,7 @@ def walk(tree: dict, jpos, bj, sp4, active, starts, gI, gamin, mac: int, theta: 
                        _p(tree["first"]), _p(tree["count"]), _p(tree["child"]), _p(tree["nchild"]),
                        _p(sp4), na, _p(active), _p(starts), _p(_c(gI, np.float32)),
                        _p(_c(gamin, np.float32)), int(mac), f32(theta), f32(delta_acc), f32(eps),
-                       f32(G), n_eval, _p(gids), _p(acc), _p(inter), _p(ntest))
+                       f32(G), n_eval, _p(gids), _p(None if b2 is None else _c(b2, np.float32)), _p(acc), _p(inter), _p(ntest))
     if rc != 0:
         raise MemoryError("oracle walk")
     return acc, inter, ntest
@@ -318,11 +323,12 @@ def morton3(qx: int, qy: int, qz: int) -> int:
     return int(lib().or_morton3(qx, qy, qz))
 
 
-def mac_accept(mac: int, theta: float, delta_acc: float, amin: float, G: float, gI, jpos, bJ) -> bool:
+def mac_accept(mac: int, theta: float, delta_acc: float, amin: float, G: float, gI, jpos, bJ,
+               B2: float = 0.0) -> bool:
     gi = _c(gI, np.float32)
     jp = _c(jpos, np.float32)
     return bool(lib().or_mac_accept(int(mac), f32(theta), f32(delta_acc), f32(amin), f32(G),
-                                    _p(gi), _p(jp), f32(bJ)))
+                                    _p(gi), _p(jp), f32(bJ), f32(B2)))
 
 
 def level_from_a2(a2: float, eta: float, eps: float, M: int, L: int) -> int:
@@ -345,18 +351,18 @@ def tree_force(p4: np.ndarray, prm: Params, aold=None, active=None, mac=None, th
     order, skey = sort(key)
     sp4 = p4[order]
     tree = build_tree(skey, prm.leaf_max)
-    jpos, bj = pseudo_j(tree, sp4)
+    m = prm.mac if mac is None else mac
+    jpos, bj, b2 = pseudo_j(tree, sp4, with_b2=True)
     if active is None:
         active = np.arange(n, dtype=np.uint32)
     saold = None if aold is None else _c(aold, np.float32)[order]
     starts = group_starts(tree, n, active, prm.group_max, prm.group_mode, bj, prm.r_crit)
     gI, gamin = groups(starts, active, sp4, saold, prm.sphere)
-    m = prm.mac if mac is None else mac
     th = prm.theta if theta is None else theta
     acc, inter, ntest = walk(tree, jpos, bj, sp4, active, starts, gI, gamin, m, th,
-                             prm.delta_acc, prm.eps, prm.G, group_ids)
+                             prm.delta_acc, prm.eps, prm.G, group_ids, b2)
     return {"key": key, "box": box, "order": order, "skey": skey, "sp4": sp4, "tree": tree,
-            "jpos": jpos, "bj": bj, "active": active, "starts": starts, "gI": gI, "gamin": gamin,
+            "jpos": jpos, "bj": bj, "b2": b2, "active": active, "starts": starts, "gI": gI, "gamin": gamin,
             "acc": acc, "inter": inter, "ntest": ntest}
 
 
@@ -452,12 +458,12 @@ class BlockStepSim:
         else:
             order = np.arange(self.n, dtype=np.uint32)
             sp4, tree, skey = p4, self.tree, self.skey
-        jpos, bj = pseudo_j(tree, sp4)
+        jpos, bj, b2 = pseudo_j(tree, sp4, with_b2=True)
         active = np.nonzero(self.t0 + self.ticks(self.level) == T)[0].astype(np.uint32)
         starts = group_starts(tree, self.n, active, prm.group_max, prm.group_mode, bj, prm.r_crit)
         gI, gamin = groups(starts, active, sp4, self.aold, prm.sphere)
         acc, inter, _ = walk(tree, jpos, bj, sp4, active, starts, gI, gamin, prm.mac,
-                             prm.theta, prm.delta_acc, prm.eps, prm.G)
+                             prm.theta, prm.delta_acc, prm.eps, prm.G, b2=b2)
         acc32 = acc.astype(np.float32)
         correct(active, acc32, T, self.dt_max, self.M, self.L, prm.eta, prm.eps, self.r0,
                 self.vh, self.t0, self.level, self.aold, self.acc)

@@ -41,8 +41,6 @@ int or_num_threads(void) {
  * still holds every particle (Sec. 2.1 asks only for a sphere that contains them). */
 #define RADIUS_MARGIN (1.0f + 0x1p-20f)
 
-static float norm3f(float dx, float dy, float dz) { return sqrtf((dx * dx + dy * dy) + dz * dz); }
-
 /* ------------------------------------------------------------------------- */
 /* O1. Direct summation, Eq. (1): a_i = sum_{j != i} G m_j (r_j - r_i) /     */
 /* (|r_j - r_i|^2 + eps^2)^{3/2}.  The potential phi_i = -sum_{j != i} G m_j  */
@@ -219,12 +217,15 @@ int64_t or_build(int64_t n, const uint64_t *skey, int leaf_max, int64_t cap,
 /* r_J is the FP32 quotient (float)S / (float)M (the paper keeps r_J in      */
 /* single precision, Sec. 2); a cell of one particle is that particle.       */
 /* b_J (FP32): a leaf's largest |r - r_J|, a cell's largest |r_c - r_J| + b_c */
-/* over its children, times (1 + 2^-20).  Children have larger node numbers  */
-/* than parents, so a reverse sweep is bottom-up.                            */
-/* jpos out: nn x (x, y, z, m) FP32; bj out: nn FP32.                        */
+/* over its children, times (1 + 2^-20).  B_2 (the multipole MAC's second   */
+/* moment, Sec. 2.2), FP32: a leaf adds m |r - r_J|^2 over its particles, a  */
+/* cell adds B_2,c + m_c |r_c - r_J|^2 over its children (parallel axes), in */
+/* the same orders.  Children have larger node numbers than parents, so a    */
+/* reverse sweep is bottom-up.                                               */
+/* jpos out: nn x (x, y, z, m) FP32; bj out: nn FP32; b2 out: nn FP32 or NULL*/
 /* ------------------------------------------------------------------------- */
 int or_pseudo_j(int64_t nn, const uint32_t *first, const uint32_t *count, const int32_t *child,
-                const uint8_t *nchild, const float *sp4, float *jpos, float *bj) {
+                const uint8_t *nchild, const float *sp4, float *jpos, float *bj, float *b2) {
     double *sum = (double *)malloc((size_t)(nn > 0 ? nn : 1) * 4 * sizeof(double));
     if (!sum) return -1;
     for (int64_t c = nn - 1; c >= 0; c--) {
@@ -256,23 +257,28 @@ int or_pseudo_j(int64_t nn, const uint32_t *first, const uint32_t *count, const 
             jx = (float)sx / mf; jy = (float)sy / mf; jz = (float)sz / mf;
         }
         jpos[4 * c + 0] = jx; jpos[4 * c + 1] = jy; jpos[4 * c + 2] = jz; jpos[4 * c + 3] = (float)m;
-        float b = 0.0f;
+        float b = 0.0f, q = 0.0f;  /* q: B2 */
         if (child[c] < 0) {
             float d2max = 0.0f;
             for (uint32_t i = first[c]; i < first[c] + count[c]; i++) {
                 const float dx = sp4[4 * i + 0] - jx, dy = sp4[4 * i + 1] - jy, dz = sp4[4 * i + 2] - jz;
                 const float d2 = (dx * dx + dy * dy) + dz * dz;
                 if (d2 > d2max) d2max = d2;
+                q = q + sp4[4 * i + 3] * d2;
             }
             b = sqrtf(d2max);
         } else {
             for (int k = 0; k < nchild[c]; k++) {
                 const int64_t ch = child[c] + k;
-                const float e = norm3f(jpos[4 * ch + 0] - jx, jpos[4 * ch + 1] - jy, jpos[4 * ch + 2] - jz) + bj[ch];
+                const float dx = jpos[4 * ch + 0] - jx, dy = jpos[4 * ch + 1] - jy, dz = jpos[4 * ch + 2] - jz;
+                const float d2 = (dx * dx + dy * dy) + dz * dz;
+                const float e = sqrtf(d2) + bj[ch];
                 if (e > b) b = e;
+                if (b2) q = q + (b2[ch] + jpos[4 * ch + 3] * d2);
             }
         }
         bj[c] = b * RADIUS_MARGIN;
+        if (b2) b2[c] = q;
     }
     free(sum);
     return 0;
@@ -433,10 +439,13 @@ void or_groups(int64_t ng, const uint32_t *starts, const uint32_t *active, const
 /*   mac 1, acceleration (Eq. 5):    d >= (G m_J b_J^2 / (D_acc |a_old|))^1/4 */
 /*          evaluated as  d^4 (D_acc |a_old|) >= (G m_J) (b_J b_J),          */
 /*          with d^4 = (d d)(d d) and D_acc |a_old| precomputed per group.   */
+/*   mac 2, multipole (Warren & Salmon, Sec. 2.2):                           */
+/*          d >= b_J/2 + sqrt(b_J^2/4 + sqrt(3 B_2 / D_mul)), B_2 = sum over   */
+/*          the cell of m |r - r_J|^2; D_mul is passed in delta_acc.         */
 /* Equality accepts, as the printed inequalities do.                         */
 /* ------------------------------------------------------------------------- */
-static int mac_accept(int mac, float theta, float dacc_amin, float G, const float *gI,
-                      float jx, float jy, float jz, float mJ, float bJ) {
+static int mac_accept(int mac, float theta, float dacc_amin, float delta, float G, const float *gI,
+                      float jx, float jy, float jz, float mJ, float bJ, float B2) {
     const float dx = jx - gI[0];
     const float dy = jy - gI[1];
     const float dz = jz - gI[2];
@@ -445,6 +454,7 @@ static int mac_accept(int mac, float theta, float dacc_amin, float G, const floa
     const float bI = gI[3];
     const float d = (bI < r) ? (r - bI) : 0.0f;
     if (mac == 0) return bJ <= theta * d;
+    if (mac == 2) return d >= 0.5f * bJ + sqrtf((0.25f * bJ) * bJ + sqrtf((3.0f * B2) / delta));
     const float d2 = d * d;
     const float lhs = (d2 * d2) * dacc_amin;
     const float rhs = (G * mJ) * (bJ * bJ);
@@ -472,7 +482,7 @@ int or_walk(int64_t nn, const float *jpos, const float *bj, const uint32_t *firs
             const uint32_t *count, const int32_t *child, const uint8_t *nchild,
             const float *sp4, int64_t n_active, const uint32_t *active, const uint32_t *starts,
             const float *gI, const float *gamin, int mac, float theta, float delta_acc,
-            float eps, float G, int64_t n_eval, const int64_t *groups,
+            float eps, float G, int64_t n_eval, const int64_t *groups, const float *b2,
             double *acc, int64_t *inter, int64_t *ntest) {
     if (nn == 0 || n_active == 0) return 0;
     int fail = 0;
@@ -496,8 +506,8 @@ int or_walk(int64_t nn, const float *jpos, const float *bj, const uint32_t *firs
             while (head < tail) {
                 const int32_t c = q[head++];
                 tests++;
-                if (mac_accept(mac, theta, dacc_amin, G, gi, jpos[4 * c + 0], jpos[4 * c + 1],
-                               jpos[4 * c + 2], jpos[4 * c + 3], bj[c])) {
+                if (mac_accept(mac, theta, dacc_amin, delta_acc, G, gi, jpos[4 * c + 0], jpos[4 * c + 1],
+                               jpos[4 * c + 2], jpos[4 * c + 3], bj[c], b2 ? b2[c] : 0.0f)) {
                     if (nl + 1 > lcap) {
                         lcap *= 2;
                         list = (float *)realloc(list, (size_t)lcap * 4 * sizeof(float));
@@ -693,8 +703,8 @@ void or_correct(int64_t n_active, const uint32_t *active, const float *acc4, int
 uint64_t or_morton3(uint64_t qx, uint64_t qy, uint64_t qz) { return interleave3(qx, qy, qz); }
 
 int or_mac_accept(int mac, float theta, float delta_acc, float amin, float G, const float *gI,
-                  const float *jp, float bJ) {
-    return mac_accept(mac, theta, delta_acc * amin, G, gI, jp[0], jp[1], jp[2], jp[3], bJ);
+                  const float *jp, float bJ, float B2) {
+    return mac_accept(mac, theta, delta_acc * amin, delta_acc, G, gI, jp[0], jp[1], jp[2], jp[3], bJ, B2);
 }
 
 int or_level_from_a2(double a2, double eta, double eps, int M, int L) {

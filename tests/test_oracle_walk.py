@@ -308,3 +308,53 @@ def test_ebs_and_geo_spheres_against_the_smallest_ball(oracle_lib):
             assert d.max() <= gI[g, 3]
             ratios.append(gI[g, 3] / _seb_radius(pts))
         assert min(ratios) >= 0.999 and np.median(ratios) < 1.2 and max(ratios) < 1.6, (sphere, ratios)
+
+
+# ---------------------------------------------------------------- multipole MAC (Sec. 2.2)
+def test_b2_moments_match_their_definition(oracle_lib):
+    """B_2 of every cell equals sum over its particles of m |r - r_J|^2 (FP64 reference);
+    the cell value is built from its children by parallel axes."""
+    O = oracle_lib
+    n = 4096
+    sp4, tree = _sorted_tree(O, n, 9)
+    jpos, bj, b2 = O.pseudo_j(tree, sp4, with_b2=True)
+    assert np.all(b2 >= 0)
+    pts = sp4[:, :3].astype(np.float64)
+    m = sp4[:, 3].astype(np.float64)
+    for c in range(tree["n_nodes"]):
+        f, k = int(tree["first"][c]), int(tree["count"][c])
+        ref = (m[f:f + k] * ((pts[f:f + k] - jpos[c, :3].astype(np.float64)) ** 2).sum(1)).sum()
+        if k == 1:
+            assert b2[c] == 0.0
+        else:
+            assert abs(b2[c] - ref) <= 1e-4 * ref + 1e-30, (c, b2[c], ref)
+
+
+def test_multipole_mac_boundary_cases(oracle_lib):
+    O = oracle_lib
+    gI = np.array([0.0, 0.0, 0.0, 0.0], np.float32)
+    # b_J = 2, B_2 = 1, Delta_mul = 3: threshold 1 + sqrt(1 + 1) = 2.41421356...
+    thr = 1.0 + np.sqrt(1.0 + np.sqrt(3.0 * 1.0 / 3.0))
+    far = np.array([np.float32(thr) * 1.001, 0, 0, 1.0], np.float32)
+    near = np.array([np.float32(thr) * 0.999, 0, 0, 1.0], np.float32)
+    assert O.mac_accept(2, 0.5, 3.0, 1.0, 1.0, gI, far, 2.0, 1.0)
+    assert not O.mac_accept(2, 0.5, 3.0, 1.0, 1.0, gI, near, 2.0, 1.0)
+    # a point mass (b_J = 0, B_2 = 0) is accepted at any distance, even inside b_I = 0
+    assert O.mac_accept(2, 0.5, 1e-6, 1.0, 1.0, gI, np.array([1e-3, 0, 0, 1.0], np.float32), 0.0, 0.0)
+
+
+def test_multipole_mac_limits(oracle_lib):
+    """Delta_mul -> 0 opens every cell with B_2 > 0: direct summation; the error falls
+    monotonically as Delta_mul decreases."""
+    O, p4, prm = _acc(oracle_lib, 2048, seed=6, kind="nfw", delta_acc=1e-30)
+    r = O.tree_force(p4, prm, mac=2)
+    d = O.direct(p4, prm.eps)[r["order"]]
+    np.testing.assert_allclose(r["acc"], d, rtol=1e-12, atol=1e-12)
+    O, p4, prm = _acc(oracle_lib, 4096, seed=3, kind="nfw")
+    d = O.direct(p4, prm.eps)
+    meds = []
+    for k in (2, 6, 10, 14):
+        prm.delta_acc = 2.0 ** -k
+        r = O.tree_force(p4, prm, mac=2)
+        meds.append(np.median(_rel(r["acc"], d[r["order"]])))
+    assert all(meds[i + 1] < meds[i] for i in range(len(meds) - 1)), meds
