@@ -57,6 +57,10 @@ extern "C" {
 #define GT_MAC_OPENING_ANGLE 0 /* Eq. (2), Barnes & Hut 1986: b_J / d <= theta   */
 #define GT_MAC_ACCELERATION 1  /* Eq. (5), Springel 2005: d >= (G m_J b_J^2 /
                                   (Delta_acc |a_old|))^(1/4)                    */
+#define GT_MAC_MULTIPOLE 2     /* Warren & Salmon 1993 (Sec. 2.2): d >= b_J/2 +
+                                  sqrt(b_J^2/4 + sqrt(3 B_2 / Delta_mul)), B_2 =
+                                  sum of m |r - r_J|^2 over the cell; Delta_mul is
+                                  taken from delta_acc                          */
 
 typedef struct CUstream_st *gt_stream; /* identical to cudaStream_t */
 

@@ -33,7 +33,9 @@ bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 int check_params(const gt_params *p) {
     if (!p) return GT_EINVAL;
-    if (p->mac != GT_MAC_OPENING_ANGLE && p->mac != GT_MAC_ACCELERATION) return GT_EINVAL;
+    if (p->mac != GT_MAC_OPENING_ANGLE && p->mac != GT_MAC_ACCELERATION && p->mac != GT_MAC_MULTIPOLE)
+        return GT_EINVAL;
+    if (p->mac == GT_MAC_MULTIPOLE && !(p->delta_acc > 0.0f)) return GT_EINVAL;  // Delta_mul
     if (p->leaf_max < 1) return GT_EINVAL;
     if (p->ij_share != 0 && (!pow2(p->ij_share) || p->ij_share > 32)) return GT_EINVAL;
     // up to 32 members with ij_share lanes each, or up to 64 with one lane per two members

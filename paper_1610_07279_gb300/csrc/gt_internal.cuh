@@ -76,8 +76,9 @@ struct Nodes {
     uint32_t *nchild;
     int32_t *parent;
     float4 *jpos;              // pseudo j-particle (x, y, z, m) FP32
-    float4 *walk;              // (b_J, link0, link1, 0): link0 = first child or first particle,
-                               // link1 = nchild, or count | GT_LEAF_FLAG for a leaf
+    float4 *walk;              // (b_J, link0, link1, B_2): link0 = first child or first particle,
+                               // link1 = nchild, or count | GT_LEAF_FLAG for a leaf; B_2 the
+                               // second moment of the multipole MAC
     DSum4 *sum;                // FP64 (m, m x, m y, m z)
     uint32_t *cells;           // every node once: the leaves bucketed by particle count, then
                                // the cells with children by level (deepest last) and, inside

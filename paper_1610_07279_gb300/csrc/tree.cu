@@ -249,16 +249,17 @@ __global__ __launch_bounds__(256) void k_pseudo_leaves(Nodes nd, const float4 *_
             jy = __fdiv_rn(d2f(sy), mf);
             jz = __fdiv_rn(d2f(sz), mf);
         }
-        float d2max = 0.0f;
+        float d2max = 0.0f, b2 = 0.0f;  // b2: B_2 of the multipole MAC
         for (uint32_t i = f; i < f + k; i++) {
             const float4 p = posm[i];
             const float d2 = sq3f(__fsub_rn(p.x, jx), __fsub_rn(p.y, jy), __fsub_rn(p.z, jz));
             if (d2 > d2max) d2max = d2;
+            b2 = __fadd_rn(b2, __fmul_rn(p.w, d2));
         }
         nd.sum[c] = DSum4{m, sx, sy, sz};
         nd.jpos[c] = make_float4(jx, jy, jz, d2f(m));
         nd.walk[c] = make_float4(__fmul_rn(__fsqrt_rn(d2max), GT_RADIUS_MARGIN), __uint_as_float(f),
-                                 __uint_as_float(k | GT_LEAF_FLAG), 0.0f);
+                                 __uint_as_float(k | GT_LEAF_FLAG), b2);
     }
 }
 
@@ -330,18 +331,19 @@ __global__ __launch_bounds__(PL) void k_pseudo_levels(Nodes nd, DevCtl *ctl) {
             const float jx = __fdiv_rn(d2f(sx), mf);
             const float jy = __fdiv_rn(d2f(sy), mf);
             const float jz = __fdiv_rn(d2f(sz), mf);
-            float b = 0.0f;
+            float b = 0.0f, b2 = 0.0f;  // b2: B_2 by parallel axes
             for (uint32_t q = 0; q < nch; q++) {
                 const float4 cj = __ldcg(&nd.jpos[ch0 + q]);
-                const float bc = __ldcg(&nd.walk[ch0 + q]).x;
-                const float e = __fadd_rn(__fsqrt_rn(sq3f(__fsub_rn(cj.x, jx), __fsub_rn(cj.y, jy),
-                                                          __fsub_rn(cj.z, jz))), bc);
+                const float4 cw = __ldcg(&nd.walk[ch0 + q]);
+                const float d2 = sq3f(__fsub_rn(cj.x, jx), __fsub_rn(cj.y, jy), __fsub_rn(cj.z, jz));
+                const float e = __fadd_rn(__fsqrt_rn(d2), cw.x);
                 if (e > b) b = e;
+                b2 = __fadd_rn(b2, __fadd_rn(cw.w, __fmul_rn(cj.w, d2)));
             }
             nd.sum[p] = DSum4{m, sx, sy, sz};
             nd.jpos[p] = make_float4(jx, jy, jz, mf);
             nd.walk[p] = make_float4(__fmul_rn(b, GT_RADIUS_MARGIN), __uint_as_float((uint32_t)ch0),
-                                     __uint_as_float(nch), 0.0f);
+                                     __uint_as_float(nch), b2);
         }
         __threadfence();  // every thread's cell is visible device-wide before the chunk counts as done
         __syncthreads();

@@ -39,8 +39,8 @@ constexpr int FLUSH_AT = 256;     // flush once the list holds this many
 // 8 children each grows the queue by <= 224 per tree level, <= ~22 x 256 in all.
 constexpr int LIFO_ROOM = 6144;
 
-__device__ __forceinline__ bool mac_accept(int mac, float theta, float dacc_amin, float G, float cx,
-                                           float cy, float cz, float bI, float4 jp, float bJ) {
+__device__ __forceinline__ bool mac_accept(int mac, float theta, float dacc_amin, float delta, float G, float cx,
+                                           float cy, float cz, float bI, float4 jp, float bJ, float B2) {
     const float dx = __fsub_rn(jp.x, cx);
     const float dy = __fsub_rn(jp.y, cy);
     const float dz = __fsub_rn(jp.z, cz);
@@ -48,6 +48,10 @@ __device__ __forceinline__ bool mac_accept(int mac, float theta, float dacc_amin
     const float r = __fsqrt_rn(r2);
     const float d = (bI < r) ? __fsub_rn(r, bI) : 0.0f;   // lambda r_JI, Eqs. (6)-(7)
     if (mac == GT_MAC_OPENING_ANGLE) return bJ <= __fmul_rn(theta, d);  // Eq. (2)
+    if (mac == GT_MAC_MULTIPOLE)  // Warren & Salmon: d >= b/2 + sqrt(b^2/4 + sqrt(3 B_2 / Delta_mul))
+        return d >= __fadd_rn(__fmul_rn(0.5f, bJ),
+                              __fsqrt_rn(__fadd_rn(__fmul_rn(__fmul_rn(0.25f, bJ), bJ),
+                                                   __fsqrt_rn(__fdiv_rn(__fmul_rn(3.0f, B2), delta)))));
     const float d2 = __fmul_rn(d, d);                                   // Eq. (5), raised to the 4th power
     return __fmul_rn(__fmul_rn(d2, d2), dacc_amin) >= __fmul_rn(__fmul_rn(G, jp.w), __fmul_rn(bJ, bJ));
 }
@@ -292,7 +296,8 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
             wk = a.walk[node];
         }
         n_tests += nb;
-        const bool ok = valid && mac_accept(a.mac, a.theta, dacc_amin, a.G, cx, cy, cz, bI, jp, wk.x);
+        const bool ok = valid && mac_accept(a.mac, a.theta, dacc_amin, a.delta_acc, a.G, cx, cy, cz, bI, jp,
+                                            wk.x, wk.w);
         const uint32_t l0 = __float_as_uint(wk.y), l1 = __float_as_uint(wk.z);
         const bool leaf = (l1 & GT_LEAF_FLAG) != 0u;
         // accepted cells -> list

@@ -29,6 +29,7 @@ GT_ENOTIMPL = -8
 GT_ESTATE = -9
 GT_MAC_OPENING_ANGLE = 0
 GT_MAC_ACCELERATION = 1
+GT_MAC_MULTIPOLE = 2
 
 
 class gt_params(C.Structure):

@@ -317,6 +317,13 @@ def test_walk_ebs_pseudo_particle(env, S, gmax, frac):
                group_mode=g.GT_GROUP_CELLS | g.GT_SPHERE_EBS)
 
 
+@pytest.mark.parametrize("S,gmax,dmul,frac", [(0, 32, 2.0 ** -6, None), (0, 64, 2.0 ** -10, None),
+                                              (2, 16, 2.0 ** -4, 0.2)])
+def test_walk_multipole_mac(env, S, gmax, dmul, frac):
+    """Sec. 2.2: Warren & Salmon's MAC with the B_2 moments of the pseudo j-particles."""
+    _walk_case(env, "plummer", 1 << 13, 3, 2, S, gmax, active_frac=frac, delta_acc=dmul)
+
+
 def test_group_max_limits(env):
     torch, g, O = env
     for S, gmax, ok in [(0, 64, True), (1, 64, True), (0, 65, False), (2, 16, True), (2, 17, False)]:
