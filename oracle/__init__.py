@@ -89,6 +89,9 @@ def _declare(L):
     L.or_correct.argtypes = [I64, P, P, I64, D, I32, I32, D, D, P, P, P, P, P, P]
     L.or_morton3.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
     L.or_morton3.restype = C.c_uint64
+    L.or_hilbert3.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
+    L.or_hilbert3.restype = C.c_uint64
+    L.or_keys_curve.argtypes = [I64, P, P, P, I32]
     L.or_mac_accept.argtypes = [I32, F, F, F, F, P, P, F, F]
     L.or_mac_accept.restype = I32
     L.or_level_from_a2.argtypes = [D, D, D, I32, I32]
@@ -125,6 +128,7 @@ class Params:
     r_crit: float = 0.0        # critical separation of a group cell's radius (Sec. 2.4); <= 0: none
     rebuild_every: int = 1     # block steps per tree build (Sec. 2.6); the topology is kept between
     sphere: int = 0            # pseudo i-particle: 0 GEO, 1 Ritter's efficient bounding sphere (App. B)
+    key_curve: int = 0         # 0 Morton, 1 Peano-Hilbert (Sec. 2.1, App. A)
 
 
 def f32(x):
@@ -146,12 +150,13 @@ def direct(p4: np.ndarray, eps: float, G: float = 1.0, idx=None) -> np.ndarray:
     return out
 
 
-def keys(p4: np.ndarray):
+def keys(p4: np.ndarray, curve: int = 0):
+    """63-bit keys of the quantised positions: curve 0 Morton, 1 Peano-Hilbert."""
     p4 = _c(p4, np.float32)
     n = p4.shape[0]
     key = np.zeros(n, np.uint64)
     box = np.zeros(5, np.float64)
-    lib().or_keys(n, _p(p4), _p(key), _p(box))
+    lib().or_keys_curve(n, _p(p4), _p(key), _p(box), int(curve))
     return key, box
 
 
@@ -319,6 +324,10 @@ def correct(active, acc4, T, dt_max, M, L, eta, eps, r0, vh, t0, level, aold, ac
                      _p(acc_store))
 
 
+def hilbert3(qx: int, qy: int, qz: int) -> int:
+    return int(lib().or_hilbert3(qx, qy, qz))
+
+
 def morton3(qx: int, qy: int, qz: int) -> int:
     return int(lib().or_morton3(qx, qy, qz))
 
@@ -347,7 +356,7 @@ def tree_force(p4: np.ndarray, prm: Params, aold=None, active=None, mac=None, th
     """
     p4 = _c(p4, np.float32)
     n = p4.shape[0]
-    key, box = keys(p4)
+    key, box = keys(p4, prm.key_curve)
     order, skey = sort(key)
     sp4 = p4[order]
     tree = build_tree(skey, prm.leaf_max)
@@ -449,7 +458,7 @@ class BlockStepSim:
         dt_min = float(np.ldexp(self.dt_max, -(self.L - 1)))
         p4 = predict(self.r0, self.vh, self.t0, self.mass, T, dt_min)
         if self.steps % max(1, int(prm.rebuild_every)) == 0 or getattr(self, "tree", None) is None:
-            key, _ = keys(p4)
+            key, _ = keys(p4, prm.key_curve)
             order, skey = sort(key)
             self._permute(order)
             sp4 = np.ascontiguousarray(p4[order])

@@ -98,7 +98,47 @@ static uint64_t interleave3(uint64_t qx, uint64_t qy, uint64_t qz) {
     return key;
 }
 
+void or_keys_curve(int64_t n, const float *p4, uint64_t *key, double *box, int curve);
+
+/* Peano-Hilbert index (Sec. 2.1, Appendix A: the paper's key curve), by Skilling's  */
+/* transpose method (Skilling 2004): the three 21-bit integers are turned into the   */
+/* "transposed" Hilbert index -- undo the rotations and reflections from the top bit */
+/* down, then a Gray code across the axes -- whose bits, interleaved with axis 0 as  */
+/* the most significant of every triplet, are the index.  As for Morton keys, the    */
+/* first 3l bits name the level-l cube, so cells are contiguous key ranges.          */
+static void hilbert_transpose(uint32_t x[3], int bits) {
+    const uint32_t top = 1u << (bits - 1);
+    for (uint32_t q = top; q > 1; q >>= 1) {
+        const uint32_t p = q - 1;
+        for (int i = 0; i < 3; i++) {
+            if (x[i] & q) {
+                x[0] ^= p;                          /* reflect */
+            } else {
+                const uint32_t t = (x[0] ^ x[i]) & p; /* swap the low bits of axes 0 and i */
+                x[0] ^= t;
+                x[i] ^= t;
+            }
+        }
+    }
+    x[1] ^= x[0];
+    x[2] ^= x[1];
+    uint32_t t = 0;
+    for (uint32_t q = top; q > 1; q >>= 1)
+        if (x[2] & q) t ^= q - 1;
+    for (int i = 0; i < 3; i++) x[i] ^= t;
+}
+
 void or_keys(int64_t n, const float *p4, uint64_t *key, double *box) {
+    or_keys_curve(n, p4, key, box, 0);
+}
+
+uint64_t or_hilbert3(uint64_t qx, uint64_t qy, uint64_t qz) {
+    uint32_t x[3] = {(uint32_t)qx, (uint32_t)qy, (uint32_t)qz};
+    hilbert_transpose(x, KEY_LEVELS);
+    return interleave3(x[0], x[1], x[2]);
+}
+
+void or_keys_curve(int64_t n, const float *p4, uint64_t *key, double *box, int curve) {
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int64_t i = 0; i < n; i++)
         for (int a = 0; a < 3; a++) {
@@ -130,7 +170,13 @@ void or_keys(int64_t n, const float *p4, uint64_t *key, double *box) {
                 if (t > qmax) t = qmax;
                 q[a] = (uint64_t)t;
             }
-        key[i] = interleave3(q[0], q[1], q[2]);
+        if (curve == 1) {
+            uint32_t x[3] = {(uint32_t)q[0], (uint32_t)q[1], (uint32_t)q[2]};
+            hilbert_transpose(x, KEY_LEVELS);
+            key[i] = interleave3(x[0], x[1], x[2]);
+        } else {
+            key[i] = interleave3(q[0], q[1], q[2]);
+        }
     }
 }
 
