@@ -103,7 +103,15 @@ typedef struct gt_params {
                            block step (the coarsest active level), minimising the walk
                            time per active particle (gt_block_step with the automatic
                            rebuild interval only; elsewhere |r_crit| is used)       */
+    int32_t key_curve;  /* GT_KEY_MORTON (default) or GT_KEY_HILBERT (Sec. 2.1, App. A:
+                           the paper's Peano-Hilbert order); either way the first 3l bits
+                           of a key name the level-l cube, so the tree holds the same
+                           cells                                                    */
+    int32_t reserved2;
 } gt_params;
+
+#define GT_KEY_MORTON 0
+#define GT_KEY_HILBERT 1
 
 #define GT_GROUP_RUNS 0
 #define GT_GROUP_CELLS 1

@@ -53,6 +53,7 @@ int check_params(const gt_params *p) {
         if (frexp(p->dt_max, &e) != 0.5) return GT_EINVAL;  // must be a power of two
     }
     if (!std::isfinite(p->r_crit)) return GT_EINVAL;
+    if (p->key_curve != GT_KEY_MORTON && p->key_curve != GT_KEY_HILBERT) return GT_EINVAL;
     return GT_OK;
 }
 
@@ -285,7 +286,7 @@ void build_tree(gt_system *s, cudaStream_t st, const float4 *posm_src) {
     gt_launch_prepare(s->ctl, 0, st);
     ph_begin(s, PH_SORT, st);
     gt_launch_bbox(posm_src, n, s->bbox_partial, s->bbox_blocks, s->ctl, st);
-    gt_launch_keys(posm_src, n, s->ctl, s->sb.key[0], s->sb.val[0], st);
+    gt_launch_keys(posm_src, n, s->ctl, s->prm.key_curve, s->sb.key[0], s->sb.val[0], st);
     gt_launch_sort(s->sb, n, s->ctl, st);
     ph_end(s, PH_SORT, st);
     ph_begin(s, PH_PERMUTE, st);

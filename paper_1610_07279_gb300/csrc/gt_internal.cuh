@@ -237,7 +237,7 @@ struct SortBufs {
 // keys.cu
 void gt_launch_bbox(const float4 *posm, int64_t n, float *partial, int nblk, DevCtl *ctl,
                     cudaStream_t st);
-void gt_launch_keys(const float4 *posm, int64_t n, const DevCtl *ctl, uint64_t *key, uint32_t *idx,
+void gt_launch_keys(const float4 *posm, int64_t n, const DevCtl *ctl, int curve, uint64_t *key, uint32_t *idx,
                     cudaStream_t st);
 // sort.cu: sorts (key, val) in buffers 0; result in buffers 0 (even passes).
 int gt_sort_tiles(int64_t n);

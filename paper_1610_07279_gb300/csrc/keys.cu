@@ -93,8 +93,31 @@ __device__ __forceinline__ unsigned long long quantise(float x, double xmin, dou
     return q < QMAX ? q : QMAX;
 }
 
+// Peano-Hilbert order (Sec. 2.1, App. A), Skilling's transpose method on the three
+// 21-bit integers: the rotations and reflections are undone from the top bit down, a
+// Gray code runs across the axes, and the transposed bits are interleaved like a Morton
+// key (axis 0 the most significant of every triplet).
+__device__ __forceinline__ void hilbert_transpose(uint32_t &x0, uint32_t &x1, uint32_t &x2) {
+#pragma unroll 4
+    for (uint32_t q = 1u << (GT_KEY_LEVELS - 1); q > 1u; q >>= 1) {
+        const uint32_t p = q - 1u;
+        if (x0 & q) x0 ^= p;  // axis 0 against itself: a reflection or nothing
+        if (x1 & q) { x0 ^= p; } else { const uint32_t t = (x0 ^ x1) & p; x0 ^= t; x1 ^= t; }
+        if (x2 & q) { x0 ^= p; } else { const uint32_t t = (x0 ^ x2) & p; x0 ^= t; x2 ^= t; }
+    }
+    x1 ^= x0;
+    x2 ^= x1;
+    uint32_t t = 0u;
+#pragma unroll 4
+    for (uint32_t q = 1u << (GT_KEY_LEVELS - 1); q > 1u; q >>= 1)
+        if (x2 & q) t ^= q - 1u;
+    x0 ^= t;
+    x1 ^= t;
+    x2 ^= t;
+}
+
 __global__ __launch_bounds__(256) void k_keys(const float4 *__restrict__ posm, long long n,
-                                              const DevCtl *__restrict__ ctl,
+                                              const DevCtl *__restrict__ ctl, int curve,
                                               unsigned long long *__restrict__ key,
                                               uint32_t *__restrict__ idx) {
     const long long i = blockIdx.x * 256ll + threadIdx.x;
@@ -106,7 +129,13 @@ __global__ __launch_bounds__(256) void k_keys(const float4 *__restrict__ posm, l
         const unsigned long long qx = quantise(p.x, f2d(ctl->bbox_min[0]), scale);
         const unsigned long long qy = quantise(p.y, f2d(ctl->bbox_min[1]), scale);
         const unsigned long long qz = quantise(p.z, f2d(ctl->bbox_min[2]), scale);
-        k = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+        if (curve == GT_KEY_HILBERT) {
+            uint32_t x0 = (uint32_t)qx, x1 = (uint32_t)qy, x2 = (uint32_t)qz;
+            hilbert_transpose(x0, x1, x2);
+            k = (spread3(x0) << 2) | (spread3(x1) << 1) | spread3(x2);
+        } else {
+            k = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+        }
     }
     key[i] = k;
     idx[i] = (uint32_t)i;
@@ -120,8 +149,8 @@ void gt_launch_bbox(const float4 *posm, int64_t n, float *partial, int nblk, Dev
     { k_bbox_final<<<1, 32, 0, st>>>(partial, nblk, n, ctl); gt_note_launches(1); }
 }
 
-void gt_launch_keys(const float4 *posm, int64_t n, const DevCtl *ctl, uint64_t *key, uint32_t *idx,
+void gt_launch_keys(const float4 *posm, int64_t n, const DevCtl *ctl, int curve, uint64_t *key, uint32_t *idx,
                     cudaStream_t st) {
     if (n <= 0) return;
-    { k_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(posm, n, ctl, (unsigned long long *)key, idx); gt_note_launches(1); }
+    { k_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(posm, n, ctl, curve, (unsigned long long *)key, idx); gt_note_launches(1); }
 }

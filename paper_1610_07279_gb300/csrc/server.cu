@@ -17,7 +17,7 @@
 
 #include "gt_system.cuh"
 
-static_assert(sizeof(gt_request) == 112 && sizeof(gt_server_stats) == 64, "serving structs of the ABI");
+static_assert(sizeof(gt_request) == 120 && sizeof(gt_server_stats) == 64, "serving structs of the ABI");
 
 namespace {
 

@@ -30,6 +30,7 @@ GT_ESTATE = -9
 GT_MAC_OPENING_ANGLE = 0
 GT_MAC_ACCELERATION = 1
 GT_MAC_MULTIPOLE = 2
+GT_KEY_MORTON, GT_KEY_HILBERT = 0, 1
 
 
 class gt_params(C.Structure):
@@ -38,7 +39,7 @@ class gt_params(C.Structure):
                 ("group_max", C.c_int32), ("ij_share", C.c_int32), ("levels", C.c_int32),
                 ("rebuild_every", C.c_int32), ("walk_queue", C.c_int32), ("node_factor", C.c_int32),
                 ("eta", C.c_double), ("dt_max", C.c_double), ("group_mode", C.c_int32),
-                ("r_crit", C.c_float)]
+                ("r_crit", C.c_float), ("key_curve", C.c_int32), ("reserved2", C.c_int32)]
 
 
 GT_GROUP_RUNS = 0

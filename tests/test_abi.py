@@ -40,13 +40,14 @@ def test_binding_loads_and_strerror(libpath):
 
 def test_struct_layout_matches_header(libpath):
     from paper_1610_07279_gb300 import gothic
-    assert ctypes.sizeof(gothic.gt_params) == 72 and gothic.gt_params.node_factor.offset == 44
+    assert ctypes.sizeof(gothic.gt_params) == 80 and gothic.gt_params.node_factor.offset == 44
+    assert gothic.gt_params.key_curve.offset == 72
     assert gothic.gt_params.group_mode.offset == 64
     assert gothic.gt_params.eta.offset == 48
     assert ctypes.sizeof(gothic.gt_stats) == 96
     assert ctypes.sizeof(gothic.gt_tune_space) == 96 and ctypes.sizeof(gothic.gt_tune_result) == 2072
     assert gothic.gt_tune_result.best_ms.offset == 16 and gothic.gt_tune_space.reps.offset == 92
-    assert ctypes.sizeof(gothic.gt_request) == 112 and gothic.gt_request.nsteps.offset == 104
+    assert ctypes.sizeof(gothic.gt_request) == 120 and gothic.gt_request.nsteps.offset == 112
     assert ctypes.sizeof(gothic.gt_server_stats) == 64
 
 

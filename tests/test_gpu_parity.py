@@ -66,7 +66,8 @@ def _oparams(O, prm):
     return O.Params(mac=prm.mac, theta=prm.theta, delta_acc=prm.delta_acc, eps=prm.eps, G=prm.G,
                     leaf_max=prm.leaf_max, group_max=prm.group_max, levels=prm.levels, eta=prm.eta,
                     dt_max=prm.dt_max, group_mode=prm.group_mode & 0xff, r_crit=max(prm.r_crit, 0.0),
-                    rebuild_every=max(prm.rebuild_every, 1), sphere=1 if prm.group_mode & 0x100 else 0)
+                    rebuild_every=max(prm.rebuild_every, 1), sphere=1 if prm.group_mode & 0x100 else 0,
+                    key_curve=prm.key_curve)
 
 
 def _rel(a, r):
@@ -94,9 +95,9 @@ def _check_tree(t, ref):
     assert np.array_equal(t["bj"].view(np.uint32), ref["bj"].view(np.uint32)), "bj"
 
 
-def _oracle_tree(O, pos, mass, leaf, cap=None):
+def _oracle_tree(O, pos, mass, leaf, cap=None, curve=0):
     p4 = _p4(pos, mass)
-    key, box = O.keys(p4)
+    key, box = O.keys(p4, curve)
     order, skey = O.sort(key)
     tree = O.build_tree(skey, leaf, cap=cap)
     jpos, bj = O.pseudo_j(tree, p4[order])
@@ -130,6 +131,27 @@ def test_tree_bitexact(env, kind, n, leaf):
     assert np.array_equal(st["id"], t["order"])
     assert np.array_equal(st["pos"], pos[t["order"]])   # the permutation moved FP64 state exactly
     s.close()
+
+
+@pytest.mark.parametrize("kind,n,leaf", [("plummer", 1 << 13, 16), ("nfw", 100003, 16), ("m31", 1 << 16, 8),
+                                         ("plummer", 3, 1), ("clustered", 20000, 3)])
+def test_tree_bitexact_hilbert(env, kind, n, leaf):
+    """Sec. 2.1 / App. A: the tree over Peano-Hilbert keys, bit for bit."""
+    torch, g, O = env
+    pos, vel, mass, eps = _model(kind, n, seed=n + 1)
+    nf = 8 if kind == "clustered" else 2
+    s = g.System(n, _params(g, eps, leaf_max=leaf, node_factor=nf, key_curve=g.GT_KEY_HILBERT))
+    s.set_state(pos, vel, mass)
+    s.build_tree()
+    t = s.get_tree()
+    s.sync()
+    _check_tree(t, _oracle_tree(O, pos, mass, leaf, cap=nf * n + 2048, curve=1))
+    s.close()
+
+
+def test_walk_and_steps_on_hilbert_keys(env):
+    _walk_case(env, "nfw", 30000, 9, 1, 0, 64, key_curve=1)
+    _walk_case(env, "plummer", 1 << 13, 9, 2, 0, 32, delta_acc=2.0 ** -8, key_curve=1)
 
 
 def test_tree_node_overflow_is_reported(env):
