@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--cpu-groups", type=int, default=2048, help="groups walked by the CPU baseline sample")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-system batch workload")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
+    ap.add_argument("--no-shared", action="store_true", help="skip the shared-step comparison")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-rho", type=str, default="0.5,0.8,1.0,1.2,2.0,burst",
                     help="load levels as multiples of the serial capacity; 'burst' = all requests at t = 0")
@@ -204,6 +205,42 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
+
+
+# ------------------------------------------------------------------ block vs shared step
+def run_shared_comparison(g, torch, pos, vel, mass, eps, block_cycle_ms, block_inter, dt_max, levels,
+                          steps: int = 16):
+    """Sec. 3.3: the same model advanced with one shared step equal to the block run's
+    finest step (every particle active at every step); a cycle of the block run spans
+    2^(L-1) such steps.  The speed-up is the shared time per cycle over the block time."""
+    dt_min = dt_max / 2 ** (levels - 1)
+    prm = g.gt_default_params()
+    prm.eps = eps
+    prm.levels = 1
+    prm.dt_max = dt_min
+    s = g.System(len(mass), prm)
+    s.set_state(pos, vel, mass)
+    s.start()
+    for _ in range(4):
+        s.block_step()
+    s.sync()
+    st = torch.cuda.current_stream()
+    i0 = s.stats()["interactions"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        s.block_step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / steps
+    inter = (s.stats()["interactions"] - i0) / steps
+    s.close()
+    ticks = 2 ** (levels - 1)
+    return {"workload": "the same model with one shared step = the block run's finest step (L = 1), "
+                        "every particle active every step; one block cycle spans 2^(L-1) shared steps",
+            "shared_step_ms": step_ms, "shared_steps_per_cycle": ticks, "shared_cycle_ms": step_ms * ticks,
+            "block_cycle_ms": block_cycle_ms, "speedup_block_vs_shared": step_ms * ticks / block_cycle_ms,
+            "interactions_per_cycle": {"shared": inter * ticks, "block": block_inter}}
 
 
 # ------------------------------------------------------------------ batch workload
@@ -548,8 +585,13 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline_entry(pos, mass, eps, args.cpu_groups)
+    dt_max_run = sysm.stats()["dt_max"]
     sysm.close()
     del sysm
+    shared = None
+    if not args.no_shared:
+        shared = run_shared_comparison(g, torch, pos, vel, mass, eps, ms_max / args.steps, inter / args.steps,
+                                       dt_max_run, args.levels)
     batch = serving = None
     if not args.no_batch:
         batch = run_batch(g, torch, args.steps)
@@ -567,7 +609,7 @@ def run_ours(args):
                 "rebuilds": st1["rebuilds"] - st0["rebuilds"],
                 "interactions": inter, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "cpu_baseline": cpu, "clocks": clk, "phase_ms": breakdown,
-                "batch": batch, "serving": serving,
+                "block_vs_shared": shared, "batch": batch, "serving": serving,
                 "gflops_paper_convention": {str(f): inter_all * f / (ms_max * 1e-3) / 1e9
                                             for f in (20, 24, 28, 38)}}
         print(json.dumps(line), flush=True)
