@@ -122,6 +122,7 @@ size_t carve(gt_system *s, char *base, int64_t n, const gt_params *p, int nsm, i
     s->acc_out = L.take<float4>(base, N);
     s->aold_tmp = L.take<float>(base, N);
     s->scratch3 = L.take<double>(base, 3 * N + 8);  // also stages 13 B per particle on resume
+    s->bscratch = L.take<uint8_t>(base, gt_build_scratch_bytes(n));
     s->bbox_blocks = nsm * 4;
     s->bbox_partial = L.take<float>(base, 6 * (size_t)s->bbox_blocks);
     s->walk_blocks = walk_blocks;
@@ -299,7 +300,7 @@ void build_tree(gt_system *s, cudaStream_t st, const float4 *posm_src) {
     }
     ph_end(s, PH_PERMUTE, st);
     ph_begin(s, PH_BUILD, st);
-    gt_launch_build(s->sb.key[0], n, s->prm.leaf_max, s->nd, s->cap, s->status, s->ctl, s->nsm, st);
+    gt_launch_build(s->sb.key[0], n, s->prm.leaf_max, s->nd, s->cap, s->status, s->bscratch, s->ctl, s->nsm, st);
     gt_launch_cell_lists(s->nd, s->cap, s->ctl, s->nsm, st);
     ph_end(s, PH_BUILD, st);
     ph_begin(s, PH_PSEUDO, st);

@@ -8,8 +8,9 @@
 
 #define GT_KEY_LEVELS 21              // 21 bits per axis -> 63-bit Morton keys
 #define GT_TREE_LEVELS 22             // tree levels 0..21
-#define GT_LEAF_BUCKETS 17            // leaves bucketed by particle count: 1..16, then larger
-#define GT_CELL_BUCKETS (GT_LEAF_BUCKETS + GT_TREE_LEVELS * 8)  // + (level, children) buckets
+#define GT_LEAF_BUCKETS 17            // a level's leaves by particle count: 1..16, then larger
+#define GT_LEVEL_BUCKETS (GT_LEAF_BUCKETS + 8)  // + its cells with children by number of children
+#define GT_CELL_BUCKETS (GT_TREE_LEVELS * GT_LEVEL_BUCKETS)
 #define GT_LEAF_FLAG 0x80000000u      // set in a node's second link word for a leaf
 #define GT_SPIN_LIMIT (1u << 22)      // bound on every device spin-wait (iterations)
 // Enclosing radii computed in FP32 are widened by (1 + 2^-20): the few roundings of
@@ -28,15 +29,15 @@ struct DevCtl {
     unsigned int epoch;               // bumped once per tree build / compaction
     unsigned int n_active;            // i-particles of the current force evaluation
     unsigned int n_groups;            // groups of the current force evaluation (cell grouping)
-    unsigned int n_leaves;            // leaves of the current tree
-    unsigned int istart[GT_TREE_LEVELS + 2];  // where every level's cells with children start in the cell list
+    unsigned int seg[2 * GT_TREE_LEVELS + 1];  // cell list: level l's leaves start at seg[2l], its
+                                               // cells with children at seg[2l + 1]; [44] = all
     unsigned int cell_bucket[GT_CELL_BUCKETS];  // bucket sizes, then fill cursors, of the cell list
     unsigned int group_next;          // dynamic group counter of the walk
     unsigned int tile_ticket[GT_TREE_LEVELS + 4];  // dynamic tile ids: levels, actives, groups, leaves, cells
     unsigned int level_start[GT_TREE_LEVELS + 2];  // first cell of each level; [22] = node count
     unsigned int sort_ticket[8];      // dynamic tile ids of the 8 sort passes
     unsigned int sort_epoch;          // look-back epoch of the sort
-    unsigned int pl_ticket;           // chunk tickets of the pseudo j-particle level pass
+    unsigned int pl_ticket;           // chunk tickets of the pseudo j-particle pass
     unsigned int pl_done[GT_TREE_LEVELS];  // finished chunks per level of that pass
     unsigned long long interactions;  // cumulative
     unsigned long long mac_tests;     // cumulative
@@ -245,8 +246,10 @@ size_t gt_sort_scratch_bytes(int64_t n);
 void gt_launch_sort(SortBufs &b, int64_t n, DevCtl *ctl, cudaStream_t st);
 void gt_sort_init();
 // tree.cu
+// scratch: gt_build_scratch_bytes(n) bytes (per-particle marks and per-tile counts)
+size_t gt_build_scratch_bytes(int64_t n);
 void gt_launch_build(const uint64_t *skey, int64_t n, int leaf_max, Nodes nd, int64_t cap,
-                     unsigned long long *status, DevCtl *ctl, int nsm, cudaStream_t st);
+                     unsigned long long *status, uint8_t *scratch, DevCtl *ctl, int nsm, cudaStream_t st);
 void gt_launch_cell_lists(Nodes nd, int64_t cap, DevCtl *ctl, int nsm, cudaStream_t st);
 // with_mass: form the FP64 mass sums (after a build); otherwise reuse the stored ones
 void gt_launch_pseudo(Nodes nd, int64_t cap, const float4 *posm, DevCtl *ctl, int nsm, bool with_mass,

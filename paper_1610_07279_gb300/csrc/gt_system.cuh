@@ -81,6 +81,7 @@ struct gt_system {
     float4 *acc_out = nullptr;
     float *aold_tmp = nullptr;
     double *scratch3 = nullptr;
+    uint8_t *bscratch = nullptr;  // tree build marks and counts
     float *bbox_partial = nullptr;
     int bbox_blocks = 0;
     uint32_t *queue = nullptr;    // the walk queue (a batch's shared queue for batch members)

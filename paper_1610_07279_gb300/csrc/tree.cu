@@ -1,19 +1,20 @@
 // Steps A4-A5: breadth-first octree over the sorted keys and the pseudo
 // j-particles (Sec. 2.1, Fig. 1).
 //
-// A4, one kernel per level (Sec. 2.1: cells are examined in parallel and their
-// children numbered serially with prefix sums).  A cell at level l with more than
-// leaf_max particles (and l < 21) splits into the non-empty ranges of the digit
-// (key >> 3(20 - l)) & 7 -- the "seven partitions" of its key range, found by a
-// lock-step 7-way binary search.  Children get consecutive numbers after the level,
-// in the order of their parents and digits, via a block scan plus a decoupled
-// look-back over tiles taken in ticket order (bounded wait).  Numbering is thus
-// level by level and, inside a level, by first particle.
+// A4.  A cell at level l with more than leaf_max particles (and l < 21) splits into the
+// non-empty ranges of its particles' level-(l + 1) digit; children are numbered after
+// their level, level by level and, inside a level, by first particle.  With leaf_max up
+// to 64 the whole tree comes from one sweep over the sorted keys (k_flat_*: every
+// particle's leaf level from the digits in which its neighbours' keys differ, then the
+// nodes' starts and ends counted, scanned and scattered by level); larger leaves take
+// one kernel per level (k_build_level: the "seven partitions" of a cell's key range by a
+// lock-step 7-way binary search, children numbered by a block scan plus a decoupled
+// look-back over tiles taken in ticket order).  Both give the same numbering.
 //
-// A5: one lane per leaf sums its particles in FP64 (mass, m x, m y, m z), then one
-// pass per level, deepest first, over the cells with children (a list compacted at
-// build time) sums the children's FP64 sums in child order -- every FP64 instruction
-// runs with full warps, which matters on this GPU's narrow FP64 pipe.  m_J = (float)M and
+// A5, one launch over a cell list bucketed by level and size: a leaf's lane sums its
+// particles in FP64 (mass, m x, m y, m z); a cell with children sums its children's FP64
+// sums in child order once the level below is done -- every FP64 instruction runs with
+// full warps, which matters on this GPU's narrow FP64 pipe.  m_J = (float)M and
 // r_J = (float)S / (float)M (a cell of one particle is that particle); b_J is the
 // largest FP32 |r - r_J| of a leaf's particles, or the largest |r_c - r_J| + b_c
 // over a cell's children, widened by (1 + 2^-20) so that FP32 rounding cannot
@@ -144,28 +145,262 @@ __global__ __launch_bounds__(BT) void k_build_level(int lvl, const unsigned long
     }
 }
 
+// ---- A4 in one sweep over the sorted keys (leaf_max <= FLAT_LWIN) ------------------
+// d(p), the index of the first 3-bit digit in which keys p - 1 and p differ (21 for equal
+// keys; -1 at p = 0 and p = n), says at which levels a new cell begins at particle p: a
+// run of particles between two positions with d < l shares its first l digits, so it is
+// one level-l cell of the full octree.  The tree keeps a level-l run iff its parent run
+// holds more than leaf_max particles, so particle i's leaf is at the first level whose
+// run around i holds at most leaf_max -- found from the d values within leaf_max of i.
+// Particle i then starts a node at every level l with d(i) < l <= leaf level(i), and ends
+// one (as its last particle) at every l with d(i + 1) < l <= leaf level(i).  Counting
+// those starts and ends per level and tile, scanning, and scattering them by rank gives
+// the same numbering as the level-by-level split: level by level, and inside a level by
+// first particle.  A node's first child starts at its own first particle; the others
+// are the next nodes of the child level that start before its end.
+constexpr int FLAT_LWIN = 64;              // the largest leaf_max of this build
+constexpr int FT = 2048;                   // particles per tile
+constexpr int FB = 256;                    // threads per block
+constexpr int NREC = 2 * GT_TREE_LEVELS;   // start and end counters per level
+
+__device__ __forceinline__ int key_diff_digit(unsigned long long a, unsigned long long b) {
+    const unsigned long long x = a ^ b;  // keys use bits 0..62, so clz >= 1
+    return x ? (__clzll((long long)x) - 1) / 3 : GT_KEY_LEVELS;
+}
+
+// Leaf level of the particle at ds[j]: the run around it at level l holds at most M
+// particles iff, for some a in [0, M), positions i - a .. i and i + 1 .. i + M - a both
+// hold a d below l; so the leaf level is 1 + min over a of max(the smallest d of the
+// first window, the smallest d of the second).  MT > 0: M = MT, unrolled in registers.
+template <int MT>
+__device__ __forceinline__ int leaf_level_of(const int8_t *ds, int j) {
+    int mr[MT + 1];  // mr[b]: smallest d over i + 1 .. i + b
+    int m = 127;
+#pragma unroll
+    for (int b = 1; b <= MT; b++) {
+        m = min(m, (int)ds[j + b]);
+        mr[b] = m;
+    }
+    int ml = 127, best = 127;
+#pragma unroll
+    for (int a = 0; a < MT; a++) {
+        ml = min(ml, (int)ds[j - a]);
+        best = min(best, max(ml, mr[MT - a]));
+    }
+    return min(best + 1, GT_KEY_LEVELS);
+}
+
+// d and the leaf level of every particle (packed (d + 1) | leaf << 8), and every tile's
+// start and end counts per level (column-major: counter k of tile t at cnt[k * ntiles + t]).
+// MT > 0: leaf_max == MT; MT == 0: any leaf_max up to FLAT_LWIN (running minima in shared memory).
+template <int MT>
+__global__ __launch_bounds__(FB) void k_flat_marks(const unsigned long long *__restrict__ skey, long long n,
+                                                   int M, uint16_t *__restrict__ dl,
+                                                   uint32_t *__restrict__ cnt, int ntiles) {
+    constexpr int W = FLAT_LWIN;
+    constexpr int MW = MT > 0 ? 1 : W;
+    __shared__ int8_t ds[FT + 2 * W + 1];      // d of positions base - W .. base + FT + W
+    __shared__ uint8_t mr[MW][FB];             // generic: 1 + smallest d over (i, i + b]
+    __shared__ unsigned int c[NREC];
+    const long long base = (long long)blockIdx.x * FT;
+    for (int j = threadIdx.x; j < FT + 2 * W + 1; j += FB) {
+        const long long p = base - W + j;
+        ds[j] = (int8_t)((p > 0 && p < n) ? key_diff_digit(skey[p - 1], skey[p]) : -1);
+    }
+    for (int j = threadIdx.x; j < NREC; j += FB) c[j] = 0;
+    __syncthreads();
+    for (int r = 0; r < FT / FB; r++) {
+        const int t = r * FB + threadIdx.x;
+        const long long i = base + t;
+        if (i >= n) break;
+        const int j = t + W;  // position i in ds
+        int leaf;
+        if constexpr (MT > 0) {
+            leaf = leaf_level_of<MT>(ds, j);
+        } else {
+            int m = 127;
+            for (int b = 1; b <= M; b++) {
+                m = min(m, (int)ds[j + b]);
+                mr[b - 1][threadIdx.x] = (uint8_t)(m + 1);
+            }
+            int ml = 127, best = 127;
+            for (int a = 0; a < M; a++) {
+                ml = min(ml, (int)ds[j - a]);
+                best = min(best, max(ml, (int)mr[M - a - 1][threadIdx.x] - 1));
+            }
+            leaf = min(best + 1, GT_KEY_LEVELS);
+        }
+        const int d0 = ds[j], d1 = ds[j + 1];
+        dl[i] = (uint16_t)((d0 + 1) | (leaf << 8));
+        for (int l = d0 + 1; l <= leaf; l++) atomicAdd(&c[l], 1u);
+        for (int l = d1 + 1; l <= leaf; l++) atomicAdd(&c[GT_TREE_LEVELS + l], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < NREC; k += FB) cnt[(size_t)k * ntiles + blockIdx.x] = c[k];
+}
+
+// one block per counter: exclusive scan over the tiles, the column total into tot[k]
+__global__ __launch_bounds__(1024) void k_flat_scan(uint32_t *__restrict__ cnt, int ntiles,
+                                                    uint32_t *__restrict__ tot) {
+    __shared__ unsigned int tmp[1024 / 32 + 1];
+    uint32_t *col = cnt + (size_t)blockIdx.x * ntiles;
+    unsigned int carry = 0;
+    for (int b0 = 0; b0 < ntiles; b0 += 1024) {
+        const int t = b0 + (int)threadIdx.x;
+        const unsigned int v = t < ntiles ? col[t] : 0u;
+        unsigned int total;
+        const unsigned int e = block_excl_scan<1024>(v, &total, tmp);
+        if (t < ntiles) col[t] = carry + e;
+        carry += total;
+    }
+    if (threadIdx.x == 0) tot[blockIdx.x] = carry;
+}
+
+// level starts from the per-level node counts (clamped to the node capacity)
+__global__ void k_flat_levels(const uint32_t *__restrict__ tot, long long cap, DevCtl *ctl) {
+    unsigned long long s = 0;
+    for (int l = 0; l < GT_TREE_LEVELS; l++) {
+        ctl->level_start[l] = (uint32_t)(s < (unsigned long long)cap ? s : (unsigned long long)cap);
+        s += tot[l];
+    }
+    if (s > (unsigned long long)cap) {
+        gt_set_error(ctl, GT_EOVERFLOW, GTK_BUILD);
+        s = (unsigned long long)cap;
+    }
+    ctl->level_start[GT_TREE_LEVELS] = (uint32_t)s;
+    ctl->level_start[GT_TREE_LEVELS + 1] = (uint32_t)s;
+}
+
+// every start and end to its node: first, the first child and the parent along a
+// particle's own chain of starts, leaves; an end goes to count (as the end position)
+__global__ __launch_bounds__(FB) void k_flat_scatter(const uint16_t *__restrict__ dl, long long n,
+                                                     const uint32_t *__restrict__ cnt, int ntiles,
+                                                     long long cap, Nodes nd, const DevCtl *__restrict__ ctl) {
+    __shared__ uint32_t lb[GT_TREE_LEVELS];
+    __shared__ uint32_t run[NREC];
+    __shared__ uint32_t wc[FB / 32][NREC];
+    __shared__ uint16_t dls[FT + 1];
+    const long long base = (long long)blockIdx.x * FT;
+    for (int k = threadIdx.x; k < GT_TREE_LEVELS; k += FB) lb[k] = ctl->level_start[k];
+    for (int k = threadIdx.x; k < NREC; k += FB) run[k] = cnt[(size_t)k * ntiles + blockIdx.x];
+    for (int j = threadIdx.x; j <= FT; j += FB) dls[j] = base + j < n ? dl[base + j] : (uint16_t)0;  // d(n) = -1
+    __syncthreads();
+    const int w = threadIdx.x >> 5;
+    const unsigned int lt = lanemask_lt();
+    for (int r = 0; r < FT / FB; r++) {
+        const int t = r * FB + threadIdx.x;
+        const long long i = base + t;
+        const bool valid = i < n;
+        const int v = dls[t];
+        const int slo = valid ? (v & 0xff) : GT_TREE_LEVELS, leaf = v >> 8;
+        const int elo = valid ? (dls[t + 1] & 0xff) : GT_TREE_LEVELS;
+        // ranks inside the round: per-warp counts, then warps in order after the tile's
+        // offset; a warp visits only the levels at which one of its lanes has a record
+        const int has = slo <= leaf || elo <= leaf;
+        const int lmin = __reduce_min_sync(0xffffffffu, has ? min(slo, elo) : GT_TREE_LEVELS);
+        const int lmax = __reduce_max_sync(0xffffffffu, has ? leaf : -1);
+        if ((threadIdx.x & 31) < GT_TREE_LEVELS) {
+            wc[w][threadIdx.x & 31] = 0;
+            wc[w][GT_TREE_LEVELS + (threadIdx.x & 31)] = 0;
+        }
+        __syncwarp();
+        for (int l = lmin; l <= lmax; l++) {
+            const unsigned int bs = __ballot_sync(0xffffffffu, slo <= l && l <= leaf);
+            const unsigned int be = __ballot_sync(0xffffffffu, elo <= l && l <= leaf);
+            if ((threadIdx.x & 31) == 0) {
+                wc[w][l] = __popc(bs);
+                wc[w][GT_TREE_LEVELS + l] = __popc(be);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < NREC) {
+            uint32_t s = run[threadIdx.x];
+            for (int q = 0; q < FB / 32; q++) {
+                const uint32_t x = wc[q][threadIdx.x];
+                wc[q][threadIdx.x] = s;
+                s += x;
+            }
+            run[threadIdx.x] = s;
+        }
+        __syncthreads();
+        long long prev = -1;  // this particle's node one level up, when it starts one there
+        for (int l = lmin; l <= lmax; l++) {
+            const bool hs = slo <= l && l <= leaf, he = elo <= l && l <= leaf;
+            const unsigned int bs = __ballot_sync(0xffffffffu, hs);
+            const unsigned int be = __ballot_sync(0xffffffffu, he);
+            if (hs) {
+                const long long id = (long long)lb[l] + wc[w][l] + __popc(bs & lt);
+                if (prev >= 0) nd.child[prev] = id < cap ? (int32_t)id : -1;
+                if (id < cap) {
+                    nd.first[id] = (uint32_t)i;
+                    if (l == 0 || prev >= 0) nd.parent[id] = (int32_t)prev;  // else: the link pass
+                    if (l == leaf) {
+                        nd.child[id] = -1;
+                        nd.nchild[id] = 0;
+                    }
+                }
+                prev = id < cap ? id : -1;
+            }
+            if (he) {
+                const long long id = (long long)lb[l] + wc[w][GT_TREE_LEVELS + l] + __popc(be & lt);
+                if (id < cap) nd.count[id] = (uint32_t)(i + 1);
+            }
+        }
+        __syncthreads();  // wc is rewritten by the next round
+    }
+}
+
+// per node: count = end - first; a node with children counts them (the nodes of the
+// next level from its first child on that start before its end) and is their parent
+__global__ __launch_bounds__(256) void k_flat_link(Nodes nd, long long cap, const DevCtl *__restrict__ ctl) {
+    __shared__ uint32_t ls[GT_TREE_LEVELS + 2];
+    for (int i = threadIdx.x; i < GT_TREE_LEVELS + 2; i += 256) ls[i] = ctl->level_start[i];
+    __syncthreads();
+    const long long nn = ls[GT_TREE_LEVELS];
+    for (long long p = blockIdx.x * 256ll + threadIdx.x; p < nn; p += (long long)gridDim.x * 256) {
+        const uint32_t f = nd.first[p], e = nd.count[p];
+        nd.count[p] = e - f;
+        const int32_t c0 = nd.child[p];
+        if (c0 < 0) continue;
+        int lvl = 0;  // the last level starting at or before p
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+            if (lvl + step < GT_TREE_LEVELS && ls[lvl + step] <= (uint32_t)p) lvl += step;
+        long long hi = ls[lvl + 2];
+        if (hi > cap) hi = cap;
+        uint32_t nch = 1;
+        for (int q = 1; q < 8; q++) {
+            const long long c = (long long)c0 + q;
+            if (c >= hi || nd.first[c] >= e) break;
+            nd.parent[c] = (int32_t)p;
+            nch++;
+        }
+        nd.nchild[p] = nch;
+    }
+}
+
 __device__ __forceinline__ float sq3f(float dx, float dy, float dz) {
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
 
-// ---- cell lists for the per-step pseudo j-particle passes -----------------------
-// Every node goes once into nd.cells: the leaves first, bucketed by particle count
-// (1..16, then all larger), then the cells with children, level by level and inside a
-// level by number of children.  A warp of the pseudo-j passes then takes cells of one
-// size, so the FP64 sums run with all lanes busy.  The order inside a bucket is free:
-// every cell's result depends on its own particles or children only.
+// ---- cell lists for the per-step pseudo j-particle pass ---------------------------
+// Every node goes once into nd.cells, level by level; inside a level the leaves come
+// first, bucketed by particle count (1..16, then all larger), then the cells with
+// children, bucketed by number of children.  A warp of the pseudo-j pass then takes
+// cells of one size, so the FP64 sums run with all lanes busy.  The order inside a
+// bucket is free: every cell's result depends on its own particles or children only.
 
 // bucket of node p, given the level ranges ls[0..GT_TREE_LEVELS]
 __device__ __forceinline__ int cell_bucket_of(const Nodes &nd, uint32_t p, const uint32_t *ls) {
-    if (nd.child[p] < 0) {
-        const uint32_t k = nd.count[p];
-        return (k >= GT_LEAF_BUCKETS ? GT_LEAF_BUCKETS : (int)k) - 1;
-    }
     int lvl = 0;  // the last level starting at or before p
 #pragma unroll
     for (int step = 16; step > 0; step >>= 1)
         if (lvl + step < GT_TREE_LEVELS && ls[lvl + step] <= p) lvl += step;
-    return GT_LEAF_BUCKETS + lvl * 8 + (int)nd.nchild[p] - 1;
+    if (nd.child[p] < 0) {
+        const uint32_t k = nd.count[p];
+        return lvl * GT_LEVEL_BUCKETS + (k >= GT_LEAF_BUCKETS ? GT_LEAF_BUCKETS : (int)k) - 1;
+    }
+    return lvl * GT_LEVEL_BUCKETS + GT_LEAF_BUCKETS + (int)nd.nchild[p] - 1;
 }
 
 __global__ __launch_bounds__(256) void k_cell_count(Nodes nd, long long cap, DevCtl *ctl) {
@@ -183,169 +418,221 @@ __global__ __launch_bounds__(256) void k_cell_count(Nodes nd, long long cap, Dev
         if (h[i]) atomicAdd(&ctl->cell_bucket[i], h[i]);
 }
 
-// one block: bucket sizes -> fill cursors; the leaf count and where every level starts
-__global__ __launch_bounds__(256) void k_cell_scan(DevCtl *ctl) {
-    static_assert(GT_CELL_BUCKETS <= 256, "one thread per bucket");
-    __shared__ uint32_t tmp[256 / 32 + 1];
+// one block: bucket sizes -> fill cursors, and where every level's leaves and cells
+// with children start
+__global__ __launch_bounds__(1024) void k_cell_scan(DevCtl *ctl) {
+    static_assert(GT_CELL_BUCKETS <= 1024, "one thread per bucket");
+    __shared__ unsigned int tmp[1024 / 32 + 1];
     const int b = threadIdx.x;
     const uint32_t v = b < GT_CELL_BUCKETS ? ctl->cell_bucket[b] : 0u;
     uint32_t total;
-    const uint32_t start = block_excl_scan<256>(v, &total, tmp);
-    if (b < GT_CELL_BUCKETS) ctl->cell_bucket[b] = start;
-    if (b == GT_LEAF_BUCKETS) ctl->n_leaves = start;
-    if (b >= GT_LEAF_BUCKETS && b < GT_CELL_BUCKETS && (b - GT_LEAF_BUCKETS) % 8 == 0)
-        ctl->istart[(b - GT_LEAF_BUCKETS) / 8] = start;
-    if (b == 0) ctl->istart[GT_TREE_LEVELS] = total;
+    const uint32_t start = block_excl_scan<1024>(v, &total, tmp);
+    if (b < GT_CELL_BUCKETS) {
+        ctl->cell_bucket[b] = start;
+        const int q = b % GT_LEVEL_BUCKETS;
+        if (q == 0) ctl->seg[2 * (b / GT_LEVEL_BUCKETS)] = start;
+        if (q == GT_LEAF_BUCKETS) ctl->seg[2 * (b / GT_LEVEL_BUCKETS) + 1] = start;
+    }
+    if (b == 0) ctl->seg[2 * GT_TREE_LEVELS] = total;
 }
+
+// A block takes a contiguous range of nodes, counts them per bucket in shared memory,
+// reserves its room in every bucket with one global atomic each, and fills it.
+constexpr int CF_NODES = 4096;  // nodes per fill block
 
 __global__ __launch_bounds__(256) void k_cell_fill(Nodes nd, long long cap, DevCtl *ctl) {
     __shared__ uint32_t ls[GT_TREE_LEVELS + 1];
+    __shared__ uint32_t h[GT_CELL_BUCKETS];
     for (int i = threadIdx.x; i <= GT_TREE_LEVELS; i += 256) ls[i] = ctl->level_start[i];
-    __syncthreads();
-    long long nn = ls[GT_TREE_LEVELS];
+    long long nn = ctl->level_start[GT_TREE_LEVELS];
     if (nn > cap) nn = cap;
-    const unsigned lt = lanemask_lt();
-    // the loop bound is warp-uniform, so every lane takes part in the match
-    for (long long p0 = blockIdx.x * 256ll + (threadIdx.x & ~31u); p0 < nn; p0 += (long long)gridDim.x * 256) {
-        const long long p = p0 + (threadIdx.x & 31);
-        const bool ok = p < nn;
-        const int b = ok ? cell_bucket_of(nd, (uint32_t)p, ls) : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, b);
-        const int leader = __ffs(peers) - 1;
-        uint32_t pos0 = 0;
-        if (ok && (peers & lt) == 0) pos0 = atomicAdd(&ctl->cell_bucket[b], (uint32_t)__popc(peers));
-        pos0 = __shfl_sync(0xffffffffu, pos0, leader);
-        if (ok) nd.cells[pos0 + __popc(peers & lt)] = (uint32_t)p;
+    for (long long b0 = (long long)blockIdx.x * CF_NODES; b0 < nn; b0 += (long long)gridDim.x * CF_NODES) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < GT_CELL_BUCKETS; i += 256) h[i] = 0;
+        __syncthreads();
+        const long long b1 = b0 + CF_NODES < nn ? b0 + CF_NODES : nn;
+        for (long long p = b0 + threadIdx.x; p < b1; p += 256)
+            atomicAdd(&h[cell_bucket_of(nd, (uint32_t)p, ls)], 1u);
+        __syncthreads();
+        for (int i = threadIdx.x; i < GT_CELL_BUCKETS; i += 256)
+            if (h[i]) h[i] = atomicAdd(&ctl->cell_bucket[i], h[i]);
+        __syncthreads();
+        for (long long p = b0 + threadIdx.x; p < b1; p += 256)
+            nd.cells[atomicAdd(&h[cell_bucket_of(nd, (uint32_t)p, ls)], 1u)] = (uint32_t)p;
     }
 }
 
-// leaves: one lane per leaf, a warp's leaves of one particle count.  The masses and the
-// cells' members do not change between tree builds, so the mass sums are formed at a
-// build (with_mass) and read back at the other block steps: the same values, one FP64
-// addition per particle fewer.
+// ---- A5: pseudo j-particles, every node in one launch ------------------------------
+// The cell list's segments (a level's leaves, a level's cells with children) are cut
+// into chunks of PL nodes, handed out by a ticket counter in this order: the leaves of
+// level 21; then, for l = 20 .. 0, the leaves of level l and the cells with children of
+// level l + 1; the cells of level 0 last.  A chunk of cells of level l waits until every
+// chunk of level l + 1 is finished: those hold smaller tickets, so the blocks holding
+// them are running and the wait ends (it is bounded all the same).  Leaves wait for
+// nothing, so their FP64 sums fill the time a level's cells wait for the one below.
+constexpr int PL = 128;  // nodes per chunk, one per thread
+constexpr int PSEUDO_LAG = 1;  // levels of leaves between a level's cells and the level below
+constexpr int NSEG = 2 * GT_TREE_LEVELS;
+
+// Leaf c: one lane sums its particles in FP64 (mass, m x, m y, m z) in particle order.
+// The masses and the cells' members do not change between tree builds, so the mass
+// sums are formed at a build (WITH_MASS) and read back at the other block steps: the
+// same values, one FP64 addition per particle fewer.
 template <bool WITH_MASS>
-__global__ __launch_bounds__(256) void k_pseudo_leaves(Nodes nd, const float4 *__restrict__ posm, DevCtl *ctl) {
-    const long long nl = ctl->n_leaves;
-    for (long long t = blockIdx.x * 256ll + threadIdx.x; t < nl; t += (long long)gridDim.x * 256) {
-        const uint32_t c = nd.cells[t];
-        const uint32_t f = nd.first[c];
-        const uint32_t k = nd.count[c];
-        double m = WITH_MASS ? 0.0 : nd.sum[c].m, sx = 0.0, sy = 0.0, sz = 0.0;
-        for (uint32_t i = f; i < f + k; i++) {
-            const float4 p = posm[i];
-            const double mi = f2d(p.w);  // m x is exact in FP64, so the fused form rounds once like + does
-            if (WITH_MASS) m = __dadd_rn(m, mi);
-            sx = __fma_rn(mi, f2d(p.x), sx);
-            sy = __fma_rn(mi, f2d(p.y), sy);
-            sz = __fma_rn(mi, f2d(p.z), sz);
-        }
-        float jx, jy, jz;
-        if (k == 1) {  // a cell of one particle is that particle
-            const float4 p = posm[f];
-            jx = p.x; jy = p.y; jz = p.z;
-        } else {
-            const float mf = d2f(m);
-            jx = __fdiv_rn(d2f(sx), mf);
-            jy = __fdiv_rn(d2f(sy), mf);
-            jz = __fdiv_rn(d2f(sz), mf);
-        }
-        float d2max = 0.0f, b2 = 0.0f;  // b2: B_2 of the multipole MAC
-        for (uint32_t i = f; i < f + k; i++) {
-            const float4 p = posm[i];
-            const float d2 = sq3f(__fsub_rn(p.x, jx), __fsub_rn(p.y, jy), __fsub_rn(p.z, jz));
-            if (d2 > d2max) d2max = d2;
-            b2 = __fadd_rn(b2, __fmul_rn(p.w, d2));
-        }
-        nd.sum[c] = DSum4{m, sx, sy, sz};
-        nd.jpos[c] = make_float4(jx, jy, jz, d2f(m));
-        nd.walk[c] = make_float4(__fmul_rn(__fsqrt_rn(d2max), GT_RADIUS_MARGIN), __uint_as_float(f),
-                                 __uint_as_float(k | GT_LEAF_FLAG), b2);
+__device__ __forceinline__ void pseudo_leaf(const Nodes &nd, const float4 *__restrict__ posm, uint32_t c) {
+    const uint32_t f = nd.first[c];
+    const uint32_t k = nd.count[c];
+    double m = WITH_MASS ? 0.0 : nd.sum[c].m, sx = 0.0, sy = 0.0, sz = 0.0;
+    for (uint32_t i = f; i < f + k; i++) {
+        const float4 p = posm[i];
+        const double mi = f2d(p.w);  // m x is exact in FP64, so the fused form rounds once like + does
+        if (WITH_MASS) m = __dadd_rn(m, mi);
+        sx = __fma_rn(mi, f2d(p.x), sx);
+        sy = __fma_rn(mi, f2d(p.y), sy);
+        sz = __fma_rn(mi, f2d(p.z), sz);
     }
+    float jx, jy, jz;
+    if (k == 1) {  // a cell of one particle is that particle
+        const float4 p = posm[f];
+        jx = p.x; jy = p.y; jz = p.z;
+    } else {
+        const float mf = d2f(m);
+        jx = __fdiv_rn(d2f(sx), mf);
+        jy = __fdiv_rn(d2f(sy), mf);
+        jz = __fdiv_rn(d2f(sz), mf);
+    }
+    float d2max = 0.0f, b2 = 0.0f;  // b2: B_2 of the multipole MAC
+    for (uint32_t i = f; i < f + k; i++) {
+        const float4 p = posm[i];
+        const float d2 = sq3f(__fsub_rn(p.x, jx), __fsub_rn(p.y, jy), __fsub_rn(p.z, jz));
+        if (d2 > d2max) d2max = d2;
+        b2 = __fadd_rn(b2, __fmul_rn(p.w, d2));
+    }
+    nd.sum[c] = DSum4{m, sx, sy, sz};
+    nd.jpos[c] = make_float4(jx, jy, jz, d2f(m));
+    nd.walk[c] = make_float4(__fmul_rn(__fsqrt_rn(d2max), GT_RADIUS_MARGIN), __uint_as_float(f),
+                             __uint_as_float(k | GT_LEAF_FLAG), b2);
 }
 
-// Cells with children, all levels in one launch.  Every level's part of the cell list
-// is cut into chunks of PL cells; chunks are handed out by a ticket counter, the deepest
-// level first.  Before a chunk of level l is summed, its block waits until every chunk
-// of level l + 1 is finished: those chunks hold smaller tickets, so the blocks holding
-// them are running, and the wait ends (it is bounded all the same).  A cell adds its
-// children's sums in child order.
-constexpr int PL = 256;
+// Cell p with children: its children's FP64 sums added in child order.  The children
+// were written by other blocks of this launch: they are read through L2 (__ldcg), an
+// SM's L1 may hold a line of them from before they were written.  Loads go out four
+// children at a time, so a level costs few L2 round trips.
+template <bool WITH_MASS>
+__device__ __forceinline__ void pseudo_cell(const Nodes &nd, uint32_t p) {
+    const int32_t ch0 = nd.child[p];
+    const uint32_t nch = nd.nchild[p];
+    double m = WITH_MASS ? 0.0 : nd.sum[p].m, sx = 0.0, sy = 0.0, sz = 0.0;
+    for (uint32_t q0 = 0; q0 < nch; q0 += 4) {
+        double2 s0[4], s1[4];  // (m, x), (y, z)
+#pragma unroll
+        for (uint32_t q = 0; q < 4; q++)
+            if (q0 + q < nch) {
+                const double2 *cs = (const double2 *)&nd.sum[ch0 + q0 + q];
+                s0[q] = __ldcg(cs);
+                s1[q] = __ldcg(cs + 1);
+            }
+#pragma unroll
+        for (uint32_t q = 0; q < 4; q++)
+            if (q0 + q < nch) {
+                if (WITH_MASS) m = __dadd_rn(m, s0[q].x);
+                sx = __dadd_rn(sx, s0[q].y);
+                sy = __dadd_rn(sy, s1[q].x);
+                sz = __dadd_rn(sz, s1[q].y);
+            }
+    }
+    const float mf = d2f(m);
+    const float jx = __fdiv_rn(d2f(sx), mf);
+    const float jy = __fdiv_rn(d2f(sy), mf);
+    const float jz = __fdiv_rn(d2f(sz), mf);
+    float b = 0.0f, b2 = 0.0f;  // b2: B_2 by parallel axes
+    for (uint32_t q0 = 0; q0 < nch; q0 += 4) {
+        float4 cj[4], cw[4];
+#pragma unroll
+        for (uint32_t q = 0; q < 4; q++)
+            if (q0 + q < nch) {
+                cj[q] = __ldcg(&nd.jpos[ch0 + q0 + q]);
+                cw[q] = __ldcg(&nd.walk[ch0 + q0 + q]);
+            }
+#pragma unroll
+        for (uint32_t q = 0; q < 4; q++)
+            if (q0 + q < nch) {
+                const float d2 = sq3f(__fsub_rn(cj[q].x, jx), __fsub_rn(cj[q].y, jy), __fsub_rn(cj[q].z, jz));
+                const float e = __fadd_rn(__fsqrt_rn(d2), cw[q].x);
+                if (e > b) b = e;
+                b2 = __fadd_rn(b2, __fadd_rn(cw[q].w, __fmul_rn(cj[q].w, d2)));
+            }
+    }
+    nd.sum[p] = DSum4{m, sx, sy, sz};
+    nd.jpos[p] = make_float4(jx, jy, jz, mf);
+    nd.walk[p] = make_float4(__fmul_rn(b, GT_RADIUS_MARGIN), __uint_as_float((uint32_t)ch0),
+                             __uint_as_float(nch), b2);
+}
 
 template <bool WITH_MASS>
-__global__ __launch_bounds__(PL) void k_pseudo_levels(Nodes nd, DevCtl *ctl) {
-    __shared__ unsigned int cum[GT_TREE_LEVELS + 1];  // first ticket of every level
+__global__ __launch_bounds__(PL) void k_pseudo(Nodes nd, const float4 *__restrict__ posm, DevCtl *ctl) {
+    __shared__ uint32_t seg[NSEG + 1];
+    __shared__ uint8_t olvl[NSEG], ocell[NSEG];      // ticket order: segment level and kind
+    __shared__ uint32_t ocum[NSEG + 1];              // first ticket of every entry
+    __shared__ uint32_t nchunk[NSEG];                // chunks of segment (2 l + kind)
     __shared__ unsigned int t_sh;
-    __shared__ int bad_sh;
-    constexpr int TOP = GT_TREE_LEVELS - 2;           // the deepest level with children
+    __shared__ int o_sh, bad_sh;
+    for (int i = threadIdx.x; i <= NSEG; i += PL) seg[i] = ctl->seg[i];
+    __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned int c = 0;
-        for (int l = TOP; l >= 0; l--) {
-            cum[l] = c;
-            c += (ctl->istart[l + 1] - ctl->istart[l] + PL - 1) / PL;
+        for (int k = 0; k < NSEG; k++) nchunk[k] = (seg[k + 1] - seg[k] + PL - 1) / PL;
+        int o = 0;  // level l's cells go right after the leaves of level l - PSEUDO_LAG
+        for (int s = 0; s < GT_TREE_LEVELS + PSEUDO_LAG; s++) {
+            const int ll = GT_TREE_LEVELS - 1 - s, lc = GT_TREE_LEVELS - 1 + PSEUDO_LAG - s;
+            if (ll >= 0) { olvl[o] = (uint8_t)ll; ocell[o] = 0; o++; }
+            if (lc >= 0 && lc < GT_TREE_LEVELS - 1) { olvl[o] = (uint8_t)lc; ocell[o] = 1; o++; }
         }
-        cum[GT_TREE_LEVELS] = c;  // total
+        // o == NSEG - 1 (level 21 has no cells with children): the last entry is empty
+        olvl[o] = 0; ocell[o] = 2;
+        uint32_t c = 0;
+        for (int k = 0; k < NSEG; k++) {
+            ocum[k] = c;
+            if (ocell[k] < 2) c += nchunk[2 * olvl[k] + ocell[k]];
+        }
+        ocum[NSEG] = c;
         bad_sh = 0;
     }
     __syncthreads();
-    const unsigned int total = cum[GT_TREE_LEVELS];
+    const uint32_t total = ocum[NSEG];
     for (;;) {
-        if (threadIdx.x == 0) t_sh = atomicAdd(&ctl->pl_ticket, 1u);
+        if (threadIdx.x == 0) {
+            const unsigned int t = atomicAdd(&ctl->pl_ticket, 1u);
+            int o = 0;
+            if (t < total)
+                while (ocum[o + 1] <= t) o++;
+            t_sh = t;
+            o_sh = o;
+            if (t < total && ocell[o] == 1 && olvl[o] + 1 < GT_TREE_LEVELS) {
+                const int l1 = olvl[o] + 1;  // every chunk of that level first
+                const unsigned int need = nchunk[2 * l1] + nchunk[2 * l1 + 1];
+                unsigned int spins = 0;
+                while (*((volatile unsigned int *)&ctl->pl_done[l1]) < need) {
+                    if (++spins > GT_SPIN_LIMIT) {
+                        gt_set_error(ctl, GT_ETIMEOUT, GTK_PSEUDO);
+                        bad_sh = 1;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                __threadfence();
+            }
+        }
         __syncthreads();
         const unsigned int t = t_sh;
-        __syncthreads();
+        const int o = o_sh;
         if (t >= total || bad_sh) break;
-        int lvl = 0;  // the level whose tickets hold t: cum decreases with the level
-        while (lvl < TOP && cum[lvl] > t) lvl++;
-        if (threadIdx.x == 0 && lvl < TOP) {
-            const unsigned int need = cum[lvl] - cum[lvl + 1];  // chunks of level lvl + 1
-            unsigned int spins = 0;
-            while (*((volatile unsigned int *)&ctl->pl_done[lvl + 1]) < need) {
-                if (++spins > GT_SPIN_LIMIT) {
-                    gt_set_error(ctl, GT_ETIMEOUT, GTK_PSEUDO);
-                    bad_sh = 1;
-                    break;
-                }
-                __nanosleep(64);
-            }
-            __threadfence();
+        const int lvl = olvl[o], kind = ocell[o];
+        const long long idx = (long long)seg[2 * lvl + kind] + (long long)(t - ocum[o]) * PL + threadIdx.x;
+        if (idx < (long long)seg[2 * lvl + kind + 1]) {
+            if (kind == 0) pseudo_leaf<WITH_MASS>(nd, posm, nd.cells[idx]);
+            else pseudo_cell<WITH_MASS>(nd, nd.cells[idx]);
         }
-        __syncthreads();
-        if (bad_sh) break;
-        const long long idx = (long long)ctl->istart[lvl] + (long long)(t - cum[lvl]) * PL + threadIdx.x;
-        if (idx < (long long)ctl->istart[lvl + 1]) {
-            const uint32_t p = nd.cells[idx];
-            const int32_t ch0 = nd.child[p];
-            const uint32_t nch = nd.nchild[p];
-            // children written by other blocks of this launch: read through L2 (__ldcg), an SM's
-            // L1 may hold a line of them from before they were written
-            double m = WITH_MASS ? 0.0 : nd.sum[p].m, sx = 0.0, sy = 0.0, sz = 0.0;
-            for (uint32_t q = 0; q < nch; q++) {
-                const double2 *cs = (const double2 *)&nd.sum[ch0 + q];
-                const double2 s0 = __ldcg(cs), s1 = __ldcg(cs + 1);  // (m, x), (y, z)
-                if (WITH_MASS) m = __dadd_rn(m, s0.x);
-                sx = __dadd_rn(sx, s0.y);
-                sy = __dadd_rn(sy, s1.x);
-                sz = __dadd_rn(sz, s1.y);
-            }
-            const float mf = d2f(m);
-            const float jx = __fdiv_rn(d2f(sx), mf);
-            const float jy = __fdiv_rn(d2f(sy), mf);
-            const float jz = __fdiv_rn(d2f(sz), mf);
-            float b = 0.0f, b2 = 0.0f;  // b2: B_2 by parallel axes
-            for (uint32_t q = 0; q < nch; q++) {
-                const float4 cj = __ldcg(&nd.jpos[ch0 + q]);
-                const float4 cw = __ldcg(&nd.walk[ch0 + q]);
-                const float d2 = sq3f(__fsub_rn(cj.x, jx), __fsub_rn(cj.y, jy), __fsub_rn(cj.z, jz));
-                const float e = __fadd_rn(__fsqrt_rn(d2), cw.x);
-                if (e > b) b = e;
-                b2 = __fadd_rn(b2, __fadd_rn(cw.w, __fmul_rn(cj.w, d2)));
-            }
-            nd.sum[p] = DSum4{m, sx, sy, sz};
-            nd.jpos[p] = make_float4(jx, jy, jz, mf);
-            nd.walk[p] = make_float4(__fmul_rn(b, GT_RADIUS_MARGIN), __uint_as_float((uint32_t)ch0),
-                                     __uint_as_float(nch), b2);
-        }
-        __threadfence();  // every thread's cell is visible device-wide before the chunk counts as done
+        __threadfence();  // every thread's node is visible device-wide before the chunk counts as done
         __syncthreads();
         if (threadIdx.x == 0) atomicAdd(&ctl->pl_done[lvl], 1u);
     }
@@ -353,8 +640,39 @@ __global__ __launch_bounds__(PL) void k_pseudo_levels(Nodes nd, DevCtl *ctl) {
 
 }  // namespace
 
+size_t gt_build_scratch_bytes(int64_t n) {
+    const size_t N = (size_t)(n > 0 ? n : 1);
+    const size_t tiles = (N + FT - 1) / FT;
+    return (2 * N + 15) / 16 * 16 + 4 * (size_t)NREC * (tiles + 1);
+}
+
 void gt_launch_build(const uint64_t *skey, int64_t n, int leaf_max, Nodes nd, int64_t cap,
-                     unsigned long long *status, DevCtl *ctl, int nsm, cudaStream_t st) {
+                     unsigned long long *status, uint8_t *scratch, DevCtl *ctl, int nsm, cudaStream_t st) {
+    if (leaf_max <= FLAT_LWIN) {
+        const int ntiles = (int)((n + FT - 1) / FT);
+        uint16_t *dl = (uint16_t *)scratch;
+        uint32_t *cnt = (uint32_t *)(scratch + (2 * (size_t)(n > 0 ? n : 1) + 15) / 16 * 16);
+        uint32_t *tot = cnt + (size_t)NREC * ntiles;
+        if (ntiles > 0) {
+            const unsigned long long *k = (const unsigned long long *)skey;
+            switch (leaf_max) {
+            case 4: k_flat_marks<4><<<ntiles, FB, 0, st>>>(k, n, leaf_max, dl, cnt, ntiles); break;
+            case 8: k_flat_marks<8><<<ntiles, FB, 0, st>>>(k, n, leaf_max, dl, cnt, ntiles); break;
+            case 16: k_flat_marks<16><<<ntiles, FB, 0, st>>>(k, n, leaf_max, dl, cnt, ntiles); break;
+            case 32: k_flat_marks<32><<<ntiles, FB, 0, st>>>(k, n, leaf_max, dl, cnt, ntiles); break;
+            default: k_flat_marks<0><<<ntiles, FB, 0, st>>>(k, n, leaf_max, dl, cnt, ntiles); break;
+            }
+            gt_note_launches(1);
+        }
+        { k_flat_scan<<<NREC, 1024, 0, st>>>(cnt, ntiles, tot); gt_note_launches(1); }
+        { k_flat_levels<<<1, 1, 0, st>>>(tot, cap, ctl); gt_note_launches(1); }
+        if (ntiles > 0) {
+            k_flat_scatter<<<ntiles, FB, 0, st>>>(dl, n, cnt, ntiles, cap, nd, ctl);
+            { k_flat_link<<<nsm * 8, 256, 0, st>>>(nd, cap, ctl); }
+            gt_note_launches(2);
+        }
+        return;
+    }
     { k_build_init<<<1, 1, 0, st>>>(n, nd, ctl); gt_note_launches(1); }
     for (int l = 0; l < GT_TREE_LEVELS; l++)
         { k_build_level<<<nsm * 4, BT, 0, st>>>(l, (const unsigned long long *)skey, leaf_max, nd, cap,
@@ -364,19 +682,16 @@ void gt_launch_build(const uint64_t *skey, int64_t n, int leaf_max, Nodes nd, in
 void gt_launch_cell_lists(Nodes nd, int64_t cap, DevCtl *ctl, int nsm, cudaStream_t st) {
     cudaMemsetAsync(ctl->cell_bucket, 0, sizeof(ctl->cell_bucket), st);
     { k_cell_count<<<nsm * 4, 256, 0, st>>>(nd, cap, ctl); gt_note_launches(1); }
-    { k_cell_scan<<<1, 256, 0, st>>>(ctl); gt_note_launches(1); }
-    { k_cell_fill<<<nsm * 4, 256, 0, st>>>(nd, cap, ctl); gt_note_launches(1); }
+    { k_cell_scan<<<1, 1024, 0, st>>>(ctl); gt_note_launches(1); }
+    { k_cell_fill<<<nsm * 2, 256, 0, st>>>(nd, cap, ctl); gt_note_launches(1); }
 }
 
 void gt_launch_pseudo(Nodes nd, int64_t cap, const float4 *posm, DevCtl *ctl, int nsm, bool with_mass,
                       cudaStream_t st) {
     (void)cap;
-    if (with_mass) { k_pseudo_leaves<true><<<nsm * 8, 256, 0, st>>>(nd, posm, ctl); }
-    else { k_pseudo_leaves<false><<<nsm * 8, 256, 0, st>>>(nd, posm, ctl); }
-    gt_note_launches(1);
-    // the level pass's ticket and per-level counters start at zero
+    // the ticket and the per-level counters start at zero
     cudaMemsetAsync(&ctl->pl_ticket, 0, sizeof(ctl->pl_ticket) + sizeof(ctl->pl_done), st);
-    if (with_mass) { k_pseudo_levels<true><<<nsm * 4, PL, 0, st>>>(nd, ctl); }
-    else { k_pseudo_levels<false><<<nsm * 4, PL, 0, st>>>(nd, ctl); }
+    if (with_mass) { k_pseudo<true><<<nsm * 8, PL, 0, st>>>(nd, posm, ctl); }
+    else { k_pseudo<false><<<nsm * 8, PL, 0, st>>>(nd, posm, ctl); }
     gt_note_launches(1);
 }

@@ -116,6 +116,12 @@ def _oracle_tree(O, pos, mass, leaf, cap=None, curve=0):
     ("m31", 1 << 16, 8),
     ("coincident", 1000, 16),     # one chain down to level 21
     ("clustered", 20000, 3),
+    ("plummer", 2049, 2),         # one particle past a tile of the one-sweep build
+    ("nfw", 70001, 64),           # the largest leaf of the one-sweep build
+    ("nfw", 50000, 65),           # larger leaves: the level-by-level build
+    ("coincident", 1000, 200),
+    ("m31", 30011, 32),
+    ("nfw", 9001, 4),
 ])
 def test_tree_bitexact(env, kind, n, leaf):
     torch, g, O = env
