@@ -483,13 +483,22 @@ __device__ __forceinline__ void pseudo_leaf(const Nodes &nd, const float4 *__res
     const uint32_t f = nd.first[c];
     const uint32_t k = nd.count[c];
     double m = WITH_MASS ? 0.0 : nd.sum[c].m, sx = 0.0, sy = 0.0, sz = 0.0;
-    for (uint32_t i = f; i < f + k; i++) {
-        const float4 p = posm[i];
-        const double mi = f2d(p.w);  // m x is exact in FP64, so the fused form rounds once like + does
-        if (WITH_MASS) m = __dadd_rn(m, mi);
-        sx = __fma_rn(mi, f2d(p.x), sx);
-        sy = __fma_rn(mi, f2d(p.y), sy);
-        sz = __fma_rn(mi, f2d(p.z), sz);
+    // in particle order; the loads of four particles go out before their sums
+    // (m x is exact in FP64, so the fused form rounds once like + does)
+    for (uint32_t i0 = f; i0 < f + k; i0 += 2) {
+        float4 p[2];
+#pragma unroll
+        for (uint32_t q = 0; q < 2; q++)
+            if (i0 + q < f + k) p[q] = posm[i0 + q];
+#pragma unroll
+        for (uint32_t q = 0; q < 2; q++)
+            if (i0 + q < f + k) {
+                const double mi = f2d(p[q].w);
+                if (WITH_MASS) m = __dadd_rn(m, mi);
+                sx = __fma_rn(mi, f2d(p[q].x), sx);
+                sy = __fma_rn(mi, f2d(p[q].y), sy);
+                sz = __fma_rn(mi, f2d(p[q].z), sz);
+            }
     }
     float jx, jy, jz;
     if (k == 1) {  // a cell of one particle is that particle
@@ -502,11 +511,18 @@ __device__ __forceinline__ void pseudo_leaf(const Nodes &nd, const float4 *__res
         jz = __fdiv_rn(d2f(sz), mf);
     }
     float d2max = 0.0f, b2 = 0.0f;  // b2: B_2 of the multipole MAC
-    for (uint32_t i = f; i < f + k; i++) {
-        const float4 p = posm[i];
-        const float d2 = sq3f(__fsub_rn(p.x, jx), __fsub_rn(p.y, jy), __fsub_rn(p.z, jz));
-        if (d2 > d2max) d2max = d2;
-        b2 = __fadd_rn(b2, __fmul_rn(p.w, d2));
+    for (uint32_t i0 = f; i0 < f + k; i0 += 2) {
+        float4 p[2];
+#pragma unroll
+        for (uint32_t q = 0; q < 2; q++)
+            if (i0 + q < f + k) p[q] = posm[i0 + q];
+#pragma unroll
+        for (uint32_t q = 0; q < 2; q++)
+            if (i0 + q < f + k) {
+                const float d2 = sq3f(__fsub_rn(p[q].x, jx), __fsub_rn(p[q].y, jy), __fsub_rn(p[q].z, jz));
+                if (d2 > d2max) d2max = d2;
+                b2 = __fadd_rn(b2, __fmul_rn(p[q].w, d2));
+            }
     }
     nd.sum[c] = DSum4{m, sx, sy, sz};
     nd.jpos[c] = make_float4(jx, jy, jz, d2f(m));
@@ -523,17 +539,17 @@ __device__ __forceinline__ void pseudo_cell(const Nodes &nd, uint32_t p) {
     const int32_t ch0 = nd.child[p];
     const uint32_t nch = nd.nchild[p];
     double m = WITH_MASS ? 0.0 : nd.sum[p].m, sx = 0.0, sy = 0.0, sz = 0.0;
-    for (uint32_t q0 = 0; q0 < nch; q0 += 4) {
-        double2 s0[4], s1[4];  // (m, x), (y, z)
+    for (uint32_t q0 = 0; q0 < nch; q0 += 2) {
+        double2 s0[2], s1[2];  // (m, x), (y, z)
 #pragma unroll
-        for (uint32_t q = 0; q < 4; q++)
+        for (uint32_t q = 0; q < 2; q++)
             if (q0 + q < nch) {
                 const double2 *cs = (const double2 *)&nd.sum[ch0 + q0 + q];
                 s0[q] = __ldcg(cs);
                 s1[q] = __ldcg(cs + 1);
             }
 #pragma unroll
-        for (uint32_t q = 0; q < 4; q++)
+        for (uint32_t q = 0; q < 2; q++)
             if (q0 + q < nch) {
                 if (WITH_MASS) m = __dadd_rn(m, s0[q].x);
                 sx = __dadd_rn(sx, s0[q].y);
@@ -546,16 +562,16 @@ __device__ __forceinline__ void pseudo_cell(const Nodes &nd, uint32_t p) {
     const float jy = __fdiv_rn(d2f(sy), mf);
     const float jz = __fdiv_rn(d2f(sz), mf);
     float b = 0.0f, b2 = 0.0f;  // b2: B_2 by parallel axes
-    for (uint32_t q0 = 0; q0 < nch; q0 += 4) {
-        float4 cj[4], cw[4];
+    for (uint32_t q0 = 0; q0 < nch; q0 += 2) {
+        float4 cj[2], cw[2];
 #pragma unroll
-        for (uint32_t q = 0; q < 4; q++)
+        for (uint32_t q = 0; q < 2; q++)
             if (q0 + q < nch) {
                 cj[q] = __ldcg(&nd.jpos[ch0 + q0 + q]);
                 cw[q] = __ldcg(&nd.walk[ch0 + q0 + q]);
             }
 #pragma unroll
-        for (uint32_t q = 0; q < 4; q++)
+        for (uint32_t q = 0; q < 2; q++)
             if (q0 + q < nch) {
                 const float d2 = sq3f(__fsub_rn(cj[q].x, jx), __fsub_rn(cj[q].y, jy), __fsub_rn(cj[q].z, jz));
                 const float e = __fadd_rn(__fsqrt_rn(d2), cw[q].x);
@@ -570,7 +586,7 @@ __device__ __forceinline__ void pseudo_cell(const Nodes &nd, uint32_t p) {
 }
 
 template <bool WITH_MASS>
-__global__ __launch_bounds__(PL) void k_pseudo(Nodes nd, const float4 *__restrict__ posm, DevCtl *ctl) {
+__global__ __launch_bounds__(PL, 8) void k_pseudo(Nodes nd, const float4 *__restrict__ posm, DevCtl *ctl) {
     __shared__ uint32_t seg[NSEG + 1];
     __shared__ uint8_t olvl[NSEG], ocell[NSEG];      // ticket order: segment level and kind
     __shared__ uint32_t ocum[NSEG + 1];              // first ticket of every entry
