@@ -8,6 +8,8 @@
 #include <new>
 #include <vector>
 
+#include <utility>
+
 #include "gt_system.cuh"
 
 static std::atomic<long long> g_launches{0};
@@ -291,7 +293,13 @@ void build_tree(gt_system *s, cudaStream_t st, const float4 *posm_src) {
     gt_launch_sort(s->sb, n, s->ctl, st);
     ph_end(s, PH_SORT, st);
     ph_begin(s, PH_PERMUTE, st);
-    if (posm_src == s->posm_tmp) {
+    if (!s->fixed_buffers) {
+        // the gathered copy becomes the state: the two buffers swap roles
+        float4 *dst = posm_src == s->posm_tmp ? s->posm : s->posm_tmp;
+        gt_launch_permute(s->st[0], s->st[1], posm_src, dst, s->sb.val[0], n, st);
+        std::swap(s->st[0], s->st[1]);
+        if (dst != s->posm) std::swap(s->posm, s->posm_tmp);
+    } else if (posm_src == s->posm_tmp) {
         gt_launch_permute(s->st[0], s->st[1], posm_src, s->posm, s->sb.val[0], n, st);
         gt_launch_copy_state(s->st[1], s->st[0], nullptr, nullptr, n, st);
     } else {
@@ -356,6 +364,7 @@ int gt_sys_init(gt_system *s, int64_t n, const gt_params *p, void *ws, size_t ws
     if (ws_bytes < need) return GT_ENOMEM;
     carve(s, (char *)ws, n, p, s->nsm, wb, own_queue);
     s->n = n;
+    s->fixed_buffers = !own_queue;
     gt_sys_apply_params(s, *p);
     // zero the control block and the look-back status words (on st, then wait for it;
     // without a stream, on the default stream and wait for the device)

@@ -66,6 +66,9 @@ struct gt_system {
     int dev = 0, nsm = 0;
     int walk_blocks = 0, walk_warps = 0;
     bool started = false, have_tree = false, last_rebuilt = false;
+    // members of a batch or a server keep their state in buffer 0 (captured graphs and
+    // kernel arguments hold those addresses); a standalone system swaps its buffers instead
+    bool fixed_buffers = false;
     long long steps = 0, rebuilds = 0;
     int64_t cap = 0;        // node capacity
     State st[2]{};

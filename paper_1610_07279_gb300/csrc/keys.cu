@@ -6,6 +6,7 @@
 #include <float.h>
 
 #include "gt_internal.cuh"
+#include "keys_quant.cuh"
 
 namespace {
 
@@ -83,13 +84,16 @@ __device__ __forceinline__ unsigned long long spread3(unsigned long long v) {
     return v;
 }
 
-__device__ __forceinline__ unsigned long long quantise(float x, double xmin, double scale) {
-    // floor((x - xmin) * 2^21/side) in FP64 with explicit rounding, clamped to 2^21 - 1.
-    // x is widened exactly on the integer pipe; the floor is the round-down conversion
-    // (the product is >= 0), so the FP64 pipe runs one sub, one mul and one conversion.
-    const double t = __dmul_rn(__dsub_rn(f2d(x), xmin), scale);
-    const unsigned long long q = __double2ull_rd(t);
-    constexpr unsigned long long QMAX = (1ull << GT_KEY_LEVELS) - 1ull;
+constexpr unsigned long long QMAX = (1ull << GT_KEY_LEVELS) - 1ull;
+
+__device__ __forceinline__ unsigned long long quantise(float x, float xmin, double scale) {
+    // floor((x - xmin) * 2^21/side) with FP64 roundings (RN difference, RN product, then
+    // the floor), clamped to 2^21 - 1: in integer arithmetic (keys_quant.cuh), or for the
+    // rare operands it does not take, on the FP64 pipe -- x widened exactly on the
+    // integer pipe, the floor the round-down conversion (the product is >= 0).
+    unsigned long long q;
+    if (quantise_exact(x, xmin, (unsigned long long)__double_as_longlong(scale), QMAX, &q)) return q;
+    q = __double2ull_rd(__dmul_rn(__dsub_rn(f2d(x), f2d(xmin)), scale));
     return q < QMAX ? q : QMAX;
 }
 
@@ -126,9 +130,9 @@ __global__ __launch_bounds__(256) void k_keys(const float4 *__restrict__ posm, l
     unsigned long long k = 0;
     if (side > 0.0) {
         const float4 p = posm[i];
-        const unsigned long long qx = quantise(p.x, f2d(ctl->bbox_min[0]), scale);
-        const unsigned long long qy = quantise(p.y, f2d(ctl->bbox_min[1]), scale);
-        const unsigned long long qz = quantise(p.z, f2d(ctl->bbox_min[2]), scale);
+        const unsigned long long qx = quantise(p.x, ctl->bbox_min[0], scale);
+        const unsigned long long qy = quantise(p.y, ctl->bbox_min[1], scale);
+        const unsigned long long qz = quantise(p.z, ctl->bbox_min[2], scale);
         if (curve == GT_KEY_HILBERT) {
             uint32_t x0 = (uint32_t)qx, x1 = (uint32_t)qy, x2 = (uint32_t)qz;
             hilbert_transpose(x0, x1, x2);

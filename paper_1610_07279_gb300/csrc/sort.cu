@@ -4,8 +4,9 @@
 // Eight passes of 8-bit digits, one kernel per pass after one histogram pass:
 //   k_hist_all     all eight digit histograms in one read of the keys   (reads 8 B/key)
 //   k_digit_bases  exclusive scans of the histograms -> where every digit starts
-//   k_onesweep     per 2048-key tile taken in ticket order: a stable rank of every key
-//                  inside the tile (warp-striped match/popc), the tile's per-digit counts
+//   k_onesweep     per 4096-key tile (512 threads) taken in ticket order: a stable rank of
+//                  every key inside the tile (warp-striped; a key's peers with the same
+//                  digit from nine ballots, its rank by popc), the tile's per-digit counts
 //                  published and each digit's exclusive prefix over earlier tiles found
 //                  by a decoupled look-back (256 digits in parallel, a window of 8 earlier
 //                  tiles per step, every wait bounded), a local sort in shared memory,
@@ -18,21 +19,28 @@
 
 namespace {
 
-constexpr int ST = 256;            // threads per tile
+#ifndef GT_SORT_ST
+#define GT_SORT_ST 512
+#endif
 #ifndef GT_SORT_IPT
 #define GT_SORT_IPT 8
 #endif
-constexpr int IPT = GT_SORT_IPT;   // keys per thread
-constexpr int TILE = ST * IPT;     // keys per tile
+#ifndef GT_SORT_MINB
+#define GT_SORT_MINB 3
+#endif
 constexpr int RB = 8;              // digit bits
 constexpr int R = 1 << RB;         // digits
+constexpr int HT = R;              // threads of the histogram and digit-base kernels
+constexpr int ST = GT_SORT_ST;     // threads per tile (the first R of them also own one digit each)
+constexpr int IPT = GT_SORT_IPT;   // keys per thread
+constexpr int TILE = ST * IPT;     // keys per tile
 constexpr int NW = ST / 32;
 constexpr int PASSES = 8;          // 64 / RB (bit 63 is always 0; the last pass is cheap)
 constexpr size_t SCATTER_SMEM = TILE * sizeof(unsigned long long) + TILE * sizeof(uint32_t) +
                                 (NW * R + 2 * R + NW + 1) * sizeof(uint32_t);
-static_assert(ST == R, "one thread per digit in the per-tile scans");
+static_assert(ST >= R && ST % 32 == 0, "one thread per digit in the per-tile scans");
 
-__global__ __launch_bounds__(ST) void k_hist_all(long long n, const unsigned long long *__restrict__ key,
+__global__ __launch_bounds__(HT) void k_hist_all(long long n, const unsigned long long *__restrict__ key,
                                                  uint32_t *__restrict__ hist /* PASSES x R */) {
     __shared__ uint32_t h[PASSES][R];
     for (int p = 0; p < PASSES; p++) h[p][threadIdx.x] = 0;
@@ -40,7 +48,7 @@ __global__ __launch_bounds__(ST) void k_hist_all(long long n, const unsigned lon
     // the keys of a tree rebuild arrive nearly sorted (the particles are still in the
     // previous key order), so a warp's 32 neighbouring keys often share their high digits:
     // such a digit is counted once for the whole warp, the others by one atomic per lane
-    for (long long i0 = (long long)blockIdx.x * ST; i0 < n; i0 += (long long)gridDim.x * ST) {
+    for (long long i0 = (long long)blockIdx.x * HT; i0 < n; i0 += (long long)gridDim.x * HT) {
         const long long i = i0 + threadIdx.x;
         const bool ok = i < n;
         const unsigned long long k = ok ? key[i] : 0ull;
@@ -62,12 +70,12 @@ __global__ __launch_bounds__(ST) void k_hist_all(long long n, const unsigned lon
 }
 
 // one block: digit starts of every pass; also opens a new look-back epoch and resets the tickets
-__global__ __launch_bounds__(ST) void k_digit_bases(const uint32_t *__restrict__ hist,
+__global__ __launch_bounds__(HT) void k_digit_bases(const uint32_t *__restrict__ hist,
                                                     uint32_t *__restrict__ base, DevCtl *ctl) {
-    __shared__ uint32_t tmp[ST / 32 + 1];
+    __shared__ uint32_t tmp[HT / 32 + 1];
     for (int p = 0; p < PASSES; p++) {
         uint32_t tot;
-        const uint32_t b = block_excl_scan<ST>(hist[p * R + threadIdx.x], &tot, tmp);
+        const uint32_t b = block_excl_scan<HT>(hist[p * R + threadIdx.x], &tot, tmp);
         base[p * R + threadIdx.x] = b;
     }
     if (threadIdx.x < PASSES) ctl->sort_ticket[threadIdx.x] = 0;
@@ -119,7 +127,7 @@ __device__ __forceinline__ uint32_t lookback_digit(const unsigned long long *sta
     return excl;
 }
 
-__global__ __launch_bounds__(ST) void k_onesweep(long long n, int pass,
+__global__ __launch_bounds__(ST, GT_SORT_MINB) void k_onesweep(long long n, int pass,
                                                  const unsigned long long *__restrict__ kin,
                                                  const uint32_t *__restrict__ vin,
                                                  unsigned long long *__restrict__ kout,
@@ -159,7 +167,12 @@ __global__ __launch_bounds__(ST) void k_onesweep(long long n, int pass,
     for (int j = 0; j < IPT; j++) {
         const bool ok = base + j * 32 + lane < n;
         const unsigned int d = ok ? (unsigned int)((k[j] >> shift) & (R - 1)) : (unsigned int)R;
-        const unsigned int peers = __match_any_sync(0xffffffffu, d);
+        unsigned int peers = 0xffffffffu;  // lanes with the same digit (bit 8: past the end)
+#pragma unroll
+        for (int b = 0; b <= RB; b++) {
+            const unsigned int bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bal : ~bal;
+        }
         const unsigned int rank = __popc(peers & lt);
         unsigned int prev = 0;
         if (ok) prev = wcnt[w * R + d];
@@ -169,25 +182,25 @@ __global__ __launch_bounds__(ST) void k_onesweep(long long n, int pass,
         loc[j] = prev + rank;
     }
     __syncthreads();
-    // thread d: exclusive offsets of the warps for digit d, the tile's count of digit d
+    // thread d < R: exclusive offsets of the warps for digit d, the tile's count of digit d
     const int d = threadIdx.x;
+    const bool dig = d < R;
     uint32_t cnt = 0;
-    for (int ww = 0; ww < NW; ww++) {
-        const uint32_t t = wcnt[ww * R + d];
-        wcnt[ww * R + d] = cnt;
-        cnt += t;
-    }
+    if (dig)
+        for (int ww = 0; ww < NW; ww++) {
+            const uint32_t t = wcnt[ww * R + d];
+            wcnt[ww * R + d] = cnt;
+            cnt += t;
+        }
     // publish this tile's count of digit d as early as possible
     const unsigned int epoch = ctl->sort_epoch * PASSES + (unsigned)pass;
     const unsigned long long tagA = (unsigned long long)(4u * epoch + 1u) << 32;
     const unsigned long long tagP = (unsigned long long)(4u * epoch + 2u) << 32;
-    unsigned long long *own = status + (size_t)tile * R + d;
-    if (tile == 0)
-        *((volatile unsigned long long *)own) = tagP | cnt;
-    else
-        *((volatile unsigned long long *)own) = tagA | cnt;
+    unsigned long long *own = status + (size_t)tile * R + (dig ? d : 0);
+    if (dig) *((volatile unsigned long long *)own) = (tile == 0 ? tagP : tagA) | cnt;
     uint32_t total;
-    dstart[d] = block_excl_scan<ST>(cnt, &total, scantmp);
+    const uint32_t ds0 = block_excl_scan<ST>(cnt, &total, scantmp);
+    if (dig) dstart[d] = ds0;
     __syncthreads();
     // local sort by digit in shared memory (stable: warp offset + rank inside the warp)
 #pragma unroll
@@ -201,12 +214,14 @@ __global__ __launch_bounds__(ST) void k_onesweep(long long n, int pass,
         }
     }
     // count of digit d in all earlier tiles, then this tile's inclusive prefix
-    uint32_t excl = 0;
-    if (tile > 0) {
-        excl = lookback_digit(status, tile, d, tagA, tagP, ctl);
-        *((volatile unsigned long long *)own) = tagP | (unsigned long long)(excl + cnt);
+    if (dig) {
+        uint32_t excl = 0;
+        if (tile > 0) {
+            excl = lookback_digit(status, tile, d, tagA, tagP, ctl);
+            *((volatile unsigned long long *)own) = tagP | (unsigned long long)(excl + cnt);
+        }
+        gbase[d] = digit_base[pass * R + d] + excl - dstart[d];
     }
-    gbase[d] = digit_base[pass * R + d] + excl - dstart[d];
     __syncthreads();
     const long long rem = n - (long long)tile * TILE;
     const int m = rem < TILE ? (int)rem : TILE;
@@ -239,9 +254,9 @@ void gt_launch_sort(SortBufs &b, int64_t n, DevCtl *ctl, cudaStream_t st) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const long long blocks = (n + ST - 1) / ST;
-    { k_hist_all<<<(unsigned)(blocks < nsm * 8 ? blocks : nsm * 8), ST, 0, st>>>(n, (const unsigned long long *)b.key[0], b.hist); gt_note_launches(1); }
-    { k_digit_bases<<<1, ST, 0, st>>>(b.hist, b.digit_base, ctl); gt_note_launches(1); }
+    const long long blocks = (n + HT - 1) / HT;
+    { k_hist_all<<<(unsigned)(blocks < nsm * 8 ? blocks : nsm * 8), HT, 0, st>>>(n, (const unsigned long long *)b.key[0], b.hist); gt_note_launches(1); }
+    { k_digit_bases<<<1, HT, 0, st>>>(b.hist, b.digit_base, ctl); gt_note_launches(1); }
     for (int p = 0; p < PASSES; p++) {
         const int src = p & 1, dst = src ^ 1;
         { k_onesweep<<<ntiles, ST, SCATTER_SMEM, st>>>(n, p, (const unsigned long long *)b.key[src], b.val[src],

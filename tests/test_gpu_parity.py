@@ -155,6 +155,39 @@ def test_tree_bitexact_hilbert(env, kind, n, leaf):
     s.close()
 
 
+@pytest.mark.parametrize("curve", [0, 1])
+def test_keys_bitexact_on_awkward_coordinates(env, curve):
+    """Sec. 2.1: the quantisation floor(RN(RN(x - xmin) 2^21 / side)) on coordinates whose
+    FP32 exponents are far from the box corner's (tiny values around 0, subnormals, zeros),
+    exact powers of two and neighbours one ulp apart -- the GPU's integer evaluation of
+    the two roundings (and its FP64 route for the rest) against the oracle, bit for bit."""
+    torch, g, O = env
+    rng = np.random.default_rng(77 + curve)
+    n = 40000
+    pos = rng.standard_normal((n, 3)) * 10.0
+    pos[:3000] *= 1e-30                                   # tiny: exponent gaps beyond 38
+    pos[3000:3100] = 0.0
+    pos[3100:3400] = np.sign(rng.standard_normal((300, 3))) * 2.0 ** rng.integers(-24, 7, (300, 3))
+    pos[3400:3500] = np.float32(1e-41) * np.sign(rng.standard_normal((100, 3)))  # FP32 subnormals
+    base = np.float32(rng.standard_normal((100, 3)))
+    pos[3500:3600] = np.nextafter(base, np.float32(np.inf))  # one ulp from the next block
+    pos[3600:3700] = base
+    pos[3700] = (-200.0, -150.0, -0.375)                  # the box corner
+    pos[3701] = (199.5, 120.0, 3.0)
+    pos = pos.astype(np.float32).astype(np.float64)
+    mass = np.full(n, 1.0 / n, np.float32)
+    s = g.System(n, _params(g, 0.01, node_factor=4, key_curve=curve))
+    s.set_state(pos, np.zeros_like(pos), mass)
+    s.build_tree()
+    t = s.get_tree()
+    s.sync()
+    key, box = O.keys(_p4(pos, mass), curve)
+    order, skey = O.sort(key)
+    assert np.array_equal(t["keys"], skey)
+    assert np.array_equal(t["order"], order)
+    s.close()
+
+
 def test_walk_and_steps_on_hilbert_keys(env):
     _walk_case(env, "nfw", 30000, 9, 1, 0, 64, key_curve=1)
     _walk_case(env, "plummer", 1 << 13, 9, 2, 0, 32, delta_acc=2.0 ** -8, key_curve=1)
