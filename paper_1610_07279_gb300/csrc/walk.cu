@@ -84,6 +84,24 @@ __device__ __forceinline__ void interact(const float4 s, float xi, float yi, flo
     ph -= mr;
 }
 
+// One source s against the lane's two members at once, on the packed FP32 pipe (two
+// lanes of work per instruction): (xi, yi, zi) hold the members' coordinates, the sums
+// the two members' accelerations and (positive) potential sums.
+__device__ __forceinline__ void interact_pair(const float4 s, float2 xi, float2 yi, float2 zi, float2 eps2,
+                                              float2 &ax, float2 &ay, float2 &az, float2 &ph) {
+    const float2 dx = __fadd2_rn(make_float2(s.x, s.x), xi);  // xi holds the negated coordinates
+    const float2 dy = __fadd2_rn(make_float2(s.y, s.y), yi);
+    const float2 dz = __fadd2_rn(make_float2(s.z, s.z), zi);
+    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, eps2)));
+    const float2 rinv = make_float2(rsqrt_sfu(r2.x), rsqrt_sfu(r2.y));
+    const float2 mr = __fmul2_rn(make_float2(s.w, s.w), rinv);
+    const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, rinv), rinv);
+    ax = __ffma2_rn(mr3, dx, ax);
+    ay = __ffma2_rn(mr3, dy, ay);
+    az = __ffma2_rn(mr3, dz, az);
+    ph = __fadd2_rn(ph, mr);
+}
+
 // (value, member) of the extreme member on one axis: the smallest (want_max false) or
 // largest value, the lowest member index on ties
 __device__ __forceinline__ void warp_arg_ext(float &v, int &m, bool want_max) {
@@ -245,18 +263,18 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
         __syncwarp();
         int j = sub;
         if (two) {  // every list entry read once for both members of the lane
+            const float2 nx = make_float2(-pi.x, -pi2.x), ny = make_float2(-pi.y, -pi2.y);
+            const float2 nz = make_float2(-pi.z, -pi2.z), e2 = make_float2(a.eps2, a.eps2);
+            float2 sx = make_float2(ax, bx), sy = make_float2(ay, by), sz = make_float2(az, bz);
+            float2 sp = make_float2(-ph, -qh);
             for (; j + 1 < list_n; j += 2) {
                 const float4 s0 = list[j], s1 = list[j + 1];
-                interact(s0, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
-                interact(s0, pi2.x, pi2.y, pi2.z, a.eps2, bx, by, bz, qh);
-                interact(s1, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
-                interact(s1, pi2.x, pi2.y, pi2.z, a.eps2, bx, by, bz, qh);
+                interact_pair(s0, nx, ny, nz, e2, sx, sy, sz, sp);
+                interact_pair(s1, nx, ny, nz, e2, sx, sy, sz, sp);
             }
-            if (j < list_n) {
-                const float4 s0 = list[j];
-                interact(s0, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
-                interact(s0, pi2.x, pi2.y, pi2.z, a.eps2, bx, by, bz, qh);
-            }
+            if (j < list_n) interact_pair(list[j], nx, ny, nz, e2, sx, sy, sz, sp);
+            ax = sx.x; bx = sx.y; ay = sy.x; by = sy.y; az = sz.x; bz = sz.y;
+            ph = -sp.x; qh = -sp.y;
             j = list_n;
         }
         for (; j + 3 * S < list_n; j += 4 * S) {
