@@ -335,8 +335,18 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
                 overflow = true;
                 break;
             }
-            const uint32_t pos = tail + incl - nch;
-            for (uint32_t k = 0; k < nch; k++) q[(pos + k) & qmask] = l0 + k;
+            // the warp writes the children together: entry e belongs to the first lane whose
+            // inclusive count exceeds e (a binary search over the lanes by shuffles)
+            const uint32_t cbase = l0 - (incl - nch);
+            for (uint32_t r = 0; r < tot; r += 32) {
+                const uint32_t e = r + (uint32_t)lane;
+                int own = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (__shfl_sync(FULL, incl, own + step - 1) <= e) own += step;
+                const uint32_t cb = __shfl_sync(FULL, cbase, own);
+                if (e < tot) q[(tail + e) & qmask] = cb + e;
+            }
             tail += tot;
         }
         // opened leaves -> their particles into the list (asynchronous copies)
@@ -346,8 +356,16 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
         if (ltot) {
             if (list_n + (int)ltot > LIST_CAP) flush();
             if (ltot <= (uint32_t)LIST_CAP) {
-                const uint32_t dst = (uint32_t)list_n + lincl - lc;
-                for (uint32_t k = 0; k < lc; k++) cp_async16(&list[dst + k], &a.posm[l0 + k]);
+                const uint32_t pbase = l0 - (lincl - lc);
+                for (uint32_t r = 0; r < ltot; r += 32) {
+                    const uint32_t e = r + (uint32_t)lane;
+                    int own = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1)
+                        if (__shfl_sync(FULL, lincl, own + step - 1) <= e) own += step;
+                    const uint32_t pb = __shfl_sync(FULL, pbase, own);
+                    if (e < ltot) cp_async16(&list[list_n + e], &a.posm[pb + e]);
+                }
                 list_n += (int)ltot;
             } else {  // leaves holding more particles than the list: one at a time, in chunks
                 unsigned lm = __ballot_sync(FULL, lc != 0u);
