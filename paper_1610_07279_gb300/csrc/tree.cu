@@ -675,6 +675,7 @@ void gt_launch_build(const uint64_t *skey, int64_t n, int leaf_max, Nodes nd, in
             case 4: k_flat_marks<4><<<ntiles, FB, 0, st>>>(k, n, leaf_max, dl, cnt, ntiles); break;
             case 8: k_flat_marks<8><<<ntiles, FB, 0, st>>>(k, n, leaf_max, dl, cnt, ntiles); break;
             case 16: k_flat_marks<16><<<ntiles, FB, 0, st>>>(k, n, leaf_max, dl, cnt, ntiles); break;
+            case 24: k_flat_marks<24><<<ntiles, FB, 0, st>>>(k, n, leaf_max, dl, cnt, ntiles); break;
             case 32: k_flat_marks<32><<<ntiles, FB, 0, st>>>(k, n, leaf_max, dl, cnt, ntiles); break;
             default: k_flat_marks<0><<<ntiles, FB, 0, st>>>(k, n, leaf_max, dl, cnt, ntiles); break;
             }

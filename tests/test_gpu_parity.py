@@ -581,10 +581,10 @@ def test_automatic_rebuild_interval(env):
 
 
 # ------------------------------------------------------------------ full sizes, sampled
-def _full_size_sampled(env, kind, n, seed, ngroups_sample=48):
+def _full_size_sampled(env, kind, n, seed, ngroups_sample=48, leaf_max=16):
     torch, g, O = env
     pos, vel, mass, eps = _model(kind, n, seed)
-    prm = _params(g, eps)
+    prm = _params(g, eps, leaf_max=leaf_max)
     oprm = _oparams(O, prm)
     ref = _oracle_tree(O, pos, mass, prm.leaf_max)
     s = g.System(n, prm)
@@ -617,4 +617,5 @@ def test_nfw_2p20_full_size(env):
 
 
 def test_andromeda_2p24_full_size(env):
-    _full_size_sampled(env, "m31", 1 << 24, 3, ngroups_sample=32)
+    """The benchmark's main workload and leaf size (24), sampled groups against the oracle."""
+    _full_size_sampled(env, "m31", 1 << 24, 3, ngroups_sample=32, leaf_max=24)
