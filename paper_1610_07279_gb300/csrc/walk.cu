@@ -16,13 +16,17 @@
 //     the set of interactions); 32 queued cells are tested at once, one per lane, with the MAC at
 //     distance lambda r_JI (Eqs. 2, 5-7) in FP32 with explicit rounding (so the decision
 //     is reproducible); accepted cells join the shared-memory interaction list,
-//     rejected cells push their children (warp prefix sum), rejected leaves copy their
-//     particles into the list with asynchronous global-to-shared copies (cp.async),
-//     waited for only when the list is flushed;
-//   * the list is flushed through Eq. (1) whenever it fills: each i-particle is held by
-//     S lanes that take every S-th list entry (FP32, rsqrt), summed with xor-shuffles at
-//     the end.  The potential is accumulated too; the member's own term -G m_i/eps is
-//     removed at the end (Eq. 1 excludes j = i).
+//     rejected cells push their children, rejected leaves copy their particles into the
+//     list with asynchronous global-to-shared copies (cp.async), waited for only when the
+//     list is flushed -- both spread over the whole warp (a warp prefix sum, then each
+//     lane finds the owner of its entry by a binary search over the lanes);
+//   * the list is kept as structure of arrays (x, y, z, m), so two consecutive entries
+//     load as packed pairs; it is flushed through Eq. (1) whenever it fills: each
+//     i-particle is held by S lanes that take every S-th pair of entries on the packed
+//     FP32 pipe (f32x2 add, mul and fma: two interactions per instruction; rsqrt on the
+//     SFU), the two halves and the S lanes summed at the end (an odd list gets a
+//     massless last entry).  The potential is accumulated too; the member's own term
+//     -G m_i/eps is removed at the end (Eq. 1 excludes j = i).
 // Bound: FP32 ALU (the force loop: 3 FADD, 3 FMUL, 7 FFMA and one MUFU rsqrt per
 // interaction); the node records (32 B per cell) stay resident in L2.
 #include <math.h>
@@ -56,9 +60,9 @@ __device__ __forceinline__ bool mac_accept(int mac, float theta, float dacc_amin
     return __fmul_rn(__fmul_rn(d2, d2), dacc_amin) >= __fmul_rn(__fmul_rn(G, jp.w), __fmul_rn(bJ, bJ));
 }
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
@@ -71,30 +75,16 @@ __device__ __forceinline__ float rsqrt_sfu(float r2) {
     return r;
 }
 
-__device__ __forceinline__ void interact(const float4 s, float xi, float yi, float zi, float eps2,
-                                         float &ax, float &ay, float &az, float &ph) {
-    const float dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-    const float rinv = rsqrt_sfu(r2);
-    const float mr = s.w * rinv;
-    const float mr3 = mr * rinv * rinv;
-    ax = fmaf(mr3, dx, ax);
-    ay = fmaf(mr3, dy, ay);
-    az = fmaf(mr3, dz, az);
-    ph -= mr;
-}
-
-// One source s against the lane's two members at once, on the packed FP32 pipe (two
-// lanes of work per instruction): (xi, yi, zi) hold the members' coordinates, the sums
-// the two members' accelerations and (positive) potential sums.
-__device__ __forceinline__ void interact_pair(const float4 s, float2 xi, float2 yi, float2 zi, float2 eps2,
-                                              float2 &ax, float2 &ay, float2 &az, float2 &ph) {
-    const float2 dx = __fadd2_rn(make_float2(s.x, s.x), xi);  // xi holds the negated coordinates
-    const float2 dy = __fadd2_rn(make_float2(s.y, s.y), yi);
-    const float2 dz = __fadd2_rn(make_float2(s.z, s.z), zi);
-    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, eps2)));
+// Two list entries (packed: x = (x_e, x_e+1), ...) against one i-particle (negated
+// coordinates nx, ny, nz) on the packed FP32 pipe; the sums keep the two entries' shares
+// in their two halves.
+__device__ __forceinline__ void interact_pairs(float2 X, float2 Y, float2 Z, float2 W, float2 nx, float2 ny,
+                                               float2 nz, float2 e2, float2 &ax, float2 &ay, float2 &az,
+                                               float2 &ph) {
+    const float2 dx = __fadd2_rn(X, nx), dy = __fadd2_rn(Y, ny), dz = __fadd2_rn(Z, nz);
+    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, e2)));
     const float2 rinv = make_float2(rsqrt_sfu(r2.x), rsqrt_sfu(r2.y));
-    const float2 mr = __fmul2_rn(make_float2(s.w, s.w), rinv);
+    const float2 mr = __fmul2_rn(W, rinv);
     const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, rinv), rinv);
     ax = __ffma2_rn(mr3, dx, ax);
     ay = __ffma2_rn(mr3, dy, ay);
@@ -183,7 +173,7 @@ __device__ __forceinline__ void ebs_centre(float4 pi, float4 pi2, bool mine1, bo
 
 // One group g of system a (Sec. 2.3): pseudo i-particle, traversal, force loop.  The
 // warp's interaction and MAC-test counts are added to n_inter and n_tests.
-__device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32_t ngroups, float4 *list,
+__device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32_t ngroups, float *lx,
                                            uint32_t *q, unsigned long long &n_inter,
                                            unsigned long long &n_tests) {
     const int lane = threadIdx.x & 31;
@@ -258,33 +248,36 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
     float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f;
     float bx = 0.f, by = 0.f, bz = 0.f, qh = 0.f;  // the second member's sums
     int list_n = 0;
+    // the list, structure of arrays: x, y, z, m of entry e at lx[e], ly[e], lz[e], lw[e]
+    float *ly = lx + LIST_CAP, *lz = lx + 2 * LIST_CAP, *lw = lx + 3 * LIST_CAP;
     auto flush = [&]() {
         cp_async_wait_all();
         __syncwarp();
-        int j = sub;
-        if (two) {  // every list entry read once for both members of the lane
-            const float2 nx = make_float2(-pi.x, -pi2.x), ny = make_float2(-pi.y, -pi2.y);
-            const float2 nz = make_float2(-pi.z, -pi2.z), e2 = make_float2(a.eps2, a.eps2);
-            float2 sx = make_float2(ax, bx), sy = make_float2(ay, by), sz = make_float2(az, bz);
-            float2 sp = make_float2(-ph, -qh);
-            for (; j + 1 < list_n; j += 2) {
-                const float4 s0 = list[j], s1 = list[j + 1];
-                interact_pair(s0, nx, ny, nz, e2, sx, sy, sz, sp);
-                interact_pair(s1, nx, ny, nz, e2, sx, sy, sz, sp);
-            }
-            if (j < list_n) interact_pair(list[j], nx, ny, nz, e2, sx, sy, sz, sp);
-            ax = sx.x; bx = sx.y; ay = sy.x; by = sy.y; az = sz.x; bz = sz.y;
-            ph = -sp.x; qh = -sp.y;
-            j = list_n;
+        // entries are taken in pairs (e, e + 1); an odd list gets a massless last entry,
+        // which adds exactly nothing
+        if (list_n & 1) {
+            if (lane == 0) { lx[list_n] = 0.f; ly[list_n] = 0.f; lz[list_n] = 0.f; lw[list_n] = 0.f; }
+            __syncwarp();
         }
-        for (; j + 3 * S < list_n; j += 4 * S) {
-            const float4 s0 = list[j], s1 = list[j + S], s2 = list[j + 2 * S], s3 = list[j + 3 * S];
-            interact(s0, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
-            interact(s1, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
-            interact(s2, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
-            interact(s3, pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
+        const int npair = (list_n + 1) >> 1;
+        const float2 *px = (const float2 *)lx, *py = (const float2 *)ly, *pz = (const float2 *)lz,
+                     *pw = (const float2 *)lw;
+        // one i-particle against pairs k0, k0 + step, ... (its sums carried in and out)
+        auto run = [&](const float4 &p, float &sx_, float &sy_, float &sz_, float &sp_, int k0, int step) {
+            const float2 e2 = make_float2(a.eps2, a.eps2);
+            const float2 nx = make_float2(-p.x, -p.x), ny = make_float2(-p.y, -p.y), nz = make_float2(-p.z, -p.z);
+            float2 sx = make_float2(sx_, 0.f), sy = make_float2(sy_, 0.f), sz = make_float2(sz_, 0.f);
+            float2 sp = make_float2(-sp_, 0.f);
+            for (int k = k0; k < npair; k += step) interact_pairs(px[k], py[k], pz[k], pw[k], nx, ny, nz, e2, sx, sy, sz, sp);
+            sx_ = __fadd_rn(sx.x, sx.y); sy_ = __fadd_rn(sy.x, sy.y); sz_ = __fadd_rn(sz.x, sz.y);
+            sp_ = -__fadd_rn(sp.x, sp.y);
+        };
+        if (two) {  // both members of the lane over every pair, one after the other
+            run(pi, ax, ay, az, ph, 0, 1);
+            run(pi2, bx, by, bz, qh, 0, 1);
+        } else {  // S lanes per i-particle: lane sub takes pairs sub, sub + S, ...
+            run(pi, ax, ay, az, ph, sub, S);
         }
-        for (; j < list_n; j += S) interact(list[j], pi.x, pi.y, pi.z, a.eps2, ax, ay, az, ph);
         n_inter += (unsigned long long)list_n * cnt;
         list_n = 0;
         __syncwarp();
@@ -323,7 +316,10 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
         if (am) {
             const int nacc = __popc(am);
             if (list_n + nacc > LIST_CAP) flush();
-            if (ok) list[list_n + __popc(am & lt)] = jp;
+            if (ok) {
+                const int e = list_n + __popc(am & lt);
+                lx[e] = jp.x; ly[e] = jp.y; lz[e] = jp.z; lw[e] = jp.w;
+            }
             list_n += nacc;
         }
         // opened cells -> queue their children
@@ -364,7 +360,13 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
                     for (int step = 16; step > 0; step >>= 1)
                         if (__shfl_sync(FULL, lincl, own + step - 1) <= e) own += step;
                     const uint32_t pb = __shfl_sync(FULL, pbase, own);
-                    if (e < ltot) cp_async16(&list[list_n + e], &a.posm[pb + e]);
+                    if (e < ltot) {
+                        const float *src = (const float *)&a.posm[pb + e];
+                        cp_async4(&lx[list_n + e], src);
+                        cp_async4(&ly[list_n + e], src + 1);
+                        cp_async4(&lz[list_n + e], src + 2);
+                        cp_async4(&lw[list_n + e], src + 3);
+                    }
                 }
                 list_n += (int)ltot;
             } else {  // leaves holding more particles than the list: one at a time, in chunks
@@ -378,8 +380,13 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
                     while (done < lcount) {
                         if (list_n == LIST_CAP) flush();
                         const uint32_t take = min(lcount - done, (uint32_t)(LIST_CAP - list_n));
-                        for (uint32_t k = lane; k < take; k += 32)
-                            cp_async16(&list[list_n + k], &a.posm[lf + done + k]);
+                        for (uint32_t k = lane; k < take; k += 32) {
+                            const float *src = (const float *)&a.posm[lf + done + k];
+                            cp_async4(&lx[list_n + k], src);
+                            cp_async4(&ly[list_n + k], src + 1);
+                            cp_async4(&lz[list_n + k], src + 2);
+                            cp_async4(&lw[list_n + k], src + 3);
+                        }
                         list_n += (int)take;
                         done += take;
                     }
@@ -426,10 +433,10 @@ __device__ __forceinline__ int system_of(const uint32_t *gprefix, int nsys, uint
     return lo;
 }
 
-__global__ __launch_bounds__(WT, 4) void k_walk(WalkArgs a) {
-    __shared__ __align__(16) float4 list_sm[NWARP][LIST_CAP];
+__global__ __launch_bounds__(WT, 3) void k_walk(WalkArgs a) {
+    __shared__ __align__(16) float list_sm[NWARP][4 * LIST_CAP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4 *list = list_sm[warp];
+    float *list = list_sm[warp];
     uint32_t *q = a.queue + (size_t)(blockIdx.x * NWARP + warp) * (size_t)a.qcap;
     const uint32_t na = a.ctl->n_active;
     const uint32_t gmax = (uint32_t)a.gmax;
@@ -452,14 +459,14 @@ __global__ __launch_bounds__(WT, 4) void k_walk(WalkArgs a) {
 // in order (gprefix), every warp takes the next one from one counter and walks it
 // with that system's arguments (copied to shared memory).  mac >= 0 overrides every
 // system's MAC (the opening-angle start-up pass).
-__global__ __launch_bounds__(WT, 4) void k_walk_batch(const WalkArgs *__restrict__ args, int nsys,
+__global__ __launch_bounds__(WT, 3) void k_walk_batch(const WalkArgs *__restrict__ args, int nsys,
                                                       const uint32_t *__restrict__ gprefix,
                                                       unsigned int *group_next, uint32_t *queue, int qcap,
                                                       int mac) {
-    __shared__ __align__(16) float4 list_sm[NWARP][LIST_CAP];
+    __shared__ __align__(16) float list_sm[NWARP][4 * LIST_CAP];
     __shared__ WalkArgs sargs[NWARP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4 *list = list_sm[warp];
+    float *list = list_sm[warp];
     uint32_t *q = queue + (size_t)(blockIdx.x * NWARP + warp) * (size_t)qcap;
     const uint32_t total = gprefix[nsys];
     for (;;) {
