@@ -205,13 +205,18 @@ __global__ __launch_bounds__(AT) void k_compact(long long n_host, const unsigned
         const uint32_t tile = tile_sh;
         __syncthreads();
         if (tile >= ntiles) break;
-        const long long i0 = (long long)tile * ATILE + threadIdx.x * AIPT;
-        uint32_t sel = 0;
+        // warp w owns items [wbase, wbase + 32 AIPT); row q is items wbase + 32 q + lane, so
+        // every load and store of a row is one coalesced access, and rows then lanes
+        // visit the items in index order (the compaction keeps it)
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const long long wbase = (long long)tile * ATILE + (long long)w * (32 * AIPT);
+        unsigned int bal[AIPT];
+        uint32_t wsel = 0;
 #pragma unroll
         for (int q = 0; q < AIPT; q++) {
-            const long long i = i0 + q;
+            const long long i = wbase + 32 * q + lane;
+            bool on = false;
             if (i < n) {
-                bool on;
                 if (mode == CM_ALL) {
                     on = true;
                 } else if (mode == CM_FLAGS) {
@@ -222,22 +227,28 @@ __global__ __launch_bounds__(AT) void k_compact(long long n_host, const unsigned
                     on = tend == T;
                     if (!on) tmin = tend < tmin ? tend : tmin;
                 }
-                if (on) sel |= 1u << q;
             }
+            bal[q] = __ballot_sync(0xffffffffu, on);
+            wsel += (uint32_t)__popc(bal[q]);
         }
+        // the warps' counts in order: one value per warp into the block scan
         uint32_t total;
-        const uint32_t excl = block_excl_scan<AT>((uint32_t)__popc(sel), &total, tmp);
+        const uint32_t wexcl = block_excl_scan<AT>(lane == 31 ? wsel : 0u, &total, tmp);
+        const uint32_t wstart = __shfl_sync(0xffffffffu, wexcl, 31);
         if (threadIdx.x < 32) {
             const uint32_t e = lookback_warp(status, tile, total, tag, ctl, GTK_ACTIVE);
             if (threadIdx.x == 0) excl_sh = e;
         }
         __syncthreads();
-        uint32_t pos = excl_sh + excl;
+        uint32_t pos = excl_sh + wstart;
+        const unsigned int lt = lanemask_lt();
 #pragma unroll
         for (int q = 0; q < AIPT; q++) {
-            const long long i = i0 + q;
-            if (i < n && prefix) prefix[i] = pos;
-            if (sel & (1u << q)) out[pos++] = (uint32_t)i;
+            const long long i = wbase + 32 * q + lane;
+            const uint32_t at = pos + (uint32_t)__popc(bal[q] & lt);
+            if (i < n && prefix) prefix[i] = at;
+            if ((bal[q] >> lane) & 1u) out[at] = (uint32_t)i;
+            pos += (uint32_t)__popc(bal[q]);
         }
         if (tile == ntiles - 1 && threadIdx.x == AT - 1) {
             *count_out = excl_sh + total;
