@@ -291,7 +291,7 @@ __global__ __launch_bounds__(256) void k_group_cells(Nodes nd, long long cap, co
 }
 
 __device__ __forceinline__ double a2_of(float4 a) {
-    const double ax = a.x, ay = a.y, az = a.z;
+    const double ax = f2d(a.x), ay = f2d(a.y), az = f2d(a.z);  // exact widenings, integer pipe
     // the squares are exact in FP64, so the fused forms round only at the additions
     return __fma_rn(az, az, __fma_rn(ay, ay, __dmul_rn(ax, ax)));
 }
@@ -316,9 +316,12 @@ __global__ __launch_bounds__(256) void k_correct(State s, const uint32_t *__rest
                                                  int L, double c2) {
     const uint32_t na = ctl->n_active;
     const long long T = (long long)ctl->tnext;
-    const double dt_max = ctl->dt_max;
-    const int M = ctl->M;
-    const double dt_min = ldexp(dt_max, -(L - 1));
+    const int M = ctl->M;  // dt_max = 2^M
+    // the step's powers of two and the exact widenings are built on the integer pipe (the
+    // FP64 pipe of this GPU is narrow); only the kicks, drifts and |a|^2 use it
+    auto p2 = [](int e) {  // 2^e
+        return (e > -1023 && e < 1024) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
+    };
     unsigned long long tmin = ~0ull;
     for (uint32_t k = blockIdx.x * 256u + threadIdx.x; k < na; k += gridDim.x * 256u) {
         const uint32_t i = active[k];
@@ -328,9 +331,9 @@ __global__ __launch_bounds__(256) void k_correct(State s, const uint32_t *__rest
         }
         const float4 a = acc[k];
         const int kold = s.level[i];
-        const double hold = 0.5 * ldexp(dt_max, -kold);
-        const double dtp = __dmul_rn((double)(T - s.t0[i]), dt_min);
-        const double ax = a.x, ay = a.y, az = a.z;
+        const double hold = p2(M - kold - 1);                  // dt(kold) / 2
+        const double dtp = i2d_scaled(T - s.t0[i], M - (L - 1));  // (T - t0) dt_min, exact
+        const double ax = f2d(a.x), ay = f2d(a.y), az = f2d(a.z);
         const double vx0 = s.vx[i], vy0 = s.vy[i], vz0 = s.vz[i];
         s.rx[i] = __fma_rn(dtp, vx0, s.rx[i]);
         s.ry[i] = __fma_rn(dtp, vy0, s.ry[i]);
@@ -347,13 +350,13 @@ __global__ __launch_bounds__(256) void k_correct(State s, const uint32_t *__rest
             const long long span = 1ll << (L - 1 - (kold - 1));
             if (T % span == 0) knew = kold - 1;
         }
-        const double hnew = 0.5 * ldexp(dt_max, -knew);
+        const double hnew = p2(M - knew - 1);
         s.vx[i] = __fma_rn(hnew, ax, vx);
         s.vy[i] = __fma_rn(hnew, ay, vy);
         s.vz[i] = __fma_rn(hnew, az, vz);
         s.level[i] = (uint8_t)knew;
         s.t0[i] = T;
-        s.aold[i] = __fsqrt_rn(__double2float_rn(a2));
+        s.aold[i] = __fsqrt_rn(d2f(a2));
         s.acc[i] = a;
         const unsigned long long tend = (unsigned long long)T + (1ull << (L - 1 - knew));
         tmin = tend < tmin ? tend : tmin;
