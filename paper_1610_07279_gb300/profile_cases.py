@@ -97,11 +97,14 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=16)
     ap.add_argument("--group-max", type=int, default=0)
     ap.add_argument("--leaf-max", type=int, default=0)
+    ap.add_argument("--rebuild-every", type=int, default=-1, help="fixed rebuild interval (0: automatic)")
     a = ap.parse_args(argv)
     if a.group_max:
         KNOBS["group_max"] = a.group_max
     if a.leaf_max:
         KNOBS["leaf_max"] = a.leaf_max
+    if a.rebuild_every >= 0:
+        KNOBS["rebuild_every"] = a.rebuild_every
     _build.build()
     g.load()
     if a.case == "walk":
