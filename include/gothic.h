@@ -328,7 +328,7 @@ GT_API int gt_measure_fp32_peak(double *flops, gt_stream stream);
  * receive the sorted pairs.  The scratch the sort needs (the alternate key and
  * value buffers, per-tile look-back status words, digit histograms and a control
  * block) lives in one file-scope device array of the library, sized for
- * GT_NOALLOC_SORT_MAX pairs (about 13.1 MiB, held on every GPU that loads the
+ * GT_NOALLOC_SORT_MAX pairs (about 12.5 MiB, held on every GPU that loads the
  * library until the process exits); nothing is allocated or freed by the call.
  *   - n > GT_NOALLOC_SORT_MAX: rejected with GT_EINVAL before any device work.
  *   - The first call on a device looks up the array's device address (once per
