@@ -187,9 +187,12 @@ GT_API int gt_set_state(gt_system *sys, const double *p_pos, const double *p_vel
 GT_API int gt_build_tree(gt_system *sys, gt_stream stream);
 
 /* Steps A6-A7: accelerations of the listed i-particles from the current tree
- * (Sec. 2.3): groups of group_max consecutive entries of d_active share one
- * walk; each group's pseudo i-particle is the sphere about the centre of its
- * bounding box (Appendix B, GEO); cells are tested with the MAC at distance
+ * (Sec. 2.3-2.4): the i-particles are cut into groups that share one walk -- with
+ * cell grouping (the default) the listed particles of one tree cell holding at most
+ * group_max of them, with run grouping consecutive runs of group_max entries of
+ * d_active; each group's pseudo i-particle is the sphere about the centre of its
+ * bounding box (Appendix B, GEO; or Ritter's sphere with GT_SPHERE_EBS); cells are
+ * tested with the MAC at distance
  * lambda r_JI (Eqs. 6-7) and the Plummer-softened sums of Eq. (1) run over the
  * accepted cells and the particles of opened leaves.
  *   d_active  n_active internal indices (uint32), or NULL for all particles
@@ -310,10 +313,44 @@ GT_API int gt_sync_status(gt_system *sys, gt_stream stream);
 /* Synchronise and read counters (see gt_stats). */
 GT_API int gt_get_stats(gt_system *sys, gt_stats *out, gt_stream stream);
 
+/* Bound of every spin-wait of this system's kernels (the decoupled look-backs of the
+ * sort, the tree build and the active-set compaction, the level waits of the pseudo
+ * j-particle pass), in polling iterations of a few tens of nanoseconds each; 0 restores
+ * the default 2^22.  A wait that runs out latches GT_ETIMEOUT in the error word and its
+ * kernel returns, so the context stays usable (the results of that call are not).  On
+ * the stream, asynchronous. */
+GT_API int gt_set_wait_limit(gt_system *sys, uint32_t iterations, gt_stream stream);
+
+/* Failure-detection check: runs, with the bound `iterations`, the same warp look-back
+ * the build and the compaction use, for a tile whose predecessor never publishes, so the
+ * wait must run out.  Synchronises and returns the latched status (GT_ETIMEOUT when the
+ * bounded wait works) and clears it, like gt_sync_status; the system's own bound is put
+ * back afterwards.  Uses two of the system's look-back status words, so call it between
+ * the system's other calls, not during them. */
+GT_API int gt_probe_bounded_wait(gt_system *sys, uint32_t iterations, gt_stream stream);
+
 /* Measure the device's FP32 FMA throughput (FLOP/s, FMA = 2 flops) with a
- * dependent-FMA-chain kernel on all SMs; the roofline denominator of the walk.
- * Synchronises; ~10 ms. */
+ * dependent-FMA-chain kernel on all SMs.  Synchronises; ~10 ms. */
 GT_API int gt_measure_fp32_peak(double *flops, gt_stream stream);
+
+/* FP32 instruction throughputs of the device, each from chains of one instruction
+ * form on every SM (lane operations per second).  The walk's force loop issues the
+ * packed form (f32x2: two FMAs, adds or multiplies per lane and instruction) and the
+ * special-function reciprocal square root.  peak_flops = 2 x the larger of the two FMA
+ * rates: the FP32 roofline of the walk.  rsqrt_flops = the larger of the add and
+ * multiply rates / the rsqrt rate: the flops one rsqrt counts for under the paper's
+ * convention (Sec. 4 and the note to Table 3: 8, 6 and 4 on its three GPUs, so that
+ * one interaction is 20 + rsqrt_flops flops).  Synchronises; ~50 ms. */
+typedef struct gt_fp32_rates {
+    double fma_per_s;    /* scalar FMA */
+    double fma2_per_s;   /* packed FMA, counted per lane operation (two per instruction) */
+    double add_per_s;    /* scalar add */
+    double mul_per_s;    /* scalar multiply */
+    double rsqrt_per_s;  /* rsqrt.approx.ftz.f32 */
+    double peak_flops;
+    double rsqrt_flops;
+} gt_fp32_rates;
+GT_API int gt_measure_fp32_rates(gt_fp32_rates *out, gt_stream stream);
 
 /* ---- sort without allocation ------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that
@@ -337,9 +374,16 @@ GT_API int gt_measure_fp32_peak(double *flops, gt_stream stream);
  *   - Every call uses the same array: calls that overlap on the GPU (on two
  *     streams, or from two threads) race and corrupt each other's results.
  *     Serialise them on one stream.
- * Asynchronous on the stream; GT_ECUDA if a launch fails. */
+ * Asynchronous on the stream; GT_ECUDA if a launch fails; device-side errors are read
+ * with gt_sort_noalloc_status. */
 #define GT_NOALLOC_SORT_MAX (1 << 20)
 GT_API int gt_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals, int64_t n, gt_stream stream);
+/* Device errors of the no-allocation sort on the current device: its look-back waits are
+ * bounded, and a wait that runs out latches GT_ETIMEOUT in the sort's own static control
+ * block (the sorted result of that call is then wrong).  Synchronises the stream, returns
+ * the latched status (GT_OK if none, or if no sort has run on this device) and clears it.
+ * Call it after the sorts whose results you use. */
+GT_API int gt_sort_noalloc_status(gt_stream stream);
 
 /* ---- batches: many independent systems, one walk launch (Sec. 2.3, 2.5) -------
  *

@@ -65,6 +65,7 @@ def _declare(L):
     P = C.c_void_p
     I64, I32, D, F = C.c_int64, C.c_int, C.c_double, C.c_float
     L.or_num_threads.restype = I32
+    L.or_set_num_threads.argtypes = [I32]
     L.or_direct.argtypes = [I64, P, D, D, I64, P, P]
     L.or_keys.argtypes = [I64, P, P, P]
     L.or_sort.argtypes = [I64, P, P, P]
@@ -108,6 +109,11 @@ def _c(a, dtype):
 
 def num_threads() -> int:
     return int(lib().or_num_threads())
+
+
+def set_num_threads(k: int) -> None:
+    """Threads of the oracle's parallel loops from now on (timing only)."""
+    lib().or_set_num_threads(int(k))
 
 
 # ------------------------------------------------------------------ parameters

@@ -36,6 +36,15 @@ int or_num_threads(void) {
 #endif
 }
 
+/* Threads of the parallel loops that follow (timing of the oracle on one core or all). */
+void or_set_num_threads(int k) {
+#ifdef _OPENMP
+    if (k > 0) omp_set_num_threads(k);
+#else
+    (void)k;
+#endif
+}
+
 /* Enclosing radii are evaluated in FP32 and widened by (1 + 2^-20): an FP32
  * distance carries a few roundings of at most 2^-24 each, so the widened radius
  * still holds every particle (Sec. 2.1 asks only for a sphere that contains them). */

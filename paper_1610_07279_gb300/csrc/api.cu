@@ -16,6 +16,23 @@ static std::atomic<long long> g_launches{0};
 
 void gt_note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+// The look-back of tile 1 over a tile 0 that never publishes: the wait on tile 0's
+// status word runs out after the control block's spin bound, latches GT_ETIMEOUT and
+// returns.  The epoch is one no build or compaction reaches, and tile 0's word is
+// cleared first, so neither the wait nor its result depends on earlier contents.
+namespace {
+constexpr unsigned int PROBE_EPOCH = 0x3fffffffu;
+__global__ void k_wait_probe(unsigned long long *status, DevCtl *ctl) {
+    if (threadIdx.x == 0) status[0] = 0ull;
+    __syncwarp();
+    (void)lookback_warp(status, 1u, 1u, PROBE_EPOCH, ctl, GTK_PROBE);
+}
+}  // namespace
+
+void gt_launch_wait_probe(unsigned long long *status, DevCtl *ctl, cudaStream_t st) {
+    { k_wait_probe<<<1, 32, 0, st>>>(status, ctl); gt_note_launches(1); }
+}
+
 namespace {
 
 constexpr size_t ALIGN = GT_WS_ALIGN;
@@ -855,6 +872,27 @@ int gt_sync_status(gt_system *s, gt_stream stream) {
         if (cudaMemcpy(&s->ctl->err, zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess) return GT_ECUDA;
     }
     return err[0];
+}
+
+int gt_set_wait_limit(gt_system *s, uint32_t iterations, gt_stream stream) {
+    if (!s) return GT_EINVAL;
+    gt_launch_set_u32(&s->ctl->spin_limit, iterations, S(stream));
+    return last_cuda();
+}
+
+int gt_probe_bounded_wait(gt_system *s, uint32_t iterations, gt_stream stream) {
+    if (!s) return GT_EINVAL;
+    cudaStream_t st = S(stream);
+    // the probe's bound replaces the system's for the probe only: read the old one back
+    unsigned int old = 0;
+    if (cudaMemcpyAsync(&old, &s->ctl->spin_limit, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return GT_ECUDA;
+    gt_launch_set_u32(&s->ctl->spin_limit, iterations, st);
+    gt_launch_wait_probe(s->status, s->ctl, st);
+    gt_launch_set_u32(&s->ctl->spin_limit, old, st);
+    if (cudaGetLastError() != cudaSuccess) return GT_ECUDA;
+    return gt_sync_status(s, stream);
 }
 
 int gt_get_stats(gt_system *s, gt_stats *o, gt_stream stream) {

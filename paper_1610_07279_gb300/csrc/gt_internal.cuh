@@ -12,14 +12,14 @@
 #define GT_LEVEL_BUCKETS (GT_LEAF_BUCKETS + 8)  // + its cells with children by number of children
 #define GT_CELL_BUCKETS (GT_TREE_LEVELS * GT_LEVEL_BUCKETS)
 #define GT_LEAF_FLAG 0x80000000u      // set in a node's second link word for a leaf
-#define GT_SPIN_LIMIT (1u << 22)      // bound on every device spin-wait (iterations)
+#define GT_SPIN_LIMIT (1u << 22)      // default bound on every device spin-wait (iterations)
 // Enclosing radii computed in FP32 are widened by (1 + 2^-20): the few roundings of
 // an FP32 distance (each <= 2^-24 relative) cannot then shrink a radius below the
 // true one.
 #define GT_RADIUS_MARGIN (1.0f + 0x1p-20f)
 
 // Kernel ids recorded with a latched error (diagnostic only).
-enum { GTK_NONE = 0, GTK_BUILD, GTK_PSEUDO, GTK_ACTIVE, GTK_WALK, GTK_SORT, GTK_CORRECT };
+enum { GTK_NONE = 0, GTK_BUILD, GTK_PSEUDO, GTK_ACTIVE, GTK_WALK, GTK_SORT, GTK_CORRECT, GTK_PROBE };
 
 // Small control block in device memory: counters, per-step scalars and the
 // error word.  One per system, inside the workspace.
@@ -51,7 +51,15 @@ struct DevCtl {
     float pad1;
     double side;                      // side of the bounding cube (FP64)
     double scale;                     // 2^21 / side
+    unsigned int spin_limit;          // bound on every spin-wait of this system; 0: GT_SPIN_LIMIT
+    unsigned int pad2;
 };
+
+// The bound of a spin-wait: the control block's own, or the default.
+__device__ __forceinline__ unsigned int gt_spin_limit(const DevCtl *ctl) {
+    const unsigned int v = *((const volatile unsigned int *)&ctl->spin_limit);
+    return v ? v : GT_SPIN_LIMIT;
+}
 
 // Particle state, structure of arrays, in internal (key) order.
 struct State {
@@ -179,8 +187,8 @@ __device__ __forceinline__ unsigned int block_excl_scan(unsigned int v, unsigned
 // values up to and including that prefix are summed by shuffles; with no prefix in
 // the window the 32 aggregates are added and the window moves back.  Tiles are taken
 // in increasing order from a ticket, so every predecessor is held by a running block
-// and the wait ends; it is still bounded, and a wait that runs out latches
-// GT_ETIMEOUT and returns the partial prefix.  Every lane gets the result.
+// and the wait ends; it is still bounded (gt_spin_limit), and a wait that runs out
+// latches GT_ETIMEOUT and returns the partial prefix.  Every lane gets the result.
 __device__ __forceinline__ unsigned int lookback_warp(unsigned long long *status, unsigned int tile,
                                                       unsigned int aggregate, unsigned int epoch,
                                                       DevCtl *ctl, int where) {
@@ -195,6 +203,7 @@ __device__ __forceinline__ unsigned int lookback_warp(unsigned long long *status
     unsigned int excl = 0;
     int base = (int)tile - 1;
     unsigned int spins = 0;
+    const unsigned int limit = gt_spin_limit(ctl);
     for (;;) {
         const int t = base - lane;
         // a slot before tile 0 reads as a published prefix of 0
@@ -205,7 +214,7 @@ __device__ __forceinline__ unsigned int lookback_warp(unsigned long long *status
         const int firstP = pmask ? __ffs(pmask) - 1 : 32;
         const unsigned int need = firstP >= 31 ? 0xffffffffu : ((1u << (firstP + 1)) - 1u);
         if ((vmask & need) != need) {
-            if (++spins > GT_SPIN_LIMIT) {
+            if (++spins > limit) {
                 if (lane == 0) gt_set_error(ctl, GT_ETIMEOUT, where);
                 break;
             }
@@ -282,6 +291,9 @@ void gt_launch_correct(const State &s, const uint32_t *active, const float4 *acc
 void gt_launch_aold(const float4 *acc, int64_t n, float *aold, cudaStream_t st);
 void gt_launch_set_clock(DevCtl *ctl, int M, int L, long long T, cudaStream_t st);
 void gt_launch_set_tnext(DevCtl *ctl, long long T, cudaStream_t st);
+void gt_launch_set_u32(unsigned int *dst, unsigned int v, cudaStream_t st);
+// api.cu: one warp's look-back over a predecessor that never publishes (bounded-wait probe)
+void gt_launch_wait_probe(unsigned long long *status, DevCtl *ctl, cudaStream_t st);
 void gt_launch_tnext_all(const State &s, int64_t n, int L, DevCtl *ctl, int nsm, cudaStream_t st);
 void gt_launch_gather_resume(const uint8_t *lv, const long long *t0, const float *ao, const float4 *acc,
                              const State &s, int64_t n, cudaStream_t st);

@@ -457,6 +457,8 @@ __global__ void k_set_clock(DevCtl *ctl, int M, int L, long long T) {
 
 __global__ void k_set_tnext(DevCtl *ctl, long long T) { ctl->tnext = (unsigned long long)T; }
 
+__global__ void k_set_u32(unsigned int *dst, unsigned int v) { *dst = v; }
+
 __global__ __launch_bounds__(256) void k_tnext_all(const long long *__restrict__ t0,
                                                    const uint8_t *__restrict__ level, long long n, int L,
                                                    DevCtl *ctl) {
@@ -582,6 +584,10 @@ void gt_launch_set_clock(DevCtl *ctl, int M, int L, long long T, cudaStream_t st
 
 void gt_launch_set_tnext(DevCtl *ctl, long long T, cudaStream_t st) {
     { k_set_tnext<<<1, 1, 0, st>>>(ctl, T); gt_note_launches(1); }
+}
+
+void gt_launch_set_u32(unsigned int *dst, unsigned int v, cudaStream_t st) {
+    { k_set_u32<<<1, 1, 0, st>>>(dst, v); gt_note_launches(1); }
 }
 
 void gt_launch_tnext_all(const State &s, int64_t n, int L, DevCtl *ctl, int nsm, cudaStream_t st) {

@@ -93,6 +93,7 @@ __device__ __forceinline__ uint32_t lookback_digit(const unsigned long long *sta
     uint32_t excl = 0;
     int t = tile - 1;
     unsigned int spins = 0;
+    const unsigned int limit = gt_spin_limit(ctl);
     while (t >= 0) {
         unsigned long long sv[LB];
 #pragma unroll
@@ -117,7 +118,7 @@ __device__ __forceinline__ uint32_t lookback_digit(const unsigned long long *sta
         if (done) break;
         t -= used;
         if (stalled) {
-            if (++spins > GT_SPIN_LIMIT) {
+            if (++spins > limit) {
                 gt_set_error(ctl, GT_ETIMEOUT, GTK_SORT);
                 break;
             }
@@ -338,4 +339,27 @@ extern "C" int gt_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals, int64_t
     b.digit_base = (uint32_t *)(base + NA_OFF_BASE);
     gt_launch_sort(b, n, ctl, st);  // an even number of passes leaves the result in d_keys/d_vals
     return cudaGetLastError() == cudaSuccess ? GT_OK : GT_ECUDA;
+}
+
+extern "C" int gt_sort_noalloc_status(gt_stream stream) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GT_ECUDA;
+    if (dev < 0 || dev >= NA_MAX_DEVICES) return GT_EINVAL;
+    char *base;
+    {
+        std::lock_guard<std::mutex> lock(g_na_mu);
+        base = g_na_addr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GT_ECUDA;
+    if (!base) return GT_OK;  // no sort has run on this device
+    DevCtl *ctl = (DevCtl *)base;
+    int err = 0;
+    if (cudaMemcpyAsync(&err, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return GT_ECUDA;
+    if (err && (cudaMemsetAsync(&ctl->err, 0, 2 * sizeof(int), st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess))
+        return GT_ECUDA;
+    return err;
 }

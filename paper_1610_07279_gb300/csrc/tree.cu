@@ -627,8 +627,9 @@ __global__ __launch_bounds__(PL, 8) void k_pseudo(Nodes nd, const float4 *__rest
                 const int l1 = olvl[o] + 1;  // every chunk of that level first
                 const unsigned int need = nchunk[2 * l1] + nchunk[2 * l1 + 1];
                 unsigned int spins = 0;
+                const unsigned int limit = gt_spin_limit(ctl);
                 while (*((volatile unsigned int *)&ctl->pl_done[l1]) < need) {
-                    if (++spins > GT_SPIN_LIMIT) {
+                    if (++spins > limit) {
                         gt_set_error(ctl, GT_ETIMEOUT, GTK_PSEUDO);
                         bad_sh = 1;
                         break;

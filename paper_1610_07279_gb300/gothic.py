@@ -59,6 +59,11 @@ class gt_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class gt_fp32_rates(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("fma_per_s", "fma2_per_s", "add_per_s", "mul_per_s", "rsqrt_per_s",
+                                          "peak_flops", "rsqrt_flops")]
+
+
 class GothicError(RuntimeError):
     def __init__(self, status: int, where: str):
         super().__init__(f"{where}: {gt_strerror(status)} ({status})")
@@ -139,6 +144,9 @@ def load(path: str | None = None):
     L.gt_get_timers.argtypes = [P, C.POINTER(C.c_double), C.POINTER(I64), P]
     L.gt_kernel_launches.argtypes = [C.POINTER(I64)]
     L.gt_sort_pairs_noalloc.argtypes = [P, P, I64, P]
+    L.gt_sort_noalloc_status.argtypes = [P]
+    L.gt_set_wait_limit.argtypes = [P, C.c_uint32, P]
+    L.gt_probe_bounded_wait.argtypes = [P, C.c_uint32, P]
     L.gt_rebuild_interval.argtypes = [C.POINTER(C.c_double), I32, C.c_double, C.POINTER(I32),
                                       C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.gt_get_tree.argtypes = [P, P, P, P, P, P, C.POINTER(I64), P]
@@ -146,6 +154,7 @@ def load(path: str | None = None):
     L.gt_sync_status.argtypes = [P, P]
     L.gt_get_stats.argtypes = [P, C.POINTER(gt_stats), P]
     L.gt_measure_fp32_peak.argtypes = [C.POINTER(C.c_double), P]
+    L.gt_measure_fp32_rates.argtypes = [C.POINTER(gt_fp32_rates), P]
     L.gt_brent_minimize.argtypes = [BRENT_FN, P, C.c_double, C.c_double, C.c_double, I32,
                                     C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(I32)]
     L.gt_batch_workspace_bytes.argtypes = [I32, P, P, I32, C.POINTER(C.c_size_t)]
@@ -199,6 +208,14 @@ def gt_measure_fp32_peak(stream: int | None = None) -> float:
     return float(f.value)
 
 
+def gt_measure_fp32_rates(stream: int | None = None) -> dict:
+    """FP32 instruction throughputs (lane operations/s), the FP32 peak in flop/s and the
+    flops one rsqrt counts for under the paper's convention."""
+    r = gt_fp32_rates()
+    _check(load().gt_measure_fp32_rates(C.byref(r), stream), "gt_measure_fp32_rates")
+    return {k: float(getattr(r, k)) for k, _ in gt_fp32_rates._fields_}
+
+
 PHASES = ("predict", "keys_sort", "permute", "build", "pseudo_j", "active", "walk", "correct")
 
 
@@ -236,6 +253,12 @@ def gt_sort_pairs_noalloc(d_keys, d_vals, n: int, stream: int | None = None):
     the library's static scratch instead of any allocation (n <= GT_NOALLOC_SORT_MAX)."""
     st = stream if stream is not None else _current_stream()
     _check(load().gt_sort_pairs_noalloc(_ptr(d_keys), _ptr(d_vals), int(n), st), "gt_sort_pairs_noalloc")
+
+
+def gt_sort_noalloc_status(stream: int | None = None) -> int:
+    """Latched device status of the no-allocation sort on this device (read and cleared)."""
+    st = stream if stream is not None else _current_stream()
+    return int(load().gt_sort_noalloc_status(st))
 
 
 def _ptr(a):
@@ -407,6 +430,13 @@ class System:
 
     def status(self) -> int:
         return int(load().gt_sync_status(self._h, self._s()))
+
+    def set_wait_limit(self, iterations: int):
+        _check(load().gt_set_wait_limit(self._h, int(iterations), self._s()), "gt_set_wait_limit")
+
+    def probe_bounded_wait(self, iterations: int) -> int:
+        """Status of a look-back whose predecessor never publishes (GT_ETIMEOUT expected)."""
+        return int(load().gt_probe_bounded_wait(self._h, int(iterations), self._s()))
 
     def stats(self) -> dict:
         st = gt_stats()

@@ -158,3 +158,69 @@ def test_pseudo_j_com_per_cell(oracle_lib):
         com = (m[:, None] * sp4[f:f + k, :3]).sum(0) / M
         assert abs(jpos[c, 3] - M) <= np.spacing(np.float32(M))
         assert np.all(np.abs(jpos[c, :3] - com) <= 2 * np.spacing(np.abs(com).astype(np.float32)) + 1e-15)
+
+
+@pytest.mark.parametrize("kind,n,leaf", [("plummer", 4000, 1), ("nfw", 6000, 2), ("plummer", 1 << 13, 16)])
+def test_pseudo_j_cell_radius_is_tight(oracle_lib, kind, n, leaf):
+    """Sec. 2.1, Fig. 1: an upper bound on a cell's b_J from geometry alone.
+
+    Let D_J be the largest distance of the cell's particles from r_J (brute force).  A
+    child's centre of mass lies in the convex hull of its particles, so its distance
+    from r_J is at most D_J; a sphere of radius b_c about it holds the child.  The child
+    bound therefore satisfies D_J <= b_J <= D_J + max_c b_c: a radius summed over the
+    children, taken about another centre, or built without the children's own radii
+    breaks one side.  Where every child is a single particle (b_c = 0) the bound is
+    exact.  Every child's sphere also lies inside its parent's.  Tolerances: FP32
+    roundings (a few ulp per level) and the 2^-20 widening per level."""
+    O = oracle_lib
+    p4 = _sorted_system(n, seed=n + 5, kind=kind)
+    key, _ = O.keys(p4)
+    order, skey = O.sort(key)
+    sp4 = p4[order].astype(np.float64)
+    t = O.build_tree(skey, leaf)
+    jpos, bj = O.pseudo_j(t, p4[order])
+    jp = jpos.astype(np.float64)
+    b = bj.astype(np.float64)
+    scale = np.abs(sp4[:, :3]).max()
+    slack = 64 * np.spacing(np.float32(scale))  # a few FP32 roundings of a coordinate
+    internal = np.nonzero(t["child"] >= 0)[0]
+    assert len(internal) > 10
+    exact = 0
+    for c in internal:
+        f, k = t["first"][c], t["count"][c]
+        D = np.linalg.norm(sp4[f:f + k, :3] - jp[c, :3], axis=1).max()
+        kids = np.arange(t["child"][c], t["child"][c] + t["nchild"][c])
+        bmax = b[kids].max()
+        assert D <= b[c]
+        assert b[c] <= (D + bmax) * (1 + 2.0 ** -17) + slack, (c, b[c], D, bmax)
+        # nesting: |r_c - r_J| + b_c <= b_J
+        dc = np.linalg.norm(jp[kids, :3] - jp[c, :3], axis=1)
+        assert np.all(dc + b[kids] <= b[c] * (1 + 2.0 ** -20) + slack)
+        if bmax == 0.0:
+            exact += 1
+            assert b[c] <= D * (1 + 2.0 ** -18) + slack
+    if leaf <= 2:
+        assert exact > 10  # the exact case is exercised
+
+
+def test_pseudo_j_radius_bound_catches_a_summed_radius(oracle_lib):
+    """The bound above rejects a plausible mistake: summing the children's reach instead
+    of taking its maximum (checked on the oracle's own tree with a planted error)."""
+    O = oracle_lib
+    p4 = _sorted_system(3000, seed=11)
+    key, _ = O.keys(p4)
+    order, skey = O.sort(key)
+    sp4 = p4[order].astype(np.float64)
+    t = O.build_tree(skey, 2)
+    jpos, bj = O.pseudo_j(t, p4[order])
+    jp = jpos.astype(np.float64)
+    bad = 0
+    for c in np.nonzero(t["child"] >= 0)[0][-200:]:
+        f, k = t["first"][c], t["count"][c]
+        D = np.linalg.norm(sp4[f:f + k, :3] - jp[c, :3], axis=1).max()
+        kids = np.arange(t["child"][c], t["child"][c] + t["nchild"][c])
+        reach = np.linalg.norm(jp[kids, :3] - jp[c, :3], axis=1) + bj[kids]
+        summed = reach.sum()
+        if summed > (D + bj[kids].max()) * (1 + 2.0 ** -17) + 1e-6:
+            bad += 1
+    assert bad > 50
