@@ -40,8 +40,22 @@ def _deps() -> list[str]:
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
+# Extra nvcc flags for tuning builds (compile-time knobs such as -DGT_WALK_MINB=4); the
+# library is rebuilt whenever they change.
+FLAGS_STAMP = os.path.join(OUT_DIR, "flags.txt")
+
+
+def _extra_flags() -> list[str]:
+    return os.environ.get("GOTHIC_NVCC_FLAGS", "").split()
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB):
+        return False
+    try:
+        if open(FLAGS_STAMP).read() != " ".join(_extra_flags()):
+            return False
+    except OSError:
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(d) <= t for d in _deps())
@@ -56,7 +70,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     obj_dir = os.path.join(OUT_DIR, "obj")
     os.makedirs(obj_dir, exist_ok=True)
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-                     "-Xcompiler", "-fvisibility=hidden"]
+                     "-Xcompiler", "-fvisibility=hidden"] + _extra_flags()
     if ptxas_verbose:
         common += ["-Xptxas", "-v"]
 
@@ -81,6 +95,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(FLAGS_STAMP, "w") as f:
+        f.write(" ".join(_extra_flags()))
     return LIB
 
 

@@ -131,6 +131,7 @@ size_t carve(gt_system *s, char *base, int64_t n, const gt_params *p, int nsm, i
     s->nd.walk = L.take<float4>(base, cap);
     s->nd.sum = L.take<DSum4>(base, cap);
     s->nd.cells = L.take<uint32_t>(base, cap);
+    s->nd.arrive = L.take<uint32_t>(base, cap);
     const int64_t st_tiles = (cap + 511) / 512 + (n + 4095) / 4096 + 64;
     s->status = L.take<unsigned long long>(base, st_tiles);
     s->active = L.take<uint32_t>(base, N);

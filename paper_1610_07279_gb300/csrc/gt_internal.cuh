@@ -37,8 +37,6 @@ struct DevCtl {
     unsigned int level_start[GT_TREE_LEVELS + 2];  // first cell of each level; [22] = node count
     unsigned int sort_ticket[8];      // dynamic tile ids of the 8 sort passes
     unsigned int sort_epoch;          // look-back epoch of the sort
-    unsigned int pl_ticket;           // chunk tickets of the pseudo j-particle pass
-    unsigned int pl_done[GT_TREE_LEVELS];  // finished chunks per level of that pass
     unsigned long long interactions;  // cumulative
     unsigned long long mac_tests;     // cumulative
     unsigned long long tnext;         // block time of the current step
@@ -92,6 +90,7 @@ struct Nodes {
     uint32_t *cells;           // every node once: the leaves bucketed by particle count, then
                                // the cells with children by level (deepest last) and, inside
                                // a level, by number of children
+    uint32_t *arrive;          // children of a cell done so far in the pseudo j-particle pass
 };
 
 __device__ __forceinline__ void gt_set_error(DevCtl *ctl, int code, int where) {

@@ -11,10 +11,11 @@
 // lock-step 7-way binary search, children numbered by a block scan plus a decoupled
 // look-back over tiles taken in ticket order).  Both give the same numbering.
 //
-// A5, one launch over a cell list bucketed by level and size: a leaf's lane sums its
-// particles in FP64 (mass, m x, m y, m z); a cell with children sums its children's FP64
-// sums in child order once the level below is done -- every FP64 instruction runs with
-// full warps, which matters on this GPU's narrow FP64 pipe.  m_J = (float)M and
+// A5, one launch over the leaves of the cell list (bucketed by level and size, so the
+// FP64 leaf sums run with full warps, which matters on this GPU's narrow FP64 pipe): a
+// leaf's lane sums its particles in FP64 (mass, m x, m y, m z); a cell with children sums
+// its children's FP64 sums in child order, computed by the thread whose child finished
+// last (no level barriers).  m_J = (float)M and
 // r_J = (float)S / (float)M (a cell of one particle is that particle); b_J is the
 // largest FP32 |r - r_J| of a leaf's particles, or the largest |r_c - r_J| + b_c
 // over a cell's children, widened by (1 + 2^-20) so that FP32 rounding cannot
@@ -462,17 +463,16 @@ __global__ __launch_bounds__(256) void k_cell_fill(Nodes nd, long long cap, DevC
     }
 }
 
-// ---- A5: pseudo j-particles, every node in one launch ------------------------------
-// The cell list's segments (a level's leaves, a level's cells with children) are cut
-// into chunks of PL nodes, handed out by a ticket counter in this order: the leaves of
-// level 21; then, for l = 20 .. 0, the leaves of level l and the cells with children of
-// level l + 1; the cells of level 0 last.  A chunk of cells of level l waits until every
-// chunk of level l + 1 is finished: those hold smaller tickets, so the blocks holding
-// them are running and the wait ends (it is bounded all the same).  Leaves wait for
-// nothing, so their FP64 sums fill the time a level's cells wait for the one below.
-constexpr int PL = 128;  // nodes per chunk, one per thread
-constexpr int PSEUDO_LAG = 1;  // levels of leaves between a level's cells and the level below
-constexpr int NSEG = 2 * GT_TREE_LEVELS;
+// ---- A5: pseudo j-particles, one launch without level barriers ---------------------
+// Every leaf is taken by one thread, in the order of the cell list (a level's leaves
+// bucketed by particle count, so the lanes of a warp run equal trip counts).  When a node
+// is done, its thread makes the node's results visible device-wide and counts itself into
+// its parent's arrival word; the thread whose arrival completes the parent's children
+// computes the parent (its children's FP64 sums added in child order), re-arms the word
+// for the next pass and climbs on.  No thread waits for another, every cell is computed
+// exactly once after all its children, and the order of every FP64 addition is fixed by
+// the tree alone, so the result does not depend on which thread computes what.
+constexpr int PL = 128;  // threads per block
 
 // Leaf c: one lane sums its particles in FP64 (mass, m x, m y, m z) in particle order.
 // The masses and the cells' members do not change between tree builds, so the mass
@@ -586,73 +586,45 @@ __device__ __forceinline__ void pseudo_cell(const Nodes &nd, uint32_t p) {
 }
 
 template <bool WITH_MASS>
-__global__ __launch_bounds__(PL, 8) void k_pseudo(Nodes nd, const float4 *__restrict__ posm, DevCtl *ctl) {
-    __shared__ uint32_t seg[NSEG + 1];
-    __shared__ uint8_t olvl[NSEG], ocell[NSEG];      // ticket order: segment level and kind
-    __shared__ uint32_t ocum[NSEG + 1];              // first ticket of every entry
-    __shared__ uint32_t nchunk[NSEG];                // chunks of segment (2 l + kind)
-    __shared__ unsigned int t_sh;
-    __shared__ int o_sh, bad_sh;
-    for (int i = threadIdx.x; i <= NSEG; i += PL) seg[i] = ctl->seg[i];
-    __syncthreads();
+__global__ __launch_bounds__(PL) void k_pseudo(Nodes nd, const float4 *__restrict__ posm,
+                                               const DevCtl *__restrict__ ctl) {
+    __shared__ uint32_t lfirst[GT_TREE_LEVELS + 1];  // prefix of the levels' leaf counts
+    __shared__ uint32_t lseg[GT_TREE_LEVELS];        // where level l's leaves start in the cell list
     if (threadIdx.x == 0) {
-        for (int k = 0; k < NSEG; k++) nchunk[k] = (seg[k + 1] - seg[k] + PL - 1) / PL;
-        int o = 0;  // level l's cells go right after the leaves of level l - PSEUDO_LAG
-        for (int s = 0; s < GT_TREE_LEVELS + PSEUDO_LAG; s++) {
-            const int ll = GT_TREE_LEVELS - 1 - s, lc = GT_TREE_LEVELS - 1 + PSEUDO_LAG - s;
-            if (ll >= 0) { olvl[o] = (uint8_t)ll; ocell[o] = 0; o++; }
-            if (lc >= 0 && lc < GT_TREE_LEVELS - 1) { olvl[o] = (uint8_t)lc; ocell[o] = 1; o++; }
-        }
-        // o == NSEG - 1 (level 21 has no cells with children): the last entry is empty
-        olvl[o] = 0; ocell[o] = 2;
         uint32_t c = 0;
-        for (int k = 0; k < NSEG; k++) {
-            ocum[k] = c;
-            if (ocell[k] < 2) c += nchunk[2 * olvl[k] + ocell[k]];
+        for (int l = 0; l < GT_TREE_LEVELS; l++) {
+            lfirst[l] = c;
+            lseg[l] = ctl->seg[2 * l];
+            c += ctl->seg[2 * l + 1] - ctl->seg[2 * l];
         }
-        ocum[NSEG] = c;
-        bad_sh = 0;
+        lfirst[GT_TREE_LEVELS] = c;
     }
     __syncthreads();
-    const uint32_t total = ocum[NSEG];
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const unsigned int t = atomicAdd(&ctl->pl_ticket, 1u);
-            int o = 0;
-            if (t < total)
-                while (ocum[o + 1] <= t) o++;
-            t_sh = t;
-            o_sh = o;
-            if (t < total && ocell[o] == 1 && olvl[o] + 1 < GT_TREE_LEVELS) {
-                const int l1 = olvl[o] + 1;  // every chunk of that level first
-                const unsigned int need = nchunk[2 * l1] + nchunk[2 * l1 + 1];
-                unsigned int spins = 0;
-                const unsigned int limit = gt_spin_limit(ctl);
-                while (*((volatile unsigned int *)&ctl->pl_done[l1]) < need) {
-                    if (++spins > limit) {
-                        gt_set_error(ctl, GT_ETIMEOUT, GTK_PSEUDO);
-                        bad_sh = 1;
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-                __threadfence();
-            }
+    const uint32_t total = lfirst[GT_TREE_LEVELS];
+    for (uint32_t t = blockIdx.x * PL + threadIdx.x; t < total; t += gridDim.x * PL) {
+        int l = 0;
+        while (lfirst[l + 1] <= t) l++;
+        uint32_t c = nd.cells[lseg[l] + (t - lfirst[l])];
+        pseudo_leaf<WITH_MASS>(nd, posm, c);
+        for (;;) {
+            const int32_t p = nd.parent[c];
+            if (p < 0) break;
+            __threadfence();  // this node's results before its arrival
+            const uint32_t seen = atomicAdd(&nd.arrive[p], 1u);
+            if (seen + 1u != nd.nchild[p]) break;
+            nd.arrive[p] = 0u;  // every child has arrived: re-armed for the next pass
+            __threadfence();    // the siblings' results after their arrivals
+            pseudo_cell<WITH_MASS>(nd, (uint32_t)p);
+            c = (uint32_t)p;
         }
-        __syncthreads();
-        const unsigned int t = t_sh;
-        const int o = o_sh;
-        if (t >= total || bad_sh) break;
-        const int lvl = olvl[o], kind = ocell[o];
-        const long long idx = (long long)seg[2 * lvl + kind] + (long long)(t - ocum[o]) * PL + threadIdx.x;
-        if (idx < (long long)seg[2 * lvl + kind + 1]) {
-            if (kind == 0) pseudo_leaf<WITH_MASS>(nd, posm, nd.cells[idx]);
-            else pseudo_cell<WITH_MASS>(nd, nd.cells[idx]);
-        }
-        __threadfence();  // every thread's node is visible device-wide before the chunk counts as done
-        __syncthreads();
-        if (threadIdx.x == 0) atomicAdd(&ctl->pl_done[lvl], 1u);
     }
+}
+
+// arrival words of a new tree start at zero
+__global__ __launch_bounds__(256) void k_zero_arrive(Nodes nd, long long cap, const DevCtl *__restrict__ ctl) {
+    long long nn = ctl->level_start[GT_TREE_LEVELS];
+    if (nn > cap) nn = cap;
+    for (long long c = blockIdx.x * 256ll + threadIdx.x; c < nn; c += (long long)gridDim.x * 256) nd.arrive[c] = 0u;
 }
 
 }  // namespace
@@ -706,10 +678,10 @@ void gt_launch_cell_lists(Nodes nd, int64_t cap, DevCtl *ctl, int nsm, cudaStrea
 
 void gt_launch_pseudo(Nodes nd, int64_t cap, const float4 *posm, DevCtl *ctl, int nsm, bool with_mass,
                       cudaStream_t st) {
-    (void)cap;
-    // the ticket and the per-level counters start at zero
-    cudaMemsetAsync(&ctl->pl_ticket, 0, sizeof(ctl->pl_ticket) + sizeof(ctl->pl_done), st);
-    if (with_mass) { k_pseudo<true><<<nsm * 8, PL, 0, st>>>(nd, posm, ctl); }
-    else { k_pseudo<false><<<nsm * 8, PL, 0, st>>>(nd, posm, ctl); }
-    gt_note_launches(1);
+    if (with_mass) {  // after a build
+        { k_zero_arrive<<<nsm * 4, 256, 0, st>>>(nd, cap, ctl); gt_note_launches(1); }
+        { k_pseudo<true><<<nsm * 16, PL, 0, st>>>(nd, posm, ctl); gt_note_launches(1); }
+    } else {
+        { k_pseudo<false><<<nsm * 16, PL, 0, st>>>(nd, posm, ctl); gt_note_launches(1); }
+    }
 }

@@ -35,6 +35,9 @@
 
 namespace {
 
+#ifndef GT_WALK_MINB
+#define GT_WALK_MINB 3            // resident blocks per SM the register budget is sized for
+#endif
 constexpr int WT = 256;           // threads per block
 constexpr int NWARP = WT / 32;
 constexpr int LIST_CAP = 384;     // interaction-list entries per warp
@@ -253,29 +256,39 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
     auto flush = [&]() {
         cp_async_wait_all();
         __syncwarp();
-        // entries are taken in pairs (e, e + 1); an odd list gets a massless last entry,
-        // which adds exactly nothing
-        if (list_n & 1) {
-            if (lane == 0) { lx[list_n] = 0.f; ly[list_n] = 0.f; lz[list_n] = 0.f; lw[list_n] = 0.f; }
+        // entries are taken four at a time (one 16-byte load per coordinate), as the pairs
+        // (e, e + 1) and (e + 2, e + 3); the list is padded with massless entries to a
+        // multiple of four, which add exactly nothing
+        const int pad = (-list_n) & 3;
+        if (pad) {
+            if (lane < pad) {
+                lx[list_n + lane] = 0.f; ly[list_n + lane] = 0.f; lz[list_n + lane] = 0.f; lw[list_n + lane] = 0.f;
+            }
             __syncwarp();
         }
-        const int npair = (list_n + 1) >> 1;
-        const float2 *px = (const float2 *)lx, *py = (const float2 *)ly, *pz = (const float2 *)lz,
-                     *pw = (const float2 *)lw;
-        // one i-particle against pairs k0, k0 + step, ... (its sums carried in and out)
+        const int nquad = (list_n + 3) >> 2;
+        const float4 *px = (const float4 *)lx, *py = (const float4 *)ly, *pz = (const float4 *)lz,
+                     *pw = (const float4 *)lw;
+        // one i-particle against quads k0, k0 + step, ... (its sums carried in and out)
         auto run = [&](const float4 &p, float &sx_, float &sy_, float &sz_, float &sp_, int k0, int step) {
             const float2 e2 = make_float2(a.eps2, a.eps2);
             const float2 nx = make_float2(-p.x, -p.x), ny = make_float2(-p.y, -p.y), nz = make_float2(-p.z, -p.z);
             float2 sx = make_float2(sx_, 0.f), sy = make_float2(sy_, 0.f), sz = make_float2(sz_, 0.f);
             float2 sp = make_float2(-sp_, 0.f);
-            for (int k = k0; k < npair; k += step) interact_pairs(px[k], py[k], pz[k], pw[k], nx, ny, nz, e2, sx, sy, sz, sp);
+            for (int k = k0; k < nquad; k += step) {
+                const float4 X = px[k], Y = py[k], Z = pz[k], W = pw[k];
+                interact_pairs(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
+                               make_float2(W.x, W.y), nx, ny, nz, e2, sx, sy, sz, sp);
+                interact_pairs(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
+                               make_float2(W.z, W.w), nx, ny, nz, e2, sx, sy, sz, sp);
+            }
             sx_ = __fadd_rn(sx.x, sx.y); sy_ = __fadd_rn(sy.x, sy.y); sz_ = __fadd_rn(sz.x, sz.y);
             sp_ = -__fadd_rn(sp.x, sp.y);
         };
         if (two) {  // both members of the lane over every pair, one after the other
             run(pi, ax, ay, az, ph, 0, 1);
             run(pi2, bx, by, bz, qh, 0, 1);
-        } else {  // S lanes per i-particle: lane sub takes pairs sub, sub + S, ...
+        } else {  // S lanes per i-particle: lane sub takes quads sub, sub + S, ...
             run(pi, ax, ay, az, ph, sub, S);
         }
         n_inter += (unsigned long long)list_n * cnt;
@@ -322,73 +335,125 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
             }
             list_n += nacc;
         }
-        // opened cells -> queue their children
+        // opened cells -> their children into the queue; opened leaves -> their particles
+        // into the list (asynchronous copies).  One warp scan counts both (children in the
+        // low 16 bits, particles in the high 16: they fit while every leaf of the batch holds
+        // fewer than 2048 particles) and one loop writes both: entry e of the batch belongs
+        // to the first lane whose inclusive count exceeds e (a binary search over the lanes
+        // by shuffles); each lane's entries are its cell's children or its leaf's particles.
         const uint32_t nch = (valid && !ok && !leaf) ? l1 : 0u;
-        const uint32_t incl = warp_incl_scan(nch);
-        const uint32_t tot = __shfl_sync(FULL, incl, 31);
-        if (tot) {
-            if (tail - head + tot > (uint32_t)a.qcap) {
+        const uint32_t lc = (valid && !ok && leaf) ? (l1 & ~GT_LEAF_FLAG) : 0u;
+        if (__all_sync(FULL, lc < 2048u)) {
+            const uint32_t mine = nch | (lc << 16);
+            const uint32_t incl = warp_incl_scan(mine);
+            const uint32_t tot = __shfl_sync(FULL, incl, 31);
+            const uint32_t tc = tot & 0xffffu, tp = tot >> 16;
+            if (tail - head + tc > (uint32_t)a.qcap) {
                 overflow = true;
                 break;
             }
-            // the warp writes the children together: entry e belongs to the first lane whose
-            // inclusive count exceeds e (a binary search over the lanes by shuffles)
-            const uint32_t cbase = l0 - (incl - nch);
-            for (uint32_t r = 0; r < tot; r += 32) {
+            const uint32_t inclm = (incl & 0xffffu) + (incl >> 16);  // entries up to this lane
+            int pbase = list_n;  // list slot of the batch's first particle
+            uint32_t pdone = 0;  // particles written by earlier rounds
+            for (uint32_t r = 0; r < tc + tp; r += 32) {
                 const uint32_t e = r + (uint32_t)lane;
                 int own = 0;
 #pragma unroll
                 for (int step = 16; step > 0; step >>= 1)
-                    if (__shfl_sync(FULL, incl, own + step - 1) <= e) own += step;
-                const uint32_t cb = __shfl_sync(FULL, cbase, own);
-                if (e < tot) q[(tail + e) & qmask] = cb + e;
+                    if (__shfl_sync(FULL, inclm, own + step - 1) <= e) own += step;
+                const uint32_t oi = __shfl_sync(FULL, incl, own);
+                const uint32_t om = __shfl_sync(FULL, mine, own);
+                const uint32_t ol = __shfl_sync(FULL, l0, own);
+                const uint32_t ec = (oi & 0xffffu) - (om & 0xffffu), ep = (oi >> 16) - (om >> 16);
+                const bool in = e < tc + tp;
+                const bool isp = in && (om >> 16) != 0u;
+                const uint32_t off = e - ec - ep;
+                const unsigned pm = __ballot_sync(FULL, isp);
+                if (pm && pbase + (int)pdone + __popc(pm) > LIST_CAP) {
+                    list_n = pbase + (int)pdone;
+                    flush();
+                    pbase = -(int)pdone;
+                }
+                if (in && !isp) q[(tail + ec + off) & qmask] = ol + off;
+                if (isp) {
+                    const int slot = pbase + (int)(ep + off);
+                    const float *src = (const float *)&a.posm[ol + off];
+                    cp_async4(&lx[slot], src);
+                    cp_async4(&ly[slot], src + 1);
+                    cp_async4(&lz[slot], src + 2);
+                    cp_async4(&lw[slot], src + 3);
+                }
+                pdone += (uint32_t)__popc(pm);
             }
-            tail += tot;
-        }
-        // opened leaves -> their particles into the list (asynchronous copies)
-        const uint32_t lc = (valid && !ok && leaf) ? (l1 & ~GT_LEAF_FLAG) : 0u;
-        const uint32_t lincl = warp_incl_scan(lc);
-        const uint32_t ltot = __shfl_sync(FULL, lincl, 31);
-        if (ltot) {
-            if (list_n + (int)ltot > LIST_CAP) flush();
-            if (ltot <= (uint32_t)LIST_CAP) {
-                const uint32_t pbase = l0 - (lincl - lc);
-                for (uint32_t r = 0; r < ltot; r += 32) {
+            tail += tc;
+            list_n = pbase + (int)pdone;
+        } else {
+            // a leaf of 2048 or more particles (coincident particles chained to level 21)
+            const uint32_t incl = warp_incl_scan(nch);
+            const uint32_t tot = __shfl_sync(FULL, incl, 31);
+            if (tot) {
+                if (tail - head + tot > (uint32_t)a.qcap) {
+                    overflow = true;
+                    break;
+                }
+                // the warp writes the children together: entry e belongs to the first lane whose
+                // inclusive count exceeds e (a binary search over the lanes by shuffles)
+                const uint32_t cbase = l0 - (incl - nch);
+                for (uint32_t r = 0; r < tot; r += 32) {
                     const uint32_t e = r + (uint32_t)lane;
                     int own = 0;
 #pragma unroll
                     for (int step = 16; step > 0; step >>= 1)
-                        if (__shfl_sync(FULL, lincl, own + step - 1) <= e) own += step;
-                    const uint32_t pb = __shfl_sync(FULL, pbase, own);
-                    if (e < ltot) {
-                        const float *src = (const float *)&a.posm[pb + e];
-                        cp_async4(&lx[list_n + e], src);
-                        cp_async4(&ly[list_n + e], src + 1);
-                        cp_async4(&lz[list_n + e], src + 2);
-                        cp_async4(&lw[list_n + e], src + 3);
-                    }
+                        if (__shfl_sync(FULL, incl, own + step - 1) <= e) own += step;
+                    const uint32_t cb = __shfl_sync(FULL, cbase, own);
+                    if (e < tot) q[(tail + e) & qmask] = cb + e;
                 }
-                list_n += (int)ltot;
-            } else {  // leaves holding more particles than the list: one at a time, in chunks
-                unsigned lm = __ballot_sync(FULL, lc != 0u);
-                while (lm) {
-                    const int src = __ffs(lm) - 1;
-                    lm &= lm - 1;
-                    const uint32_t lf = __shfl_sync(FULL, l0, src);
-                    const uint32_t lcount = __shfl_sync(FULL, lc, src);
-                    uint32_t done = 0;
-                    while (done < lcount) {
-                        if (list_n == LIST_CAP) flush();
-                        const uint32_t take = min(lcount - done, (uint32_t)(LIST_CAP - list_n));
-                        for (uint32_t k = lane; k < take; k += 32) {
-                            const float *src = (const float *)&a.posm[lf + done + k];
-                            cp_async4(&lx[list_n + k], src);
-                            cp_async4(&ly[list_n + k], src + 1);
-                            cp_async4(&lz[list_n + k], src + 2);
-                            cp_async4(&lw[list_n + k], src + 3);
+                tail += tot;
+            }
+            // opened leaves -> their particles into the list (asynchronous copies)
+            const uint32_t lincl = warp_incl_scan(lc);
+            const uint32_t ltot = __shfl_sync(FULL, lincl, 31);
+            if (ltot) {
+                if (list_n + (int)ltot > LIST_CAP) flush();
+                if (ltot <= (uint32_t)LIST_CAP) {
+                    const uint32_t pbase = l0 - (lincl - lc);
+                    for (uint32_t r = 0; r < ltot; r += 32) {
+                        const uint32_t e = r + (uint32_t)lane;
+                        int own = 0;
+#pragma unroll
+                        for (int step = 16; step > 0; step >>= 1)
+                            if (__shfl_sync(FULL, lincl, own + step - 1) <= e) own += step;
+                        const uint32_t pb = __shfl_sync(FULL, pbase, own);
+                        if (e < ltot) {
+                            const float *src = (const float *)&a.posm[pb + e];
+                            cp_async4(&lx[list_n + e], src);
+                            cp_async4(&ly[list_n + e], src + 1);
+                            cp_async4(&lz[list_n + e], src + 2);
+                            cp_async4(&lw[list_n + e], src + 3);
                         }
-                        list_n += (int)take;
-                        done += take;
+                    }
+                    list_n += (int)ltot;
+                } else {  // leaves holding more particles than the list: one at a time, in chunks
+                    unsigned lm = __ballot_sync(FULL, lc != 0u);
+                    while (lm) {
+                        const int src = __ffs(lm) - 1;
+                        lm &= lm - 1;
+                        const uint32_t lf = __shfl_sync(FULL, l0, src);
+                        const uint32_t lcount = __shfl_sync(FULL, lc, src);
+                        uint32_t done = 0;
+                        while (done < lcount) {
+                            if (list_n == LIST_CAP) flush();
+                            const uint32_t take = min(lcount - done, (uint32_t)(LIST_CAP - list_n));
+                            for (uint32_t k = lane; k < take; k += 32) {
+                                const float *src = (const float *)&a.posm[lf + done + k];
+                                cp_async4(&lx[list_n + k], src);
+                                cp_async4(&ly[list_n + k], src + 1);
+                                cp_async4(&lz[list_n + k], src + 2);
+                                cp_async4(&lw[list_n + k], src + 3);
+                            }
+                            list_n += (int)take;
+                            done += take;
+                        }
                     }
                 }
             }
@@ -433,7 +498,7 @@ __device__ __forceinline__ int system_of(const uint32_t *gprefix, int nsys, uint
     return lo;
 }
 
-__global__ __launch_bounds__(WT, 3) void k_walk(WalkArgs a) {
+__global__ __launch_bounds__(WT, GT_WALK_MINB) void k_walk(WalkArgs a) {
     __shared__ __align__(16) float list_sm[NWARP][4 * LIST_CAP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *list = list_sm[warp];

@@ -14,7 +14,6 @@ Each case prints one line with its timings and counts; inputs are the seeded mod
 from __future__ import annotations
 
 import argparse
-import time
 
 from . import build as _build
 from . import gothic as g
@@ -37,7 +36,7 @@ def _system(model: str, n: int, seed: int):
     return s, prm
 
 
-def case_walk(model: str, n: int, seed: int) -> str:
+def case_walk(model: str, n: int, seed: int, repeat: int = 1) -> str:
     import torch
     s, prm = _system(model, n, seed)
     s.build_tree()
@@ -50,16 +49,23 @@ def case_walk(model: str, n: int, seed: int) -> str:
     aold = torch.linalg.norm(acc[:, :3].double(), dim=1).float().contiguous()
     s.set_params(prm)
     st0 = s.stats()
-    t = time.perf_counter()
     s.accel_active(None, aold, acc)
     s.sync()
-    dt = time.perf_counter() - t
     st1 = s.stats()
     inter = st1["interactions"] - st0["interactions"]
     tests = st1["mac_tests"] - st0["mac_tests"]
+    # the same walk timed again with CUDA events (mean of `repeat` launches)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(repeat):
+        s.accel_active(None, aold, acc)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(repeat, 1)
     s.close()
     return (f"walk {model} n={n} nodes={st1['n_nodes']} depth={st1['depth']} interactions={inter} "
-            f"mac_tests={tests} acc_walk_ms={dt * 1e3:.3f}")
+            f"mac_tests={tests} acc_walk_ms={ms:.4f} ns_per_interaction={ms * 1e6 / max(inter, 1):.4f}")
 
 
 def case_build(model: str, n: int, seed: int, repeat: int) -> str:
@@ -108,7 +114,7 @@ def main(argv=None):
     _build.build()
     g.load()
     if a.case == "walk":
-        print(case_walk(a.model, a.n, a.seed), flush=True)
+        print(case_walk(a.model, a.n, a.seed, a.repeat), flush=True)
     elif a.case == "build":
         print(case_build(a.model, a.n, a.seed, a.repeat), flush=True)
     else:
