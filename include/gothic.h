@@ -156,7 +156,8 @@ GT_API const char *gt_strerror(int status);
  * (GT_GROUP_CELLS_TUNED), r_crit 0, automatic rebuild interval. */
 GT_API int gt_default_params(gt_params *prm);
 
-/* Bytes of device workspace a system of n particles needs (n >= 0). */
+/* Bytes of device workspace a system of n particles needs (0 <= n < 2^30; GT_EINVAL
+ * otherwise -- the sort's look-back counts hold 30 bits). */
 GT_API int gt_workspace_bytes(int64_t n, const gt_params *prm, size_t *bytes);
 
 /* Create a system of n particles inside the caller's workspace d_ws (at least
@@ -365,7 +366,7 @@ GT_API int gt_measure_fp32_rates(gt_fp32_rates *out, gt_stream stream);
  * receive the sorted pairs.  The scratch the sort needs (the alternate key and
  * value buffers, per-tile look-back status words, digit histograms and a control
  * block) lives in one file-scope device array of the library, sized for
- * GT_NOALLOC_SORT_MAX pairs (about 12.5 MiB, held on every GPU that loads the
+ * GT_NOALLOC_SORT_MAX pairs (about 14 MiB, held on every GPU that loads the
  * library until the process exits); nothing is allocated or freed by the call.
  *   - n > GT_NOALLOC_SORT_MAX: rejected with GT_EINVAL before any device work.
  *   - The first call on a device looks up the array's device address (once per

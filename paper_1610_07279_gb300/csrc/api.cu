@@ -117,7 +117,7 @@ size_t carve(gt_system *s, char *base, int64_t n, const gt_params *p, int nsm, i
         s->sb.key[b] = L.take<uint64_t>(base, N);
         s->sb.val[b] = L.take<uint32_t>(base, N);
     }
-    s->sb.status = (unsigned long long *)L.take<char>(base, gt_sort_scratch_bytes(n));
+    s->sb.status = (uint32_t *)L.take<char>(base, gt_sort_scratch_bytes(n));
     s->sb.hist = L.take<uint32_t>(base, 8 * 256);
     s->sb.digit_base = L.take<uint32_t>(base, 8 * 256);
     const int64_t cap = node_capacity(n, p);
@@ -131,7 +131,6 @@ size_t carve(gt_system *s, char *base, int64_t n, const gt_params *p, int nsm, i
     s->nd.walk = L.take<float4>(base, cap);
     s->nd.sum = L.take<DSum4>(base, cap);
     s->nd.cells = L.take<uint32_t>(base, cap);
-    s->nd.arrive = L.take<uint32_t>(base, cap);
     const int64_t st_tiles = (cap + 511) / 512 + (n + 4095) / 4096 + 64;
     s->status = L.take<unsigned long long>(base, st_tiles);
     s->active = L.take<uint32_t>(base, N);
@@ -525,7 +524,7 @@ int gt_default_params(gt_params *p) {
 }
 
 int gt_workspace_bytes(int64_t n, const gt_params *prm, size_t *bytes) {
-    if (!bytes || n < 0 || n >= (int64_t)1 << 31) return GT_EINVAL;
+    if (!bytes || n < 0 || n >= (int64_t)1 << 30) return GT_EINVAL;
     int rc = check_params(prm);
     if (rc) return rc;
     int dev, nsm;
@@ -536,7 +535,7 @@ int gt_workspace_bytes(int64_t n, const gt_params *prm, size_t *bytes) {
 }
 
 int gt_system_create(gt_system **out, int64_t n, const gt_params *prm, void *d_ws, size_t ws_bytes) {
-    if (!out || n < 0 || n >= (int64_t)1 << 31 || !d_ws) return GT_EINVAL;
+    if (!out || n < 0 || n >= (int64_t)1 << 30 || !d_ws) return GT_EINVAL;
     if (((uintptr_t)d_ws) % ALIGN) return GT_EINVAL;
     int rc = check_params(prm);
     if (rc) return rc;

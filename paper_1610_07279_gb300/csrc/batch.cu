@@ -71,7 +71,7 @@ size_t plan(int nsys, const int64_t *n, const gt_params *prm, int n_prm, int nsm
 int check_members(int nsys, const int64_t *n, const gt_params *prm, int n_prm) {
     if (nsys < 1 || !n || !prm || (n_prm != 1 && n_prm != nsys)) return GT_EINVAL;
     for (int k = 0; k < nsys; k++) {
-        if (n[k] < 0 || n[k] >= (int64_t)1 << 31) return GT_EINVAL;
+        if (n[k] < 0 || n[k] >= (int64_t)1 << 30) return GT_EINVAL;
         const int rc = gt_sys_check_params(&prm_of(prm, n_prm, k));
         if (rc) return rc;
     }

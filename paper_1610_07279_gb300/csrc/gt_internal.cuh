@@ -36,7 +36,8 @@ struct DevCtl {
     unsigned int tile_ticket[GT_TREE_LEVELS + 4];  // dynamic tile ids: levels, actives, groups, leaves, cells
     unsigned int level_start[GT_TREE_LEVELS + 2];  // first cell of each level; [22] = node count
     unsigned int sort_ticket[8];      // dynamic tile ids of the 8 sort passes
-    unsigned int sort_epoch;          // look-back epoch of the sort
+    unsigned int pl_ticket;           // chunk tickets of the pseudo j-particle cell pass
+    unsigned int pl_done[GT_TREE_LEVELS];  // finished cell chunks per level of that pass
     unsigned long long interactions;  // cumulative
     unsigned long long mac_tests;     // cumulative
     unsigned long long tnext;         // block time of the current step
@@ -90,7 +91,6 @@ struct Nodes {
     uint32_t *cells;           // every node once: the leaves bucketed by particle count, then
                                // the cells with children by level (deepest last) and, inside
                                // a level, by number of children
-    uint32_t *arrive;          // children of a cell done so far in the pseudo j-particle pass
 };
 
 __device__ __forceinline__ void gt_set_error(DevCtl *ctl, int code, int where) {
@@ -238,7 +238,7 @@ void gt_note_launches(int k);
 struct SortBufs {
     uint64_t *key[2];
     uint32_t *val[2];
-    unsigned long long *status;  // look-back status, tiles x RADIX
+    uint32_t *status;            // look-back status of the 8 passes, 8 x tiles x RADIX
     uint32_t *hist;              // digit histograms of the 8 passes, 8 x RADIX
     uint32_t *digit_base;        // digit starts of the 8 passes, 8 x RADIX
 };

@@ -332,7 +332,7 @@ int gt_server_destroy(gt_server *v) {
 }
 
 int gt_submit(gt_server *v, const gt_request *req, uint64_t *ticket) {
-    if (!v || !req || !ticket || req->n < 1 || req->n >= (int64_t)1 << 31 || req->nsteps < 0) return GT_EINVAL;
+    if (!v || !req || !ticket || req->n < 1 || req->n >= (int64_t)1 << 30 || req->nsteps < 0) return GT_EINVAL;
     if (!req->p_pos || !req->p_vel || !req->p_mass) return GT_EINVAL;
     gt_params prm = req->params;
     if (prm.walk_queue > v->qcap) prm.walk_queue = v->qcap;

@@ -8,10 +8,12 @@
 //                  every key inside the tile (warp-striped; a key's peers with the same
 //                  digit from nine ballots, its rank by popc), the tile's per-digit counts
 //                  published and each digit's exclusive prefix over earlier tiles found
-//                  by a decoupled look-back (256 digits in parallel, a window of 8 earlier
-//                  tiles per step, every wait bounded), a local sort in shared memory,
-//                  then coalesced writes of each digit run
-//                  (reads and writes 12 B/key; 8 B of status per digit and tile)
+//                  by a decoupled look-back (256 digits in parallel, a window of
+//                  GT_SORT_LB earlier tiles per step, every wait bounded), a local sort in
+//                  shared memory, then coalesced writes of each digit run
+//                  (reads and writes 12 B/key; 4 B of status per digit and tile: two flag
+//                  bits, aggregate or inclusive prefix, and a 30-bit count; every pass has
+//                  its own status rows, all cleared once per sort)
 // HBM-bound: ~25 B per key per pass.
 #include <mutex>
 
@@ -28,6 +30,9 @@ namespace {
 #ifndef GT_SORT_MINB
 #define GT_SORT_MINB 3
 #endif
+#ifndef GT_SORT_LB
+#define GT_SORT_LB 16              // earlier tiles read per look-back step
+#endif
 constexpr int RB = 8;              // digit bits
 constexpr int R = 1 << RB;         // digits
 constexpr int HT = R;              // threads of the histogram and digit-base kernels
@@ -36,6 +41,9 @@ constexpr int IPT = GT_SORT_IPT;   // keys per thread
 constexpr int TILE = ST * IPT;     // keys per tile
 constexpr int NW = ST / 32;
 constexpr int PASSES = 8;          // 64 / RB (bit 63 is always 0; the last pass is cheap)
+constexpr uint32_t ST_AGG = 1u << 30;   // status word: the tile's own count of the digit
+constexpr uint32_t ST_PRE = 2u << 30;   // status word: the inclusive count over tiles 0..t
+constexpr uint32_t ST_VAL = ST_AGG - 1u;
 constexpr size_t SCATTER_SMEM = TILE * sizeof(unsigned long long) + TILE * sizeof(uint32_t) +
                                 (NW * R + 2 * R + NW + 1) * sizeof(uint32_t);
 static_assert(ST >= R && ST % 32 == 0, "one thread per digit in the per-tile scans");
@@ -69,7 +77,7 @@ __global__ __launch_bounds__(HT) void k_hist_all(long long n, const unsigned lon
         if (h[p][threadIdx.x]) atomicAdd(&hist[p * R + threadIdx.x], h[p][threadIdx.x]);
 }
 
-// one block: digit starts of every pass; also opens a new look-back epoch and resets the tickets
+// one block: digit starts of every pass; also resets the tile tickets
 __global__ __launch_bounds__(HT) void k_digit_bases(const uint32_t *__restrict__ hist,
                                                     uint32_t *__restrict__ base, DevCtl *ctl) {
     __shared__ uint32_t tmp[HT / 32 + 1];
@@ -79,37 +87,33 @@ __global__ __launch_bounds__(HT) void k_digit_bases(const uint32_t *__restrict__
         base[p * R + threadIdx.x] = b;
     }
     if (threadIdx.x < PASSES) ctl->sort_ticket[threadIdx.x] = 0;
-    if (threadIdx.x == 0) ctl->sort_epoch += 1u;
 }
 
-// Look-back of one digit: the count of digit d in all tiles before `tile`.  Status word
-// (tag << 32 | count) of tile t, digit d sits at status[t * R + d], so the 256 threads of a
-// tile read one contiguous row per predecessor; each step reads a window of LB rows at once
-// and adds counts back to the first tile whose inclusive prefix is published.
-__device__ __forceinline__ uint32_t lookback_digit(const unsigned long long *status, int tile, int d,
-                                                   unsigned long long tagA, unsigned long long tagP,
-                                                   DevCtl *ctl) {
-    constexpr int LB = 8;
+// Look-back of one digit: the count of digit d in all tiles before `tile`.  The status
+// word of tile t, digit d sits at status[t * R + d], so the 256 threads of a tile read one
+// contiguous row per predecessor; each step reads a window of LB rows at once and adds
+// counts back to the first tile whose inclusive prefix is published.
+__device__ __forceinline__ uint32_t lookback_digit(const uint32_t *status, int tile, int d, DevCtl *ctl) {
+    constexpr int LB = GT_SORT_LB;
     uint32_t excl = 0;
     int t = tile - 1;
     unsigned int spins = 0;
     const unsigned int limit = gt_spin_limit(ctl);
     while (t >= 0) {
-        unsigned long long sv[LB];
+        uint32_t sv[LB];
 #pragma unroll
         for (int j = 0; j < LB; j++)
-            sv[j] = t - j >= 0 ? *((const volatile unsigned long long *)&status[(size_t)(t - j) * R + d]) : tagP;
+            sv[j] = t - j >= 0 ? *((const volatile uint32_t *)&status[(size_t)(t - j) * R + d]) : ST_PRE;
         int used = 0;
         bool done = false, stalled = false;
 #pragma unroll
         for (int j = 0; j < LB; j++) {
             if (done || stalled) continue;
-            const unsigned long long tag = sv[j] & 0xffffffff00000000ull;
-            if (tag == tagP) {
-                excl += (uint32_t)sv[j];
+            if (sv[j] & ST_PRE) {
+                excl += sv[j] & ST_VAL;
                 done = true;
-            } else if (tag == tagA) {
-                excl += (uint32_t)sv[j];
+            } else if (sv[j] & ST_AGG) {
+                excl += sv[j] & ST_VAL;
                 used = j + 1;
             } else {
                 stalled = true;
@@ -134,7 +138,7 @@ __global__ __launch_bounds__(ST, GT_SORT_MINB) void k_onesweep(long long n, int 
                                                  unsigned long long *__restrict__ kout,
                                                  uint32_t *__restrict__ vout,
                                                  const uint32_t *__restrict__ digit_base,
-                                                 unsigned long long *status /* ntiles x R */, int ntiles,
+                                                 uint32_t *status /* this pass: ntiles x R */, int ntiles,
                                                  DevCtl *ctl) {
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned long long *skey = (unsigned long long *)smraw;
@@ -194,11 +198,8 @@ __global__ __launch_bounds__(ST, GT_SORT_MINB) void k_onesweep(long long n, int 
             cnt += t;
         }
     // publish this tile's count of digit d as early as possible
-    const unsigned int epoch = ctl->sort_epoch * PASSES + (unsigned)pass;
-    const unsigned long long tagA = (unsigned long long)(4u * epoch + 1u) << 32;
-    const unsigned long long tagP = (unsigned long long)(4u * epoch + 2u) << 32;
-    unsigned long long *own = status + (size_t)tile * R + (dig ? d : 0);
-    if (dig) *((volatile unsigned long long *)own) = (tile == 0 ? tagP : tagA) | cnt;
+    uint32_t *own = status + (size_t)tile * R + (dig ? d : 0);
+    if (dig) *((volatile uint32_t *)own) = (tile == 0 ? ST_PRE : ST_AGG) | cnt;
     uint32_t total;
     const uint32_t ds0 = block_excl_scan<ST>(cnt, &total, scantmp);
     if (dig) dstart[d] = ds0;
@@ -218,8 +219,8 @@ __global__ __launch_bounds__(ST, GT_SORT_MINB) void k_onesweep(long long n, int 
     if (dig) {
         uint32_t excl = 0;
         if (tile > 0) {
-            excl = lookback_digit(status, tile, d, tagA, tagP, ctl);
-            *((volatile unsigned long long *)own) = tagP | (unsigned long long)(excl + cnt);
+            excl = lookback_digit(status, tile, d, ctl);
+            *((volatile uint32_t *)own) = ST_PRE | (excl + cnt);
         }
         gbase[d] = digit_base[pass * R + d] + excl - dstart[d];
     }
@@ -240,8 +241,8 @@ __global__ __launch_bounds__(ST, GT_SORT_MINB) void k_onesweep(long long n, int 
 int gt_sort_tiles(int64_t n) { return (int)((n + TILE - 1) / TILE); }
 
 size_t gt_sort_scratch_bytes(int64_t n) {
-    // look-back status (R x tiles x 8 B)
-    return (size_t)R * (size_t)(gt_sort_tiles(n) > 0 ? gt_sort_tiles(n) : 1) * sizeof(unsigned long long);
+    // look-back status of every pass (PASSES x tiles x R x 4 B)
+    return (size_t)PASSES * R * (size_t)(gt_sort_tiles(n) > 0 ? gt_sort_tiles(n) : 1) * sizeof(uint32_t);
 }
 
 void gt_sort_init() {
@@ -252,6 +253,7 @@ void gt_launch_sort(SortBufs &b, int64_t n, DevCtl *ctl, cudaStream_t st) {
     if (n <= 1) return;
     const int ntiles = gt_sort_tiles(n);
     cudaMemsetAsync(b.hist, 0, PASSES * R * sizeof(uint32_t), st);
+    cudaMemsetAsync(b.status, 0, (size_t)PASSES * R * ntiles * sizeof(uint32_t), st);
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -262,7 +264,7 @@ void gt_launch_sort(SortBufs &b, int64_t n, DevCtl *ctl, cudaStream_t st) {
         const int src = p & 1, dst = src ^ 1;
         { k_onesweep<<<ntiles, ST, SCATTER_SMEM, st>>>(n, p, (const unsigned long long *)b.key[src], b.val[src],
                                                        (unsigned long long *)b.key[dst], b.val[dst], b.digit_base,
-                                                       b.status, ntiles, ctl);
+                                                       b.status + (size_t)p * R * ntiles, ntiles, ctl);
           gt_note_launches(1); }
     }
 }
@@ -280,7 +282,7 @@ constexpr size_t NA_TILES = (GT_NOALLOC_SORT_MAX + TILE - 1) / TILE;
 constexpr size_t NA_OFF_KEY = na_up(sizeof(DevCtl));
 constexpr size_t NA_OFF_VAL = NA_OFF_KEY + na_up((size_t)GT_NOALLOC_SORT_MAX * sizeof(unsigned long long));
 constexpr size_t NA_OFF_STATUS = NA_OFF_VAL + na_up((size_t)GT_NOALLOC_SORT_MAX * sizeof(uint32_t));
-constexpr size_t NA_OFF_HIST = NA_OFF_STATUS + na_up(R * NA_TILES * sizeof(unsigned long long));
+constexpr size_t NA_OFF_HIST = NA_OFF_STATUS + na_up(PASSES * R * NA_TILES * sizeof(uint32_t));
 constexpr size_t NA_OFF_BASE = NA_OFF_HIST + na_up(PASSES * R * sizeof(uint32_t));
 constexpr size_t NA_BYTES = NA_OFF_BASE + na_up(PASSES * R * sizeof(uint32_t));
 
@@ -320,21 +322,18 @@ extern "C" int gt_sort_pairs_noalloc(uint64_t *d_keys, uint32_t *d_vals, int64_t
     if (n <= 1) return GT_OK;
     cudaStream_t st = (cudaStream_t)stream;
     DevCtl *ctl = (DevCtl *)base;
-    // the histograms are cleared by the sort itself; the look-back status words carry
-    // an epoch that the control block counts, so the control block and the status
-    // must start at zero once (the first call on a device), after which every call
-    // leaves them consistent for the next
+    // the histograms and the look-back status words are cleared by the sort itself; the
+    // control block (tickets, error word) starts at zero once, on the first call on a
+    // device, after which every call leaves it consistent for the next
     if (first_use) {
-        if (cudaMemsetAsync(ctl, 0, sizeof(DevCtl), st) != cudaSuccess ||
-            cudaMemsetAsync(base + NA_OFF_STATUS, 0, R * NA_TILES * sizeof(unsigned long long), st) != cudaSuccess)
-            return GT_ECUDA;
+        if (cudaMemsetAsync(ctl, 0, sizeof(DevCtl), st) != cudaSuccess) return GT_ECUDA;
     }
     SortBufs b;
     b.key[0] = d_keys;
     b.val[0] = d_vals;
     b.key[1] = (uint64_t *)(base + NA_OFF_KEY);
     b.val[1] = (uint32_t *)(base + NA_OFF_VAL);
-    b.status = (unsigned long long *)(base + NA_OFF_STATUS);
+    b.status = (uint32_t *)(base + NA_OFF_STATUS);
     b.hist = (uint32_t *)(base + NA_OFF_HIST);
     b.digit_base = (uint32_t *)(base + NA_OFF_BASE);
     gt_launch_sort(b, n, ctl, st);  // an even number of passes leaves the result in d_keys/d_vals

@@ -11,11 +11,11 @@
 // lock-step 7-way binary search, children numbered by a block scan plus a decoupled
 // look-back over tiles taken in ticket order).  Both give the same numbering.
 //
-// A5, one launch over the leaves of the cell list (bucketed by level and size, so the
-// FP64 leaf sums run with full warps, which matters on this GPU's narrow FP64 pipe): a
-// leaf's lane sums its particles in FP64 (mass, m x, m y, m z); a cell with children sums
-// its children's FP64 sums in child order, computed by the thread whose child finished
-// last (no level barriers).  m_J = (float)M and
+// A5, two launches over a cell list bucketed by level and size (every FP64 instruction
+// runs with full warps, which matters on this GPU's narrow FP64 pipe): first every leaf,
+// whose lane sums its particles in FP64 (mass, m x, m y, m z), with no waits; then every
+// cell with children, which sums its children's FP64 sums in child order once the level
+// below is done.  m_J = (float)M and
 // r_J = (float)S / (float)M (a cell of one particle is that particle); b_J is the
 // largest FP32 |r - r_J| of a leaf's particles, or the largest |r_c - r_J| + b_c
 // over a cell's children, widened by (1 + 2^-20) so that FP32 rounding cannot
@@ -463,16 +463,14 @@ __global__ __launch_bounds__(256) void k_cell_fill(Nodes nd, long long cap, DevC
     }
 }
 
-// ---- A5: pseudo j-particles, one launch without level barriers ---------------------
-// Every leaf is taken by one thread, in the order of the cell list (a level's leaves
-// bucketed by particle count, so the lanes of a warp run equal trip counts).  When a node
-// is done, its thread makes the node's results visible device-wide and counts itself into
-// its parent's arrival word; the thread whose arrival completes the parent's children
-// computes the parent (its children's FP64 sums added in child order), re-arms the word
-// for the next pass and climbs on.  No thread waits for another, every cell is computed
-// exactly once after all its children, and the order of every FP64 addition is fixed by
-// the tree alone, so the result does not depend on which thread computes what.
-constexpr int PL = 128;  // threads per block
+// ---- A5: pseudo j-particles in two launches ------------------------------------------
+// First every leaf, one per thread, in the order of the cell list (a level's leaves
+// bucketed by particle count, so the lanes of a warp run equal trip counts); nothing
+// waits.  Then the cells with children, in chunks of PL handed out by a ticket counter
+// from the deepest level up: a chunk of level l waits until every chunk of level l + 1 is
+// done (those hold smaller tickets, so the blocks holding them are running and the wait
+// ends; it is bounded all the same).
+constexpr int PL = 128;  // threads per block, nodes per chunk
 
 // Leaf c: one lane sums its particles in FP64 (mass, m x, m y, m z) in particle order.
 // The masses and the cells' members do not change between tree builds, so the mass
@@ -586,8 +584,8 @@ __device__ __forceinline__ void pseudo_cell(const Nodes &nd, uint32_t p) {
 }
 
 template <bool WITH_MASS>
-__global__ __launch_bounds__(PL) void k_pseudo(Nodes nd, const float4 *__restrict__ posm,
-                                               const DevCtl *__restrict__ ctl) {
+__global__ __launch_bounds__(PL, 8) void k_pseudo_leaves(Nodes nd, const float4 *__restrict__ posm,
+                                                         const DevCtl *__restrict__ ctl) {
     __shared__ uint32_t lfirst[GT_TREE_LEVELS + 1];  // prefix of the levels' leaf counts
     __shared__ uint32_t lseg[GT_TREE_LEVELS];        // where level l's leaves start in the cell list
     if (threadIdx.x == 0) {
@@ -604,27 +602,69 @@ __global__ __launch_bounds__(PL) void k_pseudo(Nodes nd, const float4 *__restric
     for (uint32_t t = blockIdx.x * PL + threadIdx.x; t < total; t += gridDim.x * PL) {
         int l = 0;
         while (lfirst[l + 1] <= t) l++;
-        uint32_t c = nd.cells[lseg[l] + (t - lfirst[l])];
-        pseudo_leaf<WITH_MASS>(nd, posm, c);
-        for (;;) {
-            const int32_t p = nd.parent[c];
-            if (p < 0) break;
-            __threadfence();  // this node's results before its arrival
-            const uint32_t seen = atomicAdd(&nd.arrive[p], 1u);
-            if (seen + 1u != nd.nchild[p]) break;
-            nd.arrive[p] = 0u;  // every child has arrived: re-armed for the next pass
-            __threadfence();    // the siblings' results after their arrivals
-            pseudo_cell<WITH_MASS>(nd, (uint32_t)p);
-            c = (uint32_t)p;
-        }
+        pseudo_leaf<WITH_MASS>(nd, posm, nd.cells[lseg[l] + (t - lfirst[l])]);
     }
 }
 
-// arrival words of a new tree start at zero
-__global__ __launch_bounds__(256) void k_zero_arrive(Nodes nd, long long cap, const DevCtl *__restrict__ ctl) {
-    long long nn = ctl->level_start[GT_TREE_LEVELS];
-    if (nn > cap) nn = cap;
-    for (long long c = blockIdx.x * 256ll + threadIdx.x; c < nn; c += (long long)gridDim.x * 256) nd.arrive[c] = 0u;
+template <bool WITH_MASS>
+__global__ __launch_bounds__(PL, 8) void k_pseudo_cells(Nodes nd, DevCtl *ctl) {
+    __shared__ uint32_t cseg[GT_TREE_LEVELS + 1];   // level l's cells: cseg[l] .. cseg[l + 1]
+    __shared__ uint32_t nchunk[GT_TREE_LEVELS];
+    __shared__ uint32_t tfirst[GT_TREE_LEVELS + 1]; // first ticket of level 20 - k at tfirst[k]
+    __shared__ unsigned int t_sh;
+    __shared__ int bad_sh;
+    if (threadIdx.x == 0) {
+        for (int l = 0; l < GT_TREE_LEVELS; l++) {
+            cseg[l] = ctl->seg[2 * l + 1];
+            nchunk[l] = (ctl->seg[2 * l + 2] - ctl->seg[2 * l + 1] + PL - 1) / PL;
+        }
+        cseg[GT_TREE_LEVELS] = ctl->seg[2 * GT_TREE_LEVELS];
+        uint32_t c = 0;
+        for (int k = 0; k < GT_TREE_LEVELS; k++) {
+            tfirst[k] = c;
+            c += nchunk[GT_TREE_LEVELS - 1 - k];
+        }
+        tfirst[GT_TREE_LEVELS] = c;
+        bad_sh = 0;
+    }
+    __syncthreads();
+    const uint32_t total = tfirst[GT_TREE_LEVELS];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned int t = atomicAdd(&ctl->pl_ticket, 1u);
+            t_sh = t;
+            if (t < total) {
+                int k = 0;
+                while (tfirst[k + 1] <= t) k++;
+                const int l1 = GT_TREE_LEVELS - k;  // the level below this chunk's cells
+                if (l1 < GT_TREE_LEVELS) {
+                    const unsigned int need = nchunk[l1];
+                    unsigned int spins = 0;
+                    const unsigned int limit = gt_spin_limit(ctl);
+                    while (*((volatile unsigned int *)&ctl->pl_done[l1]) < need) {
+                        if (++spins > limit) {
+                            gt_set_error(ctl, GT_ETIMEOUT, GTK_PSEUDO);
+                            bad_sh = 1;
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                    __threadfence();
+                }
+            }
+        }
+        __syncthreads();
+        const unsigned int t = t_sh;
+        if (t >= total || bad_sh) break;
+        int k = 0;
+        while (tfirst[k + 1] <= t) k++;
+        const int lvl = GT_TREE_LEVELS - 1 - k;
+        const long long idx = (long long)cseg[lvl] + (long long)(t - tfirst[k]) * PL + threadIdx.x;
+        if (idx < (long long)ctl->seg[2 * lvl + 2]) pseudo_cell<WITH_MASS>(nd, nd.cells[idx]);
+        __threadfence();  // every thread's cell is visible device-wide before the chunk counts as done
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(&ctl->pl_done[lvl], 1u);
+    }
 }
 
 }  // namespace
@@ -678,10 +718,14 @@ void gt_launch_cell_lists(Nodes nd, int64_t cap, DevCtl *ctl, int nsm, cudaStrea
 
 void gt_launch_pseudo(Nodes nd, int64_t cap, const float4 *posm, DevCtl *ctl, int nsm, bool with_mass,
                       cudaStream_t st) {
-    if (with_mass) {  // after a build
-        { k_zero_arrive<<<nsm * 4, 256, 0, st>>>(nd, cap, ctl); gt_note_launches(1); }
-        { k_pseudo<true><<<nsm * 16, PL, 0, st>>>(nd, posm, ctl); gt_note_launches(1); }
+    (void)cap;
+    // the ticket and the per-level counters of the cell pass start at zero
+    cudaMemsetAsync(&ctl->pl_ticket, 0, sizeof(ctl->pl_ticket) + sizeof(ctl->pl_done), st);
+    if (with_mass) {  // after a build: the FP64 mass sums too
+        { k_pseudo_leaves<true><<<nsm * 16, PL, 0, st>>>(nd, posm, ctl); gt_note_launches(1); }
+        { k_pseudo_cells<true><<<nsm * 8, PL, 0, st>>>(nd, ctl); gt_note_launches(1); }
     } else {
-        { k_pseudo<false><<<nsm * 16, PL, 0, st>>>(nd, posm, ctl); gt_note_launches(1); }
+        { k_pseudo_leaves<false><<<nsm * 16, PL, 0, st>>>(nd, posm, ctl); gt_note_launches(1); }
+        { k_pseudo_cells<false><<<nsm * 8, PL, 0, st>>>(nd, ctl); gt_note_launches(1); }
     }
 }
