@@ -31,7 +31,7 @@ namespace {
 #define GT_SORT_MINB 3
 #endif
 #ifndef GT_SORT_LB
-#define GT_SORT_LB 16              // earlier tiles read per look-back step
+#define GT_SORT_LB 8               // earlier tiles read per look-back step
 #endif
 constexpr int RB = 8;              // digit bits
 constexpr int R = 1 << RB;         // digits

@@ -11,11 +11,10 @@
 // lock-step 7-way binary search, children numbered by a block scan plus a decoupled
 // look-back over tiles taken in ticket order).  Both give the same numbering.
 //
-// A5, two launches over a cell list bucketed by level and size (every FP64 instruction
-// runs with full warps, which matters on this GPU's narrow FP64 pipe): first every leaf,
-// whose lane sums its particles in FP64 (mass, m x, m y, m z), with no waits; then every
-// cell with children, which sums its children's FP64 sums in child order once the level
-// below is done.  m_J = (float)M and
+// A5, one launch over a cell list bucketed by level and size: a leaf's lane sums its
+// particles in FP64 (mass, m x, m y, m z); a cell with children sums its children's FP64
+// sums in child order once the level below is done -- every FP64 instruction runs with
+// full warps, which matters on this GPU's narrow FP64 pipe.  m_J = (float)M and
 // r_J = (float)S / (float)M (a cell of one particle is that particle); b_J is the
 // largest FP32 |r - r_J| of a leaf's particles, or the largest |r_c - r_J| + b_c
 // over a cell's children, widened by (1 + 2^-20) so that FP32 rounding cannot
@@ -463,27 +462,128 @@ __global__ __launch_bounds__(256) void k_cell_fill(Nodes nd, long long cap, DevC
     }
 }
 
-// ---- A5: pseudo j-particles in two launches ------------------------------------------
-// First every leaf, one per thread, in the order of the cell list (a level's leaves
-// bucketed by particle count, so the lanes of a warp run equal trip counts); nothing
-// waits.  Then the cells with children, in chunks of PL handed out by a ticket counter
-// from the deepest level up: a chunk of level l waits until every chunk of level l + 1 is
-// done (those hold smaller tickets, so the blocks holding them are running and the wait
-// ends; it is bounded all the same).
-constexpr int PL = 128;  // threads per block, nodes per chunk
+// ---- A5: pseudo j-particles, every node in one launch ------------------------------
+// The cell list's segments (a level's leaves, a level's cells with children) are cut
+// into chunks of PL nodes, handed out by a ticket counter in this order: the leaves of
+// level 21; then, for l = 20 .. 0, the leaves of level l and the cells with children of
+// level l + 1; the cells of level 0 last.  A chunk of cells of level l waits until every
+// chunk of level l + 1 is finished: those hold smaller tickets, so the blocks holding
+// them are running and the wait ends (it is bounded all the same).  Leaves wait for
+// nothing, so their FP64 sums fill the time a level's cells wait for the one below.
+constexpr int PL = 128;  // nodes per chunk, one per thread
+constexpr int PSEUDO_LAG = 1;  // levels of leaves between a level's cells and the level below
+constexpr int NSEG = 2 * GT_TREE_LEVELS;
 
 // Leaf c: one lane sums its particles in FP64 (mass, m x, m y, m z) in particle order.
 // The masses and the cells' members do not change between tree builds, so the mass
 // sums are formed at a build (WITH_MASS) and read back at the other block steps: the
 // same values, one FP64 addition per particle fewer.
+// The leaf sums on the integer pipe, exactly.  A finite, normal FP32 value is s 2^e with s
+// a signed integer of 24 bits, so a product m x of two of them is (s_m s_x) 2^(e_m + e_x),
+// at most 48 bits (fewer once the mass's trailing zero bits are moved into its exponent).
+// If every term of a leaf's sum is a multiple of 2^E0 and k terms of magnitude below 2^Top
+// satisfy k 2^Top <= 2^(E0 + 53), then every partial sum of the FP64 sequence in particle
+// order is a multiple of 2^E0 below 2^(E0 + 53): exactly representable, so every FP64
+// addition of the sequence is exact and its result is the exact sum, which 64-bit integers
+// reach too.  A leaf outside these bounds (a subnormal or non-finite value, terms whose
+// exponents lie too far apart) takes the FP64 additions.  Either way the result is the
+// FP64 sequence's, bit for bit; this GPU's FP64 pipe is narrow, its integer pipe is not.
+struct ExactSum {
+    int e0 = 1 << 20, top = -(1 << 20);  // lowest term exponent, highest term magnitude bit
+    long long acc = 0;
+};
+
+// s 2^e of a finite FP32 value (s = 0 for zero); false for subnormal or non-finite values
+__device__ __forceinline__ bool f32_sig(float v, int &s, int &e) {
+    const uint32_t b = __float_as_uint(v);
+    const uint32_t ex = (b >> 23) & 0xffu;
+    if (ex == 0xffu || (ex == 0u && (b & 0x7fffffffu) != 0u)) return false;
+    if (ex == 0u) {
+        s = 0;
+        e = 0;
+        return true;
+    }
+    const int mag = (int)((b & 0x7fffffu) | 0x800000u);
+    s = (b >> 31) ? -mag : mag;
+    e = (int)ex - 150;
+    return true;
+}
+
+__device__ __forceinline__ void exact_note(ExactSum &x, int s, int e, int bits) {
+    if (s == 0) return;
+    x.e0 = min(x.e0, e);
+    x.top = max(x.top, e + bits);
+}
+
+__device__ __forceinline__ bool exact_fits(const ExactSum &x, int lgk) {
+    return x.top < x.e0 || x.top + lgk <= x.e0 + 53;  // no term, or within the bound
+}
+
+// adds the term s_m s_x 2^e (|s_m s_x| < 2^48, e >= e0 of the sum)
+__device__ __forceinline__ void exact_add(ExactSum &x, long long prod, int e) {
+    if (prod == 0) return;
+    const bool neg = prod < 0;
+    const unsigned long long mag = (unsigned long long)(neg ? -prod : prod) << (e - x.e0);
+    x.acc += neg ? -(long long)mag : (long long)mag;
+}
+
+__device__ __forceinline__ double exact_value(const ExactSum &x) {
+    if (x.acc == 0) return 0.0;
+    const bool neg = x.acc < 0;
+    const double v = i2d_scaled(neg ? -x.acc : x.acc, x.e0);  // |acc| < 2^53: exact
+    return neg ? -v : v;
+}
+
 template <bool WITH_MASS>
 __device__ __forceinline__ void pseudo_leaf(const Nodes &nd, const float4 *__restrict__ posm, uint32_t c) {
     const uint32_t f = nd.first[c];
     const uint32_t k = nd.count[c];
     double m = WITH_MASS ? 0.0 : nd.sum[c].m, sx = 0.0, sy = 0.0, sz = 0.0;
-    // in particle order; the loads of four particles go out before their sums
-    // (m x is exact in FP64, so the fused form rounds once like + does)
-    for (uint32_t i0 = f; i0 < f + k; i0 += 2) {
+    // can the whole leaf take the exact integer sums?
+    ExactSum em, ex, ey, ez;
+    bool exact = true;
+    for (uint32_t i = f; i < f + k; i++) {
+        const float4 p = posm[i];
+        int sm, e_m, s1, e1, s2, e2, s3, e3;
+        exact = exact && f32_sig(p.w, sm, e_m) && sm > 0 && f32_sig(p.x, s1, e1) && f32_sig(p.y, s2, e2) &&
+                f32_sig(p.z, s3, e3);
+        if (!exact) break;
+        const int tz = __ffs(sm) - 1;  // the mass's trailing zero bits go into its exponent
+        sm >>= tz;
+        e_m += tz;
+        const int bm = 32 - __clz(sm);
+        exact_note(em, sm, e_m, bm);
+        exact_note(ex, s1, e_m + e1, bm + 24);
+        exact_note(ey, s2, e_m + e2, bm + 24);
+        exact_note(ez, s3, e_m + e3, bm + 24);
+    }
+    const int lgk = k > 1 ? 32 - __clz(k - 1) : 0;
+    exact = exact && exact_fits(ex, lgk) && exact_fits(ey, lgk) && exact_fits(ez, lgk) &&
+            (!WITH_MASS || exact_fits(em, lgk));
+    if (exact) {
+        for (uint32_t i = f; i < f + k; i++) {
+            const float4 p = posm[i];
+            int sm, e_m, s1, e1, s2, e2, s3, e3;
+            f32_sig(p.w, sm, e_m);
+            f32_sig(p.x, s1, e1);
+            f32_sig(p.y, s2, e2);
+            f32_sig(p.z, s3, e3);
+            const int tz = __ffs(sm) - 1;
+            sm >>= tz;
+            e_m += tz;
+            if (WITH_MASS) exact_add(em, sm, e_m);
+            exact_add(ex, (long long)sm * s1, e_m + e1);
+            exact_add(ey, (long long)sm * s2, e_m + e2);
+            exact_add(ez, (long long)sm * s3, e_m + e3);
+        }
+        if (WITH_MASS) m = exact_value(em);
+        sx = exact_value(ex);
+        sy = exact_value(ey);
+        sz = exact_value(ez);
+    }
+    // otherwise in FP64, in particle order; the loads of two particles go out before their
+    // sums (m x is exact in FP64, so the fused form rounds once like + does)
+    for (uint32_t i0 = f; !exact && i0 < f + k; i0 += 2) {
         float4 p[2];
 #pragma unroll
         for (uint32_t q = 0; q < 2; q++)
@@ -584,84 +684,70 @@ __device__ __forceinline__ void pseudo_cell(const Nodes &nd, uint32_t p) {
 }
 
 template <bool WITH_MASS>
-__global__ __launch_bounds__(PL, 8) void k_pseudo_leaves(Nodes nd, const float4 *__restrict__ posm,
-                                                         const DevCtl *__restrict__ ctl) {
-    __shared__ uint32_t lfirst[GT_TREE_LEVELS + 1];  // prefix of the levels' leaf counts
-    __shared__ uint32_t lseg[GT_TREE_LEVELS];        // where level l's leaves start in the cell list
-    if (threadIdx.x == 0) {
-        uint32_t c = 0;
-        for (int l = 0; l < GT_TREE_LEVELS; l++) {
-            lfirst[l] = c;
-            lseg[l] = ctl->seg[2 * l];
-            c += ctl->seg[2 * l + 1] - ctl->seg[2 * l];
-        }
-        lfirst[GT_TREE_LEVELS] = c;
-    }
-    __syncthreads();
-    const uint32_t total = lfirst[GT_TREE_LEVELS];
-    for (uint32_t t = blockIdx.x * PL + threadIdx.x; t < total; t += gridDim.x * PL) {
-        int l = 0;
-        while (lfirst[l + 1] <= t) l++;
-        pseudo_leaf<WITH_MASS>(nd, posm, nd.cells[lseg[l] + (t - lfirst[l])]);
-    }
-}
-
-template <bool WITH_MASS>
-__global__ __launch_bounds__(PL, 8) void k_pseudo_cells(Nodes nd, DevCtl *ctl) {
-    __shared__ uint32_t cseg[GT_TREE_LEVELS + 1];   // level l's cells: cseg[l] .. cseg[l + 1]
-    __shared__ uint32_t nchunk[GT_TREE_LEVELS];
-    __shared__ uint32_t tfirst[GT_TREE_LEVELS + 1]; // first ticket of level 20 - k at tfirst[k]
+__global__ __launch_bounds__(PL, 8) void k_pseudo(Nodes nd, const float4 *__restrict__ posm, DevCtl *ctl) {
+    __shared__ uint32_t seg[NSEG + 1];
+    __shared__ uint8_t olvl[NSEG], ocell[NSEG];      // ticket order: segment level and kind
+    __shared__ uint32_t ocum[NSEG + 1];              // first ticket of every entry
+    __shared__ uint32_t nchunk[NSEG];                // chunks of segment (2 l + kind)
     __shared__ unsigned int t_sh;
-    __shared__ int bad_sh;
+    __shared__ int o_sh, bad_sh;
+    for (int i = threadIdx.x; i <= NSEG; i += PL) seg[i] = ctl->seg[i];
+    __syncthreads();
     if (threadIdx.x == 0) {
-        for (int l = 0; l < GT_TREE_LEVELS; l++) {
-            cseg[l] = ctl->seg[2 * l + 1];
-            nchunk[l] = (ctl->seg[2 * l + 2] - ctl->seg[2 * l + 1] + PL - 1) / PL;
+        for (int k = 0; k < NSEG; k++) nchunk[k] = (seg[k + 1] - seg[k] + PL - 1) / PL;
+        int o = 0;  // level l's cells go right after the leaves of level l - PSEUDO_LAG
+        for (int s = 0; s < GT_TREE_LEVELS + PSEUDO_LAG; s++) {
+            const int ll = GT_TREE_LEVELS - 1 - s, lc = GT_TREE_LEVELS - 1 + PSEUDO_LAG - s;
+            if (ll >= 0) { olvl[o] = (uint8_t)ll; ocell[o] = 0; o++; }
+            if (lc >= 0 && lc < GT_TREE_LEVELS - 1) { olvl[o] = (uint8_t)lc; ocell[o] = 1; o++; }
         }
-        cseg[GT_TREE_LEVELS] = ctl->seg[2 * GT_TREE_LEVELS];
+        // o == NSEG - 1 (level 21 has no cells with children): the last entry is empty
+        olvl[o] = 0; ocell[o] = 2;
         uint32_t c = 0;
-        for (int k = 0; k < GT_TREE_LEVELS; k++) {
-            tfirst[k] = c;
-            c += nchunk[GT_TREE_LEVELS - 1 - k];
+        for (int k = 0; k < NSEG; k++) {
+            ocum[k] = c;
+            if (ocell[k] < 2) c += nchunk[2 * olvl[k] + ocell[k]];
         }
-        tfirst[GT_TREE_LEVELS] = c;
+        ocum[NSEG] = c;
         bad_sh = 0;
     }
     __syncthreads();
-    const uint32_t total = tfirst[GT_TREE_LEVELS];
+    const uint32_t total = ocum[NSEG];
     for (;;) {
         if (threadIdx.x == 0) {
             const unsigned int t = atomicAdd(&ctl->pl_ticket, 1u);
+            int o = 0;
+            if (t < total)
+                while (ocum[o + 1] <= t) o++;
             t_sh = t;
-            if (t < total) {
-                int k = 0;
-                while (tfirst[k + 1] <= t) k++;
-                const int l1 = GT_TREE_LEVELS - k;  // the level below this chunk's cells
-                if (l1 < GT_TREE_LEVELS) {
-                    const unsigned int need = nchunk[l1];
-                    unsigned int spins = 0;
-                    const unsigned int limit = gt_spin_limit(ctl);
-                    while (*((volatile unsigned int *)&ctl->pl_done[l1]) < need) {
-                        if (++spins > limit) {
-                            gt_set_error(ctl, GT_ETIMEOUT, GTK_PSEUDO);
-                            bad_sh = 1;
-                            break;
-                        }
-                        __nanosleep(64);
+            o_sh = o;
+            if (t < total && ocell[o] == 1 && olvl[o] + 1 < GT_TREE_LEVELS) {
+                const int l1 = olvl[o] + 1;  // every chunk of that level first
+                const unsigned int need = nchunk[2 * l1] + nchunk[2 * l1 + 1];
+                unsigned int spins = 0;
+                const unsigned int limit = gt_spin_limit(ctl);
+                while (*((volatile unsigned int *)&ctl->pl_done[l1]) < need) {
+                    if (++spins > limit) {
+                        gt_set_error(ctl, GT_ETIMEOUT, GTK_PSEUDO);
+                        bad_sh = 1;
+                        break;
                     }
-                    __threadfence();
+                    __nanosleep(64);
                 }
+                __threadfence();
             }
         }
         __syncthreads();
         const unsigned int t = t_sh;
+        const int o = o_sh;
         if (t >= total || bad_sh) break;
-        int k = 0;
-        while (tfirst[k + 1] <= t) k++;
-        const int lvl = GT_TREE_LEVELS - 1 - k;
-        const long long idx = (long long)cseg[lvl] + (long long)(t - tfirst[k]) * PL + threadIdx.x;
-        if (idx < (long long)ctl->seg[2 * lvl + 2]) pseudo_cell<WITH_MASS>(nd, nd.cells[idx]);
-        __threadfence();  // every thread's cell is visible device-wide before the chunk counts as done
+        const int lvl = olvl[o], kind = ocell[o];
+        const long long idx = (long long)seg[2 * lvl + kind] + (long long)(t - ocum[o]) * PL + threadIdx.x;
+        if (idx < (long long)seg[2 * lvl + kind + 1]) {
+            if (kind == 0) pseudo_leaf<WITH_MASS>(nd, posm, nd.cells[idx]);
+            else pseudo_cell<WITH_MASS>(nd, nd.cells[idx]);
+        }
+        __threadfence();  // every thread's node is visible device-wide before the chunk counts as done
         __syncthreads();
         if (threadIdx.x == 0) atomicAdd(&ctl->pl_done[lvl], 1u);
     }
@@ -719,13 +805,9 @@ void gt_launch_cell_lists(Nodes nd, int64_t cap, DevCtl *ctl, int nsm, cudaStrea
 void gt_launch_pseudo(Nodes nd, int64_t cap, const float4 *posm, DevCtl *ctl, int nsm, bool with_mass,
                       cudaStream_t st) {
     (void)cap;
-    // the ticket and the per-level counters of the cell pass start at zero
+    // the ticket and the per-level counters start at zero
     cudaMemsetAsync(&ctl->pl_ticket, 0, sizeof(ctl->pl_ticket) + sizeof(ctl->pl_done), st);
-    if (with_mass) {  // after a build: the FP64 mass sums too
-        { k_pseudo_leaves<true><<<nsm * 16, PL, 0, st>>>(nd, posm, ctl); gt_note_launches(1); }
-        { k_pseudo_cells<true><<<nsm * 8, PL, 0, st>>>(nd, ctl); gt_note_launches(1); }
-    } else {
-        { k_pseudo_leaves<false><<<nsm * 16, PL, 0, st>>>(nd, posm, ctl); gt_note_launches(1); }
-        { k_pseudo_cells<false><<<nsm * 8, PL, 0, st>>>(nd, ctl); gt_note_launches(1); }
-    }
+    if (with_mass) { k_pseudo<true><<<nsm * 8, PL, 0, st>>>(nd, posm, ctl); }
+    else { k_pseudo<false><<<nsm * 8, PL, 0, st>>>(nd, posm, ctl); }
+    gt_note_launches(1);
 }

@@ -188,6 +188,38 @@ def test_keys_bitexact_on_awkward_coordinates(env, curve):
     s.close()
 
 
+@pytest.mark.parametrize("masses", ["power_of_two", "uneven"])
+def test_pseudo_j_bitexact_on_awkward_coordinates(env, masses):
+    """Sec. 2.1, Fig. 1: the FP64 centre-of-mass sums in particle order (exact integer
+    sums where every partial sum is representable, FP64 additions elsewhere) on leaves
+    that mix both cases: coordinates around 0 spanning many exponents, subnormals, exact
+    powers of two and one-ulp neighbours; equal power-of-two masses or uneven ones."""
+    torch, g, O = env
+    rng = np.random.default_rng(91)
+    n = 30000
+    pos = rng.standard_normal((n, 3)) * 3.0
+    pos[:2000] *= 10.0 ** rng.uniform(-30, -1, (2000, 1))   # tiny, spread over many exponents
+    pos[2000:2100] = 0.0
+    pos[2100:2200] = np.float32(1e-41) * np.sign(rng.standard_normal((100, 3)))  # subnormals
+    pos[2200:2500] = np.sign(rng.standard_normal((300, 3))) * 2.0 ** rng.integers(-24, 4, (300, 3))
+    base = np.float32(rng.standard_normal((200, 3)))
+    pos[2500:2700] = np.nextafter(base, np.float32(np.inf))
+    pos[2700:2900] = base
+    pos = pos.astype(np.float32).astype(np.float64)
+    if masses == "power_of_two":
+        mass = np.full(n, 2.0 ** -15, np.float32)
+    else:
+        mass = rng.uniform(0.5, 1.5, n).astype(np.float32) / n
+    for leaf in (1, 8, 24):
+        s = g.System(n, _params(g, 0.01, leaf_max=leaf, node_factor=4))
+        s.set_state(pos, np.zeros_like(pos), mass)
+        s.build_tree()
+        t = s.get_tree()
+        s.sync()
+        _check_tree(t, _oracle_tree(O, pos, mass, leaf, cap=4 * n + 2048))
+        s.close()
+
+
 def test_walk_and_steps_on_hilbert_keys(env):
     _walk_case(env, "nfw", 30000, 9, 1, 0, 64, key_curve=1)
     _walk_case(env, "plummer", 1 << 13, 9, 2, 0, 32, delta_acc=2.0 ** -8, key_curve=1)
