@@ -488,6 +488,9 @@ constexpr int NSEG = 2 * GT_TREE_LEVELS;
 // reach too.  A leaf outside these bounds (a subnormal or non-finite value, terms whose
 // exponents lie too far apart) takes the FP64 additions.  Either way the result is the
 // FP64 sequence's, bit for bit; this GPU's FP64 pipe is narrow, its integer pipe is not.
+#ifndef GT_PSEUDO_EXACT
+#define GT_PSEUDO_EXACT 1
+#endif
 struct ExactSum {
     int e0 = 1 << 20, top = -(1 << 20);  // lowest term exponent, highest term magnitude bit
     long long acc = 0;
@@ -541,7 +544,7 @@ __device__ __forceinline__ void pseudo_leaf(const Nodes &nd, const float4 *__res
     double m = WITH_MASS ? 0.0 : nd.sum[c].m, sx = 0.0, sy = 0.0, sz = 0.0;
     // can the whole leaf take the exact integer sums?
     ExactSum em, ex, ey, ez;
-    bool exact = true;
+    bool exact = GT_PSEUDO_EXACT != 0;
     for (uint32_t i = f; i < f + k; i++) {
         const float4 p = posm[i];
         int sm, e_m, s1, e1, s2, e2, s3, e3;
