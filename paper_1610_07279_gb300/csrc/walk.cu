@@ -337,14 +337,16 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
                 __syncwarp();
                 // member mm's units [mm nq, (mm + 1) nq) lie in lanes lane(u0) .. lane(u1 - 1),
                 // lane(u) = ceil(32 (u + 1) / U) - 1 (the last lane whose range starts at or
-                // before u)
+                // before u); with fewer than 32 units some lanes in between have none, and
+                // hold no partial sums of this flush
                 auto gather = [&](uint32_t mm, float &gx, float &gy, float &gz, float &gp) {
                     const uint32_t u0 = mm * nq, u1 = u0 + nq;
                     const uint32_t la = (32u * (u0 + 1u) + U - 1u) / U - 1u;
                     const uint32_t lb = (32u * u1 + U - 1u) / U - 1u;
                     for (uint32_t l = la; l <= lb; l++) {
-                        const uint32_t m0 = (uint32_t)(((unsigned long long)l * U) >> 5) / nq;
-                        const float4 t = part[3 * l + (mm - m0)];
+                        const uint32_t lw0 = (uint32_t)(((unsigned long long)l * U) >> 5);
+                        if (lw0 == (uint32_t)(((unsigned long long)(l + 1) * U) >> 5)) continue;  // no units
+                        const float4 t = part[3 * l + (mm - lw0 / nq)];
                         gx = __fadd_rn(gx, t.x);
                         gy = __fadd_rn(gy, t.y);
                         gz = __fadd_rn(gz, t.z);

@@ -25,6 +25,22 @@ def assign_systems(nbytes, world: int) -> list[list[int]]:
     return [sorted(v) for v in out]
 
 
+def shard_requests(work, world: int) -> list[list[int]]:
+    """Requests of a serving stream to ranks, in arrival order, each onto the rank with
+    the least work assigned so far (work[k]: an estimate such as particles x steps);
+    returns, per rank, its request indices in arrival order.  Every rank computes the
+    same plan from the same stream, so no exchange is needed to agree on it."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    load = [0.0] * world
+    out = [[] for _ in range(world)]
+    for k, w in enumerate(work):
+        r = min(range(world), key=lambda q: (load[q], q))
+        out[r].append(k)
+        load[r] += float(w)
+    return out
+
+
 def group_slice(n_groups: int, rank: int, world: int) -> tuple[int, int]:
     """Contiguous groups [g0, g1) of one rank: the first n_groups % world ranks take
     one group more."""
