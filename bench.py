@@ -301,6 +301,51 @@ def run_shared_comparison(g, torch, pos, vel, mass, eps, block_cycle_ms, block_i
             "interactions_per_cycle": {"shared": inter * ticks, "block": block_inter}}
 
 
+# ------------------------------------------------------------------ ranks
+class Comm:
+    """Max, sum and gather over the ranks of the job (identity on one rank)."""
+
+    def __init__(self, rank: int = 0, world: int = 1):
+        self.rank, self.world = rank, world
+
+    def _reduce(self, x, op):
+        if self.world == 1:
+            return x
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(x)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        import torch.distributed as dist
+        return self._reduce(x, dist.ReduceOp.MAX if self.world > 1 else None)
+
+    def sum(self, x):
+        import torch.distributed as dist
+        return self._reduce(x, dist.ReduceOp.SUM if self.world > 1 else None)
+
+    def gather(self, obj) -> list:
+        if self.world == 1:
+            return [obj]
+        import torch.distributed as dist
+        out = [None] * self.world
+        dist.all_gather_object(out, obj)
+        return out
+
+
+def batch_shard(ns, rank: int, world: int) -> list[int]:
+    """This rank's systems of a batch: whole systems, balanced by particle count."""
+    from paper_1610_07279_gb300 import partition
+    return partition.assign_systems(ns, world)[rank]
+
+
+def serving_shard(reqs, rank: int, world: int) -> list[int]:
+    """This rank's requests of a serving stream: balanced by particles x block steps."""
+    from paper_1610_07279_gb300 import partition
+    return partition.shard_requests([r["n"] * max(r["steps"], 1) for r in reqs], world)[rank]
+
+
 # ------------------------------------------------------------------ batch workload
 def direct_fp64(pos, mass, eps, G, targets):
     """Eq. (1) in FP64 for the target rows (plain numpy, chunked): the accuracy yardstick
@@ -318,13 +363,17 @@ def direct_fp64(pos, mass, eps, G, targets):
     return out
 
 
-def run_batch(g, torch, steps: int):
+def run_batch(g, torch, steps: int, comm: Comm | None = None):
     """64 independent systems (Plummer or NFW, N log-uniform in [2^12, 2^18]): one force
     evaluation of all of them per step, as a captured graph of forked builds and one
     walk launch, knobs from the autotuner; against the same members through the
-    single-system calls one after another."""
+    single-system calls one after another.  On several GPUs the 64 systems are shared
+    out whole (balanced by size, no exchange) and the job's time is the slowest rank's."""
     from paper_1610_07279_gb300 import ics
-    mem = ics.batch_systems(64, seed=4)
+    comm = comm or Comm()
+    allmem = ics.batch_systems(64, seed=4)
+    mine = batch_shard([m["n"] for m in allmem], comm.rank, comm.world)
+    mem = [allmem[k] for k in mine]
     prms = []
     for m in mem:
         p = g.gt_default_params()
@@ -381,10 +430,14 @@ def run_batch(g, torch, steps: int):
         per.append({"kind": m["kind"], "n": m["n"], "median": float(np.median(rel)),
                     "p99": float(np.percentile(rel, 99))})
     b.close()
+    ms, ms_serial = comm.max(ms), comm.max(ms_serial)
+    inter, inter_serial = comm.sum(inter), comm.sum(inter_serial)
+    per = [q for part in comm.gather(per) for q in part]
     return {"workload": "64 systems, Plummer or NFW by seeded coin, N = round(2^(12 + 6u)), own eps; "
                         "one force evaluation of every system per step (tree build + every particle "
                         "active, acceleration MAC with a_old from an opening-angle start-up pass)",
-            "total_particles": int(sum(m["n"] for m in mem)),
+            "total_particles": int(sum(m["n"] for m in allmem)), "ranks": comm.world,
+            "scaling": "strong (the 64 systems shared out whole across the ranks)",
             "autotuned": {"leaf_max": tune["leaf_max"], "group_max": tune["group_max"],
                           "walk_queue": tune["walk_queue"], "candidates_ms": tune["ms"]},
             "batched": {"ms_per_step": ms, "interactions_per_s": inter / (ms * 1e-3),
@@ -427,8 +480,11 @@ def serve_params(g, eps):
     return p
 
 
-def run_serving(g, torch, nreq: int, rhos):
+def run_serving(g, torch, nreq: int, rhos, comm: Comm | None = None):
+    """The serving stream; on several GPUs every rank serves its shard of a stream of
+    nreq requests per GPU at the per-GPU load (weak scaling), and latencies are pooled."""
     from paper_1610_07279_gb300 import ics
+    comm = comm or Comm()
     src = RequestSource()
     # serial capacity: requests alone through the single-system path, one after another
     probe = ics.serving_requests(48, seed=55, rate=1.0)
@@ -445,10 +501,13 @@ def run_serving(g, torch, nreq: int, rhos):
         s.close()
         t_serial.append(time.perf_counter() - t0)
     cap = 1.0 / float(np.mean(t_serial[4:]))  # requests/s, first few are warm-up
+    cap = comm.sum(cap) / comm.world            # the ranks' mean serial capacity
     runs = []
     for rho in rhos:
         burst = rho == "burst"
-        reqs = ics.serving_requests(nreq, seed=5, rate=cap if burst else float(rho) * cap)
+        whole = ics.serving_requests(nreq * comm.world, seed=5,
+                                     rate=(cap if burst else float(rho) * cap) * comm.world)
+        reqs = [whole[k] for k in serving_shard(whole, comm.rank, comm.world)]
         if burst:
             for r in reqs:
                 r["arrival"] = 0.0
@@ -478,25 +537,30 @@ def run_serving(g, torch, nreq: int, rhos):
                     del tickets[t]
             if not tickets and pending == [] and nxt < len(reqs):
                 time.sleep(max(0.0, min(0.002, reqs[nxt]["arrival"] - (time.perf_counter() - t_start))))
-        span = time.perf_counter() - t_start
+        span = comm.max(time.perf_counter() - t_start)
         st = srv.stats()
         srv.close()
-        runs.append({"rho": rho, "arrival_rate_per_s": None if burst else float(rho) * cap, "requests": len(reqs),
+        lat_arr = [x for part in comm.gather(lat_arr) for x in part]
+        lat_sub = [x for part in comm.gather(lat_sub) for x in part]
+        nall = len(lat_arr)
+        runs.append({"rho": rho, "arrival_rate_per_s": None if burst else float(rho) * cap * comm.world,
+                     "requests": nall,
                      "p50_latency_s": float(np.percentile(lat_arr, 50)),
                      "p99_latency_s": float(np.percentile(lat_arr, 99)),
                      "p50_submit_to_done_s": float(np.percentile(lat_sub, 50)),
                      "p99_submit_to_done_s": float(np.percentile(lat_sub, 99)),
-                     "throughput_req_per_s": len(reqs) / span, "makespan_s": span,
-                     "ticks": st["ticks"], "batched_walk_launches": st["walk_launches"]})
+                     "throughput_req_per_s": nall / span, "makespan_s": span,
+                     "ticks": int(comm.sum(st["ticks"])), "batched_walk_launches": int(comm.sum(st["walk_launches"]))})
     return {"workload": f"Poisson arrivals of Plummer/NFW systems, N log-uniform in [2^12, 2^20], 4-32 block "
                         f"steps each (8 levels, acceleration MAC, rebuild every 4 steps), {nreq} requests per "
-                        f"load level, HBM admission cap 150 GB, up to 128 resident",
+                        f"load level and GPU, HBM admission cap 150 GB per GPU, up to 128 resident per GPU",
+            "ranks": comm.world, "scaling": "weak (each GPU serves its shard of a stream of nreq x ranks)",
             "serial_capacity_req_per_s": cap,
             "serial_path": "gt_system_create + gt_set_state + gt_start + block steps + gt_get_state, one "
                            "request at a time (48 sampled requests)",
             "latency": "from arrival (queueing included); submit-to-done also given",
             "runs": runs,
-            "max_throughput_vs_serial": max(r["throughput_req_per_s"] for r in runs) / cap}
+            "max_throughput_vs_serial": max(r["throughput_req_per_s"] for r in runs) / (cap * comm.world)}
 
 
 # ------------------------------------------------------------------ NFW 2^20, 16 block steps
@@ -849,9 +913,9 @@ def run_ours(args):
                   "sweeps_plummer_2p13": accuracy_sweeps(g, torch)}
     batch = serving = None
     if not args.no_batch:
-        batch = run_batch(g, torch, args.steps)
+        batch = run_batch(g, torch, args.steps, Comm(rank, world))
     if not args.no_serve:
-        serving = run_serving(g, torch, args.serve_requests,
+        serving = run_serving(g, torch, args.serve_requests, comm=Comm(rank, world), rhos=
                               [x if x == "burst" else float(x) for x in args.serve_rho.split(",")])
 
     if rank == 0:

@@ -6,7 +6,7 @@
 //   k_digit_bases  exclusive scans of the histograms -> where every digit starts
 //   k_onesweep     per 4096-key tile (512 threads) taken in ticket order: a stable rank of
 //                  every key inside the tile (warp-striped; a key's peers with the same
-//                  digit from one warp match, its rank by popc), the tile's per-digit counts
+//                  digit from nine ballots, its rank by popc), the tile's per-digit counts
 //                  published and each digit's exclusive prefix over earlier tiles found
 //                  by a decoupled look-back (256 digits in parallel, a window of
 //                  GT_SORT_LB earlier tiles per step, every wait bounded), a local sort in
@@ -29,9 +29,6 @@ namespace {
 #endif
 #ifndef GT_SORT_MINB
 #define GT_SORT_MINB 3
-#endif
-#ifndef GT_SORT_MATCH
-#define GT_SORT_MATCH 1            // a key's peers by one match instruction (else nine ballots)
 #endif
 #ifndef GT_SORT_LB
 #define GT_SORT_LB 8               // earlier tiles read per look-back step
@@ -175,17 +172,12 @@ __global__ __launch_bounds__(ST, GT_SORT_MINB) void k_onesweep(long long n, int 
     for (int j = 0; j < IPT; j++) {
         const bool ok = base + j * 32 + lane < n;
         const unsigned int d = ok ? (unsigned int)((k[j] >> shift) & (R - 1)) : (unsigned int)R;
-        // lanes with the same digit (R: past the end)
-#if GT_SORT_MATCH
-        const unsigned int peers = __match_any_sync(0xffffffffu, d);
-#else
-        unsigned int peers = 0xffffffffu;
+        unsigned int peers = 0xffffffffu;  // lanes with the same digit (bit 8: past the end)
 #pragma unroll
         for (int b = 0; b <= RB; b++) {
             const unsigned int bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
             peers &= ((d >> b) & 1u) ? bal : ~bal;
         }
-#endif
         const unsigned int rank = __popc(peers & lt);
         unsigned int prev = 0;
         if (ok) prev = wcnt[w * R + d];

@@ -478,115 +478,14 @@ constexpr int NSEG = 2 * GT_TREE_LEVELS;
 // The masses and the cells' members do not change between tree builds, so the mass
 // sums are formed at a build (WITH_MASS) and read back at the other block steps: the
 // same values, one FP64 addition per particle fewer.
-// The leaf sums on the integer pipe, exactly.  A finite, normal FP32 value is s 2^e with s
-// a signed integer of 24 bits, so a product m x of two of them is (s_m s_x) 2^(e_m + e_x),
-// at most 48 bits (fewer once the mass's trailing zero bits are moved into its exponent).
-// If every term of a leaf's sum is a multiple of 2^E0 and k terms of magnitude below 2^Top
-// satisfy k 2^Top <= 2^(E0 + 53), then every partial sum of the FP64 sequence in particle
-// order is a multiple of 2^E0 below 2^(E0 + 53): exactly representable, so every FP64
-// addition of the sequence is exact and its result is the exact sum, which 64-bit integers
-// reach too.  A leaf outside these bounds (a subnormal or non-finite value, terms whose
-// exponents lie too far apart) takes the FP64 additions.  Either way the result is the
-// FP64 sequence's, bit for bit; this GPU's FP64 pipe is narrow, its integer pipe is not.
-#ifndef GT_PSEUDO_EXACT
-#define GT_PSEUDO_EXACT 1
-#endif
-struct ExactSum {
-    int e0 = 1 << 20, top = -(1 << 20);  // lowest term exponent, highest term magnitude bit
-    long long acc = 0;
-};
-
-// s 2^e of a finite FP32 value (s = 0 for zero); false for subnormal or non-finite values
-__device__ __forceinline__ bool f32_sig(float v, int &s, int &e) {
-    const uint32_t b = __float_as_uint(v);
-    const uint32_t ex = (b >> 23) & 0xffu;
-    if (ex == 0xffu || (ex == 0u && (b & 0x7fffffffu) != 0u)) return false;
-    if (ex == 0u) {
-        s = 0;
-        e = 0;
-        return true;
-    }
-    const int mag = (int)((b & 0x7fffffu) | 0x800000u);
-    s = (b >> 31) ? -mag : mag;
-    e = (int)ex - 150;
-    return true;
-}
-
-__device__ __forceinline__ void exact_note(ExactSum &x, int s, int e, int bits) {
-    if (s == 0) return;
-    x.e0 = min(x.e0, e);
-    x.top = max(x.top, e + bits);
-}
-
-__device__ __forceinline__ bool exact_fits(const ExactSum &x, int lgk) {
-    return x.top < x.e0 || x.top + lgk <= x.e0 + 53;  // no term, or within the bound
-}
-
-// adds the term s_m s_x 2^e (|s_m s_x| < 2^48, e >= e0 of the sum)
-__device__ __forceinline__ void exact_add(ExactSum &x, long long prod, int e) {
-    if (prod == 0) return;
-    const bool neg = prod < 0;
-    const unsigned long long mag = (unsigned long long)(neg ? -prod : prod) << (e - x.e0);
-    x.acc += neg ? -(long long)mag : (long long)mag;
-}
-
-__device__ __forceinline__ double exact_value(const ExactSum &x) {
-    if (x.acc == 0) return 0.0;
-    const bool neg = x.acc < 0;
-    const double v = i2d_scaled(neg ? -x.acc : x.acc, x.e0);  // |acc| < 2^53: exact
-    return neg ? -v : v;
-}
-
 template <bool WITH_MASS>
 __device__ __forceinline__ void pseudo_leaf(const Nodes &nd, const float4 *__restrict__ posm, uint32_t c) {
     const uint32_t f = nd.first[c];
     const uint32_t k = nd.count[c];
     double m = WITH_MASS ? 0.0 : nd.sum[c].m, sx = 0.0, sy = 0.0, sz = 0.0;
-    // can the whole leaf take the exact integer sums?
-    ExactSum em, ex, ey, ez;
-    bool exact = GT_PSEUDO_EXACT != 0;
-    for (uint32_t i = f; i < f + k; i++) {
-        const float4 p = posm[i];
-        int sm, e_m, s1, e1, s2, e2, s3, e3;
-        exact = exact && f32_sig(p.w, sm, e_m) && sm > 0 && f32_sig(p.x, s1, e1) && f32_sig(p.y, s2, e2) &&
-                f32_sig(p.z, s3, e3);
-        if (!exact) break;
-        const int tz = __ffs(sm) - 1;  // the mass's trailing zero bits go into its exponent
-        sm >>= tz;
-        e_m += tz;
-        const int bm = 32 - __clz(sm);
-        exact_note(em, sm, e_m, bm);
-        exact_note(ex, s1, e_m + e1, bm + 24);
-        exact_note(ey, s2, e_m + e2, bm + 24);
-        exact_note(ez, s3, e_m + e3, bm + 24);
-    }
-    const int lgk = k > 1 ? 32 - __clz(k - 1) : 0;
-    exact = exact && exact_fits(ex, lgk) && exact_fits(ey, lgk) && exact_fits(ez, lgk) &&
-            (!WITH_MASS || exact_fits(em, lgk));
-    if (exact) {
-        for (uint32_t i = f; i < f + k; i++) {
-            const float4 p = posm[i];
-            int sm, e_m, s1, e1, s2, e2, s3, e3;
-            f32_sig(p.w, sm, e_m);
-            f32_sig(p.x, s1, e1);
-            f32_sig(p.y, s2, e2);
-            f32_sig(p.z, s3, e3);
-            const int tz = __ffs(sm) - 1;
-            sm >>= tz;
-            e_m += tz;
-            if (WITH_MASS) exact_add(em, sm, e_m);
-            exact_add(ex, (long long)sm * s1, e_m + e1);
-            exact_add(ey, (long long)sm * s2, e_m + e2);
-            exact_add(ez, (long long)sm * s3, e_m + e3);
-        }
-        if (WITH_MASS) m = exact_value(em);
-        sx = exact_value(ex);
-        sy = exact_value(ey);
-        sz = exact_value(ez);
-    }
-    // otherwise in FP64, in particle order; the loads of two particles go out before their
-    // sums (m x is exact in FP64, so the fused form rounds once like + does)
-    for (uint32_t i0 = f; !exact && i0 < f + k; i0 += 2) {
+    // in particle order; the loads of four particles go out before their sums
+    // (m x is exact in FP64, so the fused form rounds once like + does)
+    for (uint32_t i0 = f; i0 < f + k; i0 += 2) {
         float4 p[2];
 #pragma unroll
         for (uint32_t q = 0; q < 2; q++)

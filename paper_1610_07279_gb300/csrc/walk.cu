@@ -35,19 +35,12 @@
 
 namespace {
 
-#ifndef GT_WALK_FLAT
-#define GT_WALK_FLAT 1            // the balanced force loop for groups that leave lanes idle
-#endif
 #ifndef GT_WALK_MINB
 #define GT_WALK_MINB 3            // resident blocks per SM the register budget is sized for
 #endif
 constexpr int WT = 256;           // threads per block
 constexpr int NWARP = WT / 32;
 constexpr int LIST_CAP = 384;     // interaction-list entries per warp
-// per-warp shared memory: the list (x, y, z, m arrays), the members' positions, and the
-// lanes' partial sums of the balanced force loop (three per lane)
-constexpr int WARP_SM_FLOATS = 4 * LIST_CAP + 4 * 64 + 4 * 3 * 32;
-constexpr size_t WALK_SMEM = (size_t)NWARP * WARP_SM_FLOATS * sizeof(float);
 constexpr int FLUSH_AT = 256;     // flush once the list holds this many
 // Depth-first reserve of the queue: popping the newest 32 cells and pushing at most
 // 8 children each grows the queue by <= 224 per tree level, <= ~22 x 256 in all.
@@ -208,11 +201,7 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
         if (lane == 0) gt_set_error(a.ctl, GT_EINVAL, GTK_WALK);
         return;
     }
-    // the balanced force loop (default S, and a group size that leaves lanes idle under
-    // S lanes per member: not a power of two, or more than 32) keeps member m on lane m
-    // (m - 32 as the lane's second member)
-    const bool flat = GT_WALK_FLAT && a.ij_share == 0 && (two || (cnt & (cnt - 1u)) != 0u);
-    const int S = (two || flat) ? 1 : (a.ij_share ? a.ij_share : 32 >> (cnt <= 1 ? 0 : 32 - __clz(cnt - 1)));
+    const int S = two ? 1 : (a.ij_share ? a.ij_share : 32 >> (cnt <= 1 ? 0 : 32 - __clz(cnt - 1)));
     const int logS = __ffs(S) - 1;
     const int slot = lane >> logS, sub = lane & (S - 1);
     const bool have = (uint32_t)slot < cnt;
@@ -264,13 +253,6 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
     int list_n = 0;
     // the list, structure of arrays: x, y, z, m of entry e at lx[e], ly[e], lz[e], lw[e]
     float *ly = lx + LIST_CAP, *lz = lx + 2 * LIST_CAP, *lw = lx + 3 * LIST_CAP;
-    float4 *mpos = (float4 *)(lx + 4 * LIST_CAP);  // member m's position (balanced loop)
-    float4 *part = mpos + 64;                      // lane l's partial sums, part[3 l + j]
-    if (flat) {
-        if (have) mpos[lane] = pi;
-        if (have2) mpos[lane + 32] = pi2;
-        __syncwarp();
-    }
     auto flush = [&]() {
         cp_async_wait_all();
         __syncwarp();
@@ -303,60 +285,7 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
             sx_ = __fadd_rn(sx.x, sx.y); sy_ = __fadd_rn(sy.x, sy.y); sz_ = __fadd_rn(sz.x, sz.y);
             sp_ = -__fadd_rn(sp.x, sp.y);
         };
-        if (flat) {
-            // the cnt x nquad (member, quad) units in member-major order, cut into 32 equal
-            // contiguous ranges, lane l taking [w(l), w(l + 1)) with w(l) = floor(l U / 32):
-            // every lane runs each member of its range over that member's quads in the range
-            // (at most three members), then the owner lane of each member adds the lanes'
-            // partial sums in lane order -- the same order on every run
-            const uint32_t nq = (uint32_t)nquad, U = cnt * nq;
-            if (U) {
-                const uint32_t w0 = (uint32_t)(((unsigned long long)lane * U) >> 5);
-                const uint32_t w1 = (uint32_t)(((unsigned long long)(lane + 1) * U) >> 5);
-                uint32_t m = w0 / nq, q = w0 - m * nq, w = w0;
-                for (int j = 0; w < w1; j++) {
-                    const uint32_t qe = min(nq, q + (w1 - w));
-                    const float2 e2 = make_float2(a.eps2, a.eps2);
-                    const float4 p = mpos[m];
-                    const float2 nx = make_float2(-p.x, -p.x), ny = make_float2(-p.y, -p.y),
-                                 nz = make_float2(-p.z, -p.z);
-                    float2 sx = make_float2(0.f, 0.f), sy = sx, sz = sx, sp = sx;
-                    for (uint32_t k = q; k < qe; k++) {
-                        const float4 X = px[k], Y = py[k], Z = pz[k], W = pw[k];
-                        interact_pairs(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
-                                       make_float2(W.x, W.y), nx, ny, nz, e2, sx, sy, sz, sp);
-                        interact_pairs(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
-                                       make_float2(W.z, W.w), nx, ny, nz, e2, sx, sy, sz, sp);
-                    }
-                    part[3 * lane + j] = make_float4(__fadd_rn(sx.x, sx.y), __fadd_rn(sy.x, sy.y),
-                                                     __fadd_rn(sz.x, sz.y), __fadd_rn(sp.x, sp.y));
-                    w += qe - q;
-                    q = 0;
-                    m++;
-                }
-                __syncwarp();
-                // member mm's units [mm nq, (mm + 1) nq) lie in lanes lane(u0) .. lane(u1 - 1),
-                // lane(u) = ceil(32 (u + 1) / U) - 1 (the last lane whose range starts at or
-                // before u); with fewer than 32 units some lanes in between have none, and
-                // hold no partial sums of this flush
-                auto gather = [&](uint32_t mm, float &gx, float &gy, float &gz, float &gp) {
-                    const uint32_t u0 = mm * nq, u1 = u0 + nq;
-                    const uint32_t la = (32u * (u0 + 1u) + U - 1u) / U - 1u;
-                    const uint32_t lb = (32u * u1 + U - 1u) / U - 1u;
-                    for (uint32_t l = la; l <= lb; l++) {
-                        const uint32_t lw0 = (uint32_t)(((unsigned long long)l * U) >> 5);
-                        if (lw0 == (uint32_t)(((unsigned long long)(l + 1) * U) >> 5)) continue;  // no units
-                        const float4 t = part[3 * l + (mm - lw0 / nq)];
-                        gx = __fadd_rn(gx, t.x);
-                        gy = __fadd_rn(gy, t.y);
-                        gz = __fadd_rn(gz, t.z);
-                        gp = __fsub_rn(gp, t.w);
-                    }
-                };
-                if (have) gather((uint32_t)lane, ax, ay, az, ph);
-                if (have2) gather((uint32_t)lane + 32u, bx, by, bz, qh);
-            }
-        } else if (two) {  // both members of the lane over every pair, one after the other
+        if (two) {  // both members of the lane over every pair, one after the other
             run(pi, ax, ay, az, ph, 0, 1);
             run(pi2, bx, by, bz, qh, 0, 1);
         } else {  // S lanes per i-particle: lane sub takes quads sub, sub + S, ...
@@ -570,9 +499,9 @@ __device__ __forceinline__ int system_of(const uint32_t *gprefix, int nsys, uint
 }
 
 __global__ __launch_bounds__(WT, GT_WALK_MINB) void k_walk(WalkArgs a) {
-    extern __shared__ __align__(16) float walk_sm[];
+    __shared__ __align__(16) float list_sm[NWARP][4 * LIST_CAP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *list = walk_sm + (size_t)warp * WARP_SM_FLOATS;
+    float *list = list_sm[warp];
     uint32_t *q = a.queue + (size_t)(blockIdx.x * NWARP + warp) * (size_t)a.qcap;
     const uint32_t na = a.ctl->n_active;
     const uint32_t gmax = (uint32_t)a.gmax;
@@ -599,10 +528,10 @@ __global__ __launch_bounds__(WT, 3) void k_walk_batch(const WalkArgs *__restrict
                                                       const uint32_t *__restrict__ gprefix,
                                                       unsigned int *group_next, uint32_t *queue, int qcap,
                                                       int mac) {
-    extern __shared__ __align__(16) float walk_sm[];
+    __shared__ __align__(16) float list_sm[NWARP][4 * LIST_CAP];
     __shared__ WalkArgs sargs[NWARP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *list = walk_sm + (size_t)warp * WARP_SM_FLOATS;
+    float *list = list_sm[warp];
     uint32_t *q = queue + (size_t)(blockIdx.x * NWARP + warp) * (size_t)qcap;
     const uint32_t total = gprefix[nsys];
     for (;;) {
@@ -659,16 +588,9 @@ __global__ void k_batch_prefix(DevCtl *const *__restrict__ ctls, const WalkArgs 
 
 }  // namespace
 
-// the walk kernels' dynamic shared memory above the default limit, on the current device
-void walk_init() {
-    cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WALK_SMEM);
-    cudaFuncSetAttribute(k_walk_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WALK_SMEM);
-}
-
 int gt_walk_blocks(int nsm) {
-    walk_init();
     int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk, WT, WALK_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk, WT, 0);
     if (per < 1) per = 1;
     return per * nsm;
 }
@@ -676,7 +598,7 @@ int gt_walk_blocks(int nsm) {
 int gt_walk_warps_per_block() { return NWARP; }
 
 void gt_launch_walk(const WalkArgs &a, int nblocks, cudaStream_t st) {
-    { k_walk<<<nblocks, WT, WALK_SMEM, st>>>(a); gt_note_launches(1); }
+    { k_walk<<<nblocks, WT, 0, st>>>(a); gt_note_launches(1); }
 }
 
 void gt_launch_walk_batch(DevCtl *const *ctls, const WalkArgs *args, int nsys, uint32_t *gprefix,
@@ -684,5 +606,5 @@ void gt_launch_walk_batch(DevCtl *const *ctls, const WalkArgs *args, int nsys, u
                           cudaStream_t st) {
     if (nsys <= 0) return;
     { k_batch_prefix<<<1, 32, 0, st>>>(ctls, args, nsys, gprefix, group_next); gt_note_launches(1); }
-    { k_walk_batch<<<nblocks, WT, WALK_SMEM, st>>>(args, nsys, gprefix, group_next, queue, qcap, mac); gt_note_launches(1); }
+    { k_walk_batch<<<nblocks, WT, 0, st>>>(args, nsys, gprefix, group_next, queue, qcap, mac); gt_note_launches(1); }
 }

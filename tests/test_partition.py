@@ -3,7 +3,9 @@
 Independent systems shard by whole systems (no exchange); one system's force
 evaluation can split over contiguous slices of its groups, each rank evaluating its
 slice of the same tree.  In both cases the gathered result must equal the one-rank
-result bit for bit.  The ranks run the oracle (no GPU is needed for the logic).
+result bit for bit; the ranks evaluate with the oracle, since a CPU rank has no GPU.
+The shard planning that bench.py runs on every rank under torchrun (the batch's
+systems, the serving stream's requests) is run here by two CPU ranks as it is.
 """
 import os
 import socket
@@ -143,3 +145,42 @@ def test_two_ranks_over_whole_systems_equal_one_rank():
     for k, m in enumerate(mem):
         ref = O.tree_force(_p4(m["pos"], m["mass"]), O.Params(eps=O.f32(m["eps"])), mac=0)["acc"]
         assert np.array_equal(out[k], ref), k
+
+
+def _rank_plans(rank, world, port, q):
+    """Rank `rank` plans its share of the benchmark's batch (64 systems) and serving
+    stream with the same calls bench.py makes under torchrun, with no exchange; the
+    plans are gathered only to check them."""
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    mem = ics.batch_systems(64, seed=4, log2_lo=6.0, log2_hi=8.0)  # the bench's sizes scaled down
+    ns = [m["n"] for m in mem]
+    reqs = ics.serving_requests(512 * world, seed=5, rate=100.0 * world)
+    mine = (rank, bench.batch_shard(ns, rank, world), bench.serving_shard(reqs, rank, world))
+    got = [None] * world
+    dist.all_gather_object(got, mine)
+    if rank == 0:
+        q.put((got, ns, [r["n"] * max(r["steps"], 1) for r in reqs]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_plan_disjoint_complete_shards():
+    """The shards of the batch and of the serving stream that two ranks plan
+    independently cover every system and request exactly once, are balanced, and are
+    what each rank would have planned for the other."""
+    pytest.importorskip("torch")
+    got, ns, work = _run_ranks(_rank_plans)
+    got = sorted(got)
+    bat = [b for _, b, _ in got]
+    srv = [s for _, _, s in got]
+    assert sorted(k for b in bat for k in b) == list(range(len(ns)))
+    assert sorted(k for s in srv for k in s) == list(range(len(work)))
+    import bench
+    assert bat == [bench.batch_shard(ns, r, 2) for r in range(2)]
+    loads = [sum(ns[k] for k in b) for b in bat]
+    assert max(loads) - min(loads) <= max(ns)
+    wl = [sum(work[k] for k in s) for s in srv]
+    assert max(wl) - min(wl) <= max(work)
+    assert all(s == sorted(s) for s in srv)  # arrival order kept
