@@ -846,7 +846,7 @@ def run_ours(args):
                 "peak_basis": "measured: 2 x the faster of the scalar and packed (f32x2) FMA chains on all SMs "
                               "(gt_measure_fp32_rates); the walk's force loop issues the packed form",
                 "measured_rates_per_s": {k: rates[k] for k in ("fma_per_s", "fma2_per_s", "add_per_s",
-                                                              "mul_per_s", "rsqrt_per_s")},
+                                                              "mul_per_s", "rsqrt_per_s", "fp64_fma_per_s")},
                 "rsqrt_flops_measured": rates["rsqrt_flops"],
                 "frac_at_20_flops": inter * FLOPS_BASE / (walk_ms * 1e-3) / 1e12 / peak if walk_ms > 0 else 0.0,
                 "derived_peak_tflops": derived,

@@ -350,6 +350,8 @@ typedef struct gt_fp32_rates {
     double rsqrt_per_s;  /* rsqrt.approx.ftz.f32 */
     double peak_flops;
     double rsqrt_flops;
+    double fp64_fma_per_s; /* FP64 FMA, for the FP64 sums of the pseudo j-particles and the
+                              integration (not part of the walk's roofline)  */
 } gt_fp32_rates;
 GT_API int gt_measure_fp32_rates(gt_fp32_rates *out, gt_stream stream);
 

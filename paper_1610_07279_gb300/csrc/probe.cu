@@ -6,7 +6,8 @@
 // to cover the pipe latency at full occupancy); the chains are folded into one value
 // that is stored under a condition the compiler cannot prove false, so no chain is
 // removed.  Forms: scalar FMA, packed FMA on float2 (f32x2, two FMAs per lane and
-// instruction), scalar add, scalar multiply and the SFU reciprocal square root.
+// instruction), scalar add, scalar multiply, the SFU reciprocal square root, and the FP64
+// FMA (the pipe of the centre-of-mass sums and the integration).
 #include "gt_internal.cuh"
 
 namespace {
@@ -15,7 +16,7 @@ constexpr int PT = 256;
 constexpr int UNROLL = 16;
 constexpr int CHAINS = 8;
 
-enum { OP_FMA = 0, OP_FMA2, OP_ADD, OP_MUL, OP_RSQRT, NOPS };
+enum { OP_FMA = 0, OP_FMA2, OP_ADD, OP_MUL, OP_RSQRT, OP_DFMA, NOPS };
 
 __device__ __forceinline__ float rsqrt_sfu(float x) {
     float r;
@@ -27,10 +28,12 @@ template <int OP>
 __global__ __launch_bounds__(PT) void k_chains(float *out, int iters, float seed) {
     float a[CHAINS];
     float2 p[CHAINS];
+    double da[CHAINS];
 #pragma unroll
     for (int c = 0; c < CHAINS; c++) {
         a[c] = seed + (float)(threadIdx.x & 7) + (float)c;
         p[c] = make_float2(a[c], a[c] + 0.5f);
+        da[c] = (double)a[c];
     }
     const float b = 0.999999f, cc = 1e-6f;
     const float2 b2 = make_float2(b, b), c2 = make_float2(cc, cc);
@@ -44,12 +47,13 @@ __global__ __launch_bounds__(PT) void k_chains(float *out, int iters, float seed
                 if (OP == OP_ADD) a[c] = __fadd_rn(a[c], cc);
                 if (OP == OP_MUL) a[c] = __fmul_rn(a[c], b);
                 if (OP == OP_RSQRT) a[c] = rsqrt_sfu(a[c]);  // x -> x^(-1/2): stays near 1
+                if (OP == OP_DFMA) da[c] = __fma_rn(da[c], 0.999999, 1e-6);
             }
         }
     }
     float s = 0.f;
 #pragma unroll
-    for (int c = 0; c < CHAINS; c++) s += a[c] + p[c].x + p[c].y;
+    for (int c = 0; c < CHAINS; c++) s += a[c] + p[c].x + p[c].y + (float)da[c];
     if (s == -1.0f) out[blockIdx.x] = s;
 }
 
@@ -59,7 +63,7 @@ int time_op(cudaStream_t st, int nsm, double *ops_per_s) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chains<OP>, PT, 0);
     if (per < 1) per = 1;
     const int blocks = nsm * per;
-    const int iters = OP == OP_RSQRT ? 512 : 4096;
+    const int iters = (OP == OP_RSQRT || OP == OP_DFMA) ? 64 : 4096;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) return GT_ECUDA;
     { k_chains<OP><<<blocks, PT, 0, st>>>(nullptr, 64, 1.0f); gt_note_launches(1); }  // warm-up
@@ -93,8 +97,9 @@ extern "C" int gt_measure_fp32_rates(gt_fp32_rates *out, gt_stream stream) {
     double r[NOPS] = {};
     if ((rc = time_op<OP_FMA>(st, nsm, &r[OP_FMA])) || (rc = time_op<OP_FMA2>(st, nsm, &r[OP_FMA2])) ||
         (rc = time_op<OP_ADD>(st, nsm, &r[OP_ADD])) || (rc = time_op<OP_MUL>(st, nsm, &r[OP_MUL])) ||
-        (rc = time_op<OP_RSQRT>(st, nsm, &r[OP_RSQRT])))
+        (rc = time_op<OP_RSQRT>(st, nsm, &r[OP_RSQRT])) || (rc = time_op<OP_DFMA>(st, nsm, &r[OP_DFMA])))
         return rc;
+    out->fp64_fma_per_s = r[OP_DFMA];
     out->fma_per_s = r[OP_FMA];
     out->fma2_per_s = r[OP_FMA2];
     out->add_per_s = r[OP_ADD];

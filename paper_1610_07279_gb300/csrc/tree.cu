@@ -615,9 +615,15 @@ __global__ __launch_bounds__(PL, 8) void k_pseudo(Nodes nd, const float4 *__rest
     }
     __syncthreads();
     const uint32_t total = ocum[NSEG];
+    // thread 0 holds the block's next ticket, taken while the current chunk is processed so
+    // that the atomic's latency overlaps it; a ticket only ever waits for smaller ones, and
+    // the smallest unfinished ticket is always some block's current or next one, so every
+    // wait still ends
+    unsigned int t_next = 0;
+    if (threadIdx.x == 0) t_next = atomicAdd(&ctl->pl_ticket, 1u);
     for (;;) {
         if (threadIdx.x == 0) {
-            const unsigned int t = atomicAdd(&ctl->pl_ticket, 1u);
+            const unsigned int t = t_next;
             int o = 0;
             if (t < total)
                 while (ocum[o + 1] <= t) o++;
@@ -638,6 +644,7 @@ __global__ __launch_bounds__(PL, 8) void k_pseudo(Nodes nd, const float4 *__rest
                 }
                 __threadfence();
             }
+            if (t < total && !bad_sh) t_next = atomicAdd(&ctl->pl_ticket, 1u);
         }
         __syncthreads();
         const unsigned int t = t_sh;

@@ -61,7 +61,7 @@ class gt_stats(C.Structure):
 
 class gt_fp32_rates(C.Structure):
     _fields_ = [(k, C.c_double) for k in ("fma_per_s", "fma2_per_s", "add_per_s", "mul_per_s", "rsqrt_per_s",
-                                          "peak_flops", "rsqrt_flops")]
+                                          "peak_flops", "rsqrt_flops", "fp64_fma_per_s")]
 
 
 class GothicError(RuntimeError):
