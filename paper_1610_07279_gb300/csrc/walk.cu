@@ -5,9 +5,8 @@
 // atomic counter, so slow groups do not hold a fixed share of the GPU).  A group is a
 // range of the active list: the actives of one tree cell (Sec. 2.4 reading) or a run
 // of group_max.  Per group:
-//   * S lanes per member (Sec. 2.5): fixed, or floor(32 / members) so that small groups
-//     still fill the warp (a group of more than 32: one lane per member for the first 32,
-//     floor(32 / (members - 32)) lanes per member for the rest, in a second pass);
+//   * S lanes per member (Sec. 2.5): fixed, or 32 / (members rounded up to a power of
+//     two) so that small groups still fill the warp;
 //   * pseudo i-particle: the sphere about the centre of the members' bounding box
 //     (Appendix B, "GEO"), the FP32 radius widened by (1 + 2^-20); |a_old| of the
 //     group is the smallest of its members';
@@ -114,14 +113,14 @@ __device__ __forceinline__ void warp_arg_ext(float &v, int &m, bool want_max) {
 // at most cnt times.  FP32, every operation rounded as written.  Member k < 32 is the
 // first member of the lane holding slot k (pi), member 32 + l the second of lane l (pi2).
 __device__ __forceinline__ void ebs_centre(float4 pi, float4 pi2, bool mine1, bool mine2, int slot, int lane,
-                                           int S, uint32_t cnt, float &cx, float &cy, float &cz) {
+                                           int logS, uint32_t cnt, float &cx, float &cy, float &cz) {
     const unsigned FULL = 0xffffffffu;
     const float INF = __int_as_float(0x7f800000);
     auto coord = [](const float4 &p, int a) { return a == 0 ? p.x : (a == 1 ? p.y : p.z); };
     // the member's position, fetched from the lane that holds it
     auto fetch = [&](int m, float &x, float &y, float &z) {
         const bool second = m >= 32;
-        const int src = second ? m - 32 : m * S;
+        const int src = second ? m - 32 : (m << logS);
         const float4 a1 = make_float4(__shfl_sync(FULL, pi.x, src), __shfl_sync(FULL, pi.y, src),
                                       __shfl_sync(FULL, pi.z, src), 0.f);
         const float4 a2 = make_float4(__shfl_sync(FULL, pi2.x, src), __shfl_sync(FULL, pi2.y, src),
@@ -159,7 +158,7 @@ __device__ __forceinline__ void ebs_centre(float4 pi, float4 pi2, bool mine1, bo
         const unsigned b1 = __ballot_sync(FULL, mine1 && outside(pi));
         const unsigned b2 = __ballot_sync(FULL, mine2 && outside(pi2));
         int m;
-        if (b1) m = (__ffs(b1) - 1) / S;
+        if (b1) m = (__ffs(b1) - 1) >> logS;
         else if (b2) m = 32 + __ffs(b2) - 1;
         else break;
         float px, py, pz;
@@ -202,23 +201,11 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
         if (lane == 0) gt_set_error(a.ctl, GT_EINVAL, GTK_WALK);
         return;
     }
-    // S lanes per member (Sec. 2.5): the given S, or as many as fit, floor(32 / members).  A
-    // group of more than 32 takes its first 32 members one per lane; its other r2 = cnt - 32
-    // members run as a second pass with S2 = floor(32 / r2) lanes each (slot2, sub2), their
-    // positions fetched from the lanes that hold them (lane l holds member 32 + l)
-    const int S = two ? 1 : (a.ij_share ? a.ij_share : 32 / (int)cnt);
-    const int slot = lane / S, sub = lane - slot * S;
+    const int S = two ? 1 : (a.ij_share ? a.ij_share : 32 >> (cnt <= 1 ? 0 : 32 - __clz(cnt - 1)));
+    const int logS = __ffs(S) - 1;
+    const int slot = lane >> logS, sub = lane & (S - 1);
     const bool have = (uint32_t)slot < cnt;
     const bool have2 = two && (uint32_t)(lane + 32) < cnt;
-    // the second pass's lanes (recomputed where needed, so that they hold no registers
-    // across the traversal): S2 lanes per member, lane in slot2 / sub2, member 32 + slot2
-    auto second = [&](int &S2, int &slot2, int &sub2) {
-        const int r2 = (int)cnt - 32;
-        S2 = 32 / r2;
-        slot2 = lane / S2;
-        sub2 = lane - slot2 * S2;
-        return slot2 < r2;
-    };
     const uint32_t kk = a0 + (have ? (uint32_t)slot : 0u);
     const uint32_t kk2 = a0 + (have2 ? (uint32_t)(lane + 32) : 0u);
     uint32_t i = a.active ? a.active[kk] : kk;
@@ -230,12 +217,6 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
     }
     const float4 pi = a.posm[i];
     const float4 pi2 = have2 ? a.posm[i2] : pi;
-    // the position of member 32 + slot2, from the lane that holds it
-    auto second_pos = [&](int slot2, bool valid) {
-        const int src = valid ? slot2 : 0;
-        return make_float4(__shfl_sync(FULL, pi2.x, src), __shfl_sync(FULL, pi2.y, src),
-                           __shfl_sync(FULL, pi2.z, src), __shfl_sync(FULL, pi2.w, src));
-    };
     float ao = have ? (a.aold ? a.aold[i] : 0.0f) : INFINITY;
     if (have2) ao = fminf(ao, a.aold ? a.aold[i2] : 0.0f);
 
@@ -255,7 +236,7 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
     float cx = __fmul_rn(0.5f, __fadd_rn(mnx, mxx));
     float cy = __fmul_rn(0.5f, __fadd_rn(mny, mxy));
     float cz = __fmul_rn(0.5f, __fadd_rn(mnz, mxz));
-    if (a.sphere == 1) ebs_centre(pi, pi2, have && sub == 0, have2, slot, lane, S, cnt, cx, cy, cz);
+    if (a.sphere == 1) ebs_centre(pi, pi2, have && sub == 0, have2, slot, lane, logS, cnt, cx, cy, cz);
     const float ddx = __fsub_rn(pi.x, cx), ddy = __fsub_rn(pi.y, cy), ddz = __fsub_rn(pi.z, cz);
     float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ddx, ddx), __fmul_rn(ddy, ddy)), __fmul_rn(ddz, ddz));
     {
@@ -306,9 +287,7 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
         };
         if (two) {  // both members of the lane over every pair, one after the other
             run(pi, ax, ay, az, ph, 0, 1);
-            int S2, slot2, sub2;
-            const bool v2 = second(S2, slot2, sub2);
-            run(second_pos(slot2, v2), bx, by, bz, qh, sub2, S2);
+            run(pi2, bx, by, bz, qh, 0, 1);
         } else {  // S lanes per i-particle: lane sub takes quads sub, sub + S, ...
             run(pi, ax, ay, az, ph, sub, S);
         }
@@ -492,42 +471,19 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
         return;
     }
     flush();
-    // the S (S2) lanes of a member add their shares into its first lane: a butterfly for a
-    // power of two, else in lane order
-    auto gather = [&](int s, float &x, float &y, float &z, float &w) {
-        if ((s & (s - 1)) == 0) {
-            for (int o = 1; o < s; o <<= 1) {
-                x += __shfl_xor_sync(FULL, x, o);
-                y += __shfl_xor_sync(FULL, y, o);
-                z += __shfl_xor_sync(FULL, z, o);
-                w += __shfl_xor_sync(FULL, w, o);
-            }
-        } else {
-            float tx = x, ty = y, tz = z, tw = w;
-            for (int o = 1; o < s; o++) {
-                const int src = min(lane + o, 31);
-                tx += __shfl_sync(FULL, x, src);
-                ty += __shfl_sync(FULL, y, src);
-                tz += __shfl_sync(FULL, z, src);
-                tw += __shfl_sync(FULL, w, src);
-            }
-            x = tx; y = ty; z = tz; w = tw;
-        }
-    };
-    gather(S, ax, ay, az, ph);
+    for (int o = 1; o < S; o <<= 1) {
+        ax += __shfl_xor_sync(FULL, ax, o);
+        ay += __shfl_xor_sync(FULL, ay, o);
+        az += __shfl_xor_sync(FULL, az, o);
+        ph += __shfl_xor_sync(FULL, ph, o);
+    }
     if (sub == 0 && have) {
         const float phi = fmaf(pi.w, a.inv_eps, ph);
         a.acc[kk] = make_float4(a.G * ax, a.G * ay, a.G * az, a.G * phi);
     }
-    if (two) {
-        int S2, slot2, sub2;
-        const bool v2 = second(S2, slot2, sub2);
-        const float4 pj = second_pos(slot2, v2);
-        gather(S2, bx, by, bz, qh);
-        if (v2 && sub2 == 0) {
-            const float phi = fmaf(pj.w, a.inv_eps, qh);
-            a.acc[a0 + 32u + (uint32_t)slot2] = make_float4(a.G * bx, a.G * by, a.G * bz, a.G * phi);
-        }
+    if (have2) {
+        const float phi = fmaf(pi2.w, a.inv_eps, qh);
+        a.acc[kk2] = make_float4(a.G * bx, a.G * by, a.G * bz, a.G * phi);
     }
 }
 
