@@ -530,72 +530,59 @@ __device__ __forceinline__ void pseudo_leaf(const Nodes &nd, const float4 *__res
                              __uint_as_float(k | GT_LEAF_FLAG), b2);
 }
 
-// Cell p with children, computed by the 8 lanes of its group (CW cells per chunk): lane j
-// loads child j's FP64 sums, pseudo j-particle and walk record in one round of loads; the
-// group's first lane adds the sums in child order (values passed by shuffles) and shares
-// r_J = (float)S / (float)M; every lane forms its child's reach |r_c - r_J| + b_c, the
-// group takes the largest (widened by 1 + 2^-20); the first lane adds B_2 in child order
-// (parallel axes: B_2,c + m_c |r_c - r_J|^2) and writes the cell.
-// The children were written by other blocks of this launch: they are read through L2
-// (__ldcg), an SM's L1 may hold a line of them from before they were written.
-constexpr int CL = 8;          // lanes per cell (at most 8 children)
-constexpr int CW = PL / CL;    // cells per chunk
-
+// Cell p with children: its children's FP64 sums added in child order.  The children
+// were written by other blocks of this launch: they are read through L2 (__ldcg), an
+// SM's L1 may hold a line of them from before they were written.  Loads go out four
+// children at a time, so a level costs few L2 round trips.
 template <bool WITH_MASS>
-__device__ __forceinline__ void pseudo_cell8(const Nodes &nd, uint32_t p, bool valid) {
-    const unsigned FULL = 0xffffffffu;
-    const int lane = (int)(threadIdx.x & 31u), j = lane & (CL - 1), g0 = lane & ~(CL - 1);
-    const int32_t ch0 = valid ? nd.child[p] : 0;
-    const uint32_t nch = valid ? nd.nchild[p] : 0u;
-    const bool mine = (uint32_t)j < nch;
-    double2 s0 = make_double2(0.0, 0.0), s1 = make_double2(0.0, 0.0);  // (m, x), (y, z)
-    float4 cj = make_float4(0.f, 0.f, 0.f, 0.f), cw = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (mine) {
-        const double2 *cs = (const double2 *)&nd.sum[ch0 + j];
-        s0 = __ldcg(cs);
-        s1 = __ldcg(cs + 1);
-        cj = __ldcg(&nd.jpos[ch0 + j]);
-        cw = __ldcg(&nd.walk[ch0 + j]);
-    }
-    double m = (WITH_MASS || !valid || j != 0) ? 0.0 : nd.sum[p].m, sx = 0.0, sy = 0.0, sz = 0.0;
+__device__ __forceinline__ void pseudo_cell(const Nodes &nd, uint32_t p) {
+    const int32_t ch0 = nd.child[p];
+    const uint32_t nch = nd.nchild[p];
+    double m = WITH_MASS ? 0.0 : nd.sum[p].m, sx = 0.0, sy = 0.0, sz = 0.0;
+    for (uint32_t q0 = 0; q0 < nch; q0 += 2) {
+        double2 s0[2], s1[2];  // (m, x), (y, z)
 #pragma unroll
-    for (int k = 0; k < CL; k++) {
-        const double vm = __shfl_sync(FULL, s0.x, g0 + k), vx = __shfl_sync(FULL, s0.y, g0 + k);
-        const double vy = __shfl_sync(FULL, s1.x, g0 + k), vz = __shfl_sync(FULL, s1.y, g0 + k);
-        if (j == 0 && (uint32_t)k < nch) {
-            if (WITH_MASS) m = __dadd_rn(m, vm);
-            sx = __dadd_rn(sx, vx);
-            sy = __dadd_rn(sy, vy);
-            sz = __dadd_rn(sz, vz);
-        }
-    }
-    float mf = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-    if (j == 0 && valid) {
-        mf = d2f(m);
-        jx = __fdiv_rn(d2f(sx), mf);
-        jy = __fdiv_rn(d2f(sy), mf);
-        jz = __fdiv_rn(d2f(sz), mf);
-    }
-    jx = __shfl_sync(FULL, jx, g0);
-    jy = __shfl_sync(FULL, jy, g0);
-    jz = __shfl_sync(FULL, jz, g0);
-    const float d2 = sq3f(__fsub_rn(cj.x, jx), __fsub_rn(cj.y, jy), __fsub_rn(cj.z, jz));
-    float b = mine ? __fadd_rn(__fsqrt_rn(d2), cw.x) : 0.0f;
+        for (uint32_t q = 0; q < 2; q++)
+            if (q0 + q < nch) {
+                const double2 *cs = (const double2 *)&nd.sum[ch0 + q0 + q];
+                s0[q] = __ldcg(cs);
+                s1[q] = __ldcg(cs + 1);
+            }
 #pragma unroll
-    for (int o = 1; o < CL; o <<= 1) b = fmaxf(b, __shfl_xor_sync(FULL, b, o));
-    const float t = __fadd_rn(cw.w, __fmul_rn(cj.w, d2));  // child j's share of B_2
-    float b2 = 0.0f;
+        for (uint32_t q = 0; q < 2; q++)
+            if (q0 + q < nch) {
+                if (WITH_MASS) m = __dadd_rn(m, s0[q].x);
+                sx = __dadd_rn(sx, s0[q].y);
+                sy = __dadd_rn(sy, s1[q].x);
+                sz = __dadd_rn(sz, s1[q].y);
+            }
+    }
+    const float mf = d2f(m);
+    const float jx = __fdiv_rn(d2f(sx), mf);
+    const float jy = __fdiv_rn(d2f(sy), mf);
+    const float jz = __fdiv_rn(d2f(sz), mf);
+    float b = 0.0f, b2 = 0.0f;  // b2: B_2 by parallel axes
+    for (uint32_t q0 = 0; q0 < nch; q0 += 2) {
+        float4 cj[2], cw[2];
 #pragma unroll
-    for (int k = 0; k < CL; k++) {
-        const float tk = __shfl_sync(FULL, t, g0 + k);
-        if ((uint32_t)k < nch) b2 = __fadd_rn(b2, tk);
+        for (uint32_t q = 0; q < 2; q++)
+            if (q0 + q < nch) {
+                cj[q] = __ldcg(&nd.jpos[ch0 + q0 + q]);
+                cw[q] = __ldcg(&nd.walk[ch0 + q0 + q]);
+            }
+#pragma unroll
+        for (uint32_t q = 0; q < 2; q++)
+            if (q0 + q < nch) {
+                const float d2 = sq3f(__fsub_rn(cj[q].x, jx), __fsub_rn(cj[q].y, jy), __fsub_rn(cj[q].z, jz));
+                const float e = __fadd_rn(__fsqrt_rn(d2), cw[q].x);
+                if (e > b) b = e;
+                b2 = __fadd_rn(b2, __fadd_rn(cw[q].w, __fmul_rn(cj[q].w, d2)));
+            }
     }
-    if (j == 0 && valid) {
-        nd.sum[p] = DSum4{m, sx, sy, sz};
-        nd.jpos[p] = make_float4(jx, jy, jz, mf);
-        nd.walk[p] = make_float4(__fmul_rn(b, GT_RADIUS_MARGIN), __uint_as_float((uint32_t)ch0),
-                                 __uint_as_float(nch), b2);
-    }
+    nd.sum[p] = DSum4{m, sx, sy, sz};
+    nd.jpos[p] = make_float4(jx, jy, jz, mf);
+    nd.walk[p] = make_float4(__fmul_rn(b, GT_RADIUS_MARGIN), __uint_as_float((uint32_t)ch0),
+                             __uint_as_float(nch), b2);
 }
 
 template <bool WITH_MASS>
@@ -609,10 +596,7 @@ __global__ __launch_bounds__(PL, 8) void k_pseudo(Nodes nd, const float4 *__rest
     for (int i = threadIdx.x; i <= NSEG; i += PL) seg[i] = ctl->seg[i];
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int k = 0; k < NSEG; k++) {  // leaf segments: PL nodes per chunk; cells: CW
-            const uint32_t per = (k & 1) ? (uint32_t)CW : (uint32_t)PL;
-            nchunk[k] = (seg[k + 1] - seg[k] + per - 1) / per;
-        }
+        for (int k = 0; k < NSEG; k++) nchunk[k] = (seg[k + 1] - seg[k] + PL - 1) / PL;
         int o = 0;  // level l's cells go right after the leaves of level l - PSEUDO_LAG
         for (int s = 0; s < GT_TREE_LEVELS + PSEUDO_LAG; s++) {
             const int ll = GT_TREE_LEVELS - 1 - s, lc = GT_TREE_LEVELS - 1 + PSEUDO_LAG - s;
@@ -631,15 +615,9 @@ __global__ __launch_bounds__(PL, 8) void k_pseudo(Nodes nd, const float4 *__rest
     }
     __syncthreads();
     const uint32_t total = ocum[NSEG];
-    // thread 0 holds the block's next ticket, taken while the current chunk is processed so
-    // that the atomic's latency overlaps it; a ticket only ever waits for smaller ones, and
-    // the smallest unfinished ticket is always some block's current or next one, so every
-    // wait still ends
-    unsigned int t_next = 0;
-    if (threadIdx.x == 0) t_next = atomicAdd(&ctl->pl_ticket, 1u);
     for (;;) {
         if (threadIdx.x == 0) {
-            const unsigned int t = t_next;
+            const unsigned int t = atomicAdd(&ctl->pl_ticket, 1u);
             int o = 0;
             if (t < total)
                 while (ocum[o + 1] <= t) o++;
@@ -660,20 +638,16 @@ __global__ __launch_bounds__(PL, 8) void k_pseudo(Nodes nd, const float4 *__rest
                 }
                 __threadfence();
             }
-            if (t < total && !bad_sh) t_next = atomicAdd(&ctl->pl_ticket, 1u);
         }
         __syncthreads();
         const unsigned int t = t_sh;
         const int o = o_sh;
         if (t >= total || bad_sh) break;
         const int lvl = olvl[o], kind = ocell[o];
-        if (kind == 0) {
-            const long long idx = (long long)seg[2 * lvl] + (long long)(t - ocum[o]) * PL + threadIdx.x;
-            if (idx < (long long)seg[2 * lvl + 1]) pseudo_leaf<WITH_MASS>(nd, posm, nd.cells[idx]);
-        } else {
-            const long long idx = (long long)seg[2 * lvl + 1] + (long long)(t - ocum[o]) * CW + (threadIdx.x / CL);
-            const bool valid = idx < (long long)seg[2 * lvl + 2];
-            pseudo_cell8<WITH_MASS>(nd, valid ? nd.cells[idx] : 0u, valid);  // every lane takes part
+        const long long idx = (long long)seg[2 * lvl + kind] + (long long)(t - ocum[o]) * PL + threadIdx.x;
+        if (idx < (long long)seg[2 * lvl + kind + 1]) {
+            if (kind == 0) pseudo_leaf<WITH_MASS>(nd, posm, nd.cells[idx]);
+            else pseudo_cell<WITH_MASS>(nd, nd.cells[idx]);
         }
         __threadfence();  // every thread's node is visible device-wide before the chunk counts as done
         __syncthreads();
