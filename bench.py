@@ -873,11 +873,17 @@ def run_ours(args):
         t_start = time.perf_counter()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        for _ in range(args.steps):
+        # the legs of every step, by CUDA events on the stream: inputs in, the cycle, results out
+        legs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        for k in range(args.steps):
+            legs[k][0].record(stream)
             sysm.set_state(host["pos"], host["vel"], host["mass"])
             sysm.set_integrator_state(host["level"], host["t0"], host["aold"], host["acc"], dt_max, T)
+            legs[k][1].record(stream)
             sysm.advance_cycle()
+            legs[k][2].record(stream)
             sysm.get_state(out=host)
+            legs[k][3].record(stream)
             T = sysm.stats()["T"]
         f1.record(stream)
         torch.cuda.synchronize()
@@ -887,8 +893,13 @@ def run_ours(args):
         i_e = sysm.stats()["interactions"] - i0
         ms_e_max = allreduce(ms_e, dist.ReduceOp.MAX if world > 1 else None)
         i_e_all = allreduce(float(i_e), dist.ReduceOp.SUM if world > 1 else None)
+        leg_ms = [sum(legs[k][j].elapsed_time(legs[k][j + 1]) for k in range(args.steps)) / args.steps
+                  for j in range(3)]
         e2e = {"value": i_e_all / (ms_e_max * 1e-3), "unit": "interactions/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "wall_s": wall,
+               "legs_ms_per_step": {"in": leg_ms[0], "cycle": leg_ms[1], "out": leg_ms[2],
+                                    "in_GBps": h2d / (leg_ms[0] * 1e6) if leg_ms[0] > 0 else None,
+                                    "out_GBps": d2h / (leg_ms[2] * 1e6) if leg_ms[2] > 0 else None},
                "path": "gt_set_state + gt_set_integrator_state from pinned host, one block-step cycle, "
                        "gt_get_state to pinned host, every step"}
 

@@ -6,8 +6,7 @@
 // range of the active list: the actives of one tree cell (Sec. 2.4 reading) or a run
 // of group_max.  Per group:
 //   * S lanes per member (Sec. 2.5): fixed, or 32 / (members rounded up to a power of
-//     two) so that small groups still fill the warp; a group of more than 32 runs its first
-//     32 members one per lane, then the others in a second pass spread the same way;
+//     two) so that small groups still fill the warp;
 //   * pseudo i-particle: the sphere about the centre of the members' bounding box
 //     (Appendix B, "GEO"), the FP32 radius widened by (1 + 2^-20); |a_old| of the
 //     group is the smallest of its members';
@@ -218,21 +217,6 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
     }
     const float4 pi = a.posm[i];
     const float4 pi2 = have2 ? a.posm[i2] : pi;
-    // the second pass of a group of more than 32 (r2 = cnt - 32 members) spreads its members
-    // over the warp, S2 = 32 / (r2 rounded up to a power of two) lanes each: lane l works
-    // for member 32 + (l >> log2 S2), whose position lane l >> log2 S2 holds
-    auto second = [&](int &logS2, int &slot2, int &sub2) {
-        const int r2 = (int)cnt - 32;
-        logS2 = 5 - (r2 <= 1 ? 0 : 32 - __clz(r2 - 1));
-        slot2 = lane >> logS2;
-        sub2 = lane & ((1 << logS2) - 1);
-        return slot2 < r2;
-    };
-    auto second_pos = [&](int slot2, bool valid) {
-        const int src = valid ? slot2 : 0;
-        return make_float4(__shfl_sync(FULL, pi2.x, src), __shfl_sync(FULL, pi2.y, src),
-                           __shfl_sync(FULL, pi2.z, src), __shfl_sync(FULL, pi2.w, src));
-    };
     float ao = have ? (a.aold ? a.aold[i] : 0.0f) : INFINITY;
     if (have2) ao = fminf(ao, a.aold ? a.aold[i2] : 0.0f);
 
@@ -303,9 +287,7 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
         };
         if (two) {  // both members of the lane over every pair, one after the other
             run(pi, ax, ay, az, ph, 0, 1);
-            int logS2, slot2, sub2;
-            const bool v2 = second(logS2, slot2, sub2);
-            run(second_pos(slot2, v2), bx, by, bz, qh, sub2, 1 << logS2);
+            run(pi2, bx, by, bz, qh, 0, 1);
         } else {  // S lanes per i-particle: lane sub takes quads sub, sub + S, ...
             run(pi, ax, ay, az, ph, sub, S);
         }
@@ -484,7 +466,7 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
         cp_async_wait_all();
         list_n = 0;
         if (sub == 0 && have) a.acc[kk] = make_float4(NAN, NAN, NAN, NAN);
-        if (have2) a.acc[kk2] = make_float4(NAN, NAN, NAN, NAN);  // lane l: member 32 + l
+        if (have2) a.acc[kk2] = make_float4(NAN, NAN, NAN, NAN);
         __syncwarp();
         return;
     }
@@ -499,20 +481,9 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
         const float phi = fmaf(pi.w, a.inv_eps, ph);
         a.acc[kk] = make_float4(a.G * ax, a.G * ay, a.G * az, a.G * phi);
     }
-    if (two) {
-        int logS2, slot2, sub2;
-        const bool v2 = second(logS2, slot2, sub2);
-        const float4 pj = second_pos(slot2, v2);
-        for (int o = 1; o < (1 << logS2); o <<= 1) {
-            bx += __shfl_xor_sync(FULL, bx, o);
-            by += __shfl_xor_sync(FULL, by, o);
-            bz += __shfl_xor_sync(FULL, bz, o);
-            qh += __shfl_xor_sync(FULL, qh, o);
-        }
-        if (v2 && sub2 == 0) {
-            const float phi = fmaf(pj.w, a.inv_eps, qh);
-            a.acc[a0 + 32u + (uint32_t)slot2] = make_float4(a.G * bx, a.G * by, a.G * bz, a.G * phi);
-        }
+    if (have2) {
+        const float phi = fmaf(pi2.w, a.inv_eps, qh);
+        a.acc[kk2] = make_float4(a.G * bx, a.G * by, a.G * bz, a.G * phi);
     }
 }
 
