@@ -6,9 +6,7 @@
 // range of the active list: the actives of one tree cell (Sec. 2.4 reading) or a run
 // of group_max.  Per group:
 //   * S lanes per member (Sec. 2.5): fixed, or 32 / (members rounded up to a power of
-//     two) so that small groups still fill the warp; a group of more than 32 runs its first
-//     32 members one per lane, then the others in a second pass spread the same way; the
-//     members' positions and sums wait in shared memory during the traversal;
+//     two) so that small groups still fill the warp;
 //   * pseudo i-particle: the sphere about the centre of the members' bounding box
 //     (Appendix B, "GEO"), the FP32 radius widened by (1 + 2^-20); |a_old| of the
 //     group is the smallest of its members';
@@ -42,16 +40,7 @@ namespace {
 #endif
 constexpr int WT = 256;           // threads per block
 constexpr int NWARP = WT / 32;
-#ifndef GT_WALK_LIST
-#define GT_WALK_LIST 384
-#endif
-constexpr int LIST_CAP = GT_WALK_LIST;  // interaction-list entries per warp (a multiple of 32)
-// per warp in shared memory: the list (x, y, z, m arrays of LIST_CAP) and every lane's
-// member state, parked there during the traversal (first and second member's position and
-// sums), which the force passes read and update
-constexpr int PARK = 4;           // float4 per lane: pi, pi2, sums of pi, sums of pi2
-constexpr int WARP_SM_FLOATS = 4 * LIST_CAP + 4 * PARK * 32;
-constexpr size_t WALK_SMEM = (size_t)NWARP * WARP_SM_FLOATS * sizeof(float);
+constexpr int LIST_CAP = 384;     // interaction-list entries per warp
 constexpr int FLUSH_AT = 256;     // flush once the list holds this many
 // Depth-first reserve of the queue: popping the newest 32 cells and pushing at most
 // 8 children each grows the queue by <= 224 per tree level, <= ~22 x 256 in all.
@@ -228,17 +217,6 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
     }
     const float4 pi = a.posm[i];
     const float4 pi2 = have2 ? a.posm[i2] : pi;
-    float4 *park = (float4 *)(lx + 4 * LIST_CAP) + PARK * lane;  // this lane's parked state
-    // the second pass of a group of more than 32 (r2 = cnt - 32 members) spreads its members
-    // over the warp, S2 = 32 / (r2 rounded up to a power of two) lanes each: lane l works
-    // for member 32 + (l >> log2 S2), whose position lane l >> log2 S2 has parked
-    auto second = [&](int &logS2, int &slot2, int &sub2) {
-        const int r2 = (int)cnt - 32;
-        logS2 = 5 - (r2 <= 1 ? 0 : 32 - __clz(r2 - 1));
-        slot2 = lane >> logS2;
-        sub2 = lane & ((1 << logS2) - 1);
-        return slot2 < r2;
-    };
     float ao = have ? (a.aold ? a.aold[i] : 0.0f) : INFINITY;
     if (have2) ao = fminf(ao, a.aold ? a.aold[i2] : 0.0f);
 
@@ -270,11 +248,8 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
     const float bI = __fmul_rn(__fsqrt_rn(d2), GT_RADIUS_MARGIN);
     const float dacc_amin = __fmul_rn(a.delta_acc, ao);
 
-    park[0] = pi;
-    park[1] = pi2;
-    park[2] = make_float4(0.f, 0.f, 0.f, 0.f);  // sums (x, y, z, potential) of pi
-    park[3] = make_float4(0.f, 0.f, 0.f, 0.f);  // sums of the lane's second-pass member
-    __syncwarp();
+    float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f;
+    float bx = 0.f, by = 0.f, bz = 0.f, qh = 0.f;  // the second member's sums
     int list_n = 0;
     // the list, structure of arrays: x, y, z, m of entry e at lx[e], ly[e], lz[e], lw[e]
     float *ly = lx + LIST_CAP, *lz = lx + 2 * LIST_CAP, *lw = lx + 3 * LIST_CAP;
@@ -310,21 +285,11 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
             sx_ = __fadd_rn(sx.x, sx.y); sy_ = __fadd_rn(sy.x, sy.y); sz_ = __fadd_rn(sz.x, sz.y);
             sp_ = -__fadd_rn(sp.x, sp.y);
         };
-        {
-            // S lanes per i-particle: lane sub takes quads sub, sub + S, ...; a group of more
-            // than 32 has S = 1 here, then runs its other members in a second pass
-            const float4 p1 = park[0];
-            float4 s1 = park[2];
-            run(p1, s1.x, s1.y, s1.z, s1.w, sub, S);
-            park[2] = s1;
-        }
-        if (two) {
-            int logS2, slot2, sub2;
-            const bool v2 = second(logS2, slot2, sub2);
-            const float4 p2 = ((const float4 *)(lx + 4 * LIST_CAP))[PARK * (v2 ? slot2 : 0) + 1];
-            float4 s2 = park[3];
-            run(p2, s2.x, s2.y, s2.z, s2.w, sub2, 1 << logS2);
-            park[3] = s2;
+        if (two) {  // both members of the lane over every pair, one after the other
+            run(pi, ax, ay, az, ph, 0, 1);
+            run(pi2, bx, by, bz, qh, 0, 1);
+        } else {  // S lanes per i-particle: lane sub takes quads sub, sub + S, ...
+            run(pi, ax, ay, az, ph, sub, S);
         }
         n_inter += (unsigned long long)list_n * cnt;
         list_n = 0;
@@ -506,32 +471,19 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
         return;
     }
     flush();
-    // the S lanes of a member add their shares into its first lane (butterfly)
-    auto gather = [&](int logs, float4 &t) {
-        for (int o = 1; o < (1 << logs); o <<= 1) {
-            t.x += __shfl_xor_sync(FULL, t.x, o);
-            t.y += __shfl_xor_sync(FULL, t.y, o);
-            t.z += __shfl_xor_sync(FULL, t.z, o);
-            t.w += __shfl_xor_sync(FULL, t.w, o);
-        }
-    };
-    {
-        float4 t = park[2];
-        gather(__ffs(S) - 1, t);
-        if (sub == 0 && have) {
-            const float phi = fmaf(park[0].w, a.inv_eps, t.w);
-            a.acc[kk] = make_float4(a.G * t.x, a.G * t.y, a.G * t.z, a.G * phi);
-        }
+    for (int o = 1; o < S; o <<= 1) {
+        ax += __shfl_xor_sync(FULL, ax, o);
+        ay += __shfl_xor_sync(FULL, ay, o);
+        az += __shfl_xor_sync(FULL, az, o);
+        ph += __shfl_xor_sync(FULL, ph, o);
     }
-    if (two) {
-        int logS2, slot2, sub2;
-        const bool v2 = second(logS2, slot2, sub2);
-        float4 t = park[3];
-        gather(logS2, t);
-        if (v2 && sub2 == 0) {
-            const float phi = fmaf(((const float4 *)(lx + 4 * LIST_CAP))[PARK * slot2 + 1].w, a.inv_eps, t.w);
-            a.acc[a0 + 32u + (uint32_t)slot2] = make_float4(a.G * t.x, a.G * t.y, a.G * t.z, a.G * phi);
-        }
+    if (sub == 0 && have) {
+        const float phi = fmaf(pi.w, a.inv_eps, ph);
+        a.acc[kk] = make_float4(a.G * ax, a.G * ay, a.G * az, a.G * phi);
+    }
+    if (have2) {
+        const float phi = fmaf(pi2.w, a.inv_eps, qh);
+        a.acc[kk2] = make_float4(a.G * bx, a.G * by, a.G * bz, a.G * phi);
     }
 }
 
@@ -547,9 +499,9 @@ __device__ __forceinline__ int system_of(const uint32_t *gprefix, int nsys, uint
 }
 
 __global__ __launch_bounds__(WT, GT_WALK_MINB) void k_walk(WalkArgs a) {
-    extern __shared__ __align__(16) float walk_sm[];
+    __shared__ __align__(16) float list_sm[NWARP][4 * LIST_CAP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *list = walk_sm + (size_t)warp * WARP_SM_FLOATS;
+    float *list = list_sm[warp];
     uint32_t *q = a.queue + (size_t)(blockIdx.x * NWARP + warp) * (size_t)a.qcap;
     const uint32_t na = a.ctl->n_active;
     const uint32_t gmax = (uint32_t)a.gmax;
@@ -576,10 +528,10 @@ __global__ __launch_bounds__(WT, 3) void k_walk_batch(const WalkArgs *__restrict
                                                       const uint32_t *__restrict__ gprefix,
                                                       unsigned int *group_next, uint32_t *queue, int qcap,
                                                       int mac) {
-    extern __shared__ __align__(16) float walk_sm[];
+    __shared__ __align__(16) float list_sm[NWARP][4 * LIST_CAP];
     __shared__ WalkArgs sargs[NWARP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *list = walk_sm + (size_t)warp * WARP_SM_FLOATS;
+    float *list = list_sm[warp];
     uint32_t *q = queue + (size_t)(blockIdx.x * NWARP + warp) * (size_t)qcap;
     const uint32_t total = gprefix[nsys];
     for (;;) {
@@ -636,16 +588,9 @@ __global__ void k_batch_prefix(DevCtl *const *__restrict__ ctls, const WalkArgs 
 
 }  // namespace
 
-// the walk kernels' dynamic shared memory above the default limit, on the current device
-void walk_init() {
-    cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WALK_SMEM);
-    cudaFuncSetAttribute(k_walk_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WALK_SMEM);
-}
-
 int gt_walk_blocks(int nsm) {
-    walk_init();
     int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk, WT, WALK_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk, WT, 0);
     if (per < 1) per = 1;
     return per * nsm;
 }
@@ -653,7 +598,7 @@ int gt_walk_blocks(int nsm) {
 int gt_walk_warps_per_block() { return NWARP; }
 
 void gt_launch_walk(const WalkArgs &a, int nblocks, cudaStream_t st) {
-    { k_walk<<<nblocks, WT, WALK_SMEM, st>>>(a); gt_note_launches(1); }
+    { k_walk<<<nblocks, WT, 0, st>>>(a); gt_note_launches(1); }
 }
 
 void gt_launch_walk_batch(DevCtl *const *ctls, const WalkArgs *args, int nsys, uint32_t *gprefix,
@@ -661,5 +606,5 @@ void gt_launch_walk_batch(DevCtl *const *ctls, const WalkArgs *args, int nsys, u
                           cudaStream_t st) {
     if (nsys <= 0) return;
     { k_batch_prefix<<<1, 32, 0, st>>>(ctls, args, nsys, gprefix, group_next); gt_note_launches(1); }
-    { k_walk_batch<<<nblocks, WT, WALK_SMEM, st>>>(args, nsys, gprefix, group_next, queue, qcap, mac); gt_note_launches(1); }
+    { k_walk_batch<<<nblocks, WT, 0, st>>>(args, nsys, gprefix, group_next, queue, qcap, mac); gt_note_launches(1); }
 }
