@@ -19,7 +19,15 @@ from . import build as _build
 from . import gothic as g
 from . import ics
 
-MODELS = {"m31": ics.andromeda_like, "nfw": ics.nfw, "plummer": ics.plummer}
+def _uniform(n: int, seed: int = 7):
+    """Particles uniform in the unit cube at rest (a shallow tree of nearly equal leaves)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    pos = rng.uniform(0.0, 1.0, (n, 3)).astype(np.float32).astype(np.float64)
+    return pos, np.zeros_like(pos), np.full(n, np.float32(1.0 / n)), 1.0 / 256
+
+
+MODELS = {"m31": ics.andromeda_like, "nfw": ics.nfw, "plummer": ics.plummer, "uniform": _uniform}
 
 
 KNOBS = {}  # parameter overrides from the command line
@@ -75,8 +83,10 @@ def case_build(model: str, n: int, seed: int, repeat: int) -> str:
         s.build_tree()
     s.sync()
     tm = s.timers()
+    st = s.stats()
     s.close()
-    return f"build {model} n={n} " + " ".join(f"{k}_ms={v[0] / max(v[1], 1):.3f}" for k, v in tm.items() if v[1])
+    return (f"build {model} n={n} nodes={st['n_nodes']} depth={st['depth']} "
+            + " ".join(f"{k}_ms={v[0] / max(v[1], 1):.3f}" for k, v in tm.items() if v[1]))
 
 
 def case_steps(model: str, n: int, seed: int, steps: int) -> str:
