@@ -12,7 +12,8 @@
  *     error word; gt_sync_status() or gt_get_stats() reports them.
  *   - The caller owns all memory.  A system lives inside one workspace the caller
  *     allocates (gt_workspace_bytes) and hands over; the library never calls
- *     cudaMalloc/cudaFree for a system.  Pointers named d_* must be device
+ *     cudaMalloc/cudaFree for a system (only gt_block_step's look-ahead takes 16
+ *     bytes of pinned host memory, once per system).  Pointers named d_* must be device
  *     pointers; pointers named p_* may be host (pageable or pinned) or device
  *     pointers (copied with cudaMemcpyAsync, kind inferred from the address).
  *   - Particle order: the library keeps particles sorted by their space-filling
@@ -223,7 +224,15 @@ GT_API int gt_start(gt_system *sys, const float *p_aold_boot, gt_stream stream);
  * the old topology, Sec. 2.6); select the active particles (t0 + ticks(level)
  * == T); walk them; correct their velocities, assign new levels (a shorter
  * step at once, a longer one by one level when T is aligned to it) and give
- * the next half kick.  Fully asynchronous: no host synchronisation. */
+ * the next half kick.  With a fixed rebuild interval it is fully asynchronous
+ * (no host synchronisation).  With the automatic interval (rebuild_every = 0)
+ * the on-line tuners read the previous step's times and counts, so it first
+ * waits for that step to finish; to keep the device busy meanwhile, every such
+ * step ends by enqueuing the prediction (A8) of the next one (a look-ahead into
+ * the system's scratch positions, with the control words the next call reads
+ * copied to 16 bytes of mapped pinned host memory, allocated once per system).
+ * The next gt_block_step on the same stream uses it; any call that changes the
+ * state or the tree drops it.  Results are the same bit for bit either way. */
 GT_API int gt_block_step(gt_system *sys, gt_stream stream);
 
 /* Resume a block-step integration (checkpoint/restart, or a caller-driven
@@ -252,17 +261,20 @@ GT_API int gt_correct(gt_system *sys, const uint32_t *d_active, int64_t n_active
 
 /* Run block steps until the next block time would exceed T_end (ticks of the
  * finest step); *steps (may be NULL) receives the number taken.  Reads the
- * next block time back after every step (synchronises per step).  One full
- * block-step cycle is T_end = the next multiple of 2^(L-1). */
+ * next block time back after every step (waits for every step: for the words
+ * the look-ahead of gt_block_step mirrors to the host, or else for the stream).
+ * One full block-step cycle is T_end = the next multiple of 2^(L-1). */
 GT_API int gt_advance(gt_system *sys, int64_t T_end, int64_t *steps, gt_stream stream);
 
 /* Per-phase device timers (CUDA events around each phase of gt_block_step and
  * the passes of gt_start; the paper monitors per-function times on the fly,
  * Sec. 1, Sec. 2.4, Sec. 2.6).  Phases: 0 predict, 1 keys+sort, 2 permute,
  * 3 tree build, 4 pseudo j-particles, 5 active set, 6 walk, 7 correct.
- * gt_profile(sys, 1) enables and zeroes them; timing is read at the
- * synchronisations of gt_advance / gt_get_timers.  ms_out[8] total
- * milliseconds, launches_out[8] number of timed phase executions. */
+ * gt_profile(sys, 1) enables and zeroes them; timing is read at the waits of
+ * gt_block_step (automatic interval; with a fixed interval and timers on, each
+ * step waits for the previous one to read them), gt_advance and gt_get_timers.
+ * A prediction enqueued ahead of its step counts once it has run.  ms_out[8]
+ * total milliseconds, launches_out[8] number of timed phase executions. */
 #define GT_NPHASES 8
 GT_API int gt_profile(gt_system *sys, int enable);
 GT_API int gt_get_timers(gt_system *sys, double *ms_out, int64_t *launches_out, gt_stream stream);

@@ -168,18 +168,30 @@ void ph_end(gt_system *s, int p, cudaStream_t st) {
     }
 }
 
-// fold the finished phases' times in (the stream must have been synchronised)
-void ph_collect(gt_system *s) {
+void ph_add(gt_system *s, int p, cudaEvent_t b, cudaEvent_t e) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, b, e) == cudaSuccess) {
+        s->prof.ms[p] += ms;
+        s->prof.last_ms[p] = ms;
+        s->prof.cnt[p] += 1;
+    }
+}
+
+// Fold the finished phases' times in: every phase recorded since the last call, and
+// the predictions enqueued ahead of their step -- both of them (ahead_slot < 0: the
+// stream has been synchronised) or only the one of parity ahead_slot (the other may
+// still be running).
+void ph_collect(gt_system *s, int ahead_slot = -1) {
     if (!timing(s)) return;
     for (int p = 0; p < GT_NPHASES; p++) {
         if (!s->prof.ran[p]) continue;
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, s->prof.b[p], s->prof.e[p]) == cudaSuccess) {
-            s->prof.ms[p] += ms;
-            s->prof.last_ms[p] = ms;
-            s->prof.cnt[p] += 1;
-        }
+        ph_add(s, p, s->prof.b[p], s->prof.e[p]);
         s->prof.ran[p] = false;
+    }
+    for (int q = 0; q < 2; q++) {
+        if (!s->prof.aran[q] || (ahead_slot >= 0 && q != ahead_slot)) continue;
+        ph_add(s, PH_PREDICT, s->prof.ab[q], s->prof.ae[q]);
+        s->prof.aran[q] = false;
     }
 }
 
@@ -187,8 +199,45 @@ int ensure_events(gt_system *s) {
     if (s->prof.created) return GT_OK;
     for (int p = 0; p < GT_NPHASES; p++)
         if (cudaEventCreate(&s->prof.b[p]) || cudaEventCreate(&s->prof.e[p])) return GT_ECUDA;
+    for (int q = 0; q < 2; q++)
+        if (cudaEventCreate(&s->prof.ab[q]) || cudaEventCreate(&s->prof.ae[q])) return GT_ECUDA;
     s->prof.created = true;
     return GT_OK;
+}
+
+// The look-ahead's mapped host words and events, made on first use; false if they
+// cannot be had (the block step then reads the control words after a stream sync).
+bool ahead_ready(gt_system *s) {
+    if (s->mirror) return true;
+    if (s->mirror_tried) return false;
+    s->mirror_tried = true;
+    void *h = nullptr, *d = nullptr;
+    if (cudaHostAlloc(&h, sizeof(StepMirror), cudaHostAllocMapped) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ahead_mirror, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ahead_done, cudaEventDisableTiming) != cudaSuccess) {
+        if (s->ahead_mirror) cudaEventDestroy(s->ahead_mirror);
+        if (s->ahead_done) cudaEventDestroy(s->ahead_done);
+        s->ahead_mirror = s->ahead_done = nullptr;
+        cudaFreeHost(h);
+        cudaGetLastError();
+        return false;
+    }
+    s->mirror = (StepMirror *)h;
+    s->mirror_dev = (StepMirror *)d;
+    return true;
+}
+
+// Forget the prediction enqueued ahead (the state or the tree is about to change, or
+// the next step runs on another stream); work on another stream is ordered after it,
+// since it still writes posm_tmp.
+void drop_ahead(gt_system *s, cudaStream_t st) {
+    if (!s->ahead) return;
+    if (st != s->ahead_st) cudaStreamWaitEvent(st, s->ahead_done, 0);
+    s->ahead = false;
 }
 
 // After a synchronised block step: feed its walk time (and, after a rebuild, the
@@ -439,12 +488,16 @@ WalkArgs gt_sys_walk_args(const gt_system *s, const uint32_t *active, const floa
 
 void gt_sys_aold_from_acc(gt_system *s, cudaStream_t st) { gt_launch_aold(s->acc_out, s->n, s->st[0].aold, st); }
 
-void gt_sys_step_pre(gt_system *s, cudaStream_t st, bool rebuild) {
+void gt_sys_step_pre(gt_system *s, cudaStream_t st, bool rebuild, bool predicted) {
     const int64_t n = s->n;
     gt_launch_prepare(s->ctl, 1, st);
-    ph_begin(s, PH_PREDICT, st);
-    gt_launch_predict(s->st[0], n, s->ctl, rebuild ? s->posm_tmp : s->posm, st);
-    ph_end(s, PH_PREDICT, st);
+    if (!predicted) {
+        ph_begin(s, PH_PREDICT, st);
+        gt_launch_predict(s->st[0], n, s->ctl, rebuild ? s->posm_tmp : s->posm, st);
+        ph_end(s, PH_PREDICT, st);
+    } else if (!rebuild) {
+        std::swap(s->posm, s->posm_tmp);  // the prediction enqueued ahead went to posm_tmp
+    }
     if (rebuild) {
         build_tree(s, st, s->posm_tmp);
     } else {
@@ -550,11 +603,22 @@ int gt_system_create(gt_system **out, int64_t n, const gt_params *prm, void *d_w
 }
 
 int gt_system_destroy(gt_system *s) {
-    if (s && s->prof.created)
+    if (s && s->ahead) cudaEventSynchronize(s->ahead_done);  // it writes the mapped words and the workspace
+    if (s && s->prof.created) {
         for (int p = 0; p < GT_NPHASES; p++) {
             cudaEventDestroy(s->prof.b[p]);
             cudaEventDestroy(s->prof.e[p]);
         }
+        for (int q = 0; q < 2; q++) {
+            cudaEventDestroy(s->prof.ab[q]);
+            cudaEventDestroy(s->prof.ae[q]);
+        }
+    }
+    if (s && s->mirror) {
+        cudaEventDestroy(s->ahead_mirror);
+        cudaEventDestroy(s->ahead_done);
+        cudaFreeHost(s->mirror);
+    }
     delete s;
     return GT_OK;
 }
@@ -577,6 +641,7 @@ int gt_set_state(gt_system *s, const double *p_pos, const double *p_vel, const f
                  gt_stream stream) {
     if (!s || (s->n > 0 && (!p_pos || !p_vel || !p_mass))) return GT_EINVAL;
     cudaStream_t st = S(stream);
+    drop_ahead(s, st);
     const int64_t n = s->n;
     State &t = s->st[0];
     if (n > 0) {
@@ -595,6 +660,7 @@ int gt_set_state(gt_system *s, const double *p_pos, const double *p_vel, const f
 
 int gt_build_tree(gt_system *s, gt_stream stream) {
     if (!s) return GT_EINVAL;
+    drop_ahead(s, S(stream));
     build_tree(s, S(stream), s->posm);
     return last_cuda();
 }
@@ -605,6 +671,7 @@ int gt_accel_active(gt_system *s, const uint32_t *d_active, int64_t n_active, co
     if (!d_active && n_active != s->n) return GT_EINVAL;
     if (!s->have_tree) return GT_ESTATE;
     cudaStream_t st = S(stream);
+    drop_ahead(s, st);
     const float *aold = d_aold ? d_aold : s->st[0].aold;
     if (!d_active) {
         walk_all(s, aold, (float4 *)d_acc, s->prm.mac, st);
@@ -624,6 +691,7 @@ int gt_accel_active(gt_system *s, const uint32_t *d_active, int64_t n_active, co
 int gt_start(gt_system *s, const float *p_aold_boot, gt_stream stream) {
     if (!s) return GT_EINVAL;
     cudaStream_t st = S(stream);
+    drop_ahead(s, st);
     const int64_t n = s->n;
     build_tree(s, st, s->posm);
     State &t = s->st[0];
@@ -647,17 +715,28 @@ int gt_block_step(gt_system *s, gt_stream stream) {
     cudaStream_t st = S(stream);
     const int64_t n = s->n;
     if (n == 0) return GT_OK;
+    if (s->ahead && st != s->ahead_st) drop_ahead(s, st);
+    const bool predicted = s->ahead;  // this step's prediction is already enqueued
+    s->ahead = false;
     bool rebuild;
     if (s->prm.rebuild_every == 0) {  // automatic interval (Sec. 2.6)
         if (ensure_events(s)) return GT_ECUDA;
         unsigned na = 0;
         unsigned long long tn = 0;
-        if (cudaMemcpyAsync(&na, &s->ctl->n_active, 4, cudaMemcpyDeviceToHost, st) ||
-            cudaMemcpyAsync(&tn, &s->ctl->tnext_acc, 8, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
+        if (predicted) {  // the previous step has finished once its mirror is written
+            if (cudaEventSynchronize(s->ahead_mirror) != cudaSuccess) return GT_ECUDA;
+            const volatile StepMirror *m = s->mirror;
+            na = m->n_active;
+            tn = m->tnext_acc;
+        } else if (cudaMemcpyAsync(&na, &s->ctl->n_active, 4, cudaMemcpyDeviceToHost, st) ||
+                   cudaMemcpyAsync(&tn, &s->ctl->tnext_acc, 8, cudaMemcpyDeviceToHost, st) ||
+                   cudaStreamSynchronize(st)) {
             return GT_ECUDA;
+        }
         if (s->steps > 0) {
             const bool was_rebuild = s->last_rebuilt;
-            ph_collect(s);
+            // this step's own prediction (parity steps & 1) may still be running
+            ph_collect(s, predicted ? (int)((s->steps - 1) & 1) : -1);
             tune_after_step(s, was_rebuild, na);
             if (s->prm.r_crit < 0.0f) rcrit_after_step(s, na);
         }
@@ -670,13 +749,35 @@ int gt_block_step(gt_system *s, gt_stream stream) {
         const double n_opt = s->tune.n_opt < cap ? s->tune.n_opt : cap;
         rebuild = s->steps == 0 || (double)s->tune.since >= std::ceil(n_opt);
     } else {
+        if (s->prof.on) {  // profiling: the previous step's phase times, before their events are reused
+            if (cudaStreamSynchronize(st) != cudaSuccess) return GT_ECUDA;
+            ph_collect(s);
+        }
         rebuild = s->steps % s->prm.rebuild_every == 0;
     }
     s->last_rebuilt = rebuild;
-    gt_sys_step_pre(s, st, rebuild);
+    gt_sys_step_pre(s, st, rebuild, predicted);
     State &t = s->st[0];
     walk(s, s->active, t.aold, s->acc_out, s->prm.mac, st);
     gt_sys_step_post(s, st);
+    // Look-ahead (automatic interval; the tuners wait for every step): the control
+    // words the next call reads, then the prediction of every particle to the next
+    // block time (A8 does not depend on the tuners), which then runs while the host
+    // tunes and enqueues the rest of that step.
+    if (s->prm.rebuild_every == 0 && !s->fixed_buffers && ahead_ready(s)) {
+        gt_launch_mirror(s->ctl, s->mirror_dev, st);
+        cudaEventRecord(s->ahead_mirror, st);
+        const int q = (int)(s->steps & 1);  // parity of the step it belongs to
+        if (timing(s)) cudaEventRecord(s->prof.ab[q], st);
+        gt_launch_predict(t, n, s->ctl, s->posm_tmp, st, true);
+        if (timing(s)) {
+            cudaEventRecord(s->prof.ae[q], st);
+            s->prof.aran[q] = true;
+        }
+        cudaEventRecord(s->ahead_done, st);
+        s->ahead = true;
+        s->ahead_st = st;
+    }
     return last_cuda();
 }
 
@@ -687,6 +788,7 @@ int gt_set_integrator_state(gt_system *s, const uint8_t *p_level, const int64_t 
     int e;
     if (frexp(dt_max, &e) != 0.5) return GT_EINVAL;
     cudaStream_t st = S(stream);
+    drop_ahead(s, st);
     const int64_t n = s->n;
     const int L = s->prm.levels;
     State &t = s->st[0];
@@ -715,6 +817,7 @@ int gt_predict(gt_system *s, int64_t T, float *d_posm, gt_stream stream) {
     if (!s || !d_posm || T < 0) return GT_EINVAL;
     if (!s->started) return GT_ESTATE;
     cudaStream_t st = S(stream);
+    drop_ahead(s, st);
     gt_launch_set_tnext(s->ctl, T, st);
     gt_launch_predict(s->st[0], s->n, s->ctl, (float4 *)d_posm, st);
     return last_cuda();
@@ -726,6 +829,7 @@ int gt_correct(gt_system *s, const uint32_t *d_active, int64_t n_active, const f
         return GT_EINVAL;
     if (!s->started) return GT_ESTATE;
     cudaStream_t st = S(stream);
+    drop_ahead(s, st);
     State &t = s->st[0];
     gt_launch_set_tnext(s->ctl, T, st);
     gt_launch_set_nactive(s->ctl, (unsigned)n_active, st);
@@ -745,10 +849,17 @@ int gt_advance(gt_system *s, int64_t T_end, int64_t *steps, gt_stream stream) {
     for (;;) {
         unsigned long long tn = 0;
         int err = 0;
-        if (cudaMemcpyAsync(&tn, &s->ctl->tnext_acc, 8, cudaMemcpyDeviceToHost, st) ||
-            cudaMemcpyAsync(&err, &s->ctl->err, 4, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
-            return GT_ECUDA;
-        ph_collect(s);
+        if (s->ahead && s->ahead_st == st) {  // the words mirrored after the last step
+            if (cudaEventSynchronize(s->ahead_mirror) != cudaSuccess) return GT_ECUDA;
+            const volatile StepMirror *m = s->mirror;
+            tn = m->tnext_acc;
+            err = m->err;
+        } else {
+            if (cudaMemcpyAsync(&tn, &s->ctl->tnext_acc, 8, cudaMemcpyDeviceToHost, st) ||
+                cudaMemcpyAsync(&err, &s->ctl->err, 4, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
+                return GT_ECUDA;
+            ph_collect(s);
+        }
         if (err) return err;
         if (s->n == 0 || tn == ~0ull || (long long)tn > T_end) break;
         const int rc = gt_block_step(s, stream);
@@ -768,6 +879,7 @@ int gt_profile(gt_system *s, int enable) {
         s->prof.cnt[p] = 0;
         s->prof.ran[p] = false;
     }
+    s->prof.aran[0] = s->prof.aran[1] = false;
     return GT_OK;
 }
 

@@ -265,7 +265,18 @@ void gt_launch_pseudo(Nodes nd, int64_t cap, const float4 *posm, DevCtl *ctl, in
 // integrate.cu
 void gt_launch_prepare(DevCtl *ctl, int begin_step, cudaStream_t st);
 void gt_launch_set_nactive(DevCtl *ctl, unsigned int n_active, cudaStream_t st);
-void gt_launch_predict(const State &s, int64_t n, const DevCtl *ctl, float4 *posm, cudaStream_t st);
+// T of the prediction: the current step's block time, or (ahead) the next one, still
+// in tnext_acc before k_prepare moves it
+void gt_launch_predict(const State &s, int64_t n, const DevCtl *ctl, float4 *posm, cudaStream_t st,
+                       bool ahead = false);
+// The control words the host reads between block steps, copied by the device into
+// (mapped, pinned) host memory.
+struct StepMirror {
+    unsigned long long tnext_acc;  // block time of the next step
+    unsigned int n_active;         // i-particles of the step just finished
+    int err;                       // latched device error
+};
+void gt_launch_mirror(const DevCtl *ctl, StepMirror *dst, cudaStream_t st);
 void gt_launch_load(const State &s, float4 *posm, int64_t n, cudaStream_t st);
 void gt_launch_permute(const State &src, const State &dst, const float4 *posm_in, float4 *posm_out,
                        const uint32_t *perm, int64_t n, cudaStream_t st);

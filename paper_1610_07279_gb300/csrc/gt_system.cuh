@@ -11,6 +11,10 @@ struct PhaseTimers {
     bool on = false, created = false;
     cudaEvent_t b[GT_NPHASES]{}, e[GT_NPHASES]{};
     bool ran[GT_NPHASES]{};
+    // the predictions enqueued ahead of their block step, by the step's parity: one is
+    // still running while the other's times are read
+    cudaEvent_t ab[2]{}, ae[2]{};
+    bool aran[2]{};
     double ms[GT_NPHASES]{};
     double last_ms[GT_NPHASES]{};  // the most recent execution of each phase
     long long cnt[GT_NPHASES]{};
@@ -90,6 +94,16 @@ struct gt_system {
     uint32_t *queue = nullptr;    // the walk queue (a batch's shared queue for batch members)
     int64_t queue_entries = 0;
     DevCtl *ctl = nullptr;
+    // Look-ahead of gt_block_step (automatic rebuild interval, standalone systems): after
+    // a step the device copies the control words the next step's tuners read into
+    // mapped host memory (event ahead_mirror) and predicts every particle to the next
+    // block time into posm_tmp (event ahead_done); the next call waits only for the
+    // mirror, so the prediction runs while the host tunes and enqueues the rest.
+    StepMirror *mirror = nullptr, *mirror_dev = nullptr;  // pinned, mapped; 16 B
+    bool mirror_tried = false;
+    cudaEvent_t ahead_mirror = nullptr, ahead_done = nullptr;
+    bool ahead = false;            // posm_tmp holds the prediction for the next step
+    cudaStream_t ahead_st = nullptr;
 };
 
 constexpr size_t GT_WS_ALIGN = 256;
@@ -119,6 +133,7 @@ void gt_sys_aold_from_acc(gt_system *s, cudaStream_t st);
 void gt_sys_start_levels(gt_system *s, cudaStream_t st);
 // One block step in three parts around the walk: predict, rebuild or pseudo j, active set
 // (pre); the groups of the active set (groups); correct, levels, next block time (post).
-void gt_sys_step_pre(gt_system *s, cudaStream_t st, bool rebuild);
+// predicted: the prediction for this step is already in posm_tmp (enqueued ahead)
+void gt_sys_step_pre(gt_system *s, cudaStream_t st, bool rebuild, bool predicted = false);
 void gt_sys_step_groups(gt_system *s, cudaStream_t st);
 void gt_sys_step_post(gt_system *s, cudaStream_t st);

@@ -35,13 +35,21 @@ __global__ void k_prepare(DevCtl *ctl, int begin_step) {
 
 __global__ void k_set_nactive(DevCtl *ctl, unsigned int n_active) { ctl->n_active = n_active; }
 
+__global__ void k_mirror(const DevCtl *ctl, StepMirror *dst) {
+    volatile StepMirror *d = dst;
+    d->tnext_acc = ctl->tnext_acc;
+    d->n_active = ctl->n_active;
+    d->err = ctl->err;
+    __threadfence_system();
+}
+
 // Two particles per thread with 16-byte loads (n even, so that every array of the state,
 // and the second and third coordinate arrays inside its block, start 16-byte aligned).
 __global__ __launch_bounds__(256) void k_predict2(State s, long long n, const DevCtl *__restrict__ ctl,
-                                                  float4 *__restrict__ posm) {
+                                                  float4 *__restrict__ posm, int ahead) {
     const long long i = 2 * (blockIdx.x * 256ll + threadIdx.x);
     if (i >= n) return;
-    const long long T = (long long)ctl->tnext;
+    const long long T = (long long)(ahead ? ctl->tnext_acc : ctl->tnext);
     const int k = (int)((__double_as_longlong(ctl->dt_max) >> 52) & 0x7ff) - 1023 - ctl->levels_m1;
     const longlong2 t0 = *(const longlong2 *)&s.t0[i];
     const double dt0 = ctl->dt_max > 0.0 ? i2d_scaled(T - t0.x, k) : 0.0;
@@ -56,10 +64,10 @@ __global__ __launch_bounds__(256) void k_predict2(State s, long long n, const De
 }
 
 __global__ __launch_bounds__(256) void k_predict(State s, long long n, const DevCtl *__restrict__ ctl,
-                                                 float4 *__restrict__ posm) {
+                                                 float4 *__restrict__ posm, int ahead) {
     const long long i = blockIdx.x * 256ll + threadIdx.x;
     if (i >= n) return;
-    const long long T = (long long)ctl->tnext;
+    const long long T = (long long)(ahead ? ctl->tnext_acc : ctl->tnext);
     // dt = (T - t0) dt_min with dt_min = dt_max 2^-(L-1) a power of two: exact, so it is
     // built from the bits; only the three fused multiply-adds run on the FP64 pipe
     const int k = (int)((__double_as_longlong(ctl->dt_max) >> 52) & 0x7ff) - 1023 - ctl->levels_m1;
@@ -501,13 +509,17 @@ void gt_launch_set_nactive(DevCtl *ctl, unsigned int n_active, cudaStream_t st) 
     { k_set_nactive<<<1, 1, 0, st>>>(ctl, n_active); gt_note_launches(1); }
 }
 
-void gt_launch_predict(const State &s, int64_t n, const DevCtl *ctl, float4 *posm, cudaStream_t st) {
+void gt_launch_predict(const State &s, int64_t n, const DevCtl *ctl, float4 *posm, cudaStream_t st, bool ahead) {
     if (n <= 0) return;
     const bool aligned = ((uintptr_t)s.rx | (uintptr_t)s.ry | (uintptr_t)s.rz | (uintptr_t)s.vx | (uintptr_t)s.vy |
                           (uintptr_t)s.vz | (uintptr_t)s.t0 | (uintptr_t)s.mass) % 16 == 0;
-    if (n % 2 == 0 && aligned) k_predict2<<<nblk(n / 2), 256, 0, st>>>(s, n, ctl, posm);
-    else k_predict<<<nblk(n), 256, 0, st>>>(s, n, ctl, posm);
+    if (n % 2 == 0 && aligned) k_predict2<<<nblk(n / 2), 256, 0, st>>>(s, n, ctl, posm, ahead ? 1 : 0);
+    else k_predict<<<nblk(n), 256, 0, st>>>(s, n, ctl, posm, ahead ? 1 : 0);
     gt_note_launches(1);
+}
+
+void gt_launch_mirror(const DevCtl *ctl, StepMirror *dst, cudaStream_t st) {
+    { k_mirror<<<1, 1, 0, st>>>(ctl, dst); gt_note_launches(1); }
 }
 
 void gt_launch_load(const State &s, float4 *posm, int64_t n, cudaStream_t st) {

@@ -470,7 +470,17 @@ __global__ __launch_bounds__(256) void k_cell_fill(Nodes nd, long long cap, DevC
 // chunk of level l + 1 is finished: those hold smaller tickets, so the blocks holding
 // them are running and the wait ends (it is bounded all the same).  Leaves wait for
 // nothing, so their FP64 sums fill the time a level's cells wait for the one below.
+#ifndef GT_PSEUDO_PU
+#define GT_PSEUDO_PU 2  // a leaf's particles loaded per round
+#endif
+#ifndef GT_PSEUDO_CU
+#define GT_PSEUDO_CU 2  // a cell's children loaded per round
+#endif
+#ifndef GT_PSEUDO_MINB
+#define GT_PSEUDO_MINB 8  // resident blocks per SM (the grid) the register budget is sized for
+#endif
 constexpr int PL = 128;  // nodes per chunk, one per thread
+constexpr uint32_t PU = GT_PSEUDO_PU, CU = GT_PSEUDO_CU;
 constexpr int PSEUDO_LAG = 1;  // levels of leaves between a level's cells and the level below
 constexpr int NSEG = 2 * GT_TREE_LEVELS;
 
@@ -485,13 +495,13 @@ __device__ __forceinline__ void pseudo_leaf(const Nodes &nd, const float4 *__res
     double m = WITH_MASS ? 0.0 : nd.sum[c].m, sx = 0.0, sy = 0.0, sz = 0.0;
     // in particle order; the loads of four particles go out before their sums
     // (m x is exact in FP64, so the fused form rounds once like + does)
-    for (uint32_t i0 = f; i0 < f + k; i0 += 2) {
-        float4 p[2];
+    for (uint32_t i0 = f; i0 < f + k; i0 += PU) {
+        float4 p[PU];
 #pragma unroll
-        for (uint32_t q = 0; q < 2; q++)
+        for (uint32_t q = 0; q < PU; q++)
             if (i0 + q < f + k) p[q] = posm[i0 + q];
 #pragma unroll
-        for (uint32_t q = 0; q < 2; q++)
+        for (uint32_t q = 0; q < PU; q++)
             if (i0 + q < f + k) {
                 const double mi = f2d(p[q].w);
                 if (WITH_MASS) m = __dadd_rn(m, mi);
@@ -511,13 +521,13 @@ __device__ __forceinline__ void pseudo_leaf(const Nodes &nd, const float4 *__res
         jz = __fdiv_rn(d2f(sz), mf);
     }
     float d2max = 0.0f, b2 = 0.0f;  // b2: B_2 of the multipole MAC
-    for (uint32_t i0 = f; i0 < f + k; i0 += 2) {
-        float4 p[2];
+    for (uint32_t i0 = f; i0 < f + k; i0 += PU) {
+        float4 p[PU];
 #pragma unroll
-        for (uint32_t q = 0; q < 2; q++)
+        for (uint32_t q = 0; q < PU; q++)
             if (i0 + q < f + k) p[q] = posm[i0 + q];
 #pragma unroll
-        for (uint32_t q = 0; q < 2; q++)
+        for (uint32_t q = 0; q < PU; q++)
             if (i0 + q < f + k) {
                 const float d2 = sq3f(__fsub_rn(p[q].x, jx), __fsub_rn(p[q].y, jy), __fsub_rn(p[q].z, jz));
                 if (d2 > d2max) d2max = d2;
@@ -539,17 +549,17 @@ __device__ __forceinline__ void pseudo_cell(const Nodes &nd, uint32_t p) {
     const int32_t ch0 = nd.child[p];
     const uint32_t nch = nd.nchild[p];
     double m = WITH_MASS ? 0.0 : nd.sum[p].m, sx = 0.0, sy = 0.0, sz = 0.0;
-    for (uint32_t q0 = 0; q0 < nch; q0 += 2) {
-        double2 s0[2], s1[2];  // (m, x), (y, z)
+    for (uint32_t q0 = 0; q0 < nch; q0 += CU) {
+        double2 s0[CU], s1[CU];  // (m, x), (y, z)
 #pragma unroll
-        for (uint32_t q = 0; q < 2; q++)
+        for (uint32_t q = 0; q < CU; q++)
             if (q0 + q < nch) {
                 const double2 *cs = (const double2 *)&nd.sum[ch0 + q0 + q];
                 s0[q] = __ldcg(cs);
                 s1[q] = __ldcg(cs + 1);
             }
 #pragma unroll
-        for (uint32_t q = 0; q < 2; q++)
+        for (uint32_t q = 0; q < CU; q++)
             if (q0 + q < nch) {
                 if (WITH_MASS) m = __dadd_rn(m, s0[q].x);
                 sx = __dadd_rn(sx, s0[q].y);
@@ -562,16 +572,16 @@ __device__ __forceinline__ void pseudo_cell(const Nodes &nd, uint32_t p) {
     const float jy = __fdiv_rn(d2f(sy), mf);
     const float jz = __fdiv_rn(d2f(sz), mf);
     float b = 0.0f, b2 = 0.0f;  // b2: B_2 by parallel axes
-    for (uint32_t q0 = 0; q0 < nch; q0 += 2) {
-        float4 cj[2], cw[2];
+    for (uint32_t q0 = 0; q0 < nch; q0 += CU) {
+        float4 cj[CU], cw[CU];
 #pragma unroll
-        for (uint32_t q = 0; q < 2; q++)
+        for (uint32_t q = 0; q < CU; q++)
             if (q0 + q < nch) {
                 cj[q] = __ldcg(&nd.jpos[ch0 + q0 + q]);
                 cw[q] = __ldcg(&nd.walk[ch0 + q0 + q]);
             }
 #pragma unroll
-        for (uint32_t q = 0; q < 2; q++)
+        for (uint32_t q = 0; q < CU; q++)
             if (q0 + q < nch) {
                 const float d2 = sq3f(__fsub_rn(cj[q].x, jx), __fsub_rn(cj[q].y, jy), __fsub_rn(cj[q].z, jz));
                 const float e = __fadd_rn(__fsqrt_rn(d2), cw[q].x);
@@ -586,7 +596,7 @@ __device__ __forceinline__ void pseudo_cell(const Nodes &nd, uint32_t p) {
 }
 
 template <bool WITH_MASS>
-__global__ __launch_bounds__(PL, 8) void k_pseudo(Nodes nd, const float4 *__restrict__ posm, DevCtl *ctl) {
+__global__ __launch_bounds__(PL, GT_PSEUDO_MINB) void k_pseudo(Nodes nd, const float4 *__restrict__ posm, DevCtl *ctl) {
     __shared__ uint32_t seg[NSEG + 1];
     __shared__ uint8_t olvl[NSEG], ocell[NSEG];      // ticket order: segment level and kind
     __shared__ uint32_t ocum[NSEG + 1];              // first ticket of every entry
@@ -709,7 +719,7 @@ void gt_launch_pseudo(Nodes nd, int64_t cap, const float4 *posm, DevCtl *ctl, in
     (void)cap;
     // the ticket and the per-level counters start at zero
     cudaMemsetAsync(&ctl->pl_ticket, 0, sizeof(ctl->pl_ticket) + sizeof(ctl->pl_done), st);
-    if (with_mass) { k_pseudo<true><<<nsm * 8, PL, 0, st>>>(nd, posm, ctl); }
-    else { k_pseudo<false><<<nsm * 8, PL, 0, st>>>(nd, posm, ctl); }
+    if (with_mass) { k_pseudo<true><<<nsm * GT_PSEUDO_MINB, PL, 0, st>>>(nd, posm, ctl); }
+    else { k_pseudo<false><<<nsm * GT_PSEUDO_MINB, PL, 0, st>>>(nd, posm, ctl); }
     gt_note_launches(1);
 }

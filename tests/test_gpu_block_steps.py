@@ -254,3 +254,65 @@ def test_andromeda_2p24_four_block_steps_teacher_forced(env):
     pos, vel, mass, eps = ics.andromeda_like(1 << 24, seed=3)
     prm = _params(g, eps, levels=8, rebuild_every=1, group_max=64, leaf_max=24)
     teacher_forced(env, pos, vel, mass, prm, 4, "m31-2^24")
+
+
+def _state_of(s):
+    st = s.get_state()
+    return {k: st[k] for k in ("pos", "vel", "acc", "aold", "level", "t0", "id")}
+
+
+def test_lookahead_matches_steps_without_it(env):
+    """With the automatic rebuild interval a block step enqueues the next step's
+    prediction (A8) before it returns.  The same steps without the look-ahead (a stream
+    switch before every step drops it) give the same state bit for bit, through steps
+    that refresh the pseudo j-particles on the old tree and one that rebuilds the tree
+    from the prediction made ahead.  The first three steps' decisions do not depend on
+    timings (one rebuild at the start; the group size fixed), the rest use a fixed
+    interval, so both runs take the same steps."""
+    torch, g, O = env
+    pos, vel, mass, eps = ics.plummer(6144, seed=11)
+    runs = []
+    for switch in (False, True):
+        s = g.System(len(mass), _params(g, eps, leaf_max=16, rebuild_every=0))
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        s.stream = streams[0].cuda_stream
+        s.set_state(pos, vel, mass)
+        s.start()
+        trail = []
+        for k in range(6):
+            if k == 3:
+                s.set_params(_params(g, eps, leaf_max=16, rebuild_every=3))
+            if switch:  # another stream, after the last step has finished: nothing is predicted ahead
+                torch.cuda.synchronize()
+                s.stream = streams[(k + 1) % 2].cuda_stream
+            s.block_step()
+            st = s.stats()
+            trail.append((st["T"], st["n_active"], st["interactions"], st["rebuilds"]))
+        torch.cuda.synchronize()
+        runs.append((trail, _state_of(s)))
+        s.close()
+    (ta, sa), (tb, sb) = runs
+    assert ta == tb
+    assert ta[3][3] == ta[2][3] + 1  # the fourth step rebuilt the tree
+    for k in sa:
+        np.testing.assert_array_equal(sa[k], sb[k], err_msg=k)
+
+
+def test_advance_with_lookahead_stops_at_the_end_time(env):
+    """gt_advance reads the next block time from the words mirrored after each step and
+    stops at the last block time not after T_end; the phase timers count every
+    prediction, the one made ahead of a step included."""
+    torch, g, O = env
+    pos, vel, mass, eps = ics.plummer(4096, seed=12)
+    s = g.System(len(mass), _params(g, eps, leaf_max=16, rebuild_every=0, levels=5))
+    s.set_state(pos, vel, mass)
+    s.start()
+    s.profile(True)
+    span = 1 << (5 - 1)
+    k = s.advance(span)
+    st = s.stats()
+    assert st["T"] == span and k == st["block_steps"] and k >= 1
+    tm = s.timers()
+    assert tm["predict"][1] == k + 1  # the k steps' predictions and the one ahead of step k + 1
+    assert tm["walk"][1] == k
+    s.close()
