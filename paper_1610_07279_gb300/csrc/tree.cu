@@ -477,7 +477,7 @@ __global__ __launch_bounds__(256) void k_cell_fill(Nodes nd, long long cap, DevC
 #define GT_PSEUDO_CU 2  // a cell's children loaded per round
 #endif
 #ifndef GT_PSEUDO_MINB
-#define GT_PSEUDO_MINB 8  // resident blocks per SM (the grid) the register budget is sized for
+#define GT_PSEUDO_MINB 6  // resident blocks per SM (the grid) the register budget is sized for
 #endif
 constexpr int PL = 128;  // nodes per chunk, one per thread
 constexpr uint32_t PU = GT_PSEUDO_PU, CU = GT_PSEUDO_CU;
