@@ -1,8 +1,9 @@
 // Step A1: bounding cube and 63-bit Morton keys (Sec. 2.1; Morton key layout of
 // Appendix A: every 3-bit digit is (x, y, z) with x the most significant bit).
 //
-// HBM-bound: the bounding box reads 16 B per particle, the key pass reads 16 B and
-// writes 12 B (key + index).
+// The bounding box reads 16 B per particle, the key pass reads 16 B and writes 12 B
+// (key + index); the key pass is bound by the exact quantisation's integer work, split
+// with the FP64 pipe (one axis there, two on the integer pipe).
 #include <float.h>
 
 #include "gt_internal.cuh"
@@ -97,6 +98,21 @@ __device__ __forceinline__ unsigned long long quantise(float x, float xmin, doub
     return q < QMAX ? q : QMAX;
 }
 
+// The same quantisation with the two roundings on the FP64 pipe (x and xmin widened
+// exactly on the integer pipe; the floor of the non-negative product taken from its
+// bits).  k_keys runs one axis this way and two through quantise(): the FP64 pipe is
+// narrow on this GPU, the integer pipe bounds the pass, so the two share the work.
+__device__ __forceinline__ unsigned long long quantise_fp64(float x, float xmin, double scale) {
+    const double p = __dmul_rn(__dsub_rn(f2d(x), f2d(xmin)), scale);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(p);
+    if (b >> 63) return 0ull;                    // negative (x below xmin: not produced by the bounding box)
+    const int e = (int)(b >> 52) - 1023;         // p = 1.f 2^e
+    if (e < 0) return 0ull;                      // p < 1, zero included
+    if (e >= GT_KEY_LEVELS) return QMAX;         // p >= 2^21 (and inf, nan)
+    const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
+    return m >> (52 - e);
+}
+
 // Peano-Hilbert order (Sec. 2.1, App. A), Skilling's transpose method on the three
 // 21-bit integers: the rotations and reflections are undone from the top bit down, a
 // Gray code runs across the axes, and the transposed bits are interleaved like a Morton
@@ -130,7 +146,7 @@ __global__ __launch_bounds__(256) void k_keys(const float4 *__restrict__ posm, l
     unsigned long long k = 0;
     if (side > 0.0) {
         const float4 p = posm[i];
-        const unsigned long long qx = quantise(p.x, ctl->bbox_min[0], scale);
+        const unsigned long long qx = quantise_fp64(p.x, ctl->bbox_min[0], scale);
         const unsigned long long qy = quantise(p.y, ctl->bbox_min[1], scale);
         const unsigned long long qz = quantise(p.z, ctl->bbox_min[2], scale);
         if (curve == GT_KEY_HILBERT) {
