@@ -168,12 +168,14 @@ void ph_end(gt_system *s, int p, cudaStream_t st) {
     }
 }
 
-void ph_add(gt_system *s, int p, cudaEvent_t b, cudaEvent_t e) {
+void ph_add(gt_system *s, int p, cudaEvent_t b, cudaEvent_t e, bool total = true) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, b, e) == cudaSuccess) {
-        s->prof.ms[p] += ms;
+        if (total) {
+            s->prof.ms[p] += ms;
+            s->prof.cnt[p] += 1;
+        }
         s->prof.last_ms[p] = ms;
-        s->prof.cnt[p] += 1;
     }
 }
 
@@ -185,8 +187,9 @@ void ph_collect(gt_system *s, int ahead_slot = -1) {
     if (!timing(s)) return;
     for (int p = 0; p < GT_NPHASES; p++) {
         if (!s->prof.ran[p]) continue;
-        ph_add(s, p, s->prof.b[p], s->prof.e[p]);
+        ph_add(s, p, s->prof.b[p], s->prof.e[p], !s->prof.before[p]);
         s->prof.ran[p] = false;
+        s->prof.before[p] = false;
     }
     for (int q = 0; q < 2; q++) {
         if (!s->prof.aran[q] || (ahead_slot >= 0 && q != ahead_slot)) continue;
@@ -877,7 +880,8 @@ int gt_profile(gt_system *s, int enable) {
     for (int p = 0; p < GT_NPHASES; p++) {
         s->prof.ms[p] = 0.0;
         s->prof.cnt[p] = 0;
-        s->prof.ran[p] = false;
+        // a phase still to be read keeps feeding the on-line tuners, outside the new totals
+        s->prof.before[p] = s->prof.ran[p];
     }
     s->prof.aran[0] = s->prof.aran[1] = false;
     return GT_OK;

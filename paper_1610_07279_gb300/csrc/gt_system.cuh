@@ -11,6 +11,7 @@ struct PhaseTimers {
     bool on = false, created = false;
     cudaEvent_t b[GT_NPHASES]{}, e[GT_NPHASES]{};
     bool ran[GT_NPHASES]{};
+    bool before[GT_NPHASES]{};  // recorded before the timers were last zeroed: feeds last_ms only
     // the predictions enqueued ahead of their block step, by the step's parity: one is
     // still running while the other's times are read
     cudaEvent_t ab[2]{}, ae[2]{};
