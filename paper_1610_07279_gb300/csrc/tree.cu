@@ -476,6 +476,9 @@ __global__ __launch_bounds__(256) void k_cell_fill(Nodes nd, long long cap, DevC
 #ifndef GT_PSEUDO_CU
 #define GT_PSEUDO_CU 2  // a cell's children loaded per round
 #endif
+#ifndef GT_PSEUDO_COOP
+#define GT_PSEUDO_COOP 16384  // a level's cells with children taken eight lanes each when at most this many
+#endif
 #ifndef GT_PSEUDO_MINB
 #define GT_PSEUDO_MINB 6  // resident blocks per SM (the grid) the register budget is sized for
 #endif
@@ -595,18 +598,89 @@ __device__ __forceinline__ void pseudo_cell(const Nodes &nd, uint32_t p) {
                              __uint_as_float(nch), b2);
 }
 
+// The same cell with eight lanes, one child each (lanes 8g .. 8g + 7 of the warp hold cell
+// g of four): the children's records arrive in one round of loads instead of one per
+// pair of children.  Every lane of the group forms the FP64 sums and the B_2 sum itself,
+// in child order, from its neighbours' values (shuffles), so the operations and their
+// order are those of pseudo_cell; the radius is a maximum, taken across the lanes.  For
+// the levels near the root, whose few cells each wait for the level below.  Every lane
+// of the warp must call it; `valid` marks groups that own a cell.
+template <bool WITH_MASS>
+__device__ __forceinline__ void pseudo_cell_coop(const Nodes &nd, uint32_t p, bool valid) {
+    const unsigned FULL = 0xffffffffu;
+    const uint32_t lane = threadIdx.x & 31u, j = lane & 7u, g0 = lane & ~7u;
+    const int32_t ch0 = valid ? nd.child[p] : 0;
+    const uint32_t nch = valid ? nd.nchild[p] : 0u;
+    const bool has = j < nch;
+    double2 s0 = make_double2(0.0, 0.0), s1 = make_double2(0.0, 0.0);  // (m, x), (y, z)
+    float4 cj = make_float4(0.f, 0.f, 0.f, 0.f), cw = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (has) {
+        const double2 *cs = (const double2 *)&nd.sum[ch0 + j];
+        s0 = __ldcg(cs);
+        s1 = __ldcg(cs + 1);
+        cj = __ldcg(&nd.jpos[ch0 + j]);
+        cw = __ldcg(&nd.walk[ch0 + j]);
+    }
+    double m = (WITH_MASS || !valid) ? 0.0 : nd.sum[p].m, sx = 0.0, sy = 0.0, sz = 0.0;
+#pragma unroll
+    for (uint32_t q = 0; q < 8; q++) {
+        const double cm = __shfl_sync(FULL, s0.x, g0 + q), cx = __shfl_sync(FULL, s0.y, g0 + q);
+        const double cy = __shfl_sync(FULL, s1.x, g0 + q), cz = __shfl_sync(FULL, s1.y, g0 + q);
+        if (q < nch) {
+            if (WITH_MASS) m = __dadd_rn(m, cm);
+            sx = __dadd_rn(sx, cx);
+            sy = __dadd_rn(sy, cy);
+            sz = __dadd_rn(sz, cz);
+        }
+    }
+    const float mf = d2f(m);
+    const float jx = __fdiv_rn(d2f(sx), mf);
+    const float jy = __fdiv_rn(d2f(sy), mf);
+    const float jz = __fdiv_rn(d2f(sz), mf);
+    const float d2 = sq3f(__fsub_rn(cj.x, jx), __fsub_rn(cj.y, jy), __fsub_rn(cj.z, jz));
+    float b = 0.0f;
+    if (has) {
+        const float e = __fadd_rn(__fsqrt_rn(d2), cw.x);
+        if (e > b) b = e;
+    }
+    const float t = __fadd_rn(cw.w, __fmul_rn(cj.w, d2));
+    float b2 = 0.0f;
+#pragma unroll
+    for (uint32_t q = 0; q < 8; q++) {
+        const float tq = __shfl_sync(FULL, t, g0 + q);
+        if (q < nch) b2 = __fadd_rn(b2, tq);
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        const float bo = __shfl_xor_sync(FULL, b, o);
+        if (bo > b) b = bo;
+    }
+    if (valid && j == 0) {
+        nd.sum[p] = DSum4{m, sx, sy, sz};
+        nd.jpos[p] = make_float4(jx, jy, jz, mf);
+        nd.walk[p] = make_float4(__fmul_rn(b, GT_RADIUS_MARGIN), __uint_as_float((uint32_t)ch0),
+                                 __uint_as_float(nch), b2);
+    }
+}
+
 template <bool WITH_MASS>
 __global__ __launch_bounds__(PL, GT_PSEUDO_MINB) void k_pseudo(Nodes nd, const float4 *__restrict__ posm, DevCtl *ctl) {
     __shared__ uint32_t seg[NSEG + 1];
     __shared__ uint8_t olvl[NSEG], ocell[NSEG];      // ticket order: segment level and kind
     __shared__ uint32_t ocum[NSEG + 1];              // first ticket of every entry
     __shared__ uint32_t nchunk[NSEG];                // chunks of segment (2 l + kind)
+    __shared__ uint8_t coop[NSEG];                   // cells of the segment taken eight lanes each
     __shared__ unsigned int t_sh;
     __shared__ int o_sh, bad_sh;
     for (int i = threadIdx.x; i <= NSEG; i += PL) seg[i] = ctl->seg[i];
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int k = 0; k < NSEG; k++) nchunk[k] = (seg[k + 1] - seg[k] + PL - 1) / PL;
+        for (int k = 0; k < NSEG; k++) {
+            const uint32_t cnt = seg[k + 1] - seg[k];
+            coop[k] = (k & 1) && cnt <= (uint32_t)GT_PSEUDO_COOP;
+            const uint32_t per = coop[k] ? PL / 8 : PL;
+            nchunk[k] = (cnt + per - 1) / per;
+        }
         int o = 0;  // level l's cells go right after the leaves of level l - PSEUDO_LAG
         for (int s = 0; s < GT_TREE_LEVELS + PSEUDO_LAG; s++) {
             const int ll = GT_TREE_LEVELS - 1 - s, lc = GT_TREE_LEVELS - 1 + PSEUDO_LAG - s;
@@ -653,11 +727,17 @@ __global__ __launch_bounds__(PL, GT_PSEUDO_MINB) void k_pseudo(Nodes nd, const f
         const unsigned int t = t_sh;
         const int o = o_sh;
         if (t >= total || bad_sh) break;
-        const int lvl = olvl[o], kind = ocell[o];
-        const long long idx = (long long)seg[2 * lvl + kind] + (long long)(t - ocum[o]) * PL + threadIdx.x;
-        if (idx < (long long)seg[2 * lvl + kind + 1]) {
-            if (kind == 0) pseudo_leaf<WITH_MASS>(nd, posm, nd.cells[idx]);
-            else pseudo_cell<WITH_MASS>(nd, nd.cells[idx]);
+        const int lvl = olvl[o], kind = ocell[o], sg = 2 * lvl + kind;
+        if (coop[sg]) {  // the whole block: PL / 8 cells, eight lanes each
+            const long long idx = (long long)seg[sg] + (long long)(t - ocum[o]) * (PL / 8) + (threadIdx.x >> 3);
+            const bool valid = idx < (long long)seg[sg + 1];
+            pseudo_cell_coop<WITH_MASS>(nd, valid ? nd.cells[idx] : 0u, valid);
+        } else {
+            const long long idx = (long long)seg[sg] + (long long)(t - ocum[o]) * PL + threadIdx.x;
+            if (idx < (long long)seg[sg + 1]) {
+                if (kind == 0) pseudo_leaf<WITH_MASS>(nd, posm, nd.cells[idx]);
+                else pseudo_cell<WITH_MASS>(nd, nd.cells[idx]);
+            }
         }
         __threadfence();  // every thread's node is visible device-wide before the chunk counts as done
         __syncthreads();
