@@ -18,6 +18,13 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libgothic.so")
+# The debug variant (index checks in the walk and the pseudo j-particle pass that latch
+# GT_EINVAL instead of reading outside the tree; -DGT_DEBUG=1) lives in its own directory.
+VARIANTS = {"": (OUT_DIR, []), "debug": (os.path.join(OUT_DIR, "debug"), ["-DGT_DEBUG=1"])}
+
+
+def lib_of(variant: str = "") -> str:
+    return os.path.join(VARIANTS[variant][0], "libgothic.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -45,32 +52,35 @@ def _deps() -> list[str]:
 FLAGS_STAMP = os.path.join(OUT_DIR, "flags.txt")
 
 
-def _extra_flags() -> list[str]:
-    return os.environ.get("GOTHIC_NVCC_FLAGS", "").split()
+def _extra_flags(variant: str = "") -> list[str]:
+    return VARIANTS[variant][1] + os.environ.get("GOTHIC_NVCC_FLAGS", "").split()
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(variant: str = "") -> bool:
+    lib = lib_of(variant)
+    if not os.path.exists(lib):
         return False
     try:
-        if open(FLAGS_STAMP).read() != " ".join(_extra_flags()):
+        if open(os.path.join(VARIANTS[variant][0], "flags.txt")).read() != " ".join(_extra_flags(variant)):
             return False
     except OSError:
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> str:
-    """Compile every .cu under csrc/ and link libgothic.so; returns its path."""
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False, variant: str = "") -> str:
+    """Compile every .cu under csrc/ and link libgothic.so (of the variant); returns its path."""
+    if not force and up_to_date(variant):
+        return lib_of(variant)
     nvcc = _nvcc()
-    os.makedirs(OUT_DIR, exist_ok=True)
-    obj_dir = os.path.join(OUT_DIR, "obj")
+    out_dir = VARIANTS[variant][0]
+    LIB = lib_of(variant)
+    os.makedirs(out_dir, exist_ok=True)
+    obj_dir = os.path.join(out_dir, "obj")
     os.makedirs(obj_dir, exist_ok=True)
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-                     "-Xcompiler", "-fvisibility=hidden"] + _extra_flags()
+                     "-Xcompiler", "-fvisibility=hidden"] + _extra_flags(variant)
     if ptxas_verbose:
         common += ["-Xptxas", "-v"]
 
@@ -95,11 +105,12 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
-    with open(FLAGS_STAMP, "w") as f:
-        f.write(" ".join(_extra_flags()))
+    with open(os.path.join(out_dir, "flags.txt"), "w") as f:
+        f.write(" ".join(_extra_flags(variant)))
     return LIB
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_verbose="-v" in sys.argv,
+                variant="debug" if "--debug" in sys.argv else ""))

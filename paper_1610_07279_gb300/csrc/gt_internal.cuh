@@ -18,6 +18,14 @@
 // true one.
 #define GT_RADIUS_MARGIN (1.0f + 0x1p-20f)
 
+// The debug build (-DGT_DEBUG=1, a separate library) checks the node and particle
+// indices that the walk and the pseudo j-particle pass read from the tree against the
+// node and particle counts; a failed check latches GT_EINVAL with the kernel's tag and
+// the access is skipped (no trap).  The release build compiles none of it.
+#ifndef GT_DEBUG
+#define GT_DEBUG 0
+#endif
+
 // Kernel ids recorded with a latched error (diagnostic only).
 enum { GTK_NONE = 0, GTK_BUILD, GTK_PSEUDO, GTK_ACTIVE, GTK_WALK, GTK_SORT, GTK_CORRECT, GTK_PROBE };
 

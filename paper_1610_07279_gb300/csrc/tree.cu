@@ -728,6 +728,27 @@ __global__ __launch_bounds__(PL, GT_PSEUDO_MINB) void k_pseudo(Nodes nd, const f
         const int o = o_sh;
         if (t >= total || bad_sh) break;
         const int lvl = olvl[o], kind = ocell[o], sg = 2 * lvl + kind;
+#if GT_DEBUG
+        {   // every node of the chunk: its particle or child range inside the tree
+            const uint32_t nn = ctl->level_start[GT_TREE_LEVELS], np = nd.count[0];
+            const uint32_t per = coop[sg] ? PL / 8 : PL;
+            const long long i0 = (long long)seg[sg] + (long long)(t - ocum[o]) * per;
+            bool bad = false;
+            for (long long i = i0 + threadIdx.x; i < i0 + per && i < (long long)seg[sg + 1]; i += PL) {
+                const uint32_t c = nd.cells[i];
+                if (c >= nn) { bad = true; continue; }
+                bad |= kind == 0 ? ((unsigned long long)nd.first[c] + nd.count[c] > np)
+                                 : (nd.child[c] < 0 || (unsigned long long)nd.child[c] + nd.nchild[c] > nn);
+            }
+            if (__syncthreads_or(bad)) {  // the whole chunk is skipped
+                if (threadIdx.x == 0) {
+                    gt_set_error(ctl, GT_EINVAL, GTK_PSEUDO);
+                    atomicAdd(&ctl->pl_done[lvl], 1u);
+                }
+                continue;
+            }
+        }
+#endif
         if (coop[sg]) {  // the whole block: PL / 8 cells, eight lanes each
             const long long idx = (long long)seg[sg] + (long long)(t - ocum[o]) * (PL / 8) + (threadIdx.x >> 3);
             const bool valid = idx < (long long)seg[sg + 1];

@@ -296,6 +296,9 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
         __syncwarp();
     };
 
+#if GT_DEBUG
+    const uint32_t nnodes = a.ctl->level_start[GT_TREE_LEVELS];
+#endif
     uint32_t head = 0, tail = 1;
     if (lane == 0) q[0] = 0u;  // the root
     __syncwarp();
@@ -303,7 +306,9 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
     while (head != tail) {
         const uint32_t live = tail - head;
         const uint32_t nb = min(live, 32u);
+#if !GT_DEBUG
         const bool valid = (uint32_t)lane < nb;
+#endif
         // breadth-first from the head while there is room, depth-first from the tail after
         uint32_t base;
         if ((int)live > lifo_at) {
@@ -314,11 +319,31 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, uint32_t g, uint32
             head += nb;
         }
         float4 jp = make_float4(0.f, 0.f, 0.f, 0.f), wk = make_float4(0.f, 0.f, 0.f, 0.f);
+#if GT_DEBUG
+        bool valid = (uint32_t)lane < nb;
+        if (valid) {
+            const uint32_t node = q[(base + lane) & qmask];
+            if (node >= nnodes) {
+                gt_set_error(a.ctl, GT_EINVAL, GTK_WALK);
+                valid = false;
+            } else {
+                jp = a.jpos[node];
+                wk = a.walk[node];
+                const uint32_t c = __float_as_uint(wk.z), f = __float_as_uint(wk.y);
+                const bool lf = (c & GT_LEAF_FLAG) != 0u;
+                if ((unsigned long long)f + (lf ? (c & ~GT_LEAF_FLAG) : c) > (lf ? a.n : nnodes)) {
+                    gt_set_error(a.ctl, GT_EINVAL, GTK_WALK);
+                    valid = false;
+                }
+            }
+        }
+#else
         if (valid) {
             const uint32_t node = q[(base + lane) & qmask];
             jp = a.jpos[node];
             wk = a.walk[node];
         }
+#endif
         n_tests += nb;
         const bool ok = valid && mac_accept(a.mac, a.theta, dacc_amin, a.delta_acc, a.G, cx, cy, cz, bI, jp,
                                             wk.x, wk.w);

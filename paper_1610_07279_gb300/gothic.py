@@ -9,6 +9,7 @@ loading fails loudly otherwise -- there is no CPU fallback.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import re
@@ -118,7 +119,13 @@ def load(path: str | None = None):
     global _lib
     if _lib is not None:
         return _lib
-    p = path or _build.LIB
+    _lib = open_library(path or _build.LIB)
+    return _lib
+
+
+def open_library(p: str):
+    """Open one build of the library (the release one, or a variant such as the debug
+    build) with every entry point declared; ``using`` makes the bindings call it."""
     if not os.path.exists(p):
         raise ImportError(f"libgothic is not built ({p}); run paper_1610_07279_gb300.build.build()")
     L = C.CDLL(p)
@@ -176,8 +183,19 @@ def load(path: str | None = None):
     L.gt_server_get_stats.argtypes = [P, C.POINTER(gt_server_stats)]
     for name in declared_symbols():
         getattr(L, name).restype = C.c_char_p if name == "gt_strerror" else C.c_int
-    _lib = L
     return L
+
+
+@contextlib.contextmanager
+def using(lib):
+    """Make every binding of this module call ``lib`` (from open_library) inside the block."""
+    global _lib
+    saved = load()
+    _lib = lib
+    try:
+        yield lib
+    finally:
+        _lib = saved
 
 
 def _check(rc: int, where: str):
