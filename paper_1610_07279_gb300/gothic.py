@@ -537,7 +537,22 @@ class Batch:
         _check(load().gt_batch_sync_status(self._h, inter.ctypes.data, self.stream), "device")
         return inter
 
-    def autotune(self, leaf_max=(), group_max=(), walk_queue=(), reps: int = 3) -> dict:
+    def autotune(self, leaf_max=(), group_max=(), walk_queue=(), reps: int = 3, cache: str | None = None) -> dict:
+        """Time every candidate and keep the fastest (gt_batch_autotune).  With ``cache`` (a
+        JSON file path) a choice stored for the same device, size class and candidates is
+        set on the batch without timing, and a new one is stored."""
+        key = None
+        if cache:
+            import torch
+            from . import tune_cache
+            dev = torch.cuda.get_device_properties(torch.cuda.current_device())
+            key = tune_cache.make_key(dev.name, dev.multi_processor_count, self.ns, leaf_max, group_max,
+                                      walk_queue, reps)
+            hit = tune_cache.TuneCache(cache).get(key)
+            if hit is not None:
+                self.set_knobs(hit["leaf_max"], hit["group_max"], hit["walk_queue"])
+                return {"leaf_max": hit["leaf_max"], "group_max": hit["group_max"],
+                        "walk_queue": hit["walk_queue"], "best_ms": hit.get("best_ms"), "ms": [], "cached": True}
         sp = gt_tune_space()
         sp.n_leaf, sp.n_group, sp.n_queue, sp.reps = len(leaf_max), len(group_max), len(walk_queue), int(reps)
         for i, v in enumerate(leaf_max):
@@ -548,8 +563,12 @@ class Batch:
             sp.walk_queue[i] = int(v)
         r = gt_tune_result()
         _check(load().gt_batch_autotune(self._h, C.byref(sp), C.byref(r), self.stream), "gt_batch_autotune")
-        return {"leaf_max": r.leaf_max, "group_max": r.group_max, "walk_queue": r.walk_queue,
-                "best_ms": r.best_ms, "ms": [float(r.ms[i]) for i in range(r.n_tried)]}
+        out = {"leaf_max": r.leaf_max, "group_max": r.group_max, "walk_queue": r.walk_queue,
+               "best_ms": r.best_ms, "ms": [float(r.ms[i]) for i in range(r.n_tried)], "cached": False}
+        if key is not None:
+            from . import tune_cache
+            tune_cache.TuneCache(cache).put(key, out)
+        return out
 
 
 class Server:

@@ -171,3 +171,36 @@ def test_batch_autotune_keeps_a_working_choice(env):
     acc_s, _ = _single_forces(env, m, tuned, aold)
     assert np.array_equal(acc_s.view(np.uint32), b.get_acc(k)[0].view(np.uint32))
     b.close()
+
+
+def test_batch_autotune_cache_reuses_the_choice(env, tmp_path):
+    """With a cache file, the first autotune times the candidates and stores the choice;
+    a second batch of the same size class sets the stored knobs without timing, and its
+    forces are those of a batch tuned to the same knobs."""
+    torch, g, O = env
+    cache = str(tmp_path / "tune.json")
+    mem = _members(4, seed=16, lo=10.0, hi=12.0)
+    prms = [_params(g, m["eps"]) for m in mem]
+    space = dict(leaf_max=(8, 16), group_max=(16, 32), walk_queue=(8192,), reps=2)
+    b1 = g.Batch([m["n"] for m in mem], prms)
+    _load(b1, mem)
+    b1.accel(bootstrap=True)
+    b1.sync()
+    r1 = b1.autotune(cache=cache, **space)
+    assert not r1["cached"] and len(r1["ms"]) == 4
+    b1.accel(bootstrap=False)
+    b1.sync()
+    acc1 = [b1.get_acc(k)[0].copy() for k in range(len(mem))]
+    b1.close()
+    b2 = g.Batch([m["n"] for m in mem], prms)
+    _load(b2, mem)
+    b2.accel(bootstrap=True)
+    b2.sync()
+    r2 = b2.autotune(cache=cache, **space)
+    assert r2["cached"] and (r2["leaf_max"], r2["group_max"], r2["walk_queue"]) == \
+        (r1["leaf_max"], r1["group_max"], r1["walk_queue"])
+    b2.accel(bootstrap=False)
+    b2.sync()
+    for k in range(len(mem)):
+        assert np.array_equal(acc1[k].view(np.uint32), b2.get_acc(k)[0].view(np.uint32))
+    b2.close()
