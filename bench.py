@@ -70,10 +70,11 @@ def parse():
 
 
 # ------------------------------------------------------------------ workload
-# Leaf size of the main 2^24 cycle: measured over 24 block steps of this model, leaves of
-# 8, 16, 24 and 32 particles took 92.8, 85.7, 83.1 and 83.5 ms (fewer leaves shorten the
-# pseudo j pass; the walk is cheapest at 24).  The library default stays 16.
-LEAF_MAX = 24
+# Leaf size of the main 2^24 cycle: measured over whole block-step cycles of this model
+# (automatic rebuild interval), leaves of 16, 24 and 32 particles took 437-439, 421-422 and
+# 419 ms per cycle (fewer, larger leaves shorten the pseudo j pass and the tree; the walk
+# evaluates more interactions).  The library default stays 16.
+LEAF_MAX = 32
 
 
 def workload(n: int):

@@ -245,14 +245,14 @@ def test_shared_step_free_running(env):
     free_running(env, pos, vel, mass, prm, 6, "plummer-L1")
 
 
-# ------------------------------------------------------------------ Andromeda-like 2^24, leaf 24
+# ------------------------------------------------------------------ Andromeda-like 2^24, leaf 32
 def test_andromeda_2p24_four_block_steps_teacher_forced(env):
-    """The benchmark's workload (Andromeda-like model, N = 2^24, eps = 0.01, leaves of 24,
+    """The benchmark's workload (Andromeda-like model, N = 2^24, eps = 0.01, leaves of 32,
     8 levels): the first four block steps after the oracle's start-up, every active
     particle compared (the oracle walks them all)."""
     torch, g, O = env
     pos, vel, mass, eps = ics.andromeda_like(1 << 24, seed=3)
-    prm = _params(g, eps, levels=8, rebuild_every=1, group_max=64, leaf_max=24)
+    prm = _params(g, eps, levels=8, rebuild_every=1, group_max=64, leaf_max=32)
     teacher_forced(env, pos, vel, mass, prm, 4, "m31-2^24")
 
 

@@ -210,7 +210,7 @@ def test_pseudo_j_bitexact_on_awkward_coordinates(env, masses):
         mass = np.full(n, 2.0 ** -15, np.float32)
     else:
         mass = rng.uniform(0.5, 1.5, n).astype(np.float32) / n
-    for leaf in (1, 8, 24):
+    for leaf in (1, 8, 24, 32):
         s = g.System(n, _params(g, 0.01, leaf_max=leaf, node_factor=4))
         s.set_state(pos, np.zeros_like(pos), mass)
         s.build_tree()
@@ -649,5 +649,5 @@ def test_nfw_2p20_full_size(env):
 
 
 def test_andromeda_2p24_full_size(env):
-    """The benchmark's main workload and leaf size (24), sampled groups against the oracle."""
-    _full_size_sampled(env, "m31", 1 << 24, 3, ngroups_sample=32, leaf_max=24)
+    """The benchmark's main workload and leaf size (32), sampled groups against the oracle."""
+    _full_size_sampled(env, "m31", 1 << 24, 3, ngroups_sample=32, leaf_max=32)
