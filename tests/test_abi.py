@@ -31,6 +31,23 @@ def test_library_exports_every_declared_symbol(libpath):
         assert hasattr(lib, name), name
 
 
+def test_debug_build_exports_the_same_abi_and_using_switches_back(libpath):
+    """The debug variant (index checks, its own directory) builds, exports every declared
+    entry point, and gothic.using() points the bindings at it and back."""
+    from paper_1610_07279_gb300 import build, gothic
+    dpath = build.build(variant="debug")
+    assert os.path.dirname(dpath) != os.path.dirname(libpath)
+    dbg = gothic.open_library(dpath)
+    for name in gothic.declared_symbols():
+        assert hasattr(dbg, name), name
+    rel = gothic.load()
+    with gothic.using(dbg):
+        assert gothic.load() is dbg
+        assert gothic.gt_strerror(0) == "ok"
+        assert gothic.gt_default_params().leaf_max > 0
+    assert gothic.load() is rel
+
+
 def test_binding_loads_and_strerror(libpath):
     from paper_1610_07279_gb300 import gothic
     gothic.load()
